@@ -1,0 +1,132 @@
+"""Pins for the oracle's randomness: Philox4x32-10, stream layout, uniforms,
+Lemire's bounded integers.  These check the oracle against sources other than
+itself (an independent Philox implementation, closed forms, exact counts)."""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+from scipy import stats
+
+_TRITON_SCRIPT = r"""
+import json, os, sys
+os.environ["TRITON_INTERPRET"] = "1"
+import torch, triton, triton.language as tl
+
+@triton.jit
+def _k(out_ptr, seed, c0_ptr, c1_ptr, c2_ptr, c3_ptr, n: tl.constexpr):
+    offs = tl.arange(0, n)
+    c0 = tl.load(c0_ptr + offs); c1 = tl.load(c1_ptr + offs)
+    c2 = tl.load(c2_ptr + offs); c3 = tl.load(c3_ptr + offs)
+    r0, r1, r2, r3 = tl.philox(seed, c0, c1, c2, c3, 10)
+    tl.store(out_ptr + offs * 4 + 0, r0); tl.store(out_ptr + offs * 4 + 1, r1)
+    tl.store(out_ptr + offs * 4 + 2, r2); tl.store(out_ptr + offs * 4 + 3, r3)
+
+cases = json.loads(sys.stdin.read())
+res = []
+for seed, ctrs in cases:
+    n = len(ctrs)
+    cols = [torch.tensor([c[i] for c in ctrs], dtype=torch.uint32) for i in range(4)]
+    out = torch.zeros(4 * n, dtype=torch.uint32)
+    _k[(1,)](out, seed, cols[0], cols[1], cols[2], cols[3], n)
+    res.append([int(x) & 0xFFFFFFFF for x in out.tolist()])
+print(json.dumps(res))
+"""
+
+
+def test_philox_matches_independent_implementation(oracle):
+    """Philox4x32-10 (Salmon et al., SC'11) against Triton's own Philox,
+    run by Triton's CPU interpreter: same (counter, key) -> same block."""
+    pytest.importorskip("triton")
+    rng = np.random.default_rng(12345)
+    cases = []
+    for seed in [0, 1, 7, 0xFFFFFFFF, 0x123456789ABCDEF0, 0xFFFFFFFFFFFFFFFF]:
+        ctrs = [[0, 0, 0, 0], [0xFFFFFFFF] * 4, [1, 2, 3, 4]]
+        ctrs += rng.integers(0, 2**32, size=(13, 4), dtype=np.uint64).tolist()
+        cases.append([seed, ctrs])
+    env = dict(os.environ, TRITON_INTERPRET="1")
+    p = subprocess.run([sys.executable, "-c", _TRITON_SCRIPT], input=json.dumps(cases),
+                       capture_output=True, text=True, env=env, timeout=600)
+    if p.returncode != 0:
+        pytest.skip("triton interpreter unavailable: " + p.stderr[-300:])
+    ref = json.loads(p.stdout.strip().splitlines()[-1])
+    for (seed, ctrs), want in zip(cases, ref):
+        key = [seed & 0xFFFFFFFF, seed >> 32]
+        for i, c in enumerate(ctrs):
+            assert oracle.philox4x32_10(c, key) == want[4 * i: 4 * i + 4], (seed, c)
+
+
+def test_stream_layout(oracle):
+    """Word j is word j%4 of block j//4 with counter (t, tag, id lo, id hi)
+    and key (seed lo, seed hi); value j = word 2j+1 << 32 | word 2j."""
+    seed, tag, node = 0x0123456789ABCDEF, 5, (7 << 32) | 9
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for t in [0, 1, 2, 1000, 2**32 - 1]:
+        blk = oracle.philox4x32_10([t, tag, node & 0xFFFFFFFF, node >> 32], key)
+        for w in range(4):
+            assert oracle.word(seed, tag, node, 4 * t + w) == blk[w]
+        assert oracle.value(seed, tag, node, 2 * t) == (blk[1] << 32) | blk[0]
+        assert oracle.value(seed, tag, node, 2 * t + 1) == (blk[3] << 32) | blk[2]
+
+
+def test_uniform_endpoints(oracle):
+    """U_open = ((x>>11)+1) 2^-53 in (0,1], V = (x>>11) 2^-53 in [0,1)."""
+    assert oracle.u_open(0) == 2.0**-53
+    assert oracle.u_open(2**64 - 1) == 1.0
+    assert oracle.v_closed(0) == 0.0
+    assert oracle.v_closed(2**64 - 1) == 1.0 - 2.0**-53
+    for x in [1 << 11, 12345 << 11, (2**53 - 1) << 11]:
+        assert oracle.u_open(x) == ((x >> 11) + 1) / 2.0**53
+        assert oracle.v_closed(x) == (x >> 11) / 2.0**53
+
+
+@pytest.mark.parametrize("s", [1, 2, 3, 7, 1000, 3906250, 2**31 + 1, 2**32])
+def test_lemire_small_ranges(oracle, s):
+    """Candidate j from word j: valid iff (w*s mod 2^32) >= (2^32-s) mod s,
+    value floor(w*s/2^32).  Checked against the words themselves, and the
+    valid values are uniform on [0, s)."""
+    seed, tag, node = 99, 2, 17
+    thr = (2**32 - s) % s
+    vals = []
+    for j in range(4000):
+        w = oracle.word(seed, tag, node, j)
+        ok, v = oracle.candidate(seed, tag, node, s, j)
+        prod = w * s
+        assert ok == ((prod & 0xFFFFFFFF) >= thr)
+        if ok:
+            assert v == prod >> 32 and 0 <= v < s
+            vals.append(v)
+    if 2 <= s <= 1000:
+        bins = min(s, 20)
+        h = np.bincount(np.array(vals) * bins // s, minlength=bins)
+        exp = np.array([((i + 1) * s + bins - 1) // bins - (i * s + bins - 1) // bins for i in range(bins)],
+                       dtype=float)
+        exp = exp / exp.sum() * len(vals)
+        assert stats.chisquare(h, exp).pvalue > 1e-4
+
+
+@pytest.mark.parametrize("s", [2**32 + 1, 3 * 2**40 + 5, 2**62])
+def test_lemire_large_ranges(oracle, s):
+    """s > 2^32: candidate j from 64-bit value j, 128-bit product."""
+    seed, tag, node = 3, 2, 5
+    thr = (2**64 - s) % s
+    for j in range(500):
+        x = oracle.value(seed, tag, node, j)
+        ok, v = oracle.candidate(seed, tag, node, s, j)
+        prod = x * s
+        assert ok == ((prod & (2**64 - 1)) >= thr)
+        if ok:
+            assert v == prod >> 64 and v < s
+
+
+def test_lemire_void_rate(oracle):
+    """For s = 3*2^30 + 1 the void probability is ((2^32 - s) mod s) / 2^32,
+    about 0.25; the observed rate matches it."""
+    s = 3 * 2**30 + 1
+    p_void = ((2**32 - s) % s) / 2**32
+    n = 20000
+    voids = sum(not oracle.candidate(11, 2, 1, s, j)[0] for j in range(n))
+    z = (voids - n * p_void) / np.sqrt(n * p_void * (1 - p_void))
+    assert abs(z) < 5
