@@ -1,0 +1,135 @@
+/*
+ * rs.h -- C ABI of the GB300 divide-and-conquer random sampler.
+ *
+ * Sanders, Lamm, Huebschle-Schneider, Schrade, Dachsbacher, "Efficient
+ * Parallel Random Sampling -- Vectorized, Cache-Efficient, and Online"
+ * (ACM TOMS 44(3), 2018).
+ *
+ * The sampler draws n numbers from 1..N (Sec. 1-2).  The range is split
+ * recursively at floor(S/2); a hypergeometric deviate (binomial when sampling
+ * with replacement, Sec. 4.6) gives each half its share (Sec. 3.1 Algorithm
+ * R).  Every tree node and every leaf draws from a Philox4x32-10 stream keyed
+ * by the seed and the node id, so no node waits for another (Sec. 3.2
+ * Algorithm P), and the result is a pure function of (n, N, seed, n0)
+ * whatever the launch geometry (Sec. 4.5).  Leaves produce their share with
+ * hash-style rejection (Sec. 2 Algorithm H, sorted as in Sec. 4.1) or with
+ * Bernoulli skips plus a repair (Sec. 2 Algorithm B).
+ *
+ * Conventions for every call:
+ *  - Device pointers ("_dev") are CUDA device memory owned by the caller
+ *    (e.g. a torch tensor's data_ptr()); host pointers are plain host memory.
+ *  - Output values are 1-based uint64 in 1..N.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Sampling calls are asynchronous on that stream; errors the device detects
+ *    (an iteration cap, a leaf capacity) land in the context's status word and
+ *    are returned by rs_sync.  Argument errors are returned immediately.
+ *  - A context may be used from one host thread at a time; calls that share a
+ *    context must be issued on one stream (they share its scratch memory).
+ *  - Return codes are the RS_* values below.
+ */
+#ifndef RS_H
+#define RS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    RS_OK = 0,
+    RS_EINVAL = 1,     /* invalid argument                                    */
+    RS_ECAPACITY = 2,  /* a result does not fit the caller's buffer or a limit */
+    RS_ENOMEM = 3,     /* device or host allocation failed                    */
+    RS_ECUDA = 4,      /* a CUDA runtime call failed                          */
+    RS_ETIMEOUT = 5,   /* a bounded wait gave up                              */
+    RS_EITER = 6       /* a rejection loop reached its iteration cap          */
+};
+
+/* Kinds of sample (also the `kind` field of rs_request). */
+enum {
+    RS_KIND_H = 0,   /* without replacement, hypergeometric splits, leaf H (Sec. 2, 3.1, 4.1) */
+    RS_KIND_WR = 1,  /* with replacement, binomial splits (Sec. 4.6)                         */
+    RS_KIND_B = 2    /* without replacement, Algorithm B as the base case (Sec. 2, 4.7)      */
+};
+
+typedef struct rs_ctx rs_ctx;
+typedef struct rs_tree rs_tree;
+
+/* Creates a context on CUDA device `device` (scratch memory, status word, the
+ * ln x! table).  *ctx is owned by the caller and freed with rs_destroy.
+ * Errors: RS_EINVAL (null ctx), RS_ECUDA (bad device), RS_ENOMEM. */
+int rs_create(rs_ctx** ctx, int device);
+
+/* Waits for the context's work, frees its memory.  Returns RS_OK or RS_ECUDA. */
+int rs_destroy(rs_ctx* ctx);
+
+/* Split-tree depth D for n samples (a1 plan): the least D >= 0 with
+ * n <= n0 * 2^D, lowered until 2^D <= N.  The static depth replaces Algorithm
+ * R's adaptive "n < n0" stop (Sec. 3.1) the way Algorithm P's fixed tree of
+ * PEs does (Sec. 3.2, Sec. 4.5).  Host only.  Errors: RS_EINVAL (null out,
+ * n0 = 0). */
+int rs_plan(uint64_t n, uint64_t N, uint32_t n0, int* depth_out);
+
+/* n distinct values from 1..N, strictly increasing, written to out_dev[0..n)
+ * (Sec. 3.1 Algorithm R with Algorithm H leaves, sorted output Sec. 4.1).
+ * out_dev: n uint64 slots of device memory, 8-byte aligned.
+ * Errors: RS_EINVAL (n > N, n > 0 with N = 0, N > 2^62, n0 = 0, null out
+ * with n > 0); device-side RS_EITER / RS_ECAPACITY via rs_sync.
+ * n = 0 succeeds and writes nothing. */
+int rs_sample(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0,
+              uint64_t* out_dev, void* stream);
+
+/* n values from 1..N drawn with replacement, non-decreasing (Sec. 4.6:
+ * binomial splits).  n may exceed N.  Same buffers and errors as rs_sample
+ * (except that n > N is allowed). */
+int rs_sample_with_replacement(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0,
+                               uint64_t* out_dev, void* stream);
+
+/* Like rs_sample, with Algorithm B (Bernoulli sampling with a slightly larger
+ * rate, then removal of the surplus) as the base case of the split tree
+ * (Sec. 2, Sec. 4.7).  A uniform n-subset like rs_sample, but a different
+ * one: the leaves draw from other streams. */
+int rs_sample_b(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0,
+                uint64_t* out_dev, void* stream);
+
+/* Leaf records of the split tree of (n, N, seed, n0): recs_dev[4i..4i+3] =
+ * (lo, s, n', offset) of leaf i (0-based, left to right): leaf i covers the
+ * 0-based positions [lo, lo+s), holds n' samples and writes them at
+ * out[offset..offset+n').  kind RS_KIND_WR uses binomial splits, the other
+ * kinds hypergeometric splits (Sec. 3.1, 3.2, 4.6).  recs_dev: 4*2^D uint64
+ * of device memory with 2^D <= max_leaves, else RS_ECAPACITY. */
+int rs_split_tree(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0, int kind,
+                  uint64_t* recs_dev, uint64_t max_leaves, void* stream);
+
+/* Bernoulli(p) sample of the positions 0..N-1 by independent chunks with
+ * geometric skips (Sec. 4.7, Sec. 2 Algorithm B), restricted to the window
+ * [a, b) of 0-based positions.  Chunks have 2^c positions, c the least value
+ * with 2^c p >= n0 (at most 62); a and b must be multiples of 2^c (b may also
+ * equal N).  Writes the 1-based positions in increasing order to
+ * out_dev[0..min(count, cap)) and the number in the window to *count_out
+ * (host memory); this call synchronizes `stream` to read the count.
+ * Errors: RS_EINVAL (p outside [0,1], n0 = 0, N > 2^62, bad window),
+ * RS_ECAPACITY (count > cap; *count_out is still set, the first cap values
+ * are written), RS_EITER. */
+int rs_bernoulli(rs_ctx* ctx, double p, uint64_t N, uint64_t seed, uint32_t n0,
+                 uint64_t a, uint64_t b, uint64_t* out_dev, uint64_t cap,
+                 uint64_t* count_out, void* stream);
+
+/* Waits for `stream`, then returns and clears the context's device status
+ * word (RS_OK, or the first device-side error since the last rs_sync). */
+int rs_sync(rs_ctx* ctx, void* stream);
+
+/* Static description of a return code.  Never NULL. */
+const char* rs_strerror(int code);
+
+/* Testing knob: leaves whose selection exceeds `cap` values take the
+ * general (global-memory) path instead of the shared-memory one.  The output
+ * does not change.  cap = 0 restores the default.  Errors: RS_EINVAL. */
+int rs_set_leaf_capacity(rs_ctx* ctx, uint32_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RS_H */

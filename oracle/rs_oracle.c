@@ -293,6 +293,7 @@ int or_hg(uint64_t seed, uint64_t id, uint64_t n, uint64_t K, uint64_t S, uint64
                 p = (p * ((double)(a - k) * (double)(b - k))) / ((double)(k + 1) * (double)(S - a - b + k + 1));
                 k = k + 1;
                 if (k > a) break;
+                if (p == 0.0) break;   /* p stays 0 and u unchanged: this pass can only run out */
             }
         }
     } else {
@@ -339,6 +340,7 @@ int or_bin(uint64_t seed, uint64_t id, uint64_t c, uint64_t K, uint64_t S, uint6
                 pk = (pk * ((double)(c - k) * r)) / (double)(k + 1);
                 k = k + 1;
                 if (k > c) break;
+                if (pk == 0.0) break;  /* as above */
             }
         }
         return OR_EITER;

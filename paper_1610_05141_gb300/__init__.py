@@ -1,0 +1,164 @@
+"""GB300 divide-and-conquer random sampler: thin Python binding of include/rs.h.
+
+Every function here only marshals arguments (torch tensors -> device
+pointers, the current torch stream -> cudaStream_t) and calls the C ABI of
+_build/librs_gb300.so; all sampling runs in the library's CUDA kernels.
+There is no fallback: importing fails loudly if the library is missing.
+Build it with ``python -m paper_1610_05141_gb300.build`` (or
+``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "librs_gb300.so")
+
+RS_OK, RS_EINVAL, RS_ECAPACITY, RS_ENOMEM, RS_ECUDA, RS_ETIMEOUT, RS_EITER = range(7)
+RS_KIND_H, RS_KIND_WR, RS_KIND_B = 0, 1, 2
+
+
+class RSError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {code} ({strerror(code) if _lib else code})")
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads the library (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"sampler library not built: {path} is missing "
+                           "(run python -m paper_1610_05141_gb300.build)")
+    lib = ctypes.CDLL(path)
+    u64, u32, i32, vp, dbl = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_void_p, ctypes.c_double
+    sig = {
+        "rs_create": (i32, [ctypes.POINTER(vp), i32]),
+        "rs_destroy": (i32, [vp]),
+        "rs_plan": (i32, [u64, u64, u32, ctypes.POINTER(i32)]),
+        "rs_sample": (i32, [vp, u64, u64, u64, u32, vp, vp]),
+        "rs_sample_with_replacement": (i32, [vp, u64, u64, u64, u32, vp, vp]),
+        "rs_sample_b": (i32, [vp, u64, u64, u64, u32, vp, vp]),
+        "rs_split_tree": (i32, [vp, u64, u64, u64, u32, i32, vp, u64, vp]),
+        "rs_bernoulli": (i32, [vp, dbl, u64, u64, u32, u64, u64, vp, u64, ctypes.POINTER(u64), vp]),
+        "rs_sync": (i32, [vp, vp]),
+        "rs_strerror": (ctypes.c_char_p, [i32]),
+        "rs_set_leaf_capacity": (i32, [vp, u32]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    return load().rs_strerror(code).decode()
+
+
+def _ptr(t) -> int:
+    """Device pointer of a tensor (or an int address, or None)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(rc: int, where: str) -> int:
+    if rc != RS_OK:
+        raise RSError(rc, where)
+    return rc
+
+
+class Context:
+    """Owns an rs_ctx (scratch memory and status word on one device)."""
+
+    def __init__(self, device: int = 0):
+        h = ctypes.c_void_p()
+        _check(load().rs_create(ctypes.byref(h), device), "rs_create")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            load().rs_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rs_create(device: int = 0) -> Context:
+    return Context(device)
+
+
+def rs_destroy(ctx: Context) -> None:
+    ctx.close()
+
+
+def rs_plan(n: int, N: int, n0: int) -> int:
+    d = ctypes.c_int(0)
+    _check(load().rs_plan(n, N, n0, ctypes.byref(d)), "rs_plan")
+    return d.value
+
+
+def rs_sample(ctx: Context, n, N, seed, n0, out, stream=None, check=True) -> int:
+    rc = load().rs_sample(ctx.handle, n, N, seed, n0, _ptr(out), _stream(stream))
+    return _check(rc, "rs_sample") if check else rc
+
+
+def rs_sample_with_replacement(ctx: Context, n, N, seed, n0, out, stream=None, check=True) -> int:
+    rc = load().rs_sample_with_replacement(ctx.handle, n, N, seed, n0, _ptr(out), _stream(stream))
+    return _check(rc, "rs_sample_with_replacement") if check else rc
+
+
+def rs_sample_b(ctx: Context, n, N, seed, n0, out, stream=None, check=True) -> int:
+    rc = load().rs_sample_b(ctx.handle, n, N, seed, n0, _ptr(out), _stream(stream))
+    return _check(rc, "rs_sample_b") if check else rc
+
+
+def rs_split_tree(ctx: Context, n, N, seed, n0, kind, recs, max_leaves, stream=None, check=True) -> int:
+    rc = load().rs_split_tree(ctx.handle, n, N, seed, n0, kind, _ptr(recs), max_leaves, _stream(stream))
+    return _check(rc, "rs_split_tree") if check else rc
+
+
+def rs_bernoulli(ctx: Context, p, N, seed, n0, a, b, out, cap, stream=None, check=True):
+    """Returns (rc, count)."""
+    cnt = ctypes.c_uint64(0)
+    rc = load().rs_bernoulli(ctx.handle, float(p), N, seed, n0, a, b, _ptr(out), cap, ctypes.byref(cnt),
+                             _stream(stream))
+    if check and rc != RS_OK:
+        raise RSError(rc, "rs_bernoulli")
+    return rc, cnt.value
+
+
+def rs_sync(ctx: Context, stream=None) -> int:
+    return load().rs_sync(ctx.handle, _stream(stream))
+
+
+def rs_strerror(code: int) -> str:
+    return strerror(code)
+
+
+def rs_set_leaf_capacity(ctx: Context, cap: int) -> int:
+    return _check(load().rs_set_leaf_capacity(ctx.handle, cap), "rs_set_leaf_capacity")

@@ -1,0 +1,393 @@
+// rs_bern.cu -- Bernoulli sampling by independent chunks (Sec. 4.7) and
+// Algorithm B as the base case of the split tree (Sec. 2, Sec. 4.7).
+//
+// Geometric skips: with L = ln(1-p) and U uniform in (0,1], the skip
+// floor(ln U / L) is Geometric(p), so a Bernoulli(p) sample of a range is the
+// running sum of (skip + 1) while it stays inside the range (Sec. 2,
+// Algorithm B).  Draw j of a stream gives one skip.  A warp (Bernoulli
+// chunks) or a block (leaf B) takes 32 or 512 consecutive draws at once and
+// turns them into positions with an integer prefix sum, which is exact, so
+// the positions are those of the sequential definition.  A draw with
+// ln U / L >= 2^62 ends the range.
+#include "rs_leaf.cuh"
+#include "rs_math.cuh"
+
+namespace rs {
+
+constexpr uint64_t kSat = 1ull << 63;   // saturation of skip sums
+constexpr double kTwo62 = 4611686018427387904.0;
+constexpr uint64_t kMaxDraws = 1ull << 33;   // 2^32 Philox blocks of two values
+
+RS_DEV uint64_t sat_add(uint64_t a, uint64_t b) { return a > kSat - b ? kSat : a + b; }
+
+// Skip + 1 for one draw, or 0 with *stop when the draw ends the range.  The
+// value is clamped to cmax, which exceeds every range length, so clamping
+// never changes a decision.
+RS_DEV uint64_t step_of(double q, uint64_t cmax, bool* stop) {
+    *stop = !(q < kTwo62);
+    if (*stop) return 0;
+    const uint64_t f = (uint64_t)floor(q) + 1;
+    return f < cmax ? f : cmax;
+}
+
+RS_DEV uint64_t warp_inclusive_sat(uint64_t x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x = sat_add(x, y);
+    }
+    return x;
+}
+
+// One warp walks the positions [start, end) with stream (tag, id): for each
+// chosen position (0-based) emit(k, pos) is called, k its index in the
+// range.  Returns the number of positions; *err is set if the stream ran out.
+template <typename Emit>
+RS_DEV uint64_t warp_walk(Key2 key, uint32_t tag, uint64_t id, double L, uint64_t start, uint64_t end, bool* err,
+                          Emit&& emit) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t cmax = end - start + 2;
+    uint64_t base = start;   // a step of 1 lands on `base`
+    uint64_t count = 0;
+    *err = false;
+    for (uint64_t j = 0;; j += 32) {
+        const uint64_t jl = j + lane;
+        const bool exhausted = jl >= kMaxDraws;
+        bool stop = true;
+        uint64_t step = 0;
+        if (!exhausted) {
+            const double U = u_open(stream_value(key, tag, id, jl));
+            const double q = dlog(U) / L;
+            step = step_of(q, cmax, &stop);
+        }
+        const uint64_t incl = warp_inclusive_sat(step);
+        const bool ok = !stop && incl <= end - base;   // position base - 1 + incl < end
+        const uint32_t bad = __ballot_sync(0xFFFFFFFFu, !ok);
+        const int first_bad = bad ? __ffs(bad) - 1 : 32;
+        if (lane < first_bad) emit(count + lane, base - 1 + incl);
+        count += first_bad;
+        if (first_bad < 32) {
+            *err = __shfl_sync(0xFFFFFFFFu, exhausted, first_bad);
+            return count;
+        }
+        base = base + __shfl_sync(0xFFFFFFFFu, incl, 31);
+    }
+}
+
+struct BernArgs {
+    Key2 key;
+    double p;
+    uint64_t N, C;
+    int chunk_log2;
+    uint64_t first, nchunks;
+    uint64_t* counts;
+    uint64_t* out;
+    uint64_t cap;
+    int* status;
+};
+
+__global__ void bern_count_kernel(BernArgs A) {
+    const double L = dlog1p(-A.p);
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < A.nchunks; w += warps) {
+        const uint64_t i = A.first + w;
+        const uint64_t start = i << A.chunk_log2;
+        const uint64_t end = min(start + A.C, A.N);
+        bool err;
+        const uint64_t c = warp_walk(A.key, TAG_BERN, i, L, start, end, &err, [](uint64_t, uint64_t) {});
+        if ((threadIdx.x & 31) == 0) {
+            A.counts[w] = c;
+            if (err) set_status(A.status, RS_EITER);
+        }
+    }
+}
+
+__global__ void bern_write_kernel(BernArgs A) {
+    const double L = dlog1p(-A.p);
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < A.nchunks; w += warps) {
+        const uint64_t i = A.first + w;
+        const uint64_t start = i << A.chunk_log2;
+        const uint64_t end = min(start + A.C, A.N);
+        const uint64_t off = A.counts[w];
+        if (off >= A.cap) continue;
+        uint64_t* out = A.out;
+        const uint64_t cap = A.cap;
+        bool err;
+        warp_walk(A.key, TAG_BERN, i, L, start, end, &err, [=](uint64_t k, uint64_t pos) {
+            if (off + k < cap) out[off + k] = pos + 1;
+        });
+    }
+}
+
+__global__ void fill_range_kernel(uint64_t* out, uint64_t a, uint64_t n) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        out[i] = a + i + 1;
+}
+
+__global__ void set_word_kernel(uint64_t* p, uint64_t v) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *p = v;
+}
+
+// --- exclusive scan of uint64 counts (tiles of 8192, recursive) ------------
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 8;
+constexpr uint64_t kScanTile = (uint64_t)kScanThreads * kScanPer;
+
+__global__ void scan_tiles_kernel(uint64_t* data, uint64_t n, uint64_t* tile_sums) {
+    __shared__ uint64_t warp_tot[kScanThreads / 32];
+    const uint64_t i0 = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanPer;
+    uint64_t v[kScanPer];
+    uint64_t local = 0;
+#pragma unroll
+    for (int q = 0; q < kScanPer; ++q) {
+        v[q] = (i0 + q < n) ? data[i0 + q] : 0;
+        local += v[q];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const uint64_t w = warp_tot[lane];
+        uint64_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        warp_tot[lane] = wi - w;
+        if (lane == 31) tile_sums[blockIdx.x] = wi;
+    }
+    __syncthreads();
+    uint64_t run = warp_tot[warp] + incl - local;
+#pragma unroll
+    for (int q = 0; q < kScanPer; ++q) {
+        if (i0 + q < n) data[i0 + q] = run;
+        run += v[q];
+    }
+}
+
+__global__ void scan_add_kernel(uint64_t* data, uint64_t n, const uint64_t* tile_offsets) {
+    const uint64_t off = tile_offsets[blockIdx.x];
+    const uint64_t t0 = (uint64_t)blockIdx.x * kScanTile;
+    const uint64_t t1 = min(t0 + kScanTile, n);
+    for (uint64_t i = t0 + threadIdx.x; i < t1; i += kScanThreads) data[i] += off;
+}
+
+uint64_t scan_scratch_words(uint64_t n) {
+    uint64_t w = 0;
+    while (n > 1) {
+        n = (n + kScanTile - 1) / kScanTile;
+        w += n + 1;
+    }
+    return w + 1;
+}
+
+// Exclusive scan of data[0..n) in place; data[n] receives the total.
+static cudaError_t scan_u64(uint64_t* data, uint64_t n, uint64_t* scratch, cudaStream_t st) {
+    const uint64_t tiles = (n + kScanTile - 1) / kScanTile;
+    if (tiles <= 1) {
+        scan_tiles_kernel<<<1, kScanThreads, 0, st>>>(data, n, data + n);
+        return cudaGetLastError();
+    }
+    uint64_t* sums = scratch;   // tiles + 1 words
+    scan_tiles_kernel<<<(unsigned)tiles, kScanThreads, 0, st>>>(data, n, sums);
+    cudaError_t e = scan_u64(sums, tiles, scratch + tiles + 1, st);
+    if (e != cudaSuccess) return e;
+    scan_add_kernel<<<(unsigned)tiles, kScanThreads, 0, st>>>(data, n, sums);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(data + n, sums + tiles, sizeof(uint64_t), cudaMemcpyDeviceToDevice, st);
+}
+
+cudaError_t launch_bernoulli(const BernLaunch& L, cudaStream_t st) {
+    if (L.p == 1.0) {
+        const uint64_t n = L.b - L.a;
+        const uint64_t w = std::min(n, L.cap);
+        if (w > 0) {
+            const unsigned blocks = (unsigned)std::min<uint64_t>((w + 255) / 256, 65535);
+            fill_range_kernel<<<blocks, 256, 0, st>>>(L.out, L.a, w);
+        }
+        set_word_kernel<<<1, 32, 0, st>>>(L.total, n);
+        return cudaGetLastError();
+    }
+    BernArgs A;
+    A.key = make_key(L.seed);
+    A.p = L.p;
+    A.N = L.N;
+    A.C = 1ull << L.chunk_log2;
+    A.chunk_log2 = L.chunk_log2;
+    A.first = L.chunk_first;
+    A.nchunks = L.nchunks;
+    A.counts = L.counts;
+    A.out = L.out;
+    A.cap = L.cap;
+    A.status = L.status;
+    const int threads = 256;
+    const unsigned blocks = (unsigned)std::min<uint64_t>((L.nchunks * 32 + threads - 1) / threads,
+                                                         (uint64_t)L.sms * 16);
+    bern_count_kernel<<<blocks, threads, 0, st>>>(A);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = scan_u64(L.counts, L.nchunks, L.scan_scratch, st);
+    if (e != cudaSuccess) return e;
+    bern_write_kernel<<<blocks, threads, 0, st>>>(A);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(L.total, L.counts + L.nchunks, sizeof(uint64_t), cudaMemcpyDeviceToDevice, st);
+}
+
+// ---------------------------------------------------------------------------
+// Leaf B: Bernoulli-sample the leaf with rate rho slightly above n'/s, retry
+// if short, then drop the c - n' positions whose indices are the first
+// c - n' distinct FIXUP candidates over [0, c) (Algorithm H on indices).
+// rho = min(1, (n' + 3 sqrt(n') + 10) / s); attempt a uses LEAF_B + 256 a.
+// ---------------------------------------------------------------------------
+
+constexpr uint32_t kLeafBCap = 8192;   // positions of one attempt
+
+struct LeafBShared {
+    uint64_t pos[kLeafBCap];
+    LeafShared<uint32_t> sel;
+    uint64_t warp_tot[kLeafThreads / 32];
+    uint64_t last_incl;
+    int first_bad;
+    int err;
+};
+
+// Block-wide inclusive saturating scan of one value per thread.
+RS_DEV uint64_t block_inclusive_sat(uint64_t x, LeafBShared& sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = kLeafThreads / 32;
+    uint64_t incl = warp_inclusive_sat(x);
+    if (lane == 31) sm.warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const uint64_t w = lane < NW ? sm.warp_tot[lane] : 0;
+        const uint64_t wi = warp_inclusive_sat(w);
+        if (lane < NW) sm.warp_tot[lane] = wi;   // inclusive prefix of warp totals
+    }
+    __syncthreads();
+    const uint64_t before = warp == 0 ? 0 : sm.warp_tot[warp - 1];
+    return sat_add(before, incl);
+}
+
+// Geometric-skip walk of [0, s) by the whole block; positions go to sm.pos
+// (up to the capacity).  Returns the count; sets sm.err on a run-out stream.
+RS_DEV uint64_t block_walk(Key2 key, uint32_t tag, uint64_t id, double L, uint64_t s, LeafBShared& sm) {
+    const uint64_t cmax = s + 2;
+    uint64_t base = 0, count = 0;
+    for (uint64_t j = 0;; j += kLeafThreads) {
+        const uint64_t jt = j + threadIdx.x;
+        const bool exhausted = jt >= kMaxDraws;
+        bool stop = true;
+        uint64_t step = 0;
+        if (!exhausted) {
+            const double U = u_open(stream_value(key, tag, id, jt));
+            const double q = dlog(U) / L;
+            step = step_of(q, cmax, &stop);
+        }
+        if (threadIdx.x == 0) sm.first_bad = kLeafThreads;
+        const uint64_t incl = block_inclusive_sat(step, sm);
+        const bool ok = !stop && incl <= s - base;
+        if (!ok) atomicMin(&sm.first_bad, (int)threadIdx.x);
+        if (threadIdx.x == kLeafThreads - 1) sm.last_incl = incl;
+        __syncthreads();
+        const int fb = sm.first_bad;
+        if ((int)threadIdx.x < fb && count + threadIdx.x < kLeafBCap) sm.pos[count + threadIdx.x] = base - 1 + incl;
+        if ((int)threadIdx.x == fb && exhausted) sm.err = 1;
+        count += fb;
+        const uint64_t last = sm.last_incl;
+        __syncthreads();
+        if (fb < kLeafThreads) return count;
+        base += last;
+    }
+}
+
+struct LeafBArgs {
+    const NodeRec* leaves;
+    uint64_t nleaves, first_id;
+    Key2 key;
+    uint64_t* out;
+    int* status;
+};
+
+__global__ void __launch_bounds__(kLeafThreads) leaf_b_kernel(LeafBArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    LeafBShared& sm = *reinterpret_cast<LeafBShared*>(smem_raw);
+    for (uint64_t leaf = blockIdx.x; leaf < A.nleaves; leaf += gridDim.x) {
+        const NodeRec r = A.leaves[leaf];
+        if (r.c == 0) continue;
+        const uint64_t id = A.first_id + leaf;
+        const double dn = (double)r.c;
+        double rho = (dn + 3.0 * sqrt(dn) + 10.0) / (double)r.S;
+        if (rho > 1.0) rho = 1.0;
+        uint64_t c = 0;
+        int attempt = 0;
+        bool fail = false;
+        if (threadIdx.x == 0) sm.err = 0;
+        __syncthreads();
+        if (rho == 1.0) {
+            c = r.S;
+            const uint64_t fill = c < kLeafBCap ? c : kLeafBCap;
+            for (uint64_t i = threadIdx.x; i < fill; i += kLeafThreads) sm.pos[i] = i;
+            __syncthreads();
+        } else {
+            const double L = dlog1p(-rho);
+            for (attempt = 0; attempt < 64; ++attempt) {
+                c = block_walk(A.key, TAG_LEAF_B + 256u * (uint32_t)attempt, id, L, r.S, sm);
+                if (sm.err) break;
+                if (c >= r.c) break;
+            }
+            if (sm.err || attempt == 64) {
+                if (threadIdx.x == 0) set_status(A.status, RS_EITER);
+                fail = true;
+            }
+        }
+        if (!fail && c > kLeafBCap) {
+            if (threadIdx.x == 0) set_status(A.status, RS_ECAPACITY);
+            fail = true;
+        }
+        if (fail) {
+            __syncthreads();
+            continue;
+        }
+        const uint32_t drop = (uint32_t)(c - r.c);
+        Draw<4> dr{Bounded32{c, (uint32_t)(((1ull << 32) - c) % c)}};
+        if (!select_leaf<uint32_t, 4, true>(sm.sel, dr, A.key, TAG_FIXUP, id, c, drop, A.status)) {
+            __syncthreads();
+            continue;
+        }
+        uint64_t* dst = A.out + r.off;
+        for (uint32_t i = threadIdx.x; i < c; i += kLeafThreads) {
+            const uint32_t below = lower_bound(sm.sel.keys, drop, i);
+            if (below < drop && sm.sel.keys[below] == i) continue;
+            dst[i - below] = r.lo + 1 + sm.pos[i];
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_leaves_b(const LeafBLaunch& L, cudaStream_t st) {
+    const size_t smem = sizeof(LeafBShared);
+    cudaError_t e = cudaFuncSetAttribute(leaf_b_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, leaf_b_kernel, kLeafThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    LeafBArgs A{L.leaves, L.nleaves, L.first_id, make_key(L.seed), L.out, L.status};
+    const uint64_t grid = std::min<uint64_t>(L.nleaves, (uint64_t)L.sms * per_sm);
+    leaf_b_kernel<<<(unsigned)grid, kLeafThreads, smem, st>>>(A);
+    return cudaGetLastError();
+}
+
+}  // namespace rs

@@ -1,0 +1,292 @@
+// rs_capi.cu -- the C ABI declared in include/rs.h.
+//
+// Host side of the sampler: argument checks, the plan (tree depth), scratch
+// memory, and the launch sequence tree -> leaves on the caller's stream.
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "rs_internal.h"
+
+struct rs_ctx {
+    int device = 0;
+    int sms = 0;
+    double* tab = nullptr;          // ln i!, i < 256
+    int* status = nullptr;          // first device-side error
+    rs::NodeRec* nodes = nullptr;   // heap-numbered node records
+    uint64_t nodes_cap = 0;         // records
+    uint32_t* ovf = nullptr;        // overflow list + its counter
+    uint64_t ovf_cap = 0;           // words
+    void* big_pool = nullptr;
+    uint64_t big_pool_bytes = 0;
+    uint64_t* words = nullptr;      // general scratch (Bernoulli chunk counts, leaf B positions)
+    uint64_t words_cap = 0;
+    uint32_t leaf_cap = 0;          // testing knob, 0 = default
+};
+
+namespace {
+
+// Makes ctx->device current for the duration of a call, then restores the
+// caller's device.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+int cuda_rc(cudaError_t e) {
+    if (e == cudaSuccess) return RS_OK;
+    if (e == cudaErrorMemoryAllocation) return RS_ENOMEM;
+    return RS_ECUDA;
+}
+
+// Grows a device buffer to at least `need` elements (contents not kept).
+template <typename T>
+int ensure(T*& ptr, uint64_t& cap, uint64_t need) {
+    if (cap >= need) return RS_OK;
+    if (ptr) {
+        cudaError_t e = cudaFree(ptr);   // synchronizes the device
+        ptr = nullptr;
+        cap = 0;
+        if (e != cudaSuccess) return RS_ECUDA;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, need * sizeof(T));
+    if (e != cudaSuccess) return cuda_rc(e);
+    ptr = static_cast<T*>(p);
+    cap = need;
+    return RS_OK;
+}
+
+int depth_of(uint64_t n, uint64_t N, uint32_t n0) {
+    int D = 0;
+    while ((unsigned __int128)n > ((unsigned __int128)n0 << D)) ++D;
+    while (D > 0 && ((unsigned __int128)1 << D) > (unsigned __int128)N) --D;
+    return D;
+}
+
+int check_sample_args(uint64_t n, uint64_t N, uint32_t n0, bool with_replacement, const void* out) {
+    if (n0 == 0) return RS_EINVAL;
+    if (N > (1ull << 62)) return RS_EINVAL;
+    if (n > 0 && N == 0) return RS_EINVAL;
+    if (!with_replacement && n > N) return RS_EINVAL;
+    if (n > 0 && out == nullptr) return RS_EINVAL;
+    if (out && ((uintptr_t)out & 7)) return RS_EINVAL;
+    return RS_OK;
+}
+
+// Builds the split tree for (n, N, seed, n0) into ctx->nodes.  kind selects
+// binomial (RS_KIND_WR) or hypergeometric splits.
+int build_tree(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0, int kind, cudaStream_t st,
+               int* D_out) {
+    const int D = depth_of(n, N, n0);
+    if (D > rs::kMaxDepth) return RS_ECAPACITY;
+    int rc = ensure(ctx->nodes, ctx->nodes_cap, 2ull << D);
+    if (rc) return rc;
+    *D_out = D;
+    return cuda_rc(rs::launch_tree(ctx->nodes, n, N, seed, D, kind == RS_KIND_WR, ctx->tab, ctx->status, st));
+}
+
+int sample_impl(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0, int kind, uint64_t* out,
+                void* stream) {
+    if (!ctx) return RS_EINVAL;
+    int rc = check_sample_args(n, N, n0, kind == RS_KIND_WR, out);
+    if (rc || n == 0) return rc;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RS_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int D;
+    rc = build_tree(ctx, n, N, seed, n0, kind, st, &D);
+    if (rc) return rc;
+    const uint64_t nleaves = 1ull << D;
+    const uint64_t smax = (N >> D) + ((N & (nleaves - 1)) ? 1 : 0);
+    if (kind == RS_KIND_B) {
+        rs::LeafBLaunch L{ctx->nodes + nleaves, nleaves, nleaves, seed, out, ctx->status, ctx->sms};
+        return cuda_rc(rs::launch_leaves_b(L, st));
+    }
+    rc = ensure(ctx->ovf, ctx->ovf_cap, nleaves + 1);
+    if (rc) return rc;
+    const uint32_t cap = ctx->leaf_cap ? std::min<uint32_t>(ctx->leaf_cap, rs::kLeafCap) : rs::kLeafCap;
+    // Largest selection any leaf can need: k <= n and, without replacement,
+    // k <= s/2 (the complement rule).
+    uint64_t bound = n;
+    if (kind != RS_KIND_WR) bound = std::min<uint64_t>(bound, smax / 2);
+    uint64_t big_kmax = 0;
+    if (bound > cap) {
+        big_kmax = std::min<uint64_t>(bound, rs::kBigLeafMax);
+        const uint64_t bytes = rs::big_pool_bytes(big_kmax);
+        if (ctx->big_pool_bytes < bytes) {
+            if (ctx->big_pool) cudaFree(ctx->big_pool);
+            ctx->big_pool = nullptr;
+            ctx->big_pool_bytes = 0;
+            cudaError_t e = cudaMalloc(&ctx->big_pool, bytes);
+            if (e != cudaSuccess) return cuda_rc(e);
+            ctx->big_pool_bytes = bytes;
+        }
+    }
+    rs::LeafLaunch L{};
+    L.leaves = ctx->nodes + nleaves;
+    L.nleaves = nleaves;
+    L.first_id = nleaves;
+    L.seed = seed;
+    L.smax = smax;
+    L.out = out;
+    L.status = ctx->status;
+    L.ovf_list = ctx->ovf;
+    L.ovf_count = ctx->ovf + nleaves;
+    L.big_pool = ctx->big_pool;
+    L.big_kmax = big_kmax;
+    L.cap = cap;
+    L.sms = ctx->sms;
+    L.with_replacement = kind == RS_KIND_WR;
+    return cuda_rc(rs::launch_leaves(L, st));
+}
+
+}  // namespace
+
+extern "C" {
+
+int rs_create(rs_ctx** out, int device) {
+    if (!out) return RS_EINVAL;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) return RS_ECUDA;
+    DeviceGuard g(device);
+    if (!g.ok) return RS_ECUDA;
+    rs_ctx* ctx = new (std::nothrow) rs_ctx();
+    if (!ctx) return RS_ENOMEM;
+    ctx->device = device;
+    int rc = RS_OK;
+    if (cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) rc = RS_ECUDA;
+    if (!rc) rc = cuda_rc(cudaMalloc(&ctx->tab, 256 * sizeof(double)));
+    if (!rc) rc = cuda_rc(cudaMalloc(&ctx->status, sizeof(int)));
+    if (!rc) rc = cuda_rc(cudaMemset(ctx->status, 0, sizeof(int)));
+    if (!rc) rc = cuda_rc(rs::launch_lf_table(ctx->tab, 0));
+    if (!rc) rc = cuda_rc(cudaDeviceSynchronize());
+    if (rc) {
+        rs_destroy(ctx);
+        return rc;
+    }
+    *out = ctx;
+    return RS_OK;
+}
+
+int rs_destroy(rs_ctx* ctx) {
+    if (!ctx) return RS_OK;
+    DeviceGuard g(ctx->device);
+    int rc = cuda_rc(cudaDeviceSynchronize());
+    cudaFree(ctx->tab);
+    cudaFree(ctx->status);
+    cudaFree(ctx->nodes);
+    cudaFree(ctx->ovf);
+    cudaFree(ctx->big_pool);
+    cudaFree(ctx->words);
+    delete ctx;
+    return rc;
+}
+
+int rs_plan(uint64_t n, uint64_t N, uint32_t n0, int* depth_out) {
+    if (!depth_out || n0 == 0) return RS_EINVAL;
+    *depth_out = depth_of(n, N, n0);
+    return RS_OK;
+}
+
+int rs_sample(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0, uint64_t* out_dev, void* stream) {
+    return sample_impl(ctx, n, N, seed, n0, RS_KIND_H, out_dev, stream);
+}
+
+int rs_sample_with_replacement(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0, uint64_t* out_dev,
+                               void* stream) {
+    return sample_impl(ctx, n, N, seed, n0, RS_KIND_WR, out_dev, stream);
+}
+
+int rs_sample_b(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0, uint64_t* out_dev, void* stream) {
+    return sample_impl(ctx, n, N, seed, n0, RS_KIND_B, out_dev, stream);
+}
+
+int rs_split_tree(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0, int kind, uint64_t* recs_dev,
+                  uint64_t max_leaves, void* stream) {
+    if (!ctx || kind < RS_KIND_H || kind > RS_KIND_B) return RS_EINVAL;
+    int rc = check_sample_args(n, N, n0, kind == RS_KIND_WR, recs_dev);
+    if (rc) return rc;
+    if (!recs_dev) return RS_EINVAL;
+    const int D = depth_of(n, N, n0);
+    if ((1ull << D) > max_leaves) return RS_ECAPACITY;
+    if (N == 0) return RS_OK;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RS_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int Dt;
+    rc = build_tree(ctx, n, N, seed, n0, kind, st, &Dt);
+    if (rc) return rc;
+    return cuda_rc(rs::launch_export_leaves(ctx->nodes + (1ull << D), 1ull << D, recs_dev, st));
+}
+
+int rs_bernoulli(rs_ctx* ctx, double p, uint64_t N, uint64_t seed, uint32_t n0, uint64_t a, uint64_t b,
+                 uint64_t* out_dev, uint64_t cap, uint64_t* count_out, void* stream) {
+    if (!ctx || !count_out) return RS_EINVAL;
+    *count_out = 0;
+    if (!(p >= 0.0 && p <= 1.0) || n0 == 0 || N > (1ull << 62) || a > b || b > N) return RS_EINVAL;
+    int c = 0;
+    while (c < 62 && ldexp(1.0, c) * p < (double)n0) ++c;
+    const uint64_t C = 1ull << c;
+    if (a % C != 0 || (b % C != 0 && b != N)) return RS_EINVAL;
+    if (cap > 0 && (!out_dev || ((uintptr_t)out_dev & 7))) return RS_EINVAL;
+    if (p == 0.0 || a == b) return RS_OK;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RS_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const uint64_t first = a >> c;
+    const uint64_t nchunks = ((b - 1) >> c) - first + 1;
+    int rc = ensure(ctx->words, ctx->words_cap, nchunks + 2 + rs::scan_scratch_words(nchunks));
+    if (rc) return rc;
+    rs::BernLaunch L{p, N, seed, c, first, nchunks, a, b, out_dev, cap, ctx->words, ctx->words + nchunks + 1,
+                     ctx->words + nchunks + 2, ctx->status, ctx->sms};
+    rc = cuda_rc(rs::launch_bernoulli(L, st));
+    if (rc) return rc;
+    uint64_t total = 0;
+    rc = cuda_rc(cudaMemcpyAsync(&total, ctx->words + nchunks + 1, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    if (!rc) rc = cuda_rc(cudaStreamSynchronize(st));
+    if (rc) return rc;
+    *count_out = total;
+    return total > cap ? RS_ECAPACITY : RS_OK;
+}
+
+int rs_sync(rs_ctx* ctx, void* stream) {
+    if (!ctx) return RS_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RS_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return RS_ECUDA;
+    int h = 0;
+    if (cudaMemcpy(&h, ctx->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return RS_ECUDA;
+    if (h != RS_OK && cudaMemset(ctx->status, 0, sizeof(int)) != cudaSuccess) return RS_ECUDA;
+    return h;
+}
+
+const char* rs_strerror(int code) {
+    switch (code) {
+        case RS_OK: return "ok";
+        case RS_EINVAL: return "invalid argument";
+        case RS_ECAPACITY: return "result exceeds the buffer or a size limit";
+        case RS_ENOMEM: return "out of memory";
+        case RS_ECUDA: return "CUDA runtime error";
+        case RS_ETIMEOUT: return "bounded wait gave up";
+        case RS_EITER: return "iteration cap reached";
+        default: return "unknown error code";
+    }
+}
+
+int rs_set_leaf_capacity(rs_ctx* ctx, uint32_t cap) {
+    if (!ctx) return RS_EINVAL;
+    ctx->leaf_cap = cap;
+    return RS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,30 @@
+// rs_common.cuh -- shared device/host definitions of the CUDA sampler.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/rs.h"
+
+#define RS_DEV __device__ __forceinline__
+#define RS_HD __host__ __device__ __forceinline__
+
+namespace rs {
+
+// Stream tags: one per kind of random decision (split deviates, leaf
+// candidates, Algorithm B attempts, the repair step, Bernoulli chunks).
+enum : uint32_t { TAG_SPLIT = 1, TAG_LEAF_H = 2, TAG_LEAF_B = 3, TAG_FIXUP = 4, TAG_BERN = 5, TAG_LEAF_WR = 6 };
+
+// A split-tree node: the 0-based positions [lo, lo+S) hold c samples that
+// are written at out[off .. off+c).  Heap numbering: root 1, children 2v, 2v+1.
+struct __align__(16) NodeRec {
+    uint64_t lo, S, c, off;
+};
+
+// First error wins; later errors are dropped until the host clears the word.
+RS_DEV void set_status(int* status, int code) {
+    if (code != RS_OK) atomicCAS(status, RS_OK, code);
+}
+
+RS_DEV uint64_t umulhi64(uint64_t a, uint64_t b) { return __umul64hi(a, b); }
+
+}  // namespace rs

@@ -1,0 +1,119 @@
+// rs_deviates.cuh -- the split deviates on the device.
+//
+// A node holding c samples of [lo, lo+S) sends L of them to its left half of
+// floor(S/2) positions.  Without replacement L is hypergeometric (Sec. 3),
+// with replacement binomial (Sec. 4.6).  The paper generates these with
+// Stadlober's ratio-of-uniforms method; the method here is inversion below a
+// mean of 16 and ratio-of-uniforms with the table-mountain hat above, with
+// no squeeze.  Uniforms are the 64-bit values of the node's SPLIT stream in
+// order: value r for inversion restart r, values 2i and 2i+1 for trial i.
+#pragma once
+#include "rs_math.cuh"
+#include "rs_rng.cuh"
+
+namespace rs {
+
+constexpr uint64_t kRouMaxTrials = 1ull << 20;
+constexpr uint64_t kInvMaxRestarts = 64;
+
+// HG(n, K, S): successes among n draws without replacement from S items
+// containing K successes.  Returns RS_OK or RS_EITER.
+RS_DEV int hypergeometric(Key2 key, uint64_t node, uint64_t n, uint64_t K, uint64_t S,
+                          const double* __restrict__ tab, uint64_t& out) {
+    if (n == 0 || K == 0) { out = 0; return RS_OK; }
+    if (K == S) { out = n; return RS_OK; }
+    if (n == S) { out = K; return RS_OK; }
+    const uint64_t n_in = n;
+    // Symmetries: take the smaller of K and S-K, and of n and S-n.
+    const bool flipK = K > S - K;
+    if (flipK) K = S - K;
+    const bool flipN = n > S - n;
+    if (flipN) n = S - n;
+    const uint64_t a = n < K ? n : K;
+    const uint64_t b = n < K ? K : n;
+    const double mu = ((double)a * (double)b) / (double)S;
+    uint64_t y = 0;
+    bool done = false;
+    if (mu < 16.0) {
+        // Inversion from k = 0 with the pmf recurrence
+        // f(k+1) = f(k) (a-k)(b-k) / ((k+1)(S-a-b+k+1)).
+        const double f0 = dexp(dsd(S - b, S - a - b, tab) - dsd(S, S - a, tab));
+        for (uint64_t r = 0; r < kInvMaxRestarts && !done; ++r) {
+            double u = v_closed(stream_value(key, TAG_SPLIT, node, r));
+            double f = f0;
+            for (uint64_t k = 0; k <= a; ++k) {
+                if (u < f) { y = k; done = true; break; }
+                u = u - f;
+                f = (f * ((double)(a - k) * (double)(b - k))) / ((double)(k + 1) * (double)(S - a - b + k + 1));
+                // Once f underflows to 0 it stays 0 and u no longer changes, so
+                // this pass can only run past a: restart now (same outcome).
+                if (f == 0.0) break;
+            }
+        }
+    } else {
+        const double var = mu * ((double)(S - a) / (double)S) * ((double)(S - b) / (double)(S - 1));
+        const double h = RS_HAT_D1 * sqrt(var + 0.5) + RS_HAT_D2;
+        const double alpha = mu + 0.5;
+        const uint64_t M = (uint64_t)(((unsigned __int128)(a + 1) * (b + 1)) / (S + 2));
+        const double top = (double)a + 1.0;
+        for (uint64_t i = 0; i < kRouMaxTrials; ++i) {
+            const uint4 blk = philox_block((uint32_t)i, TAG_SPLIT, node, key);
+            const double U = u_open(((uint64_t)blk.y << 32) | blk.x);
+            const double V = v_closed(((uint64_t)blk.w << 32) | blk.z);
+            const double X = alpha + h * (V - 0.5) / U;
+            if (X < 0.0 || X >= top) continue;
+            const uint64_t k = (uint64_t)X;
+            const double T = dsd(M, k, tab) + dsd(a - M, a - k, tab) + dsd(b - M, b - k, tab) +
+                             dsd(S - a - b + M, S - a - b + k, tab);
+            if (2.0 * dlog(U) <= T) { y = k; done = true; break; }
+        }
+    }
+    if (!done) return RS_EITER;
+    if (flipN) y = K - y;
+    if (flipK) y = n_in - y;
+    out = y;
+    return RS_OK;
+}
+
+// BIN(c, p = K/S) with K/S <= 1/2.  Returns RS_OK or RS_EITER.
+RS_DEV int binomial(Key2 key, uint64_t node, uint64_t c, uint64_t K, uint64_t S,
+                    const double* __restrict__ tab, uint64_t& out) {
+    if (c == 0 || K == 0) { out = 0; return RS_OK; }
+    const double p = (double)K / (double)S;
+    const double mu = (double)c * p;
+    if (mu < 16.0) {
+        const double f0 = dexp((double)c * dlog1p(-p));
+        const double r = p / (1.0 - p);
+        for (uint64_t rs = 0; rs < kInvMaxRestarts; ++rs) {
+            double u = v_closed(stream_value(key, TAG_SPLIT, node, rs));
+            double f = f0;
+            for (uint64_t k = 0; k <= c; ++k) {
+                if (u < f) { out = k; return RS_OK; }
+                u = u - f;
+                f = (f * ((double)(c - k) * r)) / (double)(k + 1);
+                if (f == 0.0) break;
+            }
+        }
+        return RS_EITER;
+    }
+    const double var = mu * (1.0 - p);
+    const double h = RS_HAT_D1 * sqrt(var + 0.5) + RS_HAT_D2;
+    const double alpha = mu + 0.5;
+    const double r = p / (1.0 - p);
+    const double logr = (r == 1.0) ? 0.0 : dlog(r);
+    const uint64_t M = (uint64_t)(((unsigned __int128)(c + 1) * K) / S);
+    const double top = (double)c + 1.0;
+    for (uint64_t i = 0; i < kRouMaxTrials; ++i) {
+        const uint4 blk = philox_block((uint32_t)i, TAG_SPLIT, node, key);
+        const double U = u_open(((uint64_t)blk.y << 32) | blk.x);
+        const double V = v_closed(((uint64_t)blk.w << 32) | blk.z);
+        const double X = alpha + h * (V - 0.5) / U;
+        if (X < 0.0 || X >= top) continue;
+        const uint64_t k = (uint64_t)X;
+        const double T = dsd(M, k, tab) + dsd(c - M, c - k, tab) + (double)((int64_t)k - (int64_t)M) * logr;
+        if (2.0 * dlog(U) <= T) { out = k; return RS_OK; }
+    }
+    return RS_EITER;
+}
+
+}  // namespace rs

@@ -1,0 +1,84 @@
+// rs_internal.h -- host-side interfaces between the library's translation units.
+#pragma once
+#include <algorithm>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "rs_common.cuh"
+
+namespace rs {
+
+// Largest leaf selection handled in shared memory by the leaf kernels.
+constexpr uint32_t kLeafCap = 8192;
+// Largest selection the general (global-memory) leaf path accepts.
+constexpr uint64_t kBigLeafMax = 1ull << 22;
+// Deepest split tree the library builds (2^27 node records of 32 bytes).
+constexpr int kMaxDepth = 26;
+
+// Builds the ln i! table (i < 256) on the device with the library's own log.
+cudaError_t launch_lf_table(double* tab, cudaStream_t st);
+
+// Split tree: writes node records 1 .. 2^(D+1)-1 of `rec` level by level;
+// the leaves are rec[2^D .. 2^(D+1)).  with_replacement selects binomial
+// splits, else hypergeometric ones.
+cudaError_t launch_tree(NodeRec* rec, uint64_t n, uint64_t N, uint64_t seed, int D, bool with_replacement,
+                        const double* tab, int* status, cudaStream_t st);
+
+// Copies leaf records rec[2^D + i] to recs_out[4i .. 4i+3].
+cudaError_t launch_export_leaves(const NodeRec* leaves, uint64_t nleaves, uint64_t* recs_out, cudaStream_t st);
+
+struct LeafLaunch {
+    const NodeRec* leaves;   // 2^D leaf records
+    uint64_t nleaves;
+    uint64_t first_id;       // heap id of leaf 0
+    uint64_t seed;
+    uint64_t smax;           // largest leaf size
+    uint64_t* out;
+    int* status;
+    uint32_t* ovf_list;      // nleaves entries
+    uint32_t* ovf_count;
+    void* big_pool;          // scratch of big_pool_bytes(big_kmax) bytes, or null when big_kmax = 0
+    uint64_t big_kmax;
+    uint32_t cap;            // 0 = kLeafCap
+    int sms;
+    bool with_replacement;
+};
+
+// Leaf H (or leaf WR) for every leaf, then the general path for the leaves
+// whose selection exceeded the capacity.
+cudaError_t launch_leaves(const LeafLaunch& L, cudaStream_t st);
+uint64_t big_pool_bytes(uint64_t kmax);
+
+struct LeafBLaunch {
+    const NodeRec* leaves;
+    uint64_t nleaves;
+    uint64_t first_id;
+    uint64_t seed;
+    uint64_t* out;
+    int* status;
+    int sms;
+};
+// Algorithm B leaves (positions of one attempt live in shared memory).
+cudaError_t launch_leaves_b(const LeafBLaunch& L, cudaStream_t st);
+
+struct BernLaunch {
+    double p;
+    uint64_t N;
+    uint64_t seed;
+    int chunk_log2;
+    uint64_t chunk_first;    // first chunk of the window
+    uint64_t nchunks;        // chunks in the window
+    uint64_t a, b;           // window of 0-based positions
+    uint64_t* out;
+    uint64_t cap;
+    uint64_t* counts;        // nchunks + 1 words of scratch
+    uint64_t* total;         // device word: number of positions in the window
+    uint64_t* scan_scratch;  // scan_scratch_words(nchunks) words
+    int* status;
+    int sms;
+};
+// Count pass, exclusive scan of the chunk counts, write pass.
+cudaError_t launch_bernoulli(const BernLaunch& L, cudaStream_t st);
+uint64_t scan_scratch_words(uint64_t n);
+
+}  // namespace rs

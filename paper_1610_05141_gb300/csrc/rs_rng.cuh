@@ -1,0 +1,72 @@
+// rs_rng.cuh -- counter-based randomness on the device.
+//
+// Every random decision is keyed by the subtree it belongs to, so no node
+// waits for another (Sec. 3.2: the t-th deviate of subproblem j..k is a hash
+// of (j, k, t), a PE's local generator is seeded by its number).  Here the
+// keyed source is Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11):
+// key = (seed lo, seed hi), counter = (block t, tag, node id lo, node id hi).
+#pragma once
+#include "rs_common.cuh"
+
+namespace rs {
+
+struct Key2 { uint32_t k0, k1; };
+
+RS_HD Key2 make_key(uint64_t seed) { return Key2{(uint32_t)seed, (uint32_t)(seed >> 32)}; }
+
+// One Philox4x32-10 block: ten rounds of two 32x32->64 multiplies and xors,
+// the key bumped by the Weyl constants between rounds.
+RS_DEV uint4 philox_block(uint32_t t, uint32_t tag, uint64_t id, Key2 key) {
+    uint32_t x0 = t, x1 = tag, x2 = (uint32_t)id, x3 = (uint32_t)(id >> 32);
+    uint32_t k0 = key.k0, k1 = key.k1;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * x0, hi0 = __umulhi(0xD2511F53u, x0);
+        const uint32_t lo1 = 0xCD9E8D57u * x2, hi1 = __umulhi(0xCD9E8D57u, x2);
+        const uint32_t y0 = hi1 ^ x1 ^ k0;
+        const uint32_t y2 = hi0 ^ x3 ^ k1;
+        x0 = y0; x1 = lo1; x2 = y2; x3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return make_uint4(x0, x1, x2, x3);
+}
+
+// 64-bit value j of a stream: words 2j and 2j+1 (low, high), block j/2.
+RS_DEV uint64_t stream_value(Key2 key, uint32_t tag, uint64_t id, uint64_t j) {
+    uint4 b = philox_block((uint32_t)(j >> 1), tag, id, key);
+    return (j & 1) ? (((uint64_t)b.w << 32) | b.z) : (((uint64_t)b.y << 32) | b.x);
+}
+
+// Uniforms from a 64-bit value, exact: U in (0,1], V in [0,1).
+RS_DEV double u_open(uint64_t x) { return (double)((x >> 11) + 1) * (1.0 / 9007199254740992.0); }
+RS_DEV double v_closed(uint64_t x) { return (double)(x >> 11) * (1.0 / 9007199254740992.0); }
+
+// Lemire's multiply-and-reject for a range of s <= 2^32 values, one 32-bit
+// word per candidate; a rejected ("void") candidate still consumes its word.
+// thr = (2^32 - s) mod s.
+struct Bounded32 {
+    uint64_t s;
+    uint32_t thr;
+    RS_DEV bool draw(uint32_t w, uint32_t& v) const {
+        const uint64_t prod = (uint64_t)w * s;
+        v = (uint32_t)(prod >> 32);
+        return (uint32_t)prod >= thr;
+    }
+};
+
+// Same for s > 2^32 with one 64-bit value per candidate; thr = (2^64 - s) mod s.
+struct Bounded64 {
+    uint64_t s;
+    uint64_t thr;
+    RS_DEV bool draw(uint64_t x, uint64_t& v) const {
+        v = __umul64hi(x, s);
+        return x * s >= thr;
+    }
+};
+
+// Host helpers for the rejection thresholds.
+inline uint32_t bounded32_threshold(uint64_t s) { return (uint32_t)(((1ull << 32) - s) % s); }
+inline uint64_t bounded64_threshold(uint64_t s) { return (0ull - s) % s; }
+
+}  // namespace rs

@@ -1,0 +1,200 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle: bit-exact
+for every output (integers), on the same seeded inputs, at sizes the oracle
+finishes in seconds (several leaves and ragged tails), plus edge cases
+(empty, single element, full range, complement leaves, 64-bit leaves,
+the general path for oversized leaves)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1610_05141_gb300 as rs
+    from paper_1610_05141_gb300 import build
+    build.build()
+    rs.load()
+    return rs
+
+
+@pytest.fixture(scope="module")
+def ctx(rs):
+    c = rs.rs_create(0)
+    yield c
+    c.close()
+
+
+def run(rs, ctx, fn, n, N, seed, n0):
+    out = torch.full((max(n, 1),), -1, dtype=torch.int64, device="cuda")
+    fn(ctx, n, N, seed, n0, out)
+    rc = rs.rs_sync(ctx)
+    assert rc == rs.RS_OK, rs.strerror(rc)
+    return out[:n].cpu().numpy().view(np.uint64)
+
+
+def assert_same(got, want, what):
+    assert got.shape == want.shape, (what, got.shape, want.shape)
+    if not np.array_equal(got, want):
+        bad = int(np.argmax(got != want))
+        raise AssertionError(f"{what}: first mismatch at {bad}: gpu {got[bad]} oracle {want[bad]}")
+
+
+H_CASES = [
+    (10**6, 10**9, 1, 4096),            # n = 10^6 from N = 10^9 (the small workload)
+    (1, 1, 5, 4),
+    (5, 5, 1, 1),
+    (1000, 1000, 2, 16),                # every leaf full: complement path
+    (999, 1000, 3, 16),
+    (600, 1000, 4, 64),
+    (501, 1000, 7, 1024),
+    (4096, 10**9, 9, 4096),             # one leaf, k = n0
+    (7000, 10**4, 17, 4096),            # complement leaves with many duplicate draws
+    (10**5, 2**62, 11, 4096),           # 64-bit candidates and keys
+    (3 * 10**5, 3 * 2**40 + 7, 13, 1024),
+    (10**5, 2**32 + 12345, 12, 512),
+    (2 * 10**5, 2**33, 14, 4096),
+    (10**6, 2**33 + 1, 15, 2),          # tiny leaves
+    (100, 150, 16, 1),                  # depth capped by N
+    (123457, 3906250 * 3 + 17, 21, 333),
+    (8191, 2**20, 22, 8191),            # one leaf near the shared-memory capacity
+]
+
+
+@pytest.mark.parametrize("n,N,seed,n0", H_CASES)
+def test_sample_matches_oracle(rs, ctx, oracle, n, N, seed, n0):
+    got = run(rs, ctx, rs.rs_sample, n, N, seed, n0)
+    assert_same(got, oracle.sample(n, N, seed, n0, oracle.KIND_H), (n, N, seed, n0))
+
+
+def test_sample_empty(rs, ctx):
+    out = torch.full((4,), -1, dtype=torch.int64, device="cuda")
+    rs.rs_sample(ctx, 0, 10, 1, 4, out)
+    assert rs.rs_sync(ctx) == rs.RS_OK
+    assert out.cpu().tolist() == [-1] * 4
+
+
+WR_CASES = [
+    (10**6, 2**40, 1, 4096),
+    (10**5, 1000, 2, 512),               # n > N
+    (50, 3, 3, 4),
+    (10**5, 2**62, 4, 4096),
+    (77777, 10**9 + 7, 5, 100),
+]
+
+
+@pytest.mark.parametrize("n,N,seed,n0", WR_CASES)
+def test_with_replacement_matches_oracle(rs, ctx, oracle, n, N, seed, n0):
+    got = run(rs, ctx, rs.rs_sample_with_replacement, n, N, seed, n0)
+    assert_same(got, oracle.sample(n, N, seed, n0, oracle.KIND_WR), (n, N, seed, n0))
+
+
+B_CASES = [
+    (10**5, 10**8, 1, 4096),
+    (999, 1000, 2, 16),
+    (300, 10**12, 3, 64),
+    (20000, 2**62, 4, 2048),
+    (5000, 6000, 5, 128),
+]
+
+
+@pytest.mark.parametrize("n,N,seed,n0", B_CASES)
+def test_leaf_b_matches_oracle(rs, ctx, oracle, n, N, seed, n0):
+    got = run(rs, ctx, rs.rs_sample_b, n, N, seed, n0)
+    assert_same(got, oracle.sample(n, N, seed, n0, oracle.KIND_B), (n, N, seed, n0))
+
+
+@pytest.mark.parametrize("cap", [64, 1000])
+def test_general_leaf_path_matches_oracle(rs, oracle, cap):
+    """Leaves whose selection exceeds the capacity take the global-memory
+    path; forcing a tiny capacity must not change a single value."""
+    c = rs.rs_create(0)
+    try:
+        rs.rs_set_leaf_capacity(c, cap)
+        for fn, kind, n, N, seed, n0 in [(rs.rs_sample, oracle.KIND_H, 20000, 10**8, 18, 4096),
+                                         (rs.rs_sample, oracle.KIND_H, 3000, 5000, 19, 4096),
+                                         (rs.rs_sample, oracle.KIND_H, 5000, 2**50, 20, 8192),
+                                         (rs.rs_sample_with_replacement, oracle.KIND_WR, 9000, 5000, 21, 4096)]:
+            got = run(rs, c, fn, n, N, seed, n0)
+            assert_same(got, oracle.sample(n, N, seed, n0, kind), (cap, n, N))
+    finally:
+        c.close()
+
+
+TREE_CASES = [
+    (10**6, 10**9, 1, 4096, 0),
+    (10**9, 2**50, 1, 4096, 0),          # the large workload: all 2^18 leaf records
+    (10**9, 2**40, 1, 4096, 1),          # with replacement: binomial splits
+    (999, 1000, 3, 3, 0),
+    (5000, 77, 16, 16, 1),
+    (10**5, 2**62, 4, 4096, 0),
+]
+
+
+@pytest.mark.parametrize("n,N,seed,n0,kind", TREE_CASES)
+def test_split_tree_matches_oracle(rs, ctx, oracle, n, N, seed, n0, kind):
+    want, D = oracle.tree(n, N, seed, n0, kind)
+    recs = torch.zeros(4 * len(want), dtype=torch.int64, device="cuda")
+    rs.rs_split_tree(ctx, n, N, seed, n0, kind, recs, len(want))
+    assert rs.rs_sync(ctx) == rs.RS_OK
+    got = recs.cpu().numpy().view(np.uint64).reshape(-1, 4)
+    assert_same(got.ravel(), want.ravel(), (n, N, kind))
+
+
+BERN_CASES = [
+    (1e-4, 2**28, 7, 4096),
+    (1e-2, 2**24, 7, 4096),
+    (0.5, 2**20, 7, 4096),
+    (0.3, 10**6 + 7, 8, 64),
+    (0.999, 5000, 9, 16),
+    (1e-15, 2**62, 5, 4096),
+]
+
+
+@pytest.mark.parametrize("p,N,seed,n0", BERN_CASES)
+def test_bernoulli_matches_oracle(rs, ctx, oracle, p, N, seed, n0):
+    want = oracle.bernoulli(p, N, seed, n0)
+    cap = len(want) + 16
+    out = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
+    rc, cnt = rs.rs_bernoulli(ctx, p, N, seed, n0, 0, N, out, cap)
+    assert rs.rs_sync(ctx) == rs.RS_OK
+    assert cnt == len(want)
+    assert_same(out[:cnt].cpu().numpy().view(np.uint64), want, (p, N))
+
+
+def test_bernoulli_windows_degenerate_and_capacity(rs, ctx, oracle):
+    p, N, seed, n0 = 0.01, 10**7 + 123, 7, 1024
+    C = 1 << oracle.bern_chunk_log2(p, n0)
+    for a, b in [(0, C), (C, 5 * C), (3 * C, N), ((N // C) * C, N)]:
+        want = oracle.bernoulli(p, N, seed, n0, a, b)
+        out = torch.empty(len(want) + 8, dtype=torch.int64, device="cuda")
+        rc, cnt = rs.rs_bernoulli(ctx, p, N, seed, n0, a, b, out, len(want) + 8)
+        assert cnt == len(want)
+        assert_same(out[:cnt].cpu().numpy().view(np.uint64), want, (a, b))
+    out = torch.empty(1000, dtype=torch.int64, device="cuda")
+    rc, cnt = rs.rs_bernoulli(ctx, 1.0, 1000, 1, 16, 0, 1000, out, 1000)
+    assert cnt == 1000 and out.cpu().tolist() == list(range(1, 1001))
+    rc, cnt = rs.rs_bernoulli(ctx, 0.0, 1000, 1, 16, 0, 1000, out, 1000)
+    assert cnt == 0
+    want = oracle.bernoulli(0.5, 1000, 1, 16)
+    rc, cnt = rs.rs_bernoulli(ctx, 0.5, 1000, 1, 16, 0, 1000, out, 10, check=False)
+    assert rc == rs.RS_ECAPACITY and cnt == len(want)
+    assert_same(out[:10].cpu().numpy().view(np.uint64), want[:10], "capped")
+    rc, _ = rs.rs_bernoulli(ctx, 0.5, 1000, 1, 16, 3, 1000, out, 1000, check=False)
+    assert rc == rs.RS_EINVAL
+
+
+def test_argument_errors(rs, ctx):
+    out = torch.empty(16, dtype=torch.int64, device="cuda")
+    assert rs.rs_sample(ctx, 11, 10, 1, 4, out, check=False) == rs.RS_EINVAL
+    assert rs.rs_sample(ctx, 1, 10, 1, 0, out, check=False) == rs.RS_EINVAL
+    assert rs.rs_sample(ctx, 1, 0, 1, 4, out, check=False) == rs.RS_EINVAL
+    assert rs.rs_sample(ctx, 1, 2**62 + 1, 1, 4, out, check=False) == rs.RS_EINVAL
+    assert rs.rs_sample(ctx, 1, 10, 1, 4, None, check=False) == rs.RS_EINVAL
+    assert rs.rs_sample(ctx, 1, 10, 1, 4, out.data_ptr() + 4, check=False) == rs.RS_EINVAL
+    assert rs.rs_sample_with_replacement(ctx, 11, 10, 1, 4, out, check=False) == rs.RS_OK
+    assert rs.rs_sync(ctx) == rs.RS_OK
