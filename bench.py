@@ -1,0 +1,366 @@
+#!/usr/bin/env python3
+"""Benchmark: sorted sampling without replacement, n = 10^9 distinct values
+from 1..2^50 (n0 = 4096: 2^18 leaves of 2^32 positions), on one GB300.
+
+One step = one whole pass of the sampler: split tree (2^18 - 1 hypergeometric
+deviates) + every leaf (selection, sort, write-out of 8 GB of uint64).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `value` is samples/s over the device-timed steps
+(output buffer resident; the 8 GB output exceeds the 129 MB L2, so no flush
+is needed); `e2e` adds the device-to-host copy of each step's sample into
+pinned host memory.  `roofline` relates the leaf kernel's algorithmic write
+bytes (8 B per sample) per launch to its CUDA-event duration on its own
+stream.  Under torchrun with N > 1, every rank runs an independent replica
+(seed + rank) on its own GPU: the path does not shard.
+`--impl reference` times the CPU oracle on a bounded sample of the same
+workload (rank 0 only).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_SAMPLES = 10**9
+UNIVERSE = 2**50
+N0 = 4096
+SEED = 1
+BYTES_PER_SAMPLE = 8
+WORKLOAD = "sorted sampling without replacement: n=1e9 distinct uint64 from 1..2^50, n0=4096 (2^18 leaves)"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_PATH = os.path.join(ROOT, "profiles", "leaf_kernel_traffic.json")
+LEAF_SOURCES = ["rs_leaf.cu", "rs_leaf.cuh", "rs_block.cuh", "rs_rng.cuh", "rs_common.cuh", "rs_internal.h"]
+
+
+def set_workload(n, log2N):
+    """Smaller cases of the same shape (used for ncu captures of a few GB)."""
+    global N_SAMPLES, UNIVERSE, WORKLOAD
+    if n is None and log2N is None:
+        return
+    N_SAMPLES = n if n is not None else N_SAMPLES
+    UNIVERSE = 2**log2N if log2N is not None else UNIVERSE
+    WORKLOAD = (f"sorted sampling without replacement: n={N_SAMPLES} distinct uint64 from 1..2^{UNIVERSE.bit_length() - 1}"
+                f", n0={N0} (reduced case)")
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS_PATH) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def leaf_source_hash():
+    h = hashlib.sha256()
+    for name in LEAF_SOURCES:
+        with open(os.path.join(ROOT, "paper_1610_05141_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def leaf_traffic():
+    """DRAM bytes per launch of the leaf kernel from the committed ncu
+    summary, scaled to this workload, or None if the kernel changed since."""
+    try:
+        with open(TRAFFIC_PATH) as f:
+            t = json.load(f)
+    except Exception:
+        return None
+    if t.get("source_hash") != leaf_source_hash():
+        return None
+    return t["dram_bytes_per_sample"] * N_SAMPLES
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0=None, t1=None):
+        """Median SM clock and throttle reasons of the samples taken between
+        the wall-clock times t0 and t1 (all samples if not given)."""
+        import datetime
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) < 9:
+                        continue
+                    try:
+                        ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                    except ValueError:
+                        continue
+                    if (t0 is None or ts >= t0) and (t1 is None or ts <= t1):
+                        rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples in the timed region"],
+                    "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        mhz = []
+        for r in rows:
+            try:
+                mhz.append(float(r[1]))
+            except ValueError:
+                pass
+            for name, val in zip(names, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        try:
+            max_mhz = float(rows[0][2])
+        except ValueError:
+            max_mhz = None
+        power = []
+        for r in rows:
+            try:
+                power.append(float(r[3]))
+            except ValueError:
+                pass
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": max_mhz,
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max(power) if power else None}
+
+
+def cpu_baseline(budget_s=15.0):
+    """The oracle, as it stands, on one host core: the full split tree plus
+    leaves in order until the time budget is spent."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    recs, D = oracle.tree(N_SAMPLES, UNIVERSE, SEED, N0, oracle.KIND_H)
+    samples = 0
+    leaves = 0
+    while time.perf_counter() - t0 < budget_s and leaves < len(recs):
+        samples += len(oracle.leaf(SEED, oracle.KIND_H, D, leaves, recs[leaves]))
+        leaves += 1
+    dt = time.perf_counter() - t0
+    return {"value": samples / dt, "unit": "samples/s", "cores": 1, "kind": "oracle",
+            "sample": f"full split tree (2^18 leaf records) + the first {leaves} leaves ({samples} samples) "
+                      f"in {dt:.1f} s on one core"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    # each step: the full split tree plus a slice of leaves, sized so that the
+    # whole run stays within about two and a half minutes
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    t0 = time.perf_counter()
+    recs, D = oracle.tree(N_SAMPLES, UNIVERSE, SEED, N0, oracle.KIND_H)
+    t_tree = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for i in range(50):
+        oracle.leaf(SEED, oracle.KIND_H, D, i, recs[i])
+    t_leaf = (time.perf_counter() - t0) / 50
+    leaves_per_step = int(min(len(recs) - 1, 4000, max(20, (budget - t_tree) / t_leaf)))
+
+    def step(k):
+        t0 = time.perf_counter()
+        r, d = oracle.tree(N_SAMPLES, UNIVERSE, SEED + k, N0, oracle.KIND_H)
+        s = 0
+        first = (k * leaves_per_step) % max(1, len(r) - leaves_per_step)
+        for i in range(first, first + leaves_per_step):
+            s += len(oracle.leaf(SEED + k, oracle.KIND_H, d, i, r[i]))
+        return s, time.perf_counter() - t0
+
+    for k in range(args.warmup):
+        step(k)
+    tot_s, tot_t = 0, 0.0
+    for k in range(args.steps):
+        s, t = step(args.warmup + k)
+        tot_s += s
+        tot_t += t
+    value = tot_s / tot_t
+    line = {"impl": "reference", "metric": "sorted samples/s", "value": value, "unit": "samples/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * tot_t / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N_SAMPLES, "N": UNIVERSE, "n0": N0},
+            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": 1, "kind": "oracle",
+                             "sample": f"per step: full split tree + {leaves_per_step} leaves "
+                                       f"(~{tot_s // max(args.steps, 1)} samples), one core"},
+            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import torch
+    import paper_1610_05141_gb300 as rs
+    from paper_1610_05141_gb300 import build as rs_build
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or world == 1:
+        rs_build.build()
+    if dist is not None:
+        dist.barrier()
+    rs.load()
+    ctx = rs.rs_create(local)
+    stream = torch.cuda.Stream()
+    out = torch.empty(N_SAMPLES, dtype=torch.int64, device="cuda")
+    seed = SEED + rank
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    with ClockSampler(local) as clocks, torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            rs.rs_sample(ctx, N_SAMPLES, UNIVERSE, seed, N0, out, stream)
+        stream.synchronize()
+        rc = rs.rs_sync(ctx, stream)
+        if rc != rs.RS_OK:
+            raise RuntimeError(f"device status {rc}: {rs.strerror(rc)}")
+        # device-timed steps
+        rs.rs_set_profiling(ctx, True)
+        launches0 = rs.rs_launch_count(ctx)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        wall0 = time.time()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            rs.rs_sample(ctx, N_SAMPLES, UNIVERSE, seed, N0, out, stream)
+        ev1.record(stream)
+        stream.synchronize()
+        torch.cuda.synchronize()
+        wall1 = time.time()
+        barrier()
+        launches = rs.rs_launch_count(ctx) - launches0
+        ms_total = ev0.elapsed_time(ev1)
+        tree_ms, leaf_ms, calls = rs.rs_phase_totals(ctx)
+        rs.rs_set_profiling(ctx, False)
+        rc = rs.rs_sync(ctx, stream)
+        if rc != rs.RS_OK:
+            raise RuntimeError(f"device status {rc}: {rs.strerror(rc)}")
+        # end to end: sample + copy of the sample into pinned host memory
+        e2e_steps = max(1, min(args.steps, 10))
+        host = torch.empty(N_SAMPLES, dtype=torch.int64, pin_memory=True)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            rs.rs_sample(ctx, N_SAMPLES, UNIVERSE, seed, N0, out, stream)
+            host.copy_(out, non_blocking=True)
+        e1.record(stream)
+        stream.synchronize()
+        barrier()
+        e2e_ms = e0.elapsed_time(e1) / e2e_steps
+        e2e_wall_ms = 1000 * (time.perf_counter() - t0) / e2e_steps
+        del host
+    clk = clocks.summary(wall0, wall1)
+
+    ms_per_step = ms_total / args.steps
+    e2e_step = max(e2e_ms, e2e_wall_ms)
+    if dist is not None:
+        t = torch.tensor([ms_per_step, e2e_step], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_per_step, e2e_step = t.tolist()
+        lt = torch.tensor([launches], dtype=torch.int64, device="cuda")
+        dist.all_reduce(lt)
+        launches = int(lt.item())
+    value = world * N_SAMPLES / (ms_per_step / 1000)
+    leaf_avg_ms = leaf_ms / calls
+    peak, peak_kind = hbm_peak()
+    achieved = BYTES_PER_SAMPLE * N_SAMPLES / (leaf_avg_ms / 1000) / 1e9
+    line = {
+        "metric": "sorted samples/s", "value": value, "unit": "samples/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_SAMPLES, "N": UNIVERSE, "n0": N0, "seed": SEED,
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "no flush: each step writes 8 GB, 62x the 129 MB L2"},
+        "write_gbs": BYTES_PER_SAMPLE * N_SAMPLES / (ms_per_step / 1000) / 1e9,
+        "phases_ms": {"split_tree": tree_ms / calls, "leaves": leaf_avg_ms},
+        "roofline": {"bound": "hbm", "kernel": "leaf_kernel<uint32,H>", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs)",
+                     "traffic": leaf_traffic()},
+        "e2e": {"value": world * N_SAMPLES / (e2e_step / 1000), "unit": "samples/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": BYTES_PER_SAMPLE * N_SAMPLES, "ms_per_step": e2e_step},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=None, help="smaller n (profiling cases only)")
+    ap.add_argument("--log2N", type=int, default=None, help="smaller universe 2^log2N (profiling cases only)")
+    args = ap.parse_args()
+    set_workload(args.n, args.log2N)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

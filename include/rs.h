@@ -128,6 +128,17 @@ const char* rs_strerror(int code);
  * does not change.  cap = 0 restores the default.  Errors: RS_EINVAL. */
 int rs_set_leaf_capacity(rs_ctx* ctx, uint32_t cap);
 
+/* Phase timing (tracing): while on, every sampling call records CUDA events
+ * on its stream around its split-tree phase and its leaf phase (no host
+ * synchronization).  Turning it on clears the totals.  rs_phase_totals waits
+ * for the recorded calls and returns the summed durations in milliseconds
+ * and the number of calls.  Errors: RS_EINVAL, RS_ECUDA, RS_ENOMEM. */
+int rs_set_profiling(rs_ctx* ctx, int on);
+int rs_phase_totals(rs_ctx* ctx, double* tree_ms, double* leaf_ms, uint64_t* calls);
+
+/* Number of kernels this context has launched since it was created. */
+int rs_launch_count(rs_ctx* ctx, uint64_t* count);
+
 #ifdef __cplusplus
 }
 #endif

@@ -50,6 +50,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "rs_sync": (i32, [vp, vp]),
         "rs_strerror": (ctypes.c_char_p, [i32]),
         "rs_set_leaf_capacity": (i32, [vp, u32]),
+        "rs_set_profiling": (i32, [vp, i32]),
+        "rs_phase_totals": (i32, [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(u64)]),
+        "rs_launch_count": (i32, [vp, ctypes.POINTER(u64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -162,3 +165,20 @@ def rs_strerror(code: int) -> str:
 
 def rs_set_leaf_capacity(ctx: Context, cap: int) -> int:
     return _check(load().rs_set_leaf_capacity(ctx.handle, cap), "rs_set_leaf_capacity")
+
+
+def rs_set_profiling(ctx: Context, on: bool) -> int:
+    return _check(load().rs_set_profiling(ctx.handle, 1 if on else 0), "rs_set_profiling")
+
+
+def rs_phase_totals(ctx: Context):
+    """(tree_ms, leaf_ms, calls) summed over the profiled sampling calls."""
+    t, l, c = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_uint64(0)
+    _check(load().rs_phase_totals(ctx.handle, ctypes.byref(t), ctypes.byref(l), ctypes.byref(c)), "rs_phase_totals")
+    return t.value, l.value, c.value
+
+
+def rs_launch_count(ctx: Context) -> int:
+    c = ctypes.c_uint64(0)
+    _check(load().rs_launch_count(ctx.handle, ctypes.byref(c)), "rs_launch_count")
+    return c.value

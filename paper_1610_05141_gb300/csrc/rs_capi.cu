@@ -5,6 +5,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "rs_internal.h"
 
@@ -22,6 +23,10 @@ struct rs_ctx {
     uint64_t* words = nullptr;      // general scratch (Bernoulli chunk counts, leaf B positions)
     uint64_t words_cap = 0;
     uint32_t leaf_cap = 0;          // testing knob, 0 = default
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;   // 3 events per profiled call: tree start, leaves start, end
+    size_t ev_used = 0;
+    uint64_t launches = 0;
 };
 
 namespace {
@@ -64,6 +69,22 @@ int ensure(T*& ptr, uint64_t& cap, uint64_t need) {
     return RS_OK;
 }
 
+// Records event `which` (0, 1, 2) of the current profiled call; a new call
+// starts at which = 0.  Events are created on demand and reused.
+void record_phase(rs_ctx* ctx, int which, cudaStream_t st) {
+    const size_t idx = ctx->ev_used + (size_t)which;
+    while (ctx->ev_pool.size() <= idx) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            ctx->profiling = false;
+            return;
+        }
+        ctx->ev_pool.push_back(e);
+    }
+    cudaEventRecord(ctx->ev_pool[idx], st);
+    if (which == 2) ctx->ev_used += 3;
+}
+
 int depth_of(uint64_t n, uint64_t N, uint32_t n0) {
     int D = 0;
     while ((unsigned __int128)n > ((unsigned __int128)n0 << D)) ++D;
@@ -90,6 +111,8 @@ int build_tree(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0, 
     int rc = ensure(ctx->nodes, ctx->nodes_cap, 2ull << D);
     if (rc) return rc;
     *D_out = D;
+    if (ctx->profiling) record_phase(ctx, 0, st);
+    ctx->launches += 1 + (uint64_t)D;
     return cuda_rc(rs::launch_tree(ctx->nodes, n, N, seed, D, kind == RS_KIND_WR, ctx->tab, ctx->status, st));
 }
 
@@ -106,9 +129,13 @@ int sample_impl(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0,
     if (rc) return rc;
     const uint64_t nleaves = 1ull << D;
     const uint64_t smax = (N >> D) + ((N & (nleaves - 1)) ? 1 : 0);
+    if (ctx->profiling) record_phase(ctx, 1, st);
     if (kind == RS_KIND_B) {
         rs::LeafBLaunch L{ctx->nodes + nleaves, nleaves, nleaves, seed, out, ctx->status, ctx->sms};
-        return cuda_rc(rs::launch_leaves_b(L, st));
+        ctx->launches += 1;
+        rc = cuda_rc(rs::launch_leaves_b(L, st));
+        if (ctx->profiling) record_phase(ctx, 2, st);
+        return rc;
     }
     rc = ensure(ctx->ovf, ctx->ovf_cap, nleaves + 1);
     if (rc) return rc;
@@ -145,7 +172,10 @@ int sample_impl(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0,
     L.cap = cap;
     L.sms = ctx->sms;
     L.with_replacement = kind == RS_KIND_WR;
-    return cuda_rc(rs::launch_leaves(L, st));
+    ctx->launches += big_kmax ? 2 : 1;
+    rc = cuda_rc(rs::launch_leaves(L, st));
+    if (ctx->profiling) record_phase(ctx, 2, st);
+    return rc;
 }
 
 }  // namespace
@@ -187,6 +217,7 @@ int rs_destroy(rs_ctx* ctx) {
     cudaFree(ctx->ovf);
     cudaFree(ctx->big_pool);
     cudaFree(ctx->words);
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     delete ctx;
     return rc;
 }
@@ -281,6 +312,36 @@ const char* rs_strerror(int code) {
         case RS_EITER: return "iteration cap reached";
         default: return "unknown error code";
     }
+}
+
+int rs_set_profiling(rs_ctx* ctx, int on) {
+    if (!ctx) return RS_EINVAL;
+    ctx->profiling = on != 0;
+    ctx->ev_used = 0;
+    return RS_OK;
+}
+
+int rs_phase_totals(rs_ctx* ctx, double* tree_ms, double* leaf_ms, uint64_t* calls) {
+    if (!ctx || !tree_ms || !leaf_ms || !calls) return RS_EINVAL;
+    DeviceGuard g(ctx->device);
+    *tree_ms = 0.0;
+    *leaf_ms = 0.0;
+    *calls = ctx->ev_used / 3;
+    for (size_t i = 0; i + 2 < ctx->ev_used; i += 3) {
+        float t = 0.f, l = 0.f;
+        if (cudaEventSynchronize(ctx->ev_pool[i + 2]) != cudaSuccess) return RS_ECUDA;
+        if (cudaEventElapsedTime(&t, ctx->ev_pool[i], ctx->ev_pool[i + 1]) != cudaSuccess) return RS_ECUDA;
+        if (cudaEventElapsedTime(&l, ctx->ev_pool[i + 1], ctx->ev_pool[i + 2]) != cudaSuccess) return RS_ECUDA;
+        *tree_ms += t;
+        *leaf_ms += l;
+    }
+    return RS_OK;
+}
+
+int rs_launch_count(rs_ctx* ctx, uint64_t* count) {
+    if (!ctx || !count) return RS_EINVAL;
+    *count = ctx->launches;
+    return RS_OK;
 }
 
 int rs_set_leaf_capacity(rs_ctx* ctx, uint32_t cap) {
