@@ -139,13 +139,16 @@ int sample_impl(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0,
     }
     rc = ensure(ctx->ovf, ctx->ovf_cap, nleaves + 1);
     if (rc) return rc;
-    const uint32_t cap = ctx->leaf_cap ? std::min<uint32_t>(ctx->leaf_cap, rs::kLeafCap) : rs::kLeafCap;
+    const uint32_t cap = ctx->leaf_cap ? std::min<uint32_t>(ctx->leaf_cap, rs::kLeafFastCap) : rs::kLeafFastCap;
     // Largest selection any leaf can need: k <= n and, without replacement,
     // k <= s/2 (the complement rule).
+    // A leaf also leaves the fast path when a complement does not fit the
+    // bitmap or a probe runs past the table: keep the general path ready
+    // whenever a leaf can hold more than a handful of values.
     uint64_t bound = n;
-    if (kind != RS_KIND_WR) bound = std::min<uint64_t>(bound, smax / 2);
+    if (kind != RS_KIND_WR) bound = std::min<uint64_t>(bound, smax - smax / 2);
     uint64_t big_kmax = 0;
-    if (bound > cap) {
+    if (bound > 64) {
         big_kmax = std::min<uint64_t>(bound, rs::kBigLeafMax);
         const uint64_t bytes = rs::big_pool_bytes(big_kmax);
         if (ctx->big_pool_bytes < bytes) {

@@ -1,0 +1,562 @@
+// rs_hash_leaf.cuh -- leaf H and leaf WR with MSB-addressed tables.
+//
+// Algorithm H (Sec. 2) keeps the sample in a hash table addressed by the
+// most significant bits of the key; since the keys are random that address
+// is a good hash, and since it is monotone in the key the table reads out in
+// sorted order once the keys that share an address are put in order
+// (Sec. 4.1).  One thread block owns one leaf at a time and keeps the table
+// in shared memory.  The leaf's values are the first k distinct valid
+// candidates of its stream (k = n', or s - n' for a complement leaf, where
+// more than half the leaf is taken: Sec. 2's n > N/2 rule applied per leaf).
+//
+// Three ways to compute them, all with the same result:
+//
+//  bucket path (the common case): candidates [0, k) are dropped into
+//    buckets of 8 entries addressed by their top bits (a shared-memory
+//    atomic add hands out the entry; a full bucket spills to a short side
+//    list).  A scan of the bucket counts gives every bucket its output
+//    offset; one lane per bucket sorts its keys with a 19-comparator network
+//    and stages them; a coalesced copy writes the leaf.  If a key repeats or
+//    a candidate was void, the first k candidates do not give k distinct
+//    values and the leaf goes to the probing path.
+//  bitmap path (complement leaves, and selections dense in a small range):
+//    an atomic OR sets bit v and tells whether it was already set; the
+//    read-out walks the bits in order.
+//  probing path (fallback): linear probing with compare-and-swap in rounds.
+//    Round 1 inserts candidates [0, k); each later round inserts exactly as
+//    many further candidates as values are still missing, so the set after
+//    the last round is the first k distinct valid candidates whatever the
+//    order of concurrent inserts.  The read-out ranks each key inside its
+//    cluster of occupied slots (a key's home slot lies inside its cluster and
+//    homes are monotone in the key, so clusters come out in key order).
+//
+// For sampling with replacement (Sec. 4.6) duplicates are kept: the bucket
+// path only needs valid candidates, and the probing path orders equal keys
+// by slot.
+#pragma once
+#include "rs_block.cuh"
+#include "rs_internal.h"
+#include "rs_rng.cuh"
+
+namespace rs {
+
+constexpr uint32_t kHashCap = kLeafFastCap;         // largest selection of the shared-memory paths
+constexpr uint32_t kHashSlack = 64;                 // probing: slots past the end instead of wrap-around
+constexpr uint32_t kHashSlots = 2 * kHashCap + kHashSlack;
+constexpr uint32_t kBitmapBits = 32 * kHashSlots;  // largest leaf range of the bitmap path
+constexpr uint32_t kBucketWays = 8;                 // entries per bucket
+constexpr uint32_t kMaxBuckets = 2 * kHashCap / kBucketWays;
+constexpr uint32_t kSpillCap = 128;                 // side list of keys whose bucket was full
+constexpr uint32_t kWarpStage = 32 * kBucketWays + 32;   // outputs of one warp iteration (32 buckets)
+
+template <typename KeyT>
+struct HashEmpty;
+template <>
+struct HashEmpty<uint32_t> { static constexpr uint32_t v = 0xFFFFFFFFu; };
+template <>
+struct HashEmpty<uint64_t> { static constexpr uint64_t v = ~0ull; };
+
+template <typename KeyT, int NW>
+struct HashShared {
+    KeyT tab[kHashSlots];          // bucket entries / probing table / bitmap
+    KeyT wstage[NW][kWarpStage];   // per warp: the sorted keys of its current 32 buckets
+    uint32_t cnt[kMaxBuckets + 1]; // bucket counts, then their exclusive prefix
+    KeyT spill[kSpillCap];
+    KeyT spill_sorted[kSpillCap];
+    uint32_t scan_tmp[NW + 1];
+    uint32_t warp_cnt[NW];
+    uint32_t newcount[3];          // rounds: values added in round r go to newcount[r % 3]
+    uint32_t topcount;             // probing, 32-bit keys: copies of 2^32-1 (it equals the empty mark)
+    uint32_t overflow;             // probing ran past the slack
+    uint32_t nspill;
+    uint32_t flags;                // bucket path: 1 = void candidate, 2 = side list full
+    uint32_t nover;                // overfull buckets listed for the fix-up pass
+    uint32_t over[kSpillCap];
+    uint64_t thr;                  // Lemire rejection threshold of the leaf
+    uint64_t mult;                 // address multiplier of the current table
+};
+
+// Lemire rejection threshold for a leaf of size s: (2^32 - s) mod s for
+// 32-bit candidates, (2^64 - s) mod s for 64-bit ones.
+RS_DEV uint64_t lemire_threshold(uint64_t s) {
+    return s <= (1ull << 32) ? ((1ull << 32) - s) % s : (0ull - s) % s;
+}
+
+// Barrier over the NT threads of a leaf group (named barrier `ID`).
+template <int ID, int NT>
+RS_DEV void group_sync() {
+    if (ID == 0) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(NT) : "memory");
+}
+
+template <int ID, int NT>
+RS_DEV bool group_sync_or(bool p) {
+    if (ID == 0) return __syncthreads_or(p) != 0;
+    uint32_t r;
+    asm volatile("{ .reg .pred a, b; setp.ne.u32 a, %1, 0; bar.red.or.pred b, %2, %3, a; selp.u32 %0, 1, 0, b; }"
+                 : "=r"(r) : "r"((uint32_t)p), "n"(ID), "n"(NT) : "memory");
+    return r != 0;
+}
+
+RS_DEV uint32_t hash_slot(uint32_t v, uint64_t mult) { return __umulhi(v, (uint32_t)mult); }
+RS_DEV uint32_t hash_slot(uint64_t v, uint64_t mult) { return (uint32_t)__umul64hi(v, mult); }
+
+// Multiplier of the monotone address map v -> floor(v * mult / 2^width),
+// which sends [0, s) into [0, T).
+template <typename KeyT>
+RS_DEV uint64_t slot_mult(uint64_t s, uint32_t T) {
+    if (sizeof(KeyT) == 4) {
+        const uint64_t m = ((uint64_t)T << 32) / s;
+        return m > 0xFFFFFFFFull ? 0xFFFFFFFFull : m;
+    }
+    return (uint64_t)T >= s ? ~0ull : (uint64_t)(((unsigned __int128)T << 64) / s);
+}
+
+RS_DEV uint32_t cas_key(uint32_t* p, uint32_t cmp, uint32_t val) { return atomicCAS(p, cmp, val); }
+RS_DEV uint64_t cas_key(uint64_t* p, uint64_t cmp, uint64_t val) {
+    return (uint64_t)atomicCAS((unsigned long long*)p, (unsigned long long)cmp, (unsigned long long)val);
+}
+
+struct LeafRec {
+    uint64_t lo, s, np, off, id;
+};
+
+// Walks the candidates [J, J+m) of the leaf's stream; calls f(v) for each
+// valid one and sets *void_seen if one was void.  32-bit words when
+// s <= 2^32, 64-bit values otherwise.
+template <int NT, typename F>
+RS_DEV void for_candidates(const LeafRec& r, uint64_t thr64, Key2 key, uint32_t tag, uint64_t J, uint32_t m,
+                           uint32_t tid, bool* void_seen, F&& f) {
+    // Block and candidate indices stay below 2^32 and 2^34 (callers stop a
+    // round earlier), so the block index is 32-bit; offsets are relative to J.
+    if (r.s <= (1ull << 32)) {
+        const uint32_t thr = (uint32_t)thr64;
+        const uint32_t s32 = (uint32_t)(r.s - 1);   // s - 1 fits 32 bits; s = (s - 1) + 1
+        const uint32_t b0 = (uint32_t)(J >> 2);
+        const uint32_t nblk = (uint32_t)(((J + m - 1) >> 2) - (J >> 2) + 1);
+        const uint32_t skip = (uint32_t)(J & 3);   // candidates of the first block before J
+        auto use = [&](uint32_t w, uint32_t rel) {
+            if (rel >= m) return;
+            // w * s = w * (s - 1) + w, exact in 64 bits
+            const uint64_t prod = (uint64_t)w * s32 + w;
+            if ((uint32_t)prod < thr) {
+                *void_seen = true;
+                return;
+            }
+            f((uint64_t)(prod >> 32));
+        };
+        for (uint32_t i = tid; i < nblk; i += 2 * NT) {
+            const uint32_t i2 = i + NT;
+            const uint4 w = philox_block(b0 + i, tag, r.id, key);
+            uint4 w2 = make_uint4(0, 0, 0, 0);
+            if (i2 < nblk) w2 = philox_block(b0 + i2, tag, r.id, key);
+            const uint32_t base = 4 * i - skip, base2 = 4 * i2 - skip;   // relative index of word 0 (mod 2^32)
+            if (i > 0 || skip == 0) use(w.x, base);
+            if (i > 0 || skip <= 1) use(w.y, base + 1);
+            if (i > 0 || skip <= 2) use(w.z, base + 2);
+            use(w.w, base + 3);
+            if (i2 < nblk) {
+                use(w2.x, base2);
+                use(w2.y, base2 + 1);
+                use(w2.z, base2 + 2);
+                use(w2.w, base2 + 3);
+            }
+        }
+    } else {
+        const uint64_t thr = thr64;
+        const uint32_t b0 = (uint32_t)(J >> 1);
+        const uint32_t nblk = (uint32_t)(((J + m - 1) >> 1) - (J >> 1) + 1);
+        const uint32_t skip = (uint32_t)(J & 1);
+        for (uint32_t i = tid; i < nblk; i += NT) {
+            const uint4 w = philox_block(b0 + i, tag, r.id, key);
+            const uint64_t xs[2] = {((uint64_t)w.y << 32) | w.x, ((uint64_t)w.w << 32) | w.z};
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                if (i == 0 && (uint32_t)c < skip) continue;
+                const uint32_t rel = 2 * i + c - skip;
+                if (rel >= m) continue;
+                if (xs[c] * r.s < thr) {
+                    *void_seen = true;
+                    continue;
+                }
+                f(__umul64hi(xs[c], r.s));
+            }
+        }
+    }
+}
+
+template <typename KeyT>
+RS_DEV void cmpswap(KeyT& a, KeyT& b) {
+    const KeyT lo = a < b ? a : b, hi = a < b ? b : a;
+    a = lo;
+    b = hi;
+}
+
+// Batcher's odd-even merge sort of 8 keys (19 comparators).
+template <typename KeyT>
+RS_DEV void sort8(KeyT (&x)[8]) {
+    cmpswap(x[0], x[1]); cmpswap(x[2], x[3]); cmpswap(x[4], x[5]); cmpswap(x[6], x[7]);
+    cmpswap(x[0], x[2]); cmpswap(x[1], x[3]); cmpswap(x[4], x[6]); cmpswap(x[5], x[7]);
+    cmpswap(x[1], x[2]); cmpswap(x[5], x[6]);
+    cmpswap(x[0], x[4]); cmpswap(x[1], x[5]); cmpswap(x[2], x[6]); cmpswap(x[3], x[7]);
+    cmpswap(x[2], x[4]); cmpswap(x[3], x[5]);
+    cmpswap(x[1], x[2]); cmpswap(x[3], x[4]); cmpswap(x[5], x[6]);
+}
+
+// Bucket path.  Returns true on success (leaf written), false if the leaf
+// must take the probing path (whatever was written is overwritten later).
+template <typename KeyT, int NT, int BAR, bool WR>
+RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32>& sm, const LeafRec& r, Key2 key, uint32_t k,
+                        uint64_t* __restrict__ dst, uint32_t tid) {
+    constexpr uint32_t W = kBucketWays;
+    const uint32_t tag = WR ? TAG_LEAF_WR : TAG_LEAF_H;
+    const uint32_t nb = max(32u, ((2 * k + W - 1) / W + 31) & ~31u);
+    for (uint32_t i = tid; i <= nb; i += NT) sm.cnt[i] = 0;
+    if (tid == 0) {
+        sm.nspill = 0;
+        sm.flags = 0;
+        sm.nover = 0;
+        sm.mult = slot_mult<KeyT>(r.s, nb);
+        sm.thr = lemire_threshold(r.s);
+    }
+    group_sync<BAR, NT>();
+    const uint64_t mult = sm.mult, thr = sm.thr;
+    bool void_seen = false;
+    for_candidates<NT>(r, thr, key, tag, 0, k, tid, &void_seen, [&](uint64_t v) {
+        const uint32_t b = hash_slot((KeyT)v, mult);
+        const uint32_t e = atomicAdd(&sm.cnt[b], 1u);
+        if (e < W) {
+            sm.tab[e * nb + b] = (KeyT)v;   // entry e of bucket b: transposed for conflict-free reads
+        } else {
+            const uint32_t o = atomicAdd(&sm.nspill, 1u);
+            if (o < kSpillCap) sm.spill[o] = (KeyT)v;
+            else atomicOr(&sm.flags, 2u);
+        }
+    });
+    if (void_seen) atomicOr(&sm.flags, 1u);
+    group_sync<BAR, NT>();
+    const uint32_t flags = sm.flags;
+    const uint32_t nspill = min(sm.nspill, kSpillCap);
+    group_sync<BAR, NT>();   // everyone has read flags before the scan reuses scan_tmp
+    if (flags) return false;
+    // Warp 0 sorts the side list (by value, hence by bucket) while the block
+    // scans the counts; the scan's barriers publish it.
+    if (tid < 32) {
+        for (uint32_t i = tid; i < nspill; i += 32) {
+            const KeyT y = sm.spill[i];
+            uint32_t rank = 0;
+            for (uint32_t j = 0; j < nspill; ++j) {
+                const KeyT z = sm.spill[j];
+                rank += (z < y) || (z == y && j < i);
+            }
+            sm.spill_sorted[rank] = y;
+        }
+    }
+    block_scan_counts<NT>(sm.cnt, nb, sm.scan_tmp);   // cnt[b] = offset of bucket b, cnt[nb] = k
+    // Each warp takes 32 consecutive buckets at a time, one per lane: sort,
+    // check for repeats, stage in the warp's buffer, then copy the run of
+    // output positions they cover with coalesced stores.
+    const uint32_t lane = tid & 31, warp = tid >> 5;
+    KeyT* ws = sm.wstage[warp];
+    const uint64_t base = r.lo + 1;
+    bool dup = false;
+    for (uint32_t b0 = warp * 32; b0 < nb; b0 += NT) {
+        const uint32_t b = b0 + lane;   // nb is a multiple of 32
+        const uint32_t q0 = sm.cnt[b0], q1 = sm.cnt[b0 + 32];
+        const bool direct = q1 - q0 > kWarpStage;   // too many spilled keys: write in place
+        const uint32_t p = sm.cnt[b], c = sm.cnt[b + 1] - p;
+        auto put = [&](uint32_t pos, KeyT v) {
+            if (direct) dst[pos] = base + v;
+            else ws[pos - q0] = v;
+        };
+        if (c > W) {
+            // overfull: the fix-up pass places this bucket with a whole warp
+            sm.over[atomicAdd(&sm.nover, 1u)] = b;
+        } else if (c > 0) {
+            KeyT x[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) x[t] = (uint32_t)t < c ? sm.tab[t * nb + b] : HashEmpty<KeyT>::v;
+            sort8(x);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                if ((uint32_t)t < c) {
+                    put(p + t, x[t]);
+                    if (t > 0 && x[t] == x[t - 1]) dup = true;
+                }
+            }
+        }
+        __syncwarp();
+        if (!direct) {
+            for (uint32_t o = lane; o < q1 - q0; o += 32) dst[q0 + o] = base + ws[o];
+        }
+        __syncwarp();
+    }
+    // The copy-outs above wrote placeholders over the ranges of overfull
+    // buckets; after this barrier the fix-up writes win.
+    group_sync<BAR, NT>();
+    const uint32_t nover = sm.nover;   // at most one per spilled key, so <= kSpillCap
+    bool fail = false;
+    for (uint32_t o = warp; o < nover; o += NT / 32) {
+        const uint32_t b = sm.over[o];
+        const uint32_t p = sm.cnt[b], c = sm.cnt[b + 1] - p;
+        // the spilled keys of bucket b are a run of the sorted side list
+        uint32_t lo = 0, hi = nspill;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (hash_slot(sm.spill_sorted[mid], mult) < b) lo = mid + 1; else hi = mid;
+        }
+        if (c > 32) {   // more keys than lanes: leave the leaf to the probing path
+            fail = true;
+            continue;
+        }
+        const bool has = lane < c;
+        KeyT y = HashEmpty<KeyT>::v;
+        if (has) y = lane < W ? sm.tab[lane * nb + b] : sm.spill_sorted[lo + lane - W];
+        uint32_t rank = 0;
+        for (uint32_t j = 0; j < c; ++j) {
+            const KeyT z = __shfl_sync(0xFFFFFFFFu, y, j);
+            rank += (z < y) || (z == y && j < lane);
+            if (has && z == y && j != lane) dup = true;
+        }
+        if (has) dst[p + rank] = base + y;
+    }
+    if (WR) dup = false;
+    const bool any_fail = group_sync_or<BAR, NT>(dup || fail);
+    return !any_fail;   // on a repeat the probing path rewrites the whole leaf
+}
+
+// Rounds of distinct insertion shared by the bitmap and probing paths:
+// insert(v) returns 1 if v was new.  Returns false if the candidate stream
+// ran out (status set).
+template <int NT, int BAR, typename Insert, typename Abort>
+RS_DEV bool distinct_rounds(uint32_t* newcount, const LeafRec& r, uint64_t thr, Key2 key, uint32_t tag, uint32_t k,
+                            int* status, uint32_t tid, Insert&& insert, Abort&& aborted) {
+    uint32_t d = 0, round = 0;
+    uint64_t J = 0;
+    const uint64_t jlimit = r.s > (1ull << 32) ? (1ull << 33) : (1ull << 34);
+    while (d < k) {
+        const uint32_t m = k - d;
+        if (J + m > jlimit) {
+            if (tid == 0) set_status(status, RS_EITER);
+            group_sync<BAR, NT>();
+            return false;
+        }
+        uint32_t added = 0;
+        bool vs = false;
+        for_candidates<NT>(r, thr, key, tag, J, m, tid, &vs, [&](uint64_t v) { added += insert(v); });
+        if (added) atomicAdd(&newcount[round % 3], added);
+        // Counter (round+1) % 3 was last read before the previous round's
+        // barrier, which this thread has passed, and is next written after
+        // this round's barrier: clearing it here races with nothing.
+        if (tid == 0) newcount[(round + 1) % 3] = 0;
+        group_sync<BAR, NT>();
+        d += newcount[round % 3];
+        J += m;
+        ++round;
+        if (aborted()) return true;
+    }
+    return true;
+}
+
+// Count path for dense leaves with replacement (s < kHashSlots): the first
+// n' valid candidates are tallied per value; an exclusive scan of the tallies
+// gives each value's run of output positions.
+template <typename KeyT, int NT, int BAR>
+RS_DEV void count_leaf(HashShared<KeyT, NT / 32>& sm, const LeafRec& r, Key2 key, uint32_t k,
+                       uint64_t* __restrict__ dst, int* status, uint32_t tid) {
+    uint32_t* h = reinterpret_cast<uint32_t*>(sm.tab);
+    const uint32_t s = (uint32_t)r.s;
+    for (uint32_t i = tid; i <= s; i += NT) h[i] = 0;
+    if (tid < 3) sm.newcount[tid] = 0;
+    if (tid == 0) sm.thr = lemire_threshold(r.s);
+    group_sync<BAR, NT>();
+    const bool ok = distinct_rounds<NT, BAR>(
+        sm.newcount, r, sm.thr, key, TAG_LEAF_WR, k, status, tid,
+        [&](uint64_t v) -> uint32_t {
+            atomicAdd(&h[v], 1u);
+            return 1u;
+        },
+        [] { return false; });
+    if (!ok) return;
+    block_scan_counts<NT>(h, s, sm.scan_tmp);   // h[v] = first position of value v, h[s] = k
+    for (uint32_t o = tid; o < k; o += NT) {
+        uint32_t lo = 0, hi = s;   // the value whose run holds o: last v with h[v] <= o
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (h[mid] <= o) lo = mid; else hi = mid;
+        }
+        dst[o] = r.lo + 1 + lo;
+    }
+    group_sync<BAR, NT>();
+}
+
+// Bitmap path for leaves without replacement with s <= kBitmapBits.
+template <typename KeyT, int NT, int BAR>
+RS_DEV void bitmap_leaf(HashShared<KeyT, NT / 32>& sm, const LeafRec& r, Key2 key, uint32_t k, bool comp,
+                        uint64_t* __restrict__ dst, int* status, uint32_t tid) {
+    constexpr int NW = NT / 32;
+    const uint32_t lane = tid & 31, warp = tid >> 5;
+    uint32_t* bm = reinterpret_cast<uint32_t*>(sm.tab);
+    const uint32_t words = (uint32_t)((r.s + 31) >> 5);
+    for (uint32_t i = tid; i < words; i += NT) bm[i] = 0;
+    if (tid < 3) sm.newcount[tid] = 0;
+    if (tid == 0) sm.thr = lemire_threshold(r.s);
+    group_sync<BAR, NT>();
+    const bool ok = distinct_rounds<NT, BAR>(
+        sm.newcount, r, sm.thr, key, TAG_LEAF_H, k, status, tid,
+        [&](uint64_t v) -> uint32_t {
+            const uint32_t bit = 1u << (v & 31);
+            return (atomicOr(&bm[v >> 5], bit) & bit) ? 0u : 1u;
+        },
+        [] { return false; });
+    if (!ok) return;
+    // each warp takes a contiguous run of words; a lane takes one bit of the
+    // current word so that the writes are coalesced
+    const uint32_t per = (words + NW - 1) / NW;
+    const uint32_t w0 = min(warp * per, words), w1 = min(w0 + per, words);
+    auto bits_of = [&](uint32_t w) {
+        uint32_t bits = bm[w];
+        if (comp) {
+            bits = ~bits;
+            if ((uint64_t)w * 32 + 32 > r.s) bits &= (1u << (uint32_t)(r.s & 31)) - 1u;   // beyond the leaf
+        }
+        return bits;
+    };
+    uint32_t cnt = 0;
+    for (uint32_t w = w0 + lane; w < w1; w += 32) cnt += __popc(bits_of(w));
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+    if (lane == 0) sm.warp_cnt[warp] = cnt;
+    group_sync<BAR, NT>();
+    uint32_t base = 0;
+    for (uint32_t i = 0; i < warp; ++i) base += sm.warp_cnt[i];
+    for (uint32_t w = w0; w < w1; ++w) {
+        const uint32_t bits = bits_of(w);
+        if ((bits >> lane) & 1u) dst[base + __popc(bits & ((1u << lane) - 1u))] = r.lo + 1 + (uint64_t)w * 32 + lane;
+        base += __popc(bits);
+    }
+    group_sync<BAR, NT>();
+}
+
+// Probing path.  Returns false if a probe ran past the slack (general path).
+template <typename KeyT, int NT, int BAR, bool WR>
+RS_DEV bool probe_leaf(HashShared<KeyT, NT / 32>& sm, const LeafRec& r, Key2 key, uint32_t k,
+                       uint64_t* __restrict__ dst, int* status, uint32_t tid) {
+    constexpr int NW = NT / 32;
+    constexpr KeyT E = HashEmpty<KeyT>::v;
+    const uint32_t tag = WR ? TAG_LEAF_WR : TAG_LEAF_H;
+    const uint32_t lane = tid & 31, warp = tid >> 5;
+    const uint32_t T = ((2 * k + 127) / 128) * 128;
+    {
+        uint32_t* w32 = reinterpret_cast<uint32_t*>(sm.tab);
+        const uint32_t n32 = (T + kHashSlack) * (uint32_t)(sizeof(KeyT) / 4);
+        uint4* w128 = reinterpret_cast<uint4*>(w32);
+        for (uint32_t i = tid; i < n32 / 4; i += NT) w128[i] = make_uint4(~0u, ~0u, ~0u, ~0u);
+        if (tid == 0) {
+            sm.newcount[0] = 0;
+            sm.newcount[1] = 0;
+            sm.newcount[2] = 0;
+            sm.topcount = 0;
+            sm.overflow = 0;
+            sm.mult = slot_mult<KeyT>(r.s, T);
+            sm.thr = lemire_threshold(r.s);
+        }
+    }
+    group_sync<BAR, NT>();
+    const uint64_t mult = sm.mult;
+    const bool ok = distinct_rounds<NT, BAR>(
+        sm.newcount, r, sm.thr, key, tag, k, status, tid,
+        [&](uint64_t v64) -> uint32_t {
+            const KeyT v = (KeyT)v64;
+            if (sizeof(KeyT) == 4 && v == E) {
+                const uint32_t old = atomicAdd(&sm.topcount, 1u);
+                return WR ? 1u : (old == 0);
+            }
+            uint32_t i = hash_slot(v, mult);
+            const uint32_t end = T + kHashSlack;
+            while (i < end) {
+                const KeyT old = cas_key(&sm.tab[i], E, v);
+                if (old == E) return 1u;
+                if (!WR && old == v) return 0u;
+                ++i;
+            }
+            sm.overflow = 1;
+            return 0u;
+        },
+        [&] { return sm.overflow != 0; });
+    if (!ok) return true;
+    if (sm.overflow != 0) {
+        group_sync<BAR, NT>();
+        return false;
+    }
+    // read-out: count occupied slots per warp chunk, then rank inside clusters
+    const uint32_t chunk = ((T / NW) + 31) & ~31u;
+    const uint32_t c0 = min(warp * chunk, T), c1 = min(c0 + chunk, T);
+    const uint32_t c1x = (warp == NW - 1) ? T + kHashSlack : c1;   // the last warp owns the slack
+    uint32_t cnt = 0;
+    for (uint32_t i = c0 + lane; i < c1x; i += 32) cnt += sm.tab[i] != E;
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+    if (lane == 0) sm.warp_cnt[warp] = cnt;
+    group_sync<BAR, NT>();
+    uint32_t base = 0;
+    for (uint32_t i = 0; i < warp; ++i) base += sm.warp_cnt[i];
+    for (uint32_t i0 = c0; i0 < c1x; i0 += 32) {
+        const uint32_t i = i0 + lane;
+        const KeyT v = i < c1x ? sm.tab[i] : E;
+        const bool occ = v != E;
+        const uint32_t mask = __ballot_sync(0xFFFFFFFFu, occ);
+        if (occ) {
+            const uint32_t before = base + __popc(mask & ((1u << lane) - 1u));
+            const bool left = lane > 0 ? ((mask >> (lane - 1)) & 1u) : (i > 0 && sm.tab[i - 1] != E);
+            const bool right = lane < 31 ? ((mask >> (lane + 1)) & 1u) : (i + 1 < T + kHashSlack && sm.tab[i + 1] != E);
+            uint32_t pos = before;
+            if (left || right) {
+                uint32_t cs = i, ce = i + 1;
+                while (cs > 0 && sm.tab[cs - 1] != E) --cs;
+                while (ce < T + kHashSlack && sm.tab[ce] != E) ++ce;
+                uint32_t rank = 0;
+                for (uint32_t t = cs; t < ce; ++t) {
+                    const KeyT y = sm.tab[t];
+                    rank += (y < v) || (WR && y == v && t < i);
+                }
+                pos = before - (i - cs) + rank;
+            }
+            dst[pos] = r.lo + 1 + (uint64_t)v;
+        }
+        base += __popc(mask);
+    }
+    if (sizeof(KeyT) == 4) {
+        const uint32_t top = WR ? sm.topcount : (sm.topcount ? 1u : 0u);   // copies of 2^32-1 go last
+        for (uint32_t t = tid; t < top; t += NT) dst[k - top + t] = r.lo + 1 + 0xFFFFFFFFull;
+    }
+    group_sync<BAR, NT>();
+    return true;
+}
+
+// Selects the leaf's values and writes them sorted to out[off ..].  Returns
+// false if the leaf must go to the general (global-memory) path, having
+// written nothing of use.  All NT threads of the group call it; tid is the
+// thread's index in the group.
+template <typename KeyT, int NT, int BAR, bool WR>
+RS_DEV bool hash_leaf(HashShared<KeyT, NT / 32>& sm, const LeafRec& r, Key2 key, uint64_t* __restrict__ out,
+                      int* status, uint32_t tid, uint32_t cap) {
+    const bool comp = !WR && (r.np > r.s - r.np);
+    const uint64_t k64 = comp ? r.s - r.np : r.np;
+    if (k64 > cap) return false;
+    const uint32_t k = (uint32_t)k64;
+    uint64_t* dst = out + r.off;
+    const bool use_bitmap = !WR && r.s <= kBitmapBits && (comp || r.s <= 64ull * k);
+    if (comp && !use_bitmap) return false;
+    if (k == 0 && !comp) return true;
+    if (WR && r.s < kHashSlots && r.s <= 64ull * k) {
+        count_leaf<KeyT, NT, BAR>(sm, r, key, k, dst, status, tid);
+        return true;
+    }
+    if (use_bitmap) {
+        bitmap_leaf<KeyT, NT, BAR>(sm, r, key, k, comp, dst, status, tid);
+        return true;
+    }
+    if (bucket_leaf<KeyT, NT, BAR, WR>(sm, r, key, k, dst, tid)) return true;
+    return probe_leaf<KeyT, NT, BAR, WR>(sm, r, key, k, dst, status, tid);
+}
+
+}  // namespace rs

@@ -8,8 +8,11 @@
 
 namespace rs {
 
-// Largest leaf selection handled in shared memory by the leaf kernels.
+// Largest leaf selection of the shared-memory counting-sort machinery
+// (leaf B's repair step).
 constexpr uint32_t kLeafCap = 8192;
+// Largest leaf selection of the shared-memory table of leaf H / leaf WR.
+constexpr uint32_t kLeafFastCap = 4864;
 // Largest selection the general (global-memory) leaf path accepts.
 constexpr uint64_t kBigLeafMax = 1ull << 22;
 // Deepest split tree the library builds (2^27 node records of 32 bytes).

@@ -8,6 +8,7 @@
 //
 // Leaf WR (Sec. 4.6) is the same machinery without the distinctness rule:
 // the first n' valid candidates of its LEAF_WR stream, sorted as a multiset.
+#include "rs_hash_leaf.cuh"
 #include "rs_leaf.cuh"
 
 namespace rs {
@@ -24,38 +25,22 @@ struct LeafJob {
     uint32_t cap;            // largest selection handled here
 };
 
+constexpr int kHashThreads = 256;
+
+// One block per leaf at a time, persistent over the leaves; leaves the
+// shared-memory table cannot take go to the general path's list.
 template <typename KeyT, bool WR>
-__global__ void __launch_bounds__(kLeafThreads) leaf_kernel(LeafJob job) {
+__global__ void __launch_bounds__(kHashThreads) leaf_kernel(LeafJob job) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    LeafShared<KeyT>& sm = *reinterpret_cast<LeafShared<KeyT>*>(smem_raw);
+    auto& sm = *reinterpret_cast<HashShared<KeyT, kHashThreads / 32>*>(smem_raw);
     const Key2 key = make_key(job.seed);
-    const uint32_t tag = WR ? TAG_LEAF_WR : TAG_LEAF_H;
     for (uint64_t leaf = blockIdx.x; leaf < job.nleaves; leaf += gridDim.x) {
         const NodeRec r = job.leaves[leaf];
         if (r.c == 0) continue;
-        const bool comp = !WR && (r.c > r.S - r.c);
-        const uint64_t k64 = comp ? r.S - r.c : r.c;
-        if (k64 > job.cap) {
+        const LeafRec lr{r.lo, r.S, r.c, r.off, job.first_id + leaf};
+        if (!hash_leaf<KeyT, kHashThreads, 0, WR>(sm, lr, key, job.out, job.status, threadIdx.x, job.cap)) {
             if (threadIdx.x == 0) job.ovf_list[atomicAdd(job.ovf_count, 1u)] = (uint32_t)leaf;
-            continue;
         }
-        const uint32_t k = (uint32_t)k64;
-        const uint64_t id = job.first_id + leaf;
-        bool ok = true;
-        if (k > 0) {
-            if (sizeof(KeyT) == 8 && r.S > (1ull << 32)) {
-                Draw<2> dr{Bounded64{r.S, (0ull - r.S) % r.S}};
-                ok = select_leaf<KeyT, 2, !WR>(sm, dr, key, tag, id, r.S, k, job.status);
-            } else {
-                Draw<4> dr{Bounded32{r.S, (uint32_t)(((1ull << 32) - r.S) % r.S)}};
-                ok = select_leaf<KeyT, 4, !WR>(sm, dr, key, tag, id, r.S, k, job.status);
-            }
-        }
-        if (ok) {
-            if (comp) write_complement<KeyT>(sm.keys, k, r.S, r.lo, job.out + r.off);
-            else write_sorted<KeyT>(sm.keys, k, r.lo, job.out + r.off);
-        }
-        __syncthreads();
     }
 }
 
@@ -271,22 +256,22 @@ __global__ void __launch_bounds__(kBigThreads) big_leaf_kernel(LeafJob job, BigS
 
 template <typename KeyT, bool WR>
 static cudaError_t launch_fast(const LeafJob& job, int sms, cudaStream_t st) {
-    const size_t smem = sizeof(LeafShared<KeyT>);
+    const size_t smem = sizeof(HashShared<KeyT, kHashThreads / 32>);
     auto kern = leaf_kernel<KeyT, WR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLeafThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kHashThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     const uint64_t grid = std::min<uint64_t>(job.nleaves, (uint64_t)sms * per_sm);
-    kern<<<(unsigned)grid, kLeafThreads, smem, st>>>(job);
+    kern<<<(unsigned)grid, kHashThreads, smem, st>>>(job);
     return cudaGetLastError();
 }
 
 cudaError_t launch_leaves(const LeafLaunch& L, cudaStream_t st) {
     LeafJob job{L.leaves, L.nleaves, L.first_id, L.seed, L.out, L.status, L.ovf_list, L.ovf_count,
-                L.cap ? std::min<uint32_t>(L.cap, kLeafCap) : kLeafCap};
+                L.cap ? std::min<uint32_t>(L.cap, kHashCap) : kHashCap};
     cudaError_t e = cudaMemsetAsync(L.ovf_count, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
     const bool narrow = L.smax <= (1ull << 32);

@@ -21,11 +21,12 @@ RS_DEV uint4 philox_block(uint32_t t, uint32_t tag, uint64_t id, Key2 key) {
     uint32_t k0 = key.k0, k1 = key.k1;
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * x0, hi0 = __umulhi(0xD2511F53u, x0);
-        const uint32_t lo1 = 0xCD9E8D57u * x2, hi1 = __umulhi(0xCD9E8D57u, x2);
-        const uint32_t y0 = hi1 ^ x1 ^ k0;
-        const uint32_t y2 = hi0 ^ x3 ^ k1;
-        x0 = y0; x1 = lo1; x2 = y2; x3 = lo0;
+        // one 32x32 -> 64 product per multiplier gives both halves
+        const uint64_t p0 = (uint64_t)0xD2511F53u * x0;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * x2;
+        const uint32_t y0 = (uint32_t)(p1 >> 32) ^ x1 ^ k0;
+        const uint32_t y2 = (uint32_t)(p0 >> 32) ^ x3 ^ k1;
+        x0 = y0; x1 = (uint32_t)p1; x2 = y2; x3 = (uint32_t)p0;
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
     }
