@@ -139,6 +139,24 @@ int rs_phase_totals(rs_ctx* ctx, double* tree_ms, double* leaf_ms, uint64_t* cal
 /* Number of kernels this context has launched since it was created. */
 int rs_launch_count(rs_ctx* ctx, uint64_t* count);
 
+/* rs_sample for callers that cannot allocate device memory while they run
+ * (an allocator that owns the whole device, a host application that forbids
+ * cudaMalloc after start-up, a loop that cannot take the device-wide stall of
+ * cudaMalloc/cudaFree).  The paper has no counterpart: this is an interface
+ * choice of this library.  It needs no context and allocates nothing: all
+ * scratch memory is one static device array of about 6.6 MB that every GPU
+ * using the library holds until the process exits.  Output is identical to
+ * rs_sample with the same arguments.
+ *  - Limits: split-tree depth <= 16 (n <= n0 * 2^16), else RS_ECAPACITY
+ *    before any work; a leaf selecting more than 2^16 values ends with the
+ *    device status RS_ECAPACITY.
+ *  - Runs on the current CUDA device and `stream`, waits for `stream`, and
+ *    returns the call's device status (RS_OK, RS_EITER, RS_ECAPACITY).
+ *  - The first call on a device looks up the array's device address and
+ *    builds its ln x! table: make that first call before any stream capture.
+ *  - Every call shares the array: calls that overlap on the GPU race. */
+int rs_sample_static(uint64_t n, uint64_t N, uint64_t seed, uint32_t n0, uint64_t* out_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -53,6 +53,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "rs_set_profiling": (i32, [vp, i32]),
         "rs_phase_totals": (i32, [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(u64)]),
         "rs_launch_count": (i32, [vp, ctypes.POINTER(u64)]),
+        "rs_sample_static": (i32, [u64, u64, u64, u32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -182,3 +183,9 @@ def rs_launch_count(ctx: Context) -> int:
     c = ctypes.c_uint64(0)
     _check(load().rs_launch_count(ctx.handle, ctypes.byref(c)), "rs_launch_count")
     return c.value
+
+
+def rs_sample_static(n, N, seed, n0, out, stream=None) -> int:
+    """rs_sample without device allocation (static scratch); returns the
+    call's device status after waiting for the stream."""
+    return load().rs_sample_static(n, N, seed, n0, _ptr(out), _stream(stream))
