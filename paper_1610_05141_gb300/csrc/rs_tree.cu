@@ -9,8 +9,8 @@
 // no samples draws nothing.  Depth D is fixed in advance (as in Algorithm P's
 // tree over PEs and the p' >> p jobs of Sec. 4.5), so the tree, and with it
 // the sample, does not depend on how the work is scheduled.
-#include "rs_deviates.cuh"
 #include "rs_internal.h"
+#include "rs_tree_warp.cuh"
 
 namespace rs {
 
@@ -30,36 +30,42 @@ __global__ void tree_root_kernel(NodeRec* rec, uint64_t n, uint64_t N) {
     if (threadIdx.x == 0 && blockIdx.x == 0) rec[1] = NodeRec{0, N, n, 0};
 }
 
+constexpr int kTreeWarps = 4;            // warps per block of the level kernel
+constexpr uint32_t kTreeBatch = 128;     // nodes per warp (lanes refill from it)
+
+// One level of the tree: each warp takes a batch of consecutive nodes.
 template <bool WR>
-__global__ void tree_level_kernel(NodeRec* __restrict__ rec, int level, uint64_t seed,
-                                  const double* __restrict__ tab, int* status) {
-    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (1ull << level)) return;
-    const uint64_t v = (1ull << level) + i;
-    const NodeRec r = rec[v];
-    const uint64_t K = r.S / 2;
-    uint64_t L = 0;
-    if (r.c > 0) {
-        const Key2 key = make_key(seed);
-        const int rc = WR ? binomial(key, v, r.c, K, r.S, tab, L) : hypergeometric(key, v, r.c, K, r.S, tab, L);
-        if (rc != RS_OK) {
-            set_status(status, rc);
-            L = 0;
-        }
-    }
-    rec[2 * v] = NodeRec{r.lo, K, L, r.off};
-    rec[2 * v + 1] = NodeRec{r.lo + K, r.S - K, r.c - L, r.off + L};
+__global__ void __launch_bounds__(kTreeWarps * 32) tree_level_kernel(NodeRec* __restrict__ rec, int level,
+                                                                    uint32_t batch, uint64_t seed,
+                                                                    const double* __restrict__ tab, int* status) {
+    extern __shared__ double tree_logs[];
+    const uint32_t warp = threadIdx.x >> 5;
+    const uint64_t nodes = 1ull << level;
+    const uint64_t start = ((uint64_t)blockIdx.x * kTreeWarps + warp) * batch;
+    if (start >= nodes) return;
+    const uint64_t left = nodes - start;
+    const uint32_t count = left < batch ? (uint32_t)left : batch;
+    tree_batch_warp<WR>(rec, nodes + start, count, make_key(seed), tab, status,
+                        tree_logs + warp * 32 * kLogSlots);
 }
 
 cudaError_t launch_tree(NodeRec* rec, uint64_t n, uint64_t N, uint64_t seed, int D, bool with_replacement,
                         const double* tab, int* status, cudaStream_t st) {
     tree_root_kernel<<<1, 32, 0, st>>>(rec, n, N);
+    const size_t smem = (size_t)kTreeWarps * 32 * kLogSlots * sizeof(double);
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     for (int level = 0; level < D; ++level) {
         const uint64_t nodes = 1ull << level;
-        const unsigned threads = nodes < 128 ? 32 : 128;
-        const unsigned blocks = (unsigned)((nodes + threads - 1) / threads);
-        if (with_replacement) tree_level_kernel<true><<<blocks, threads, 0, st>>>(rec, level, seed, tab, status);
-        else tree_level_kernel<false><<<blocks, threads, 0, st>>>(rec, level, seed, tab, status);
+        // one node per lane until the level has enough warps for every SM;
+        // beyond that, batches grow (up to kTreeBatch) and lanes refill
+        uint64_t per = nodes / ((uint64_t)sms * 2 * kTreeWarps);
+        per = std::max<uint64_t>(32, std::min<uint64_t>(kTreeBatch, per & ~31ull));
+        const uint32_t batch = (uint32_t)std::min<uint64_t>(per, nodes);
+        const uint64_t warps = (nodes + batch - 1) / batch;
+        const unsigned blocks = (unsigned)((warps + kTreeWarps - 1) / kTreeWarps);
+        if (with_replacement) tree_level_kernel<true><<<blocks, kTreeWarps * 32, smem, st>>>(rec, level, batch, seed, tab, status);
+        else tree_level_kernel<false><<<blocks, kTreeWarps * 32, smem, st>>>(rec, level, batch, seed, tab, status);
     }
     return cudaGetLastError();
 }

@@ -1,0 +1,292 @@
+// rs_tree_warp.cuh -- split-tree nodes processed a warp at a time.
+//
+// The split deviates (Sec. 3: hypergeometric, Sec. 4.6: binomial) are
+// rejection loops whose trial count varies per node, and their log-factorial
+// differences take different branches per node.  FP64 instructions cost the
+// same however many lanes of a warp are active, so a warp here keeps all
+// lanes busy:
+//  - lane refill: a warp owns a batch of nodes; a lane whose node is done
+//    takes the next one, so trial counts no longer idle lanes;
+//  - cooperative logarithms: each ratio-of-uniforms trial first records the
+//    arguments of every logarithm it needs (ln U, ln Y, ln(1 + D/Y), the
+//    terms of short sums, ...), the whole warp evaluates them together, and
+//    each lane then assembles its acceptance test from the results in
+//    exactly the operations and order of the scalar definition
+//    (rs_deviates.cuh), so the results are the same bits.
+#pragma once
+#include "rs_deviates.cuh"
+
+namespace rs {
+
+constexpr int kLogSlots = 40;   // logarithm arguments per lane per trial (at most 4 * 8 + 1)
+
+// Log-factorial difference lfdiff(x, y), x >= y, split in two halves: args()
+// lists the logarithm arguments it needs, eval() computes the value from
+// their logarithms, consumed in the same order.
+struct LfdArgs {
+    double* a;
+    int n;
+    RS_DEV void push(double v) { a[n++] = v; }
+};
+struct LfdLogs {
+    const double* l;
+    int n;
+    RS_DEV double next() { return l[n++]; }
+};
+
+RS_DEV void lfd_args(uint64_t x, uint64_t y, LfdArgs& A) {
+    const uint64_t d = x - y;
+    if (d == 0 || x < 256) return;
+    if (d <= 8) {
+        for (uint64_t i = y + 1; i <= x; ++i) A.push((double)i);
+        return;
+    }
+    const double X = (double)x;
+    if (y < 256) {
+        A.push(X);
+        return;
+    }
+    const double Y = (double)y, D = (double)d;
+    const double u = 1.0 + D / Y;
+    if (u != 1.0) A.push(u);
+    A.push(Y);
+}
+
+RS_DEV double lfd_eval(uint64_t x, uint64_t y, const double* __restrict__ tab, LfdLogs& L) {
+    const uint64_t d = x - y;
+    if (d == 0) return 0.0;
+    if (x < 256) return tab[x] - tab[y];
+    if (d <= 8) {
+        double acc = 0.0;
+        for (uint64_t i = y + 1; i <= x; ++i) acc = acc + L.next();
+        return acc;
+    }
+    const double X = (double)x;
+    if (y < 256) return ((X + 0.5) * L.next() - X + RS_HL2PI + stirling_tail(X)) - tab[y];
+    const double Y = (double)y, D = (double)d;
+    const double z = D / Y;
+    const double u = 1.0 + z;
+    const double lp = (u == 1.0) ? z : L.next() * (z / (u - 1.0));
+    return (X + 0.5) * lp + D * L.next() - D + (stirling_tail(X) - stirling_tail(Y));
+}
+
+RS_DEV void sd_args(uint64_t x, uint64_t y, LfdArgs& A) {
+    if (x >= y) lfd_args(x, y, A);
+    else lfd_args(y, x, A);
+}
+RS_DEV double sd_eval(uint64_t x, uint64_t y, const double* __restrict__ tab, LfdLogs& L) {
+    return x >= y ? lfd_eval(x, y, tab, L) : -lfd_eval(y, x, tab, L);
+}
+
+// Parameters of one node's ratio-of-uniforms loop (rs_deviates.cuh).
+struct RouNode {
+    uint64_t v;          // node id
+    uint64_t lo, S, c, off, K;
+    uint64_t a, b, M;    // hypergeometric: reduced draws/successes; binomial: a = c
+    uint64_t n_in, Kp;   // un-reduction of the hypergeometric result
+    double h, alpha, top, logr;
+    uint32_t trial;
+    bool flipN, flipK;
+};
+
+RS_DEV void write_children(NodeRec* __restrict__ rec, uint64_t v, const NodeRec& r, uint64_t K, uint64_t L) {
+    rec[2 * v] = NodeRec{r.lo, K, L, r.off};
+    rec[2 * v + 1] = NodeRec{r.lo + K, r.S - K, r.c - L, r.off + L};
+}
+
+// Prepares node v.  Returns true if the node needs ratio-of-uniforms trials
+// (state in *q); otherwise the node is finished here (children written):
+// no samples, a fast path, or inversion.
+template <bool WR>
+RS_DEV bool node_setup(NodeRec* __restrict__ rec, uint64_t v, Key2 key, const double* __restrict__ tab, int* status,
+                       RouNode* q) {
+    const NodeRec r = rec[v];
+    const uint64_t K = r.S / 2;
+    auto finish = [&](uint64_t L) {
+        write_children(rec, v, r, K, L);
+        return false;
+    };
+    if (r.c == 0) return finish(0);
+    if (WR) {
+        const uint64_t c = r.c;
+        if (K == 0) return finish(0);
+        const double p = (double)K / (double)r.S;
+        const double mu = (double)c * p;
+        if (mu < 16.0) {
+            uint64_t L = 0;
+            const int rc = binomial(key, v, c, K, r.S, tab, L);
+            if (rc != RS_OK) { set_status(status, rc); L = 0; }
+            return finish(L);
+        }
+        const double var = mu * (1.0 - p);
+        q->h = RS_HAT_D1 * sqrt(var + 0.5) + RS_HAT_D2;
+        q->alpha = mu + 0.5;
+        const double rr = p / (1.0 - p);
+        q->logr = (rr == 1.0) ? 0.0 : dlog(rr);
+        q->M = (uint64_t)(((unsigned __int128)(c + 1) * K) / r.S);
+        q->top = (double)c + 1.0;
+        q->a = c;
+    } else {
+        uint64_t n = r.c, Kh = K;
+        const uint64_t S = r.S;
+        if (Kh == 0) return finish(0);
+        if (Kh == S) return finish(n);
+        if (n == S) return finish(Kh);
+        q->n_in = n;
+        q->flipK = Kh > S - Kh;
+        if (q->flipK) Kh = S - Kh;
+        q->flipN = n > S - n;
+        if (q->flipN) n = S - n;
+        const uint64_t a = n < Kh ? n : Kh;
+        const uint64_t b = n < Kh ? Kh : n;
+        const double mu = ((double)a * (double)b) / (double)S;
+        if (mu < 16.0) {
+            uint64_t L = 0;
+            const int rc = hypergeometric(key, v, r.c, K, S, tab, L);
+            if (rc != RS_OK) { set_status(status, rc); L = 0; }
+            return finish(L);
+        }
+        const double var = mu * ((double)(S - a) / (double)S) * ((double)(S - b) / (double)(S - 1));
+        q->h = RS_HAT_D1 * sqrt(var + 0.5) + RS_HAT_D2;
+        q->alpha = mu + 0.5;
+        q->M = (uint64_t)(((unsigned __int128)(a + 1) * (b + 1)) / (S + 2));
+        q->top = (double)a + 1.0;
+        q->a = a;
+        q->b = b;
+        q->Kp = Kh;
+    }
+    q->v = v;
+    q->lo = r.lo;
+    q->S = r.S;
+    q->c = r.c;
+    q->off = r.off;
+    q->K = K;
+    q->trial = 0;
+    return true;
+}
+
+// Processes nodes v0 .. v0+count-1 (one level) with the calling warp.
+// `logs` is this warp's scratch of 32 * kLogSlots doubles in shared memory.
+template <bool WR>
+RS_DEV void tree_batch_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t count, Key2 key,
+                            const double* __restrict__ tab, int* status, double* logs) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    double* mine = logs + lane * kLogSlots;
+    RouNode q;
+    bool active = false;
+    uint32_t next = 0;   // batch cursor (warp-uniform)
+    for (;;) {
+        // refill free lanes, in order, until none is free or the batch is used up
+        for (;;) {
+            const uint32_t freem = __ballot_sync(0xFFFFFFFFu, !active);
+            if (freem == 0 || next >= count) break;
+            const uint32_t take = min((uint32_t)__popc(freem), count - next);
+            const uint32_t rank = __popc(freem & lt_mask);
+            if (!active && rank < take) active = node_setup<WR>(rec, v0 + next + rank, key, tab, status, &q);
+            next += take;
+        }
+        if (__ballot_sync(0xFFFFFFFFu, active) == 0) break;
+        // one trial per active lane: uniforms, candidate, logarithm arguments
+        double U = 1.0;
+        uint64_t k = 0;
+        bool inr = false;
+        int nargs = 0;
+        if (active) {
+            const uint4 blk = philox_block(q.trial, TAG_SPLIT, q.v, key);
+            U = u_open(((uint64_t)blk.y << 32) | blk.x);
+            const double V = v_closed(((uint64_t)blk.w << 32) | blk.z);
+            const double X = q.alpha + q.h * (V - 0.5) / U;
+            inr = !(X < 0.0 || X >= q.top);
+            if (inr) {
+                k = (uint64_t)X;
+                LfdArgs A{mine, 0};
+                A.push(U);
+                if (WR) {
+                    sd_args(q.M, k, A);
+                    sd_args(q.a - q.M, q.a - k, A);
+                } else {
+                    const uint64_t m = q.S - q.a - q.b;
+                    sd_args(q.M, k, A);
+                    sd_args(q.a - q.M, q.a - k, A);
+                    sd_args(q.b - q.M, q.b - k, A);
+                    sd_args(m + q.M, m + k, A);
+                }
+                nargs = A.n;
+            }
+        }
+        __syncwarp();
+        // the warp evaluates all logarithms together: item g of the
+        // concatenated per-lane lists goes to lane g mod 32; its owner is the
+        // first lane whose inclusive prefix exceeds g
+        uint32_t incl = (uint32_t)nargs;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= (uint32_t)o) incl += y;
+        }
+        const uint32_t excl = incl - (uint32_t)nargs;
+        const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        // four items per lane at a time so that their dependent chains overlap
+        for (uint32_t base = 0; base < total; base += 128) {
+            double* slot[4];
+            double x[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t g = base + 32 * j + lane;
+                uint32_t pos = 0;
+#pragma unroll
+                for (uint32_t step = 16; step >= 1; step >>= 1) {
+                    const uint32_t v = __shfl_sync(0xFFFFFFFFu, incl, pos + step - 1);
+                    if (v <= g) pos += step;
+                }
+                const uint32_t owner_excl = __shfl_sync(0xFFFFFFFFu, excl, pos);
+                slot[j] = (g < total) ? logs + pos * kLogSlots + (g - owner_excl) : nullptr;
+                x[j] = slot[j] ? *slot[j] : 1.0;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) x[j] = dlog(x[j]);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (slot[j]) *slot[j] = x[j];
+        }
+        __syncwarp();
+        if (active) {
+            bool done = false;
+            uint64_t L = 0;
+            if (inr) {
+                LfdLogs Lg{mine, 0};
+                const double lU = Lg.next();
+                double T;
+                if (WR) {
+                    T = sd_eval(q.M, k, tab, Lg) + sd_eval(q.a - q.M, q.a - k, tab, Lg) +
+                        (double)((int64_t)k - (int64_t)q.M) * q.logr;
+                } else {
+                    const uint64_t m = q.S - q.a - q.b;
+                    T = sd_eval(q.M, k, tab, Lg) + sd_eval(q.a - q.M, q.a - k, tab, Lg) +
+                        sd_eval(q.b - q.M, q.b - k, tab, Lg) + sd_eval(m + q.M, m + k, tab, Lg);
+                }
+                if (2.0 * lU <= T) {
+                    done = true;
+                    L = k;
+                    if (!WR) {
+                        if (q.flipN) L = q.Kp - L;
+                        if (q.flipK) L = q.n_in - L;
+                    }
+                }
+            }
+            if (!done && ++q.trial >= kRouMaxTrials) {
+                set_status(status, RS_EITER);
+                done = true;
+                L = 0;
+            }
+            if (done) {
+                write_children(rec, q.v, NodeRec{q.lo, q.S, q.c, q.off}, q.K, L);
+                active = false;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace rs
