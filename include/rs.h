@@ -116,6 +116,50 @@ int rs_bernoulli(rs_ctx* ctx, double p, uint64_t N, uint64_t seed, uint32_t n0,
                  uint64_t a, uint64_t b, uint64_t* out_dev, uint64_t cap,
                  uint64_t* count_out, void* stream);
 
+/* ---- Batches: many independent requests in one device run -------------
+ * Each request is its own sample (own tree, own seed), exactly the output of
+ * the corresponding single call (kind RS_KIND_H: rs_sample, RS_KIND_WR:
+ * rs_sample_with_replacement, RS_KIND_B: rs_sample_b): the result depends on
+ * the request alone (Sec. 4.5), and requests need no coordination (Sec.
+ * 3.2).  Request r writes its n values at out_pool[out_off .. out_off + n);
+ * the caller keeps the ranges disjoint. */
+typedef struct {
+    uint64_t n, N, seed, out_off;
+    uint32_t n0, kind;
+} rs_request;
+
+typedef struct rs_batchplan rs_batchplan;
+
+/* Plans a batch from host-resident requests: validates them (a request with
+ * bad arguments gets RS_EINVAL in its status word at every run and does no
+ * work), lays out the node records of all trees, the per-level work items and
+ * the leaf groups, and allocates the plan's device memory.  The context must
+ * outlive the plan.  Errors: RS_EINVAL, RS_ENOMEM, RS_ECUDA. */
+int rs_batch_plan(rs_ctx* ctx, const rs_request* reqs_host, uint32_t R, rs_batchplan** plan);
+
+/* Runs a plan on `stream` (asynchronous; device work only).  status_dev:
+ * R int32 words of device memory, set by the run (RS_OK, RS_EINVAL,
+ * RS_ECAPACITY, RS_EITER per request).  The first run issues plain launches;
+ * later runs replay a CUDA graph captured for (out_pool_dev, status_dev)
+ * (captured again if those pointers change). */
+int rs_batch_run(rs_batchplan* plan, uint64_t* out_pool_dev, int32_t* status_dev, void* stream);
+
+/* Picks, by timing whole runs, the leaf kernels' blocks per SM (an
+ * output-invariant knob: the schedule of leaves over blocks never changes a
+ * value).  Synchronizes `stream`. */
+int rs_batch_tune(rs_batchplan* plan, uint64_t* out_pool_dev, int32_t* status_dev, void* stream);
+
+/* Kernels one run launches. */
+int rs_batch_launch_count(rs_batchplan* plan, uint64_t* per_run);
+
+/* Waits for the device and frees the plan. */
+int rs_batch_destroy(rs_batchplan* plan);
+
+/* One-shot batch from device-resident requests: copies them to the host,
+ * plans, runs, waits for `stream` and frees the plan. */
+int rs_batch(rs_ctx* ctx, const rs_request* reqs_dev, uint32_t R, uint64_t* out_pool_dev,
+             int32_t* status_dev, void* stream);
+
 /* Waits for `stream`, then returns and clears the context's device status
  * word (RS_OK, or the first device-side error since the last rs_sync). */
 int rs_sync(rs_ctx* ctx, void* stream);

@@ -54,6 +54,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "rs_phase_totals": (i32, [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(u64)]),
         "rs_launch_count": (i32, [vp, ctypes.POINTER(u64)]),
         "rs_sample_static": (i32, [u64, u64, u64, u32, vp, vp]),
+        "rs_batch_plan": (i32, [vp, vp, u32, ctypes.POINTER(vp)]),
+        "rs_batch_run": (i32, [vp, vp, vp, vp]),
+        "rs_batch_tune": (i32, [vp, vp, vp, vp]),
+        "rs_batch_launch_count": (i32, [vp, ctypes.POINTER(u64)]),
+        "rs_batch_destroy": (i32, [vp]),
+        "rs_batch": (i32, [vp, vp, u32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -189,3 +195,62 @@ def rs_sample_static(n, N, seed, n0, out, stream=None) -> int:
     """rs_sample without device allocation (static scratch); returns the
     call's device status after waiting for the stream."""
     return load().rs_sample_static(n, N, seed, n0, _ptr(out), _stream(stream))
+
+
+class Request(ctypes.Structure):
+    """rs_request: one sampling request of a batch."""
+    _fields_ = [("n", ctypes.c_uint64), ("N", ctypes.c_uint64), ("seed", ctypes.c_uint64),
+                ("out_off", ctypes.c_uint64), ("n0", ctypes.c_uint32), ("kind", ctypes.c_uint32)]
+
+
+def requests_array(n, N, seed, out_off, n0, kind):
+    """A ctypes array of rs_request from equal-length sequences."""
+    arr = (Request * len(n))()
+    for i in range(len(n)):
+        arr[i] = Request(int(n[i]), int(N[i]), int(seed[i]), int(out_off[i]), int(n0[i]), int(kind[i]))
+    return arr
+
+
+class BatchPlan:
+    """Owns an rs_batch plan."""
+
+    def __init__(self, ctx: Context, reqs):
+        h = ctypes.c_void_p()
+        _check(load().rs_batch_plan(ctx.handle, ctypes.cast(reqs, ctypes.c_void_p), len(reqs), ctypes.byref(h)),
+               "rs_batch_plan")
+        self.handle = h
+        self.ctx = ctx   # the context must outlive the plan
+
+    def close(self):
+        if self.handle:
+            load().rs_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rs_batch_plan(ctx: Context, reqs) -> BatchPlan:
+    return BatchPlan(ctx, reqs)
+
+
+def rs_batch_run(plan: BatchPlan, out_pool, status, stream=None) -> int:
+    return _check(load().rs_batch_run(plan.handle, _ptr(out_pool), _ptr(status), _stream(stream)), "rs_batch_run")
+
+
+def rs_batch_tune(plan: BatchPlan, out_pool, status, stream=None) -> int:
+    return _check(load().rs_batch_tune(plan.handle, _ptr(out_pool), _ptr(status), _stream(stream)), "rs_batch_tune")
+
+
+def rs_batch_launch_count(plan: BatchPlan) -> int:
+    c = ctypes.c_uint64(0)
+    _check(load().rs_batch_launch_count(plan.handle, ctypes.byref(c)), "rs_batch_launch_count")
+    return c.value
+
+
+def rs_batch(ctx: Context, reqs_dev, R, out_pool, status, stream=None) -> int:
+    return _check(load().rs_batch(ctx.handle, _ptr(reqs_dev), R, _ptr(out_pool), _ptr(status), _stream(stream)),
+                  "rs_batch")

@@ -9,6 +9,7 @@
 // turns them into positions with an integer prefix sum, which is exact, so
 // the positions are those of the sequential definition.  A draw with
 // ln U / L >= 2^62 ends the range.
+#include "rs_batch.cuh"
 #include "rs_leaf.cuh"
 #include "rs_math.cuh"
 
@@ -320,60 +321,86 @@ struct LeafBArgs {
     int* status;
 };
 
+// One leaf of Algorithm B, by the whole block.
+RS_DEV void leaf_b_one(LeafBShared& sm, const NodeRec& r, uint64_t id, Key2 key, uint64_t* __restrict__ out,
+                       int* status) {
+    if (r.c == 0) return;
+    const double dn = (double)r.c;
+    double rho = (dn + 3.0 * sqrt(dn) + 10.0) / (double)r.S;
+    if (rho > 1.0) rho = 1.0;
+    uint64_t c = 0;
+    int attempt = 0;
+    bool fail = false;
+    if (threadIdx.x == 0) sm.err = 0;
+    __syncthreads();
+    if (rho == 1.0) {
+        c = r.S;
+        const uint64_t fill = c < kLeafBCap ? c : kLeafBCap;
+        for (uint64_t i = threadIdx.x; i < fill; i += kLeafThreads) sm.pos[i] = i;
+        __syncthreads();
+    } else {
+        const double L = dlog1p(-rho);
+        for (attempt = 0; attempt < 64; ++attempt) {
+            c = block_walk(key, TAG_LEAF_B + 256u * (uint32_t)attempt, id, L, r.S, sm);
+            if (sm.err) break;
+            if (c >= r.c) break;
+        }
+        if (sm.err || attempt == 64) {
+            if (threadIdx.x == 0) set_status(status, RS_EITER);
+            fail = true;
+        }
+    }
+    if (!fail && c > kLeafBCap) {
+        if (threadIdx.x == 0) set_status(status, RS_ECAPACITY);
+        fail = true;
+    }
+    if (fail) {
+        __syncthreads();
+        return;
+    }
+    const uint32_t drop = (uint32_t)(c - r.c);
+    Draw<4> dr{Bounded32{c, (uint32_t)(((1ull << 32) - c) % c)}};
+    if (!select_leaf<uint32_t, 4, true>(sm.sel, dr, key, TAG_FIXUP, id, c, drop, status)) {
+        __syncthreads();
+        return;
+    }
+    uint64_t* dst = out + r.off;
+    for (uint32_t i = threadIdx.x; i < c; i += kLeafThreads) {
+        const uint32_t below = lower_bound(sm.sel.keys, drop, i);
+        if (below < drop && sm.sel.keys[below] == i) continue;
+        dst[i - below] = r.lo + 1 + sm.pos[i];
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(kLeafThreads) leaf_b_kernel(LeafBArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     LeafBShared& sm = *reinterpret_cast<LeafBShared*>(smem_raw);
-    for (uint64_t leaf = blockIdx.x; leaf < A.nleaves; leaf += gridDim.x) {
-        const NodeRec r = A.leaves[leaf];
-        if (r.c == 0) continue;
-        const uint64_t id = A.first_id + leaf;
-        const double dn = (double)r.c;
-        double rho = (dn + 3.0 * sqrt(dn) + 10.0) / (double)r.S;
-        if (rho > 1.0) rho = 1.0;
-        uint64_t c = 0;
-        int attempt = 0;
-        bool fail = false;
-        if (threadIdx.x == 0) sm.err = 0;
-        __syncthreads();
-        if (rho == 1.0) {
-            c = r.S;
-            const uint64_t fill = c < kLeafBCap ? c : kLeafBCap;
-            for (uint64_t i = threadIdx.x; i < fill; i += kLeafThreads) sm.pos[i] = i;
-            __syncthreads();
-        } else {
-            const double L = dlog1p(-rho);
-            for (attempt = 0; attempt < 64; ++attempt) {
-                c = block_walk(A.key, TAG_LEAF_B + 256u * (uint32_t)attempt, id, L, r.S, sm);
-                if (sm.err) break;
-                if (c >= r.c) break;
-            }
-            if (sm.err || attempt == 64) {
-                if (threadIdx.x == 0) set_status(A.status, RS_EITER);
-                fail = true;
-            }
-        }
-        if (!fail && c > kLeafBCap) {
-            if (threadIdx.x == 0) set_status(A.status, RS_ECAPACITY);
-            fail = true;
-        }
-        if (fail) {
-            __syncthreads();
-            continue;
-        }
-        const uint32_t drop = (uint32_t)(c - r.c);
-        Draw<4> dr{Bounded32{c, (uint32_t)(((1ull << 32) - c) % c)}};
-        if (!select_leaf<uint32_t, 4, true>(sm.sel, dr, A.key, TAG_FIXUP, id, c, drop, A.status)) {
-            __syncthreads();
-            continue;
-        }
-        uint64_t* dst = A.out + r.off;
-        for (uint32_t i = threadIdx.x; i < c; i += kLeafThreads) {
-            const uint32_t below = lower_bound(sm.sel.keys, drop, i);
-            if (below < drop && sm.sel.keys[below] == i) continue;
-            dst[i - below] = r.lo + 1 + sm.pos[i];
-        }
-        __syncthreads();
+    for (uint64_t leaf = blockIdx.x; leaf < A.nleaves; leaf += gridDim.x)
+        leaf_b_one(sm, A.leaves[leaf], A.first_id + leaf, A.key, A.out, A.status);
+}
+
+// Algorithm B leaves of a batch group.
+__global__ void __launch_bounds__(kLeafThreads) batch_leaf_b_kernel(BatchGroupView G) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    LeafBShared& sm = *reinterpret_cast<LeafBShared*>(smem_raw);
+    for (uint64_t g = blockIdx.x; g < G.nleaves; g += gridDim.x) {
+        const ResolvedLeaf L = resolve_leaf(G, g);
+        leaf_b_one(sm, L.rec, L.id, make_key(L.seed), L.out, L.status);
     }
+}
+
+cudaError_t launch_batch_leaves_b(const BatchGroupView& G, int sms, cudaStream_t st) {
+    const size_t smem = sizeof(LeafBShared);
+    cudaError_t e = cudaFuncSetAttribute(batch_leaf_b_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_leaf_b_kernel, kLeafThreads, smem);
+    if (e != cudaSuccess) return e;
+    const uint64_t grid = std::min<uint64_t>(G.nleaves, (uint64_t)sms * std::max(per_sm, 1));
+    if (grid == 0) return cudaSuccess;
+    batch_leaf_b_kernel<<<(unsigned)grid, kLeafThreads, smem, st>>>(G);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_leaves_b(const LeafBLaunch& L, cudaStream_t st) {

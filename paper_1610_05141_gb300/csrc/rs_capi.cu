@@ -183,6 +183,14 @@ int sample_impl(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0,
 
 }  // namespace
 
+namespace rs {
+// Accessors for the other translation units (the batch planner).
+int ctx_device(rs_ctx* ctx) { return ctx->device; }
+int ctx_sms(rs_ctx* ctx) { return ctx->sms; }
+const double* ctx_tab(rs_ctx* ctx) { return ctx->tab; }
+void ctx_count_launches(rs_ctx* ctx, uint64_t n) { ctx->launches += n; }
+}  // namespace rs
+
 extern "C" {
 
 int rs_create(rs_ctx** out, int device) {

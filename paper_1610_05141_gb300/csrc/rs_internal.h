@@ -84,4 +84,8 @@ struct BernLaunch {
 cudaError_t launch_bernoulli(const BernLaunch& L, cudaStream_t st);
 uint64_t scan_scratch_words(uint64_t n);
 
+struct BatchGroupView;
+// Algorithm B leaves of a batch group (rs_bern.cu).
+cudaError_t launch_batch_leaves_b(const BatchGroupView& G, int sms, cudaStream_t st);
+
 }  // namespace rs
