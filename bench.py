@@ -19,6 +19,8 @@ workload (rank 0 only).
 """
 import argparse
 import hashlib
+
+import numpy as np
 import json
 import os
 import statistics
@@ -231,6 +233,77 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_batch(rs, ctx, stream, args):
+    """Batched requests (100k independent samples in one graph-replayed run)
+    against one rs_sample launch per request on the same GPU and stream."""
+    import torch
+    from paper_1610_05141_gb300.workloads import batch_requests
+    n, N, seeds, off, n0, total = batch_requests(R=args.batch_requests)
+    kinds = np.zeros(len(n), dtype=np.uint32)
+    arr = rs.requests_array(n, N, seeds, off, n0, kinds)
+    t0 = time.perf_counter()
+    plan = rs.rs_batch_plan(ctx, arr)
+    plan_s = time.perf_counter() - t0
+    pool = torch.empty(total, dtype=torch.int64, device="cuda")
+    status = torch.empty(len(n), dtype=torch.int32, device="cuda")
+    rs.rs_batch_run(plan, pool, status, stream)        # eager run
+    rs.rs_batch_tune(plan, pool, status, stream)
+    for _ in range(2):
+        rs.rs_batch_run(plan, pool, status, stream)    # graph capture + replay
+    stream.synchronize()
+    if not bool((status == 0).all()):
+        raise RuntimeError("batch request failed")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    runs = args.batch_runs
+    e0.record(stream)
+    for _ in range(runs):
+        rs.rs_batch_run(plan, pool, status, stream)
+    e1.record(stream)
+    stream.synchronize()
+    batch_ms = e0.elapsed_time(e1) / runs
+    launches = rs.rs_batch_launch_count(plan)
+    plan.close()
+    del pool
+    # unbatched: the first `m` requests, one call (and its launches) each
+    m = min(args.unbatched_requests, len(n))
+    outs = torch.empty(int(n[:m].sum()), dtype=torch.int64, device="cuda")
+    for i in range(min(m, 50)):   # warm-up
+        rs.rs_sample(ctx, int(n[i]), int(N[i]), int(seeds[i]), int(n0[i]), outs[int(off[i]):], stream)
+    stream.synchronize()
+    e0.record(stream)
+    for i in range(m):
+        rs.rs_sample(ctx, int(n[i]), int(N[i]), int(seeds[i]), int(n0[i]), outs[int(off[i]):], stream)
+    e1.record(stream)
+    stream.synchronize()
+    single_ms = e0.elapsed_time(e1)
+    # the same slice batched
+    plan = rs.rs_batch_plan(ctx, rs.requests_array(n[:m], N[:m], seeds[:m], off[:m], n0[:m], kinds[:m]))
+    st2 = torch.empty(m, dtype=torch.int32, device="cuda")
+    for _ in range(3):
+        rs.rs_batch_run(plan, outs, st2, stream)
+    stream.synchronize()
+    e0.record(stream)
+    for _ in range(runs):
+        rs.rs_batch_run(plan, outs, st2, stream)
+    e1.record(stream)
+    stream.synchronize()
+    slice_ms = e0.elapsed_time(e1) / runs
+    plan.close()
+    return {
+        "workload": f"{len(n)} requests, n log-uniform in [1,1e6), N log-uniform in [n,2^48], n0=4096, "
+                    "PCG64 seed 20161017",
+        "requests": len(n), "samples": total, "ms_per_run": batch_ms,
+        "req_per_s": len(n) / (batch_ms / 1000), "samples_per_s": total / (batch_ms / 1000),
+        "write_gbs": 8 * total / (batch_ms / 1000) / 1e9,
+        "latency_ms": {"p50": batch_ms, "p99": batch_ms,
+                       "note": "every request of a run completes with the run"},
+        "kernel_launches_per_run": launches, "plan_s": plan_s,
+        "unbatched": {"requests": m, "req_per_s": m / (single_ms / 1000),
+                      "batched_same_requests_req_per_s": m / (slice_ms / 1000),
+                      "speedup": single_ms / slice_ms},
+    }
+
+
 def run_ours(args):
     import torch
     import paper_1610_05141_gb300 as rs
@@ -304,6 +377,11 @@ def run_ours(args):
         e2e_ms = e0.elapsed_time(e1) / e2e_steps
         e2e_wall_ms = 1000 * (time.perf_counter() - t0) / e2e_steps
         del host
+        batch = None
+        if not args.no_batch:
+            del out
+            torch.cuda.empty_cache()
+            batch = run_batch(rs, ctx, stream, args)
     clk = clocks.summary(wall0, wall1)
 
     ms_per_step = ms_total / args.steps
@@ -336,6 +414,8 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if batch is not None:
+        line["batch"] = batch
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -352,6 +432,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-requests measurement")
+    ap.add_argument("--batch-requests", type=int, default=100_000)
+    ap.add_argument("--batch-runs", type=int, default=5)
+    ap.add_argument("--unbatched-requests", type=int, default=3000)
     ap.add_argument("--n", type=int, default=None, help="smaller n (profiling cases only)")
     ap.add_argument("--log2N", type=int, default=None, help="smaller universe 2^log2N (profiling cases only)")
     args = ap.parse_args()

@@ -197,18 +197,16 @@ def rs_sample_static(n, N, seed, n0, out, stream=None) -> int:
     return load().rs_sample_static(n, N, seed, n0, _ptr(out), _stream(stream))
 
 
-class Request(ctypes.Structure):
-    """rs_request: one sampling request of a batch."""
-    _fields_ = [("n", ctypes.c_uint64), ("N", ctypes.c_uint64), ("seed", ctypes.c_uint64),
-                ("out_off", ctypes.c_uint64), ("n0", ctypes.c_uint32), ("kind", ctypes.c_uint32)]
+REQUEST_DTYPE = [("n", "<u8"), ("N", "<u8"), ("seed", "<u8"), ("out_off", "<u8"), ("n0", "<u4"), ("kind", "<u4")]
 
 
 def requests_array(n, N, seed, out_off, n0, kind):
-    """A ctypes array of rs_request from equal-length sequences."""
-    arr = (Request * len(n))()
-    for i in range(len(n)):
-        arr[i] = Request(int(n[i]), int(N[i]), int(seed[i]), int(out_off[i]), int(n0[i]), int(kind[i]))
-    return arr
+    """rs_request records (a numpy structured array with the C layout)."""
+    import numpy as np
+    a = np.zeros(len(n), dtype=np.dtype(REQUEST_DTYPE))
+    a["n"], a["N"], a["seed"], a["out_off"] = n, N, seed, out_off
+    a["n0"], a["kind"] = n0, kind
+    return a
 
 
 class BatchPlan:
@@ -216,8 +214,7 @@ class BatchPlan:
 
     def __init__(self, ctx: Context, reqs):
         h = ctypes.c_void_p()
-        _check(load().rs_batch_plan(ctx.handle, ctypes.cast(reqs, ctypes.c_void_p), len(reqs), ctypes.byref(h)),
-               "rs_batch_plan")
+        _check(load().rs_batch_plan(ctx.handle, reqs.ctypes.data, len(reqs), ctypes.byref(h)), "rs_batch_plan")
         self.handle = h
         self.ctx = ctx   # the context must outlive the plan
 

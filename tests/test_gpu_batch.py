@@ -104,7 +104,7 @@ def test_batch_one_shot_device_requests_and_tune(rs, ctx, oracle):
     off[1:] = np.cumsum(n)[:-1]
     arr = rs.requests_array(n, [r[1] for r in reqs], [r[2] for r in reqs], off, [r[3] for r in reqs],
                             [r[4] for r in reqs])
-    raw = np.frombuffer(bytes(arr), dtype=np.uint8)
+    raw = np.frombuffer(arr.tobytes(), dtype=np.uint8)
     reqs_dev = torch.from_numpy(raw.copy()).to("cuda")
     pool = torch.empty(sum(n), dtype=torch.int64, device="cuda")
     status = torch.empty(len(reqs), dtype=torch.int32, device="cuda")
