@@ -160,6 +160,129 @@ int rs_batch_destroy(rs_batchplan* plan);
 int rs_batch(rs_ctx* ctx, const rs_request* reqs_dev, uint32_t R, uint64_t* out_pool_dev,
              int32_t* status_dev, void* stream);
 
+/* ---- Resident trees and online sorted range queries -------------------
+ * A resident tree holds, in device memory owned by the library, the leaf
+ * records (range, count, output offset) of the split tree of one sample
+ * (Sec. 3.1 Algorithm R; the records fix each leaf's share and output
+ * position, Sec. 4.5).  A range query regenerates only the leaves whose
+ * ranges overlap the queried values and returns the sample's values inside
+ * them in increasing order (Sec. 4.1: sorted generation of a piece of the
+ * sample without the rest).  The result equals the slice of the full
+ * sample (rs_sample, rs_sample_with_replacement or rs_sample_b with the same
+ * arguments) whose values lie in [a, b). */
+
+/* Builds the split tree of (n, N, seed, n0) for sample kind `kind` (an
+ * RS_KIND_* value) on `stream` and keeps its leaf records; waits for
+ * `stream`.  The tree uses the context (its ln x! table and scratch) and
+ * must be destroyed before it.  Device memory: 32 bytes per leaf plus the
+ * query workspace.  Errors: RS_EINVAL (as rs_sample, or a bad kind),
+ * RS_ECAPACITY (depth above the library's limit), RS_ENOMEM, RS_ECUDA, and
+ * the device errors of the tree build (RS_EITER). */
+int rs_tree_create(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0, int kind, void* stream,
+                   rs_tree** tree);
+
+/* Writes the sample's values v with a <= v < b, in increasing order (with
+ * repeats for RS_KIND_WR), to out_dev[0..count) and count to *count_out
+ * (host memory); synchronizes `stream`.  out_dev: device memory for `cap`
+ * uint64 values, 8-byte aligned (may be NULL when cap = 0).  a and b are
+ * clamped to 1..N+1; an empty range gives count 0.  Errors: RS_EINVAL,
+ * RS_ECAPACITY (count > cap: *count_out is set, out_dev holds no useful
+ * values), RS_ENOMEM, RS_ECUDA, RS_EITER.  Queries on one tree must be
+ * issued from one host thread (they share the tree's workspace). */
+int rs_tree_query(rs_tree* tree, uint64_t a, uint64_t b, uint64_t* out_dev, uint64_t cap, uint64_t* count_out,
+                  void* stream);
+
+/* Depth of the tree and its largest leaf count.  Errors: RS_EINVAL. */
+int rs_tree_info(rs_tree* tree, int* depth, uint64_t* max_leaf_count);
+
+/* Waits for the device and frees the tree. */
+int rs_tree_destroy(rs_tree* tree);
+
+/* ---- Serving: continuous batching of sampling jobs and range queries ----
+ * A server owns a worker thread, an output arena in device memory and
+ * `lanes` CUDA streams, each with a fixed workspace.  Jobs are admitted in
+ * submission order when an in-flight slot is free and, for jobs that write
+ * into the arena, when the arena has room for their output (admission by
+ * memory).  Whenever a lane is idle and jobs are waiting, the worker issues
+ * all admissible waiting jobs as one group on that lane (the batch
+ * machinery above: one launch per tree level across the group's requests,
+ * one leaf kernel per leaf kind, the three query steps), so jobs that arrive
+ * while other groups are running are admitted as slots and memory free up
+ * and run alongside them on the device.  A job's result is exactly that of
+ * the corresponding single call (rs_sample / rs_sample_with_replacement /
+ * rs_sample_b / rs_tree_query): samples depend on their own arguments only
+ * (Sec. 4.5).  The paper has no serving layer; this is the library's. */
+
+typedef struct rs_server rs_server;
+
+enum { RS_OP_SAMPLE = 0, RS_OP_QUERY = 1 };
+
+typedef struct {
+    uint32_t op;          /* RS_OP_SAMPLE or RS_OP_QUERY                          */
+    uint32_t kind;        /* RS_OP_SAMPLE: an RS_KIND_* value                     */
+    uint64_t n, N, seed;  /* RS_OP_SAMPLE: as rs_sample                           */
+    uint32_t n0;          /* RS_OP_SAMPLE                                         */
+    uint32_t reserved;
+    rs_tree* tree;        /* RS_OP_QUERY: a tree on the server's device            */
+    uint64_t a, b, cap;   /* RS_OP_QUERY: values in [a, b), room for cap of them   */
+    uint64_t* out_dev;    /* output buffer (device, 8-byte aligned), or NULL: the
+                             server's arena (n values, or cap values for a query) */
+} rs_job;
+
+typedef struct {
+    uint64_t ticket;
+    int32_t status;       /* RS_OK or the job's error                             */
+    uint32_t reserved;
+    uint64_t count;       /* values written                                       */
+    uint64_t* out_dev;    /* where they are; arena memory stays reserved until
+                             rs_server_release                                    */
+    double submit_ms, launch_ms, done_ms;   /* since the server started; done_ms
+                             is when the worker saw the job's group finish        */
+} rs_result;
+
+typedef struct {
+    uint64_t arena_bytes;    /* output arena (0: no arena; jobs must bring out_dev)  */
+    uint32_t max_inflight;   /* admitted jobs not yet completed (default 4096)       */
+    uint32_t lanes;          /* streams, i.e. groups on the device at once (default 4) */
+    uint32_t max_group;      /* jobs per group (default 4096)                        */
+    uint32_t reserved;
+    uint64_t lane_bytes;     /* device workspace per lane (default 256 MiB)          */
+} rs_server_config;
+
+typedef struct {
+    uint64_t submitted, completed, groups, launches;
+    uint64_t max_group_seen, peak_inflight, peak_arena_bytes, arena_bytes_in_use;
+} rs_server_stats;
+
+/* Creates a server on the context's device.  cfg may be NULL (defaults
+ * above, arena 1 GiB).  The context must outlive the server and is not
+ * otherwise used while the server runs.  Errors: RS_EINVAL, RS_ENOMEM,
+ * RS_ECUDA. */
+int rs_server_create(rs_ctx* ctx, const rs_server_config* cfg, rs_server** server);
+
+/* Queues a job and returns its ticket (never blocks on the device).  A job
+ * with bad arguments, or one that can never be admitted (its output larger
+ * than the arena, its workspace larger than a lane), completes at once with
+ * RS_EINVAL or RS_ECAPACITY in its result.  Errors of the call itself:
+ * RS_EINVAL (null arguments, a query without a tree). */
+int rs_server_submit(rs_server* server, const rs_job* job, uint64_t* ticket);
+
+/* Moves up to `max` completed jobs' results into results[0..*got), waiting
+ * up to wait_us microseconds for the first one.  Errors: RS_EINVAL. */
+int rs_server_poll(rs_server* server, rs_result* results, uint32_t max, uint32_t* got, uint32_t wait_us);
+
+/* Returns a completed job's arena memory to the server (no-op for jobs
+ * with their own out_dev).  Errors: RS_EINVAL (unknown or unfinished
+ * ticket). */
+int rs_server_release(rs_server* server, uint64_t ticket);
+
+/* Counters since creation.  Errors: RS_EINVAL. */
+int rs_server_stats_get(rs_server* server, rs_server_stats* stats);
+
+/* Stops the worker (jobs still queued are dropped), waits for the device,
+ * frees everything. */
+int rs_server_destroy(rs_server* server);
+
 /* Waits for `stream`, then returns and clears the context's device status
  * word (RS_OK, or the first device-side error since the last rs_sync). */
 int rs_sync(rs_ctx* ctx, void* stream);

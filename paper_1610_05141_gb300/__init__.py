@@ -25,6 +25,36 @@ class RSError(RuntimeError):
         super().__init__(f"{where}: {code} ({strerror(code) if _lib else code})")
 
 
+RS_OP_SAMPLE, RS_OP_QUERY = 0, 1
+
+
+class Job(ctypes.Structure):
+    """rs_job."""
+    _fields_ = [("op", ctypes.c_uint32), ("kind", ctypes.c_uint32), ("n", ctypes.c_uint64),
+                ("N", ctypes.c_uint64), ("seed", ctypes.c_uint64), ("n0", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("tree", ctypes.c_void_p), ("a", ctypes.c_uint64),
+                ("b", ctypes.c_uint64), ("cap", ctypes.c_uint64), ("out_dev", ctypes.c_void_p)]
+
+
+class Result(ctypes.Structure):
+    """rs_result."""
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32), ("reserved", ctypes.c_uint32),
+                ("count", ctypes.c_uint64), ("out_dev", ctypes.c_void_p), ("submit_ms", ctypes.c_double),
+                ("launch_ms", ctypes.c_double), ("done_ms", ctypes.c_double)]
+
+
+class ServerConfig(ctypes.Structure):
+    """rs_server_config."""
+    _fields_ = [("arena_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32), ("lanes", ctypes.c_uint32),
+                ("max_group", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("lane_bytes", ctypes.c_uint64)]
+
+
+class ServerStats(ctypes.Structure):
+    """rs_server_stats."""
+    _fields_ = [(k, ctypes.c_uint64) for k in ("submitted", "completed", "groups", "launches", "max_group_seen",
+                                               "peak_inflight", "peak_arena_bytes", "arena_bytes_in_use")]
+
+
 _lib = None
 
 
@@ -60,6 +90,16 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "rs_batch_launch_count": (i32, [vp, ctypes.POINTER(u64)]),
         "rs_batch_destroy": (i32, [vp]),
         "rs_batch": (i32, [vp, vp, u32, vp, vp, vp]),
+        "rs_tree_create": (i32, [vp, u64, u64, u64, u32, i32, vp, ctypes.POINTER(vp)]),
+        "rs_tree_query": (i32, [vp, u64, u64, vp, u64, ctypes.POINTER(u64), vp]),
+        "rs_tree_info": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(u64)]),
+        "rs_tree_destroy": (i32, [vp]),
+        "rs_server_create": (i32, [vp, ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]),
+        "rs_server_submit": (i32, [vp, ctypes.POINTER(Job), ctypes.POINTER(u64)]),
+        "rs_server_poll": (i32, [vp, ctypes.POINTER(Result), u32, ctypes.POINTER(u32), u32]),
+        "rs_server_release": (i32, [vp, u64]),
+        "rs_server_stats_get": (i32, [vp, ctypes.POINTER(ServerStats)]),
+        "rs_server_destroy": (i32, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -251,3 +291,127 @@ def rs_batch_launch_count(plan: BatchPlan) -> int:
 def rs_batch(ctx: Context, reqs_dev, R, out_pool, status, stream=None) -> int:
     return _check(load().rs_batch(ctx.handle, _ptr(reqs_dev), R, _ptr(out_pool), _ptr(status), _stream(stream)),
                   "rs_batch")
+
+
+class Tree:
+    """Owns an rs_tree (the resident leaf records of one sample's split tree)."""
+
+    def __init__(self, ctx: Context, n, N, seed, n0, kind=RS_KIND_H, stream=None):
+        h = ctypes.c_void_p()
+        _check(load().rs_tree_create(ctx.handle, n, N, seed, n0, kind, _stream(stream), ctypes.byref(h)),
+               "rs_tree_create")
+        self.handle = h
+        self.ctx = ctx   # the context must outlive the tree
+        self.n, self.N, self.seed, self.n0, self.kind = n, N, seed, n0, kind
+
+    def close(self):
+        if self.handle:
+            load().rs_tree_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rs_tree_create(ctx: Context, n, N, seed, n0, kind=RS_KIND_H, stream=None) -> Tree:
+    return Tree(ctx, n, N, seed, n0, kind, stream)
+
+
+def rs_tree_destroy(tree: Tree) -> None:
+    tree.close()
+
+
+def rs_tree_query(tree: Tree, a, b, out, cap, stream=None, check=True):
+    """Returns (rc, count)."""
+    cnt = ctypes.c_uint64(0)
+    rc = load().rs_tree_query(tree.handle, a, b, _ptr(out), cap, ctypes.byref(cnt), _stream(stream))
+    if check and rc != RS_OK:
+        raise RSError(rc, "rs_tree_query")
+    return rc, cnt.value
+
+
+def rs_tree_info(tree: Tree):
+    """(depth, largest leaf count)."""
+    d, m = ctypes.c_int(0), ctypes.c_uint64(0)
+    _check(load().rs_tree_info(tree.handle, ctypes.byref(d), ctypes.byref(m)), "rs_tree_info")
+    return d.value, m.value
+
+
+def sample_job(n, N, seed, n0, kind=RS_KIND_H, out=None) -> Job:
+    return Job(op=RS_OP_SAMPLE, kind=kind, n=n, N=N, seed=seed, n0=n0, out_dev=_ptr(out))
+
+
+def query_job(tree: Tree, a, b, cap, out=None) -> Job:
+    return Job(op=RS_OP_QUERY, tree=tree.handle, a=a, b=b, cap=cap, out_dev=_ptr(out))
+
+
+class Server:
+    """Owns an rs_server (worker thread, output arena, lanes)."""
+
+    def __init__(self, ctx: Context, arena_bytes=1 << 30, max_inflight=0, lanes=0, max_group=0, lane_bytes=0):
+        cfg = ServerConfig(arena_bytes=arena_bytes, max_inflight=max_inflight, lanes=lanes, max_group=max_group,
+                           lane_bytes=lane_bytes)
+        h = ctypes.c_void_p()
+        _check(load().rs_server_create(ctx.handle, ctypes.byref(cfg), ctypes.byref(h)), "rs_server_create")
+        self.handle = h
+        self.ctx = ctx
+        self._buf = (Result * 1024)()
+
+    def submit(self, job: Job) -> int:
+        t = ctypes.c_uint64(0)
+        _check(load().rs_server_submit(self.handle, ctypes.byref(job), ctypes.byref(t)), "rs_server_submit")
+        return t.value
+
+    def poll(self, wait_us=0, max_results=1024):
+        """Completed jobs' results (a list of Result copies)."""
+        got = ctypes.c_uint32(0)
+        n = min(max_results, len(self._buf))
+        _check(load().rs_server_poll(self.handle, self._buf, n, ctypes.byref(got), wait_us), "rs_server_poll")
+        out = []
+        for i in range(got.value):
+            r = Result()
+            ctypes.pointer(r)[0] = self._buf[i]
+            out.append(r)
+        return out
+
+    def release(self, ticket: int) -> None:
+        _check(load().rs_server_release(self.handle, ticket), "rs_server_release")
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(load().rs_server_stats_get(self.handle, ctypes.byref(s)), "rs_server_stats_get")
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.handle:
+            load().rs_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rs_server_create(ctx: Context, **cfg) -> Server:
+    return Server(ctx, **cfg)
+
+
+class _DeviceArray:
+    """__cuda_array_interface__ of n uint64 at a raw device address (read as int64)."""
+
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<i8", "data": (ptr, False), "version": 2}
+
+
+def device_view(ptr: int, n: int):
+    """A torch int64 tensor viewing n values at a device address (e.g. a
+    server result in the arena); no copy."""
+    import torch
+    if n == 0:
+        return torch.empty(0, dtype=torch.int64, device="cuda")
+    return torch.as_tensor(_DeviceArray(ptr, n), device="cuda")

@@ -1,22 +1,24 @@
-// rs_batch.cu -- many independent sampling requests in one device run.
+// rs_batch.cu -- groups of device work: many independent sampling requests
+// (the batch API) and range queries on resident trees, each group one fixed
+// sequence of launches on one stream.
 //
 // A plan (host) validates the requests, computes every tree depth and lays
-// out: the node records of all requests in one scratch array, per tree level
-// a list of warp items (request, first node, count), and the leaves grouped
-// by kind and key width.  A run (device only) is a fixed sequence of
-// launches -- roots, one launch per tree level across all requests, one
-// persistent leaf kernel per group, the general path for oversized leaves --
-// that is captured once into a CUDA graph and replayed.  Each request's
+// out: the node records of all requests in one array, per tree level a list
+// of warp items (request, first node, count), and the leaves grouped by kind
+// and key width; for queries, their boundary leaves, interior leaves and
+// results.  The batch API issues a plan once with plain launches, then
+// captures the sequence into a CUDA graph and replays it.  Each request's
 // output equals its own rs_sample / rs_sample_with_replacement / rs_sample_b
 // output: the sample is a function of the request alone (Sec. 4.5).
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
-#include "rs_batch.cuh"
 #include "rs_big_leaf.cuh"
+#include "rs_group.h"
 #include "rs_hash_leaf.cuh"
-#include "rs_internal.h"
 #include "rs_tree_warp.cuh"
 
 namespace rs {
@@ -24,6 +26,7 @@ namespace rs {
 constexpr int kBatchTreeWarps = 4;
 constexpr int kBatchLeafThreads = 256;
 constexpr uint32_t kBatchTreeBatch = 128;
+constexpr int kLocateThreads = 256;
 
 __global__ void batch_init_kernel(const BatchReq* __restrict__ reqs, uint32_t R, NodeRec* __restrict__ nodes,
                                   int* __restrict__ status) {
@@ -52,8 +55,10 @@ __global__ void __launch_bounds__(kBatchTreeWarps * 32) batch_tree_kernel(const 
         tree_batch_warp<false>(nodes + q.node_base, e.v0, e.count, make_key(q.seed), tab, status + e.req, logs);
 }
 
-template <typename KeyT, bool WR>
-__global__ void __launch_bounds__(kBatchLeafThreads) batch_leaf_kernel(BatchGroupView G, uint32_t* ovf_list,
+// Leaf H / leaf WR over the leaves of a view, one block per leaf at a time;
+// leaves the shared-memory table cannot take go to the overflow list.
+template <typename KeyT, bool WR, class View>
+__global__ void __launch_bounds__(kBatchLeafThreads) group_leaf_kernel(View G, uint32_t* ovf_list,
                                                                        uint32_t* ovf_count, uint32_t cap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto& sm = *reinterpret_cast<HashShared<KeyT, kBatchLeafThreads / 32>*>(smem_raw);
@@ -67,8 +72,9 @@ __global__ void __launch_bounds__(kBatchLeafThreads) batch_leaf_kernel(BatchGrou
     }
 }
 
-template <bool WR>
-__global__ void __launch_bounds__(kBigThreads) batch_big_kernel(BatchGroupView G, const uint32_t* ovf_list,
+// The general path for the overflow list of a view.
+template <bool WR, class View>
+__global__ void __launch_bounds__(kBigThreads) group_big_kernel(View G, const uint32_t* ovf_list,
                                                                 const uint32_t* ovf_count, BigScratch sc) {
     __shared__ uint32_t tmp[kBigThreads / 32 + 1];
     const uint32_t count = *ovf_count;
@@ -87,56 +93,427 @@ __global__ void __launch_bounds__(kBigThreads) batch_big_kernel(BatchGroupView G
     }
 }
 
-}  // namespace rs
+// Index of the first of the sorted x[0..n) that is >= key, by one warp:
+// 32-way splits of the range, then one probe per lane.
+RS_DEV uint64_t warp_lower_bound(const uint64_t* __restrict__ x, uint64_t n, uint64_t key) {
+    const uint32_t lane = threadIdx.x & 31;
+    uint64_t lo = 0, hi = n;
+    while (hi - lo > 32) {
+        const uint64_t step = (hi - lo + 31) / 32;
+        const uint64_t p = lo + lane * step;
+        const uint32_t t = __popc(__ballot_sync(0xFFFFFFFFu, p < hi && x[p] < key));
+        if (t == 0) return lo;   // x[lo] >= key
+        const uint64_t next = lo + (uint64_t)t * step;   // first probe >= key, or past hi
+        lo = lo + (uint64_t)(t - 1) * step + 1;
+        if (next < hi) hi = next;
+    }
+    const uint64_t p = lo + lane;
+    return lo + __popc(__ballot_sync(0xFFFFFFFFu, p < hi && x[p] < key));
+}
+
+// Locate step of each query (one block per query): where [a, b) starts in
+// boundary leaf i0 and ends in leaf i0+m-1, the count, the base offset; the
+// boundary parts are copied to the output if the count fits.
+__global__ void __launch_bounds__(kLocateThreads) query_locate_kernel(const QueryDesc* __restrict__ qs,
+                                                                      QueryRes* __restrict__ res, uint32_t nq) {
+    __shared__ uint64_t sh_k[2];
+    const uint32_t warp = threadIdx.x >> 5;
+    for (uint32_t qi = blockIdx.x; qi < nq; qi += gridDim.x) {
+        const QueryDesc& Q = qs[qi];
+        const NodeRec r0 = Q.leaves[Q.i0];
+        const NodeRec r1 = Q.leaves[Q.i0 + Q.m - 1];
+        const uint64_t* hi_part = Q.m == 1 ? Q.scratch : Q.scratch + r0.c;
+        const uint64_t hi_n = Q.m == 1 ? r0.c : r1.c;
+        if (warp == 0) {
+            const uint64_t k = warp_lower_bound(Q.scratch, r0.c, Q.a);
+            if ((threadIdx.x & 31) == 0) sh_k[0] = k;
+        } else if (warp == 1) {
+            const uint64_t k = warp_lower_bound(hi_part, hi_n, Q.b);
+            if ((threadIdx.x & 31) == 0) sh_k[1] = k;
+        }
+        __syncthreads();
+        const uint64_t k_lo = sh_k[0], k_hi = sh_k[1];
+        const uint64_t base = r0.off + k_lo;
+        const uint64_t end = (Q.m == 1 ? r0.off : r1.off) + k_hi;
+        const uint64_t count = end - base;
+        int st = res[qi].status;   // errors of the boundary leaves
+        if (st == RS_OK && count > Q.cap) st = RS_ECAPACITY;
+        if (threadIdx.x == 0) {
+            res[qi].count = count;
+            res[qi].base = base;
+            res[qi].status = st;
+            res[qi].go = (st == RS_OK && Q.m > 2) ? 1 : 0;
+        }
+        if (st == RS_OK) {
+            if (Q.m == 1) {
+                for (uint64_t i = threadIdx.x; i < count; i += kLocateThreads) Q.out[i] = Q.scratch[k_lo + i];
+            } else {
+                const uint64_t n0 = r0.c - k_lo;
+                for (uint64_t i = threadIdx.x; i < n0; i += kLocateThreads) Q.out[i] = Q.scratch[k_lo + i];
+                uint64_t* dst = Q.out + (r1.off - base);
+                for (uint64_t i = threadIdx.x; i < k_hi; i += kLocateThreads) dst[i] = hi_part[i];
+            }
+        }
+        __syncthreads();
+    }
+}
 
 // ---------------------------------------------------------------------------
-// Host side.
+// Host side: the group planner.
 // ---------------------------------------------------------------------------
 
 namespace {
 
-struct Group {
-    int kind = 0;
-    bool wide = false;
-    uint32_t m = 0;
-    uint64_t nleaves = 0;
-    uint32_t* req_of = nullptr;    // device
-    uint64_t* prefix = nullptr;    // device, m + 1
-    uint32_t* ovf = nullptr;       // device, nleaves + 1 (list, then count)
-    int grid_per_sm = 0;           // leaf kernel blocks per SM (0 = occupancy limit)
-};
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
-int cuda_rc(cudaError_t e) { return e == cudaSuccess ? RS_OK : (e == cudaErrorMemoryAllocation ? RS_ENOMEM : RS_ECUDA); }
+int group_of(int kind, bool wide) { return kind == RS_KIND_B ? 4 : kind * 2 + (wide ? 1 : 0); }
 
-int depth_for(uint64_t n, uint64_t N, uint32_t n0) {
+// Counter slots of the zeroed block: sample leaf groups, query boundary
+// subgroups, query interior subgroups.
+constexpr int kCounters = 16;
+int counter_of(int part, int gi) { return part * 5 + gi; }
+
+int cuda_rc(cudaError_t e) {
+    if (e == cudaSuccess) return RS_OK;
+    return e == cudaErrorMemoryAllocation ? RS_ENOMEM : RS_ECUDA;
+}
+
+// Largest number of blocks of `kern` per SM on the current device (sets the
+// kernel's shared-memory limit first), cached per kernel and device.
+int blocks_per_sm(const void* kern, size_t smem, int threads) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find({kern, dev});
+    if (it != cache.end()) return it->second;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem) != cudaSuccess) return -1;
+    per = std::max(per, 1);
+    cache[{kern, dev}] = per;
+    return per;
+}
+
+// One leaf kernel (+ the general path) over the leaves of a view.
+template <class View>
+int issue_leaves(const View& V, int kind, bool wide, uint32_t* ovf, uint32_t* ovf_count, void* big,
+                 uint64_t big_kmax, int per_sm_cap, int sms, cudaStream_t st, uint64_t* nl) {
+    if (V.nleaves == 0) return RS_OK;
+    if (kind == RS_KIND_B) {
+        ++*nl;
+        return cuda_rc(launch_batch_leaves_b(V, sms, st));
+    }
+    const bool wr = kind == RS_KIND_WR;
+    void (*kern)(View, uint32_t*, uint32_t*, uint32_t);
+    size_t smem;
+    if (wide) {
+        kern = wr ? group_leaf_kernel<uint64_t, true, View> : group_leaf_kernel<uint64_t, false, View>;
+        smem = sizeof(HashShared<uint64_t, kBatchLeafThreads / 32>);
+    } else {
+        kern = wr ? group_leaf_kernel<uint32_t, true, View> : group_leaf_kernel<uint32_t, false, View>;
+        smem = sizeof(HashShared<uint32_t, kBatchLeafThreads / 32>);
+    }
+    int per = blocks_per_sm(reinterpret_cast<const void*>(kern), smem, kBatchLeafThreads);
+    if (per < 0) return RS_ECUDA;
+    if (per_sm_cap > 0) per = std::min(per, per_sm_cap);
+    const uint64_t grid = std::min<uint64_t>(V.nleaves, (uint64_t)sms * per);
+    kern<<<(unsigned)grid, kBatchLeafThreads, smem, st>>>(V, ovf, ovf_count, kLeafFastCap);
+    ++*nl;
+    if (big_kmax) {
+        const BigScratch sc = carve_big_scratch(big, big_kmax);
+        if (wr) group_big_kernel<true, View><<<1, kBigThreads, 0, st>>>(V, ovf, ovf_count, sc);
+        else group_big_kernel<false, View><<<1, kBigThreads, 0, st>>>(V, ovf, ovf_count, sc);
+        ++*nl;
+    }
+    return cuda_rc(cudaGetLastError());
+}
+
+}  // namespace
+
+int plan_depth(uint64_t n, uint64_t N, uint32_t n0) {
     int D = 0;
     while ((unsigned __int128)n > ((unsigned __int128)n0 << D)) ++D;
     while (D > 0 && ((unsigned __int128)1 << D) > (unsigned __int128)N) --D;
     return D;
 }
 
-template <typename T>
-int upload(T** dst, const std::vector<T>& v) {
-    *dst = nullptr;
-    if (v.empty()) return RS_OK;
-    int rc = cuda_rc(cudaMalloc((void**)dst, v.size() * sizeof(T)));
-    if (rc) return rc;
-    return cuda_rc(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+uint64_t leaf_of_position(uint64_t N, int D, uint64_t pos) {
+    uint64_t lo = 0, S = N, idx = 0;
+    for (int l = 0; l < D; ++l) {
+        const uint64_t K = S / 2;
+        if (pos < lo + K) {
+            idx = 2 * idx;
+            S = K;
+        } else {
+            idx = 2 * idx + 1;
+            lo += K;
+            S -= K;
+        }
+    }
+    return idx;
 }
 
-}  // namespace
+void GroupPlan::request_cost(const rs_request& q, uint64_t* up, uint64_t* work) {
+    *up = sizeof(BatchReq) + 16;
+    *work = 0;
+    if (q.n == 0 || q.n0 == 0) return;
+    const int D = plan_depth(q.n, q.N, q.n0);
+    uint64_t items = 0;
+    for (int l = 0; l < D; ++l) items += std::max<uint64_t>(1, (1ull << l) / kBatchTreeBatch);
+    *up += items * sizeof(BatchTreeItem);
+    *work = (2ull << D) * sizeof(NodeRec) + (1ull << D) * 4;
+}
+
+void GroupPlan::query_cost(const TreeInfo& t, uint64_t a, uint64_t b, uint64_t* up, uint64_t* work) {
+    *up = sizeof(QueryDesc) + 24;
+    *work = sizeof(QueryRes) + 2 * t.maxc * 8 + 16;
+    if (t.D < 0 || a >= b) return;
+    const uint64_t i0 = leaf_of_position(t.N, t.D, a - 1);
+    const uint64_t i1 = leaf_of_position(t.N, t.D, b - 2);
+    *work += (i1 - i0 + 1) * 4;
+}
+
+void GroupPlan::build(const rs_request* reqs, uint64_t* const* out_ptrs, uint32_t R, const GroupQuery* qs,
+                      uint32_t Q) {
+    R_ = R;
+    Q_ = Q;
+    reqs_.assign(R, BatchReq{});
+    levels_.clear();
+    qdesc_.clear();
+    qscratch_.clear();
+    for (int gi = 0; gi < 5; ++gi) {
+        groups_[gi] = Sub{};
+        groups_[gi].kind = gi == 4 ? RS_KIND_B : gi / 2;
+        groups_[gi].wide = gi < 4 && (gi & 1);
+        qgroups_[gi] = groups_[gi];
+    }
+    nodes_ = 0;
+    uint64_t bound = 0;
+    int Dmax = -1;
+    for (uint32_t r = 0; r < R; ++r) {
+        const rs_request& q = reqs[r];
+        BatchReq& b = reqs_[r];
+        b.n = q.n;
+        b.N = q.N;
+        b.seed = q.seed;
+        b.out_off = q.out_off;
+        b.out_ptr = out_ptrs ? out_ptrs[r] : nullptr;
+        b.n0 = q.n0;
+        b.kind = q.kind;
+        b.D = -1;
+        b.node_base = 0;
+        b.status0 = RS_OK;
+        const bool wr = q.kind == RS_KIND_WR;
+        if (q.kind > RS_KIND_B || q.n0 == 0 || q.N > (1ull << 62) || (q.n > 0 && q.N == 0) || (!wr && q.n > q.N)) {
+            b.status0 = RS_EINVAL;
+            continue;
+        }
+        if (q.n == 0) continue;
+        const int D = plan_depth(q.n, q.N, q.n0);
+        if (D > kMaxDepth) {
+            b.status0 = RS_ECAPACITY;
+            continue;
+        }
+        b.D = D;
+        b.node_base = nodes_;
+        nodes_ += 2ull << D;
+        Dmax = std::max(Dmax, D);
+        const uint64_t nleaves = 1ull << D;
+        const uint64_t smax = (q.N >> D) + ((q.N & (nleaves - 1)) ? 1 : 0);
+        Sub& G = groups_[group_of((int)q.kind, smax > (1ull << 32))];
+        if (G.p64.empty()) G.p64.push_back(0);
+        G.a32.push_back(r);
+        G.p64.push_back(G.p64.back() + nleaves);
+        G.n1 += nleaves;
+        if (q.kind != RS_KIND_B) bound = std::max<uint64_t>(bound, wr ? q.n : std::min<uint64_t>(q.n, smax - smax / 2));
+    }
+    // tree levels: warp items of up to kBatchTreeBatch consecutive nodes
+    for (int level = 0; level < Dmax; ++level) {
+        std::vector<BatchTreeItem> items;
+        const uint64_t cnt = 1ull << level;
+        const uint32_t per = (uint32_t)std::min<uint64_t>(cnt, kBatchTreeBatch);
+        for (uint32_t r = 0; r < R; ++r) {
+            if (reqs_[r].D <= level) continue;
+            for (uint64_t s = 0; s < cnt; s += per)
+                items.push_back(BatchTreeItem{r, (uint32_t)std::min<uint64_t>(per, cnt - s), cnt + s});
+        }
+        levels_.push_back(std::move(items));
+    }
+    // queries
+    for (uint32_t qi = 0; qi < Q; ++qi) {
+        const GroupQuery& g = qs[qi];
+        const TreeInfo& t = *g.tree;
+        QueryDesc d{};
+        d.leaves = t.leaves;
+        d.first_id = 1ull << t.D;
+        d.seed = t.seed;
+        d.a = g.a;
+        d.b = g.b;
+        d.i0 = leaf_of_position(t.N, t.D, g.a - 1);
+        d.m = leaf_of_position(t.N, t.D, g.b - 2) - d.i0 + 1;
+        d.out = g.out;
+        d.cap = g.cap;
+        d.scratch_cap = (d.m == 1 ? 1 : 2) * t.maxc;
+        qdesc_.push_back(d);
+        qscratch_.push_back(std::max<uint64_t>(d.scratch_cap, 1));
+        Sub& G = qgroups_[group_of(t.kind, t.wide)];
+        G.a32.push_back(qi << 1);
+        if (d.m > 1) G.a32.push_back((qi << 1) | 1);
+        G.n1 = G.a32.size();
+        if (d.m > 2) {
+            if (G.p64.empty()) G.p64.push_back(0);
+            G.b32.push_back(qi);
+            G.p64.push_back(G.p64.back() + (d.m - 2));
+            G.n2 += d.m - 2;
+        }
+        if (t.kind != RS_KIND_B) bound = std::max<uint64_t>(bound, t.maxk);
+    }
+    big_kmax_ = bound > 64 ? std::min<uint64_t>(bound, kBigLeafMax) : 0;
+    layout();
+}
+
+void GroupPlan::layout() {
+    size_t up = 0, work = 0;
+    auto take = [](size_t& at, size_t bytes) {
+        const size_t o = at;
+        at = align_up(at + bytes);
+        return o;
+    };
+    o_reqs_ = take(up, reqs_.size() * sizeof(BatchReq));
+    o_levels_.clear();
+    for (auto& lv : levels_) o_levels_.push_back(take(up, lv.size() * sizeof(BatchTreeItem)));
+    for (Sub& G : groups_) {
+        G.o_a32 = take(up, G.a32.size() * 4);
+        G.o_p64 = take(up, G.p64.size() * 8);
+    }
+    o_qdesc_ = take(up, qdesc_.size() * sizeof(QueryDesc));
+    for (Sub& G : qgroups_) {
+        G.o_a32 = take(up, G.a32.size() * 4);
+        G.o_b32 = take(up, G.b32.size() * 4);
+        G.o_p64 = take(up, G.p64.size() * 8);
+    }
+    o_nodes_ = take(work, nodes_ * sizeof(NodeRec));
+    o_zero_ = work;
+    zero_bytes_ = kCounters * 4 + Q_ * sizeof(QueryRes);
+    o_qres_ = o_zero_ + kCounters * 4;
+    take(work, zero_bytes_);
+    for (Sub& G : groups_) G.o_ovf1 = take(work, G.n1 * 4);
+    for (Sub& G : qgroups_) {
+        G.o_ovf1 = take(work, G.n1 * 4);
+        G.o_ovf2 = take(work, G.n2 * 4);
+    }
+    uint64_t scr = 0;
+    for (uint64_t s : qscratch_) scr += s;
+    o_qscr_ = take(work, scr * 8);
+    up_bytes_ = std::max<size_t>(up, kAlign);
+    work_bytes_ = std::max<size_t>(work, kAlign);
+}
+
+void GroupPlan::bind(unsigned char* up, unsigned char* work, void* big, unsigned char* img) {
+    up_ = up;
+    work_ = work;
+    big_ = big;
+    qres_ = reinterpret_cast<QueryRes*>(work + o_qres_);
+    uint64_t at = 0;
+    for (uint32_t qi = 0; qi < Q_; ++qi) {
+        qdesc_[qi].scratch = reinterpret_cast<uint64_t*>(work + o_qscr_) + at;
+        at += qscratch_[qi];
+    }
+    auto put = [img](size_t o, const void* src, size_t bytes) {
+        if (bytes) std::memcpy(img + o, src, bytes);
+    };
+    put(o_reqs_, reqs_.data(), reqs_.size() * sizeof(BatchReq));
+    for (size_t l = 0; l < levels_.size(); ++l)
+        put(o_levels_[l], levels_[l].data(), levels_[l].size() * sizeof(BatchTreeItem));
+    for (const Sub& G : groups_) {
+        put(G.o_a32, G.a32.data(), G.a32.size() * 4);
+        put(G.o_p64, G.p64.data(), G.p64.size() * 8);
+    }
+    put(o_qdesc_, qdesc_.data(), qdesc_.size() * sizeof(QueryDesc));
+    for (const Sub& G : qgroups_) {
+        put(G.o_a32, G.a32.data(), G.a32.size() * 4);
+        put(G.o_b32, G.b32.data(), G.b32.size() * 4);
+        put(G.o_p64, G.p64.data(), G.p64.size() * 8);
+    }
+}
+
+int GroupPlan::issue(const double* tab, int sms, uint64_t* pool, int* status, cudaStream_t st, uint64_t* launches) {
+    uint64_t nl = 0;
+    int rc = cuda_rc(cudaMemsetAsync(work_ + o_zero_, 0, zero_bytes_, st));
+    uint32_t* counters = reinterpret_cast<uint32_t*>(work_ + o_zero_);
+    const BatchReq* reqs = reinterpret_cast<const BatchReq*>(up_ + o_reqs_);
+    NodeRec* nodes = reinterpret_cast<NodeRec*>(work_ + o_nodes_);
+    if (!rc && R_ > 0) {
+        batch_init_kernel<<<(R_ + 255) / 256, 256, 0, st>>>(reqs, R_, nodes, status);
+        ++nl;
+        const size_t tree_smem = (size_t)kBatchTreeWarps * 32 * kLogSlots * sizeof(double);
+        for (size_t l = 0; l < levels_.size(); ++l) {
+            const uint32_t n = (uint32_t)levels_[l].size();
+            if (n == 0) continue;
+            const auto* items = reinterpret_cast<const BatchTreeItem*>(up_ + o_levels_[l]);
+            batch_tree_kernel<<<(n + kBatchTreeWarps - 1) / kBatchTreeWarps, kBatchTreeWarps * 32, tree_smem, st>>>(
+                reqs, items, n, nodes, tab, status);
+            ++nl;
+        }
+        for (int gi = 0; !rc && gi < 5; ++gi) {
+            const Sub& G = groups_[gi];
+            if (G.n1 == 0) continue;
+            BatchGroupView V{reqs, reinterpret_cast<const uint32_t*>(up_ + G.o_a32),
+                             reinterpret_cast<const uint64_t*>(up_ + G.o_p64), (uint32_t)G.a32.size(), G.n1,
+                             nodes, pool, status};
+            rc = issue_leaves(V, G.kind, G.wide, reinterpret_cast<uint32_t*>(work_ + G.o_ovf1),
+                              counters + counter_of(0, gi), big_, big_kmax_, per_sm_, sms, st, &nl);
+        }
+    }
+    if (!rc && Q_ > 0) {
+        const QueryDesc* qd = reinterpret_cast<const QueryDesc*>(up_ + o_qdesc_);
+        for (int gi = 0; !rc && gi < 5; ++gi) {
+            const Sub& G = qgroups_[gi];
+            if (G.n1 == 0) continue;
+            QueryBoundView V{qd, qres_, reinterpret_cast<const uint32_t*>(up_ + G.o_a32), G.n1};
+            rc = issue_leaves(V, G.kind, G.wide, reinterpret_cast<uint32_t*>(work_ + G.o_ovf1),
+                              counters + counter_of(1, gi), big_, big_kmax_, per_sm_, sms, st, &nl);
+        }
+        if (!rc) {
+            const unsigned grid = (unsigned)std::min<uint64_t>(Q_, (uint64_t)sms * 8);
+            query_locate_kernel<<<grid, kLocateThreads, 0, st>>>(qd, qres_, Q_);
+            ++nl;
+        }
+        for (int gi = 0; !rc && gi < 5; ++gi) {
+            const Sub& G = qgroups_[gi];
+            if (G.n2 == 0) continue;
+            QueryInnerView V{qd,
+                             qres_,
+                             reinterpret_cast<const uint32_t*>(up_ + G.o_b32),
+                             reinterpret_cast<const uint64_t*>(up_ + G.o_p64),
+                             (uint32_t)G.b32.size(),
+                             G.n2};
+            rc = issue_leaves(V, G.kind, G.wide, reinterpret_cast<uint32_t*>(work_ + G.o_ovf2),
+                              counters + counter_of(2, gi), big_, big_kmax_, per_sm_, sms, st, &nl);
+        }
+    }
+    if (launches) *launches = nl;
+    if (rc) return rc;
+    return cuda_rc(cudaGetLastError());
+}
+
+}  // namespace rs
+
+// ---------------------------------------------------------------------------
+// The batch API.
+// ---------------------------------------------------------------------------
 
 struct rs_batchplan {
     int device = 0;
     int sms = 0;
-    uint32_t R = 0;
     const double* tab = nullptr;   // the context's ln i! table
-    rs::BatchReq* reqs = nullptr;
-    rs::NodeRec* nodes = nullptr;
-    std::vector<std::pair<rs::BatchTreeItem*, uint32_t>> levels;   // device items, count
-    Group groups[5];
+    rs::GroupPlan plan;
+    unsigned char* up = nullptr;
+    unsigned char* work = nullptr;
     void* big_pool = nullptr;
-    uint64_t big_kmax = 0;
     // graph of the last run
     bool ran_eagerly = false;
     cudaGraphExec_t exec = nullptr;
@@ -147,68 +524,6 @@ struct rs_batchplan {
 };
 
 namespace {
-
-// The device work of a run, issued on `st`.
-int issue_run(rs_batchplan* B, uint64_t* pool, int32_t* status, cudaStream_t st, uint64_t* launches) {
-    uint64_t nl = 0;
-    int* stat = reinterpret_cast<int*>(status);
-    rs::batch_init_kernel<<<(B->R + 255) / 256, 256, 0, st>>>(B->reqs, B->R, B->nodes, stat);
-    ++nl;
-    const size_t tree_smem = (size_t)rs::kBatchTreeWarps * 32 * rs::kLogSlots * sizeof(double);
-    for (auto& lv : B->levels) {
-        const unsigned blocks = (lv.second + rs::kBatchTreeWarps - 1) / rs::kBatchTreeWarps;
-        rs::batch_tree_kernel<<<blocks, rs::kBatchTreeWarps * 32, tree_smem, st>>>(B->reqs, lv.first, lv.second,
-                                                                                   B->nodes, B->tab, stat);
-        ++nl;
-    }
-    for (Group& G : B->groups) {
-        if (G.nleaves == 0) continue;
-        rs::BatchGroupView V{B->reqs, G.req_of, G.prefix, G.m, G.nleaves, B->nodes, pool, stat};
-        if (G.kind == RS_KIND_B) {
-            if (rs::launch_batch_leaves_b(V, B->sms, st) != cudaSuccess) return RS_ECUDA;
-            ++nl;
-            continue;
-        }
-        if (cudaMemsetAsync(G.ovf + G.nleaves, 0, sizeof(uint32_t), st) != cudaSuccess) return RS_ECUDA;
-        const bool wr = G.kind == RS_KIND_WR;
-        void (*kern)(rs::BatchGroupView, uint32_t*, uint32_t*, uint32_t);
-        size_t smem;
-        if (G.wide) {
-            kern = wr ? rs::batch_leaf_kernel<uint64_t, true> : rs::batch_leaf_kernel<uint64_t, false>;
-            smem = sizeof(rs::HashShared<uint64_t, rs::kBatchLeafThreads / 32>);
-        } else {
-            kern = wr ? rs::batch_leaf_kernel<uint32_t, true> : rs::batch_leaf_kernel<uint32_t, false>;
-            smem = sizeof(rs::HashShared<uint32_t, rs::kBatchLeafThreads / 32>);
-        }
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-            return RS_ECUDA;
-        int per_sm = 1;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, rs::kBatchLeafThreads, smem) != cudaSuccess)
-            return RS_ECUDA;
-        if (G.grid_per_sm > 0) per_sm = std::min(per_sm, G.grid_per_sm);
-        const uint64_t grid = std::min<uint64_t>(G.nleaves, (uint64_t)B->sms * std::max(per_sm, 1));
-        kern<<<(unsigned)grid, rs::kBatchLeafThreads, smem, st>>>(V, G.ovf, G.ovf + G.nleaves, rs::kLeafFastCap);
-        ++nl;
-        if (B->big_kmax) {
-            rs::BigScratch sc;
-            uint64_t tmax = 32;
-            while (tmax < B->big_kmax) tmax <<= 1;
-            unsigned char* p = static_cast<unsigned char*>(B->big_pool);
-            sc.keys = reinterpret_cast<uint64_t*>(p); p += B->big_kmax * 8;
-            sc.cand = reinterpret_cast<uint64_t*>(p); p += B->big_kmax * 8;
-            sc.tmp = reinterpret_cast<uint64_t*>(p); p += B->big_kmax * 8;
-            sc.bkt = reinterpret_cast<uint32_t*>(p); p += B->big_kmax * 4;
-            sc.arr = reinterpret_cast<uint32_t*>(p); p += B->big_kmax * 4;
-            sc.cnt = reinterpret_cast<uint32_t*>(p);
-            sc.kmax = B->big_kmax;
-            if (wr) rs::batch_big_kernel<true><<<1, rs::kBigThreads, 0, st>>>(V, G.ovf, G.ovf + G.nleaves, sc);
-            else rs::batch_big_kernel<false><<<1, rs::kBigThreads, 0, st>>>(V, G.ovf, G.ovf + G.nleaves, sc);
-            ++nl;
-        }
-    }
-    *launches = nl;
-    return cuda_rc(cudaGetLastError());
-}
 
 struct Guard {
     int prev = -1;
@@ -221,6 +536,10 @@ struct Guard {
         if (prev >= 0) cudaSetDevice(prev);
     }
 };
+
+int issue_run(rs_batchplan* B, uint64_t* pool, int32_t* status, cudaStream_t st, uint64_t* launches) {
+    return B->plan.issue(B->tab, B->sms, pool, reinterpret_cast<int*>(status), st, launches);
+}
 
 }  // namespace
 
@@ -240,14 +559,8 @@ int rs_batch_destroy(rs_batchplan* B) {
     cudaDeviceSynchronize();
     if (B->exec) cudaGraphExecDestroy(B->exec);
     if (B->capture_stream) cudaStreamDestroy(B->capture_stream);
-    cudaFree(B->reqs);
-    cudaFree(B->nodes);
-    for (auto& lv : B->levels) cudaFree(lv.first);
-    for (Group& G : B->groups) {
-        cudaFree(G.req_of);
-        cudaFree(G.prefix);
-        cudaFree(G.ovf);
-    }
+    cudaFree(B->up);
+    cudaFree(B->work);
     cudaFree(B->big_pool);
     delete B;
     return RS_OK;
@@ -263,78 +576,20 @@ int rs_batch_plan(rs_ctx* ctx, const rs_request* reqs, uint32_t R, rs_batchplan*
     B->device = rs::ctx_device(ctx);
     B->sms = rs::ctx_sms(ctx);
     B->tab = rs::ctx_tab(ctx);
-    B->R = R;
-    std::vector<rs::BatchReq> h(R);
-    uint64_t nodes = 0, bound = 0;
-    int Dmax = -1;
-    std::vector<uint32_t> req_of[5];
-    std::vector<uint64_t> prefix[5];
-    auto group_of = [](uint32_t kind, bool wide) { return kind == RS_KIND_B ? 4 : (int)kind * 2 + (wide ? 1 : 0); };
-    for (uint32_t r = 0; r < R; ++r) {
-        const rs_request& q = reqs[r];
-        rs::BatchReq& b = h[r];
-        b.n = q.n;
-        b.N = q.N;
-        b.seed = q.seed;
-        b.out_off = q.out_off;
-        b.n0 = q.n0;
-        b.kind = q.kind;
-        b.D = -1;
-        b.node_base = 0;
-        b.status0 = RS_OK;
-        const bool wr = q.kind == RS_KIND_WR;
-        if (q.kind > RS_KIND_B || q.n0 == 0 || q.N > (1ull << 62) || (q.n > 0 && q.N == 0) || (!wr && q.n > q.N)) {
-            b.status0 = RS_EINVAL;
-            continue;
+    int rc = RS_OK;
+    try {
+        B->plan.build(reqs, nullptr, R, nullptr, 0);
+        std::vector<unsigned char> img(B->plan.upload_bytes());
+        rc = rs::cuda_rc(cudaMalloc(&B->up, B->plan.upload_bytes()));
+        if (!rc) rc = rs::cuda_rc(cudaMalloc(&B->work, B->plan.work_bytes()));
+        if (!rc && B->plan.big_kmax())
+            rc = rs::cuda_rc(cudaMalloc(&B->big_pool, rs::big_pool_bytes(B->plan.big_kmax())));
+        if (!rc) {
+            B->plan.bind(B->up, B->work, B->big_pool, img.data());
+            rc = rs::cuda_rc(cudaMemcpy(B->up, img.data(), img.size(), cudaMemcpyHostToDevice));
         }
-        if (q.n == 0) continue;
-        const int D = depth_for(q.n, q.N, q.n0);
-        if (D > rs::kMaxDepth) {
-            b.status0 = RS_ECAPACITY;
-            continue;
-        }
-        b.D = D;
-        b.node_base = nodes;
-        nodes += 2ull << D;
-        Dmax = std::max(Dmax, D);
-        const uint64_t nleaves = 1ull << D;
-        const uint64_t smax = (q.N >> D) + ((q.N & (nleaves - 1)) ? 1 : 0);
-        const int gi = group_of(q.kind, smax > (1ull << 32));
-        if (prefix[gi].empty()) prefix[gi].push_back(0);
-        req_of[gi].push_back(r);
-        prefix[gi].push_back(prefix[gi].back() + nleaves);
-        if (q.kind != RS_KIND_B) bound = std::max<uint64_t>(bound, wr ? q.n : std::min<uint64_t>(q.n, smax - smax / 2));
-    }
-    int rc = upload(&B->reqs, h);
-    if (!rc && nodes) rc = cuda_rc(cudaMalloc(&B->nodes, nodes * sizeof(rs::NodeRec)));
-    // tree levels: warp items of up to kBatchTreeBatch consecutive nodes
-    for (int level = 0; !rc && level < Dmax; ++level) {
-        std::vector<rs::BatchTreeItem> items;
-        const uint64_t cnt = 1ull << level;
-        const uint32_t per = (uint32_t)std::min<uint64_t>(cnt, rs::kBatchTreeBatch);
-        for (uint32_t r = 0; r < R; ++r) {
-            if (h[r].D <= level) continue;
-            for (uint64_t s = 0; s < cnt; s += per)
-                items.push_back(rs::BatchTreeItem{r, (uint32_t)std::min<uint64_t>(per, cnt - s), cnt + s});
-        }
-        rs::BatchTreeItem* d = nullptr;
-        rc = upload(&d, items);
-        if (!rc) B->levels.emplace_back(d, (uint32_t)items.size());
-    }
-    for (int gi = 0; !rc && gi < 5; ++gi) {
-        Group& G = B->groups[gi];
-        G.kind = gi == 4 ? RS_KIND_B : gi / 2;
-        G.wide = gi < 4 && (gi & 1);
-        G.m = (uint32_t)req_of[gi].size();
-        if (G.m == 0) continue;
-        G.nleaves = prefix[gi].back();
-        rc = upload(&G.req_of, req_of[gi]);
-        if (!rc) rc = upload(&G.prefix, prefix[gi]);
-        if (!rc && G.kind != RS_KIND_B) rc = cuda_rc(cudaMalloc(&G.ovf, (G.nleaves + 1) * sizeof(uint32_t)));
-    }
-    if (!rc && bound > 64) {
-        B->big_kmax = std::min<uint64_t>(bound, rs::kBigLeafMax);
-        rc = cuda_rc(cudaMalloc(&B->big_pool, rs::big_pool_bytes(B->big_kmax)));
+    } catch (const std::bad_alloc&) {
+        rc = RS_ENOMEM;
     }
     if (rc) {
         rs_batch_destroy(B);
@@ -380,7 +635,7 @@ int rs_batch_run(rs_batchplan* B, uint64_t* out_pool_dev, int32_t* status_dev, v
         B->graph_pool = out_pool_dev;
         B->graph_status = status_dev;
     }
-    return cuda_rc(cudaGraphLaunch(B->exec, st));
+    return rs::cuda_rc(cudaGraphLaunch(B->exec, st));
 }
 
 int rs_batch_launch_count(rs_batchplan* B, uint64_t* per_run) {
@@ -401,7 +656,7 @@ int rs_batch_tune(rs_batchplan* B, uint64_t* out_pool_dev, int32_t* status_dev, 
     int best = 0;
     float best_ms = 1e30f;
     for (int per : {0, 4, 3, 2, 1}) {
-        for (Group& G : B->groups) G.grid_per_sm = per;
+        B->plan.set_blocks_per_sm(per);
         uint64_t nl = 0;
         int rc = issue_run(B, out_pool_dev, status_dev, st, &nl);   // warm
         cudaEventRecord(e0, st);
@@ -419,7 +674,7 @@ int rs_batch_tune(rs_batchplan* B, uint64_t* out_pool_dev, int32_t* status_dev, 
             best = per;
         }
     }
-    for (Group& G : B->groups) G.grid_per_sm = best;
+    B->plan.set_blocks_per_sm(best);
     if (B->exec) {
         cudaGraphExecDestroy(B->exec);
         B->exec = nullptr;

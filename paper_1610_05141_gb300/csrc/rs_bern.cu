@@ -380,8 +380,9 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_b_kernel(LeafBArgs A) {
         leaf_b_one(sm, A.leaves[leaf], A.first_id + leaf, A.key, A.out, A.status);
 }
 
-// Algorithm B leaves of a batch group.
-__global__ void __launch_bounds__(kLeafThreads) batch_leaf_b_kernel(BatchGroupView G) {
+// Algorithm B leaves of a batch group or of range queries.
+template <class View>
+__global__ void __launch_bounds__(kLeafThreads) group_leaf_b_kernel(View G) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     LeafBShared& sm = *reinterpret_cast<LeafBShared*>(smem_raw);
     for (uint64_t g = blockIdx.x; g < G.nleaves; g += gridDim.x) {
@@ -390,17 +391,29 @@ __global__ void __launch_bounds__(kLeafThreads) batch_leaf_b_kernel(BatchGroupVi
     }
 }
 
-cudaError_t launch_batch_leaves_b(const BatchGroupView& G, int sms, cudaStream_t st) {
+template <class View>
+static cudaError_t launch_group_leaves_b(const View& G, int sms, cudaStream_t st) {
     const size_t smem = sizeof(LeafBShared);
-    cudaError_t e = cudaFuncSetAttribute(batch_leaf_b_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = group_leaf_b_kernel<View>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 1;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_leaf_b_kernel, kLeafThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLeafThreads, smem);
     if (e != cudaSuccess) return e;
     const uint64_t grid = std::min<uint64_t>(G.nleaves, (uint64_t)sms * std::max(per_sm, 1));
     if (grid == 0) return cudaSuccess;
-    batch_leaf_b_kernel<<<(unsigned)grid, kLeafThreads, smem, st>>>(G);
+    kern<<<(unsigned)grid, kLeafThreads, smem, st>>>(G);
     return cudaGetLastError();
+}
+
+cudaError_t launch_batch_leaves_b(const BatchGroupView& G, int sms, cudaStream_t st) {
+    return launch_group_leaves_b(G, sms, st);
+}
+cudaError_t launch_batch_leaves_b(const QueryBoundView& G, int sms, cudaStream_t st) {
+    return launch_group_leaves_b(G, sms, st);
+}
+cudaError_t launch_batch_leaves_b(const QueryInnerView& G, int sms, cudaStream_t st) {
+    return launch_group_leaves_b(G, sms, st);
 }
 
 cudaError_t launch_leaves_b(const LeafBLaunch& L, cudaStream_t st) {

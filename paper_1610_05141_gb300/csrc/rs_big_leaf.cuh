@@ -22,6 +22,20 @@ struct BigScratch {
     uint64_t kmax;
 };
 
+// The scratch arrays carved from one pool of big_pool_bytes(kmax) bytes.
+inline BigScratch carve_big_scratch(void* pool, uint64_t kmax) {
+    BigScratch sc;
+    unsigned char* p = static_cast<unsigned char*>(pool);
+    sc.keys = reinterpret_cast<uint64_t*>(p); p += kmax * 8;
+    sc.cand = reinterpret_cast<uint64_t*>(p); p += kmax * 8;
+    sc.tmp = reinterpret_cast<uint64_t*>(p); p += kmax * 8;
+    sc.bkt = reinterpret_cast<uint32_t*>(p); p += kmax * 4;
+    sc.arr = reinterpret_cast<uint32_t*>(p); p += kmax * 4;
+    sc.cnt = reinterpret_cast<uint32_t*>(p);
+    sc.kmax = kmax;
+    return sc;
+}
+
 template <int CPB>
 RS_DEV void big_round(const Draw<CPB>& draw, Key2 key, uint32_t tag, uint64_t id, uint64_t s, uint64_t J,
                       uint64_t m, uint32_t T, uint64_t d, const BigScratch& sc, uint32_t* tmp, uint64_t* mv_out,

@@ -189,6 +189,14 @@ int ctx_device(rs_ctx* ctx) { return ctx->device; }
 int ctx_sms(rs_ctx* ctx) { return ctx->sms; }
 const double* ctx_tab(rs_ctx* ctx) { return ctx->tab; }
 void ctx_count_launches(rs_ctx* ctx, uint64_t n) { ctx->launches += n; }
+// Builds the split tree of (n, N, seed, n0) in the context's node records
+// (leaves at (*nodes)[2^D ..)); valid until the context's next call.
+int ctx_build_tree(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0, int kind, cudaStream_t st,
+                   int* D, NodeRec** nodes) {
+    const int rc = build_tree(ctx, n, N, seed, n0, kind, st, D);
+    *nodes = ctx->nodes;
+    return rc;
+}
 }  // namespace rs
 
 extern "C" {

@@ -85,7 +85,11 @@ cudaError_t launch_bernoulli(const BernLaunch& L, cudaStream_t st);
 uint64_t scan_scratch_words(uint64_t n);
 
 struct BatchGroupView;
-// Algorithm B leaves of a batch group (rs_bern.cu).
+struct QueryBoundView;
+struct QueryInnerView;
+// Algorithm B leaves of a batch group, or of range queries (rs_bern.cu).
 cudaError_t launch_batch_leaves_b(const BatchGroupView& G, int sms, cudaStream_t st);
+cudaError_t launch_batch_leaves_b(const QueryBoundView& G, int sms, cudaStream_t st);
+cudaError_t launch_batch_leaves_b(const QueryInnerView& G, int sms, cudaStream_t st);
 
 }  // namespace rs
