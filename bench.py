@@ -304,6 +304,160 @@ def run_batch(rs, ctx, stream, args):
     }
 
 
+def _pct(x, q):
+    return float(np.percentile(np.asarray(x, dtype=np.float64), q)) if len(x) else None
+
+
+def run_serve(rs, ctx, stream, args):
+    """Serving: a Poisson stream of sampling jobs (n log-uniform in
+    [1e2, 1e8), N log-uniform in [n, 2^56]) and range queries (20%, 1e3..1e5
+    expected hits) on resident trees, through the server's continuous
+    batching with a 64 GB output arena.  Capacity = completion rate with the
+    queue kept full; then open-loop runs at fractions of it give p50/p99
+    latency (submit to completion, server clock).  The same jobs, one call
+    each on one stream, give the unbatched rate."""
+    import torch
+    from paper_1610_05141_gb300.workloads import serve_jobs, serve_trees
+    tspec = serve_trees()
+    trees = [rs.rs_tree_create(ctx, n, N, seed, N0, rs.RS_KIND_H, stream) for (n, N, seed) in tspec]
+    server = rs.Server(ctx, arena_bytes=args.serve_arena_gb << 30, max_inflight=4096, lanes=4, max_group=4096)
+
+    def job(J, i):
+        if J["op"][i] == 0:
+            return rs.sample_job(int(J["n"][i]), int(J["N"][i]), int(J["seed"][i]), N0, rs.RS_KIND_H)
+        return rs.query_job(trees[int(J["tree"][i])], int(J["a"][i]), int(J["b"][i]), int(J["cap"][i]))
+
+    def finish(results, r, J=None, idx=None):
+        results.append(r)
+        if r.status != rs.RS_OK:
+            raise RuntimeError(f"serve job failed: status {r.status}")
+        server.release(r.ticket)
+
+    def drain(results, want, timeout_s=120.0):
+        t_end = time.time() + timeout_s
+        while len(results) < want:
+            if time.time() > t_end:
+                raise RuntimeError("server did not drain")
+            for r in server.poll(wait_us=2000):
+                finish(results, r)
+
+    def summarize(results, t_first, wall_s=None):
+        lat = [r.done_ms - r.submit_ms for r in results]
+        span_ms = max(r.done_ms for r in results) - t_first
+        return {"jobs": len(results), "req_per_s": len(results) / (span_ms / 1000),
+                "latency_ms": {"p50": _pct(lat, 50), "p99": _pct(lat, 99), "max": max(lat)},
+                "queue_ms_p99": _pct([r.launch_ms - r.submit_ms for r in results], 99)}
+
+    # warm-up (kernel attributes, lanes)
+    W = serve_jobs(200, tspec, seed=4)
+    res = []
+    for i in range(200):
+        server.submit(job(W, i))
+    drain(res, 200)
+    # capacity: everything queued at once
+    C = serve_jobs(args.serve_capacity_jobs, tspec, seed=5)
+    res = []
+    st0 = server.stats()
+    for i in range(len(C["op"])):
+        server.submit(job(C, i))
+    drain(res, len(C["op"]))
+    t_first = min(r.submit_ms for r in res)
+    cap = summarize(res, t_first)
+    st1 = server.stats()
+    capacity = cap["req_per_s"]
+    samples_cap = int(sum(r.count for r in res))
+    cap["samples_per_s"] = samples_cap / ((max(r.done_ms for r in res) - t_first) / 1000)
+    cap["groups"] = st1["groups"] - st0["groups"]
+    cap["kernel_launches"] = st1["launches"] - st0["launches"]
+    # open loop at fractions of capacity
+    loads = {}
+    for k, frac in enumerate((0.25, 0.5, 0.8)):
+        lam = frac * capacity
+        count = max(50, int(lam * args.serve_seconds))
+        J = serve_jobs(count, tspec, seed=50 + k)
+        arrivals = np.cumsum(np.random.Generator(np.random.PCG64(500 + k)).exponential(1.0 / lam, count))
+        res = []
+        lag = []
+        t0 = time.perf_counter()
+        i = 0
+        while i < count:
+            now = time.perf_counter() - t0
+            if now >= arrivals[i]:
+                server.submit(job(J, i))
+                lag.append(1000 * (now - arrivals[i]))
+                i += 1
+                continue
+            for r in server.poll(wait_us=0):
+                finish(res, r)
+        drain(res, count)
+        t_first = min(r.submit_ms for r in res)
+        out = summarize(res, t_first)
+        out["offered_req_per_s"] = lam
+        out["submit_lag_ms_p99"] = _pct(lag, 99)
+        loads[str(frac)] = out
+    stats = server.stats()
+    # exactness spot check: jobs of the mix (own buffers) against solo calls
+    chk = serve_jobs(64, tspec, seed=6, log10_n_max=6.0)
+    bufs, tks = {}, []
+    for i in range(64):
+        sz = int(chk["n"][i]) if chk["op"][i] == 0 else int(chk["cap"][i])
+        bufs[i] = torch.empty(max(sz, 1), dtype=torch.int64, device="cuda")
+        if chk["op"][i] == 0:
+            tks.append(server.submit(rs.sample_job(int(chk["n"][i]), int(chk["N"][i]), int(chk["seed"][i]), N0,
+                                                   rs.RS_KIND_H, bufs[i])))
+        else:
+            tks.append(server.submit(rs.query_job(trees[int(chk["tree"][i])], int(chk["a"][i]), int(chk["b"][i]),
+                                                  int(chk["cap"][i]), bufs[i])))
+    res = []
+    drain(res, 64)
+    counts = {r.ticket: r.count for r in res}
+    server.close()
+    exact = 0
+    for i in range(64):
+        cnt = counts[tks[i]]
+        solo = torch.empty_like(bufs[i])
+        if chk["op"][i] == 0:
+            rs.rs_sample(ctx, int(chk["n"][i]), int(chk["N"][i]), int(chk["seed"][i]), N0, solo, stream)
+            stream.synchronize()
+        else:
+            _, c2 = rs.rs_tree_query(trees[int(chk["tree"][i])], int(chk["a"][i]), int(chk["b"][i]), solo,
+                                     int(chk["cap"][i]), stream)
+            if c2 != cnt:
+                raise RuntimeError("served query count differs from the solo call")
+        if not torch.equal(solo[:cnt], bufs[i][:cnt]):
+            raise RuntimeError(f"served job {i} differs from its solo call")
+        exact += 1
+    # unbatched: the capacity mix's first jobs, one call each on one stream
+    m = min(args.serve_unbatched_jobs, len(C["op"]))
+    big = torch.empty(int(max(C["n"][:m].max(), C["cap"][:m].max())), dtype=torch.int64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(m):
+        if C["op"][i] == 0:
+            rs.rs_sample(ctx, int(C["n"][i]), int(C["N"][i]), int(C["seed"][i]), N0, big, stream)
+        else:
+            rs.rs_tree_query(trees[int(C["tree"][i])], int(C["a"][i]), int(C["b"][i]), big, int(C["cap"][i]), stream)
+    stream.synchronize()
+    single_s = time.perf_counter() - t0
+    if rs.rs_sync(ctx, stream) != rs.RS_OK:
+        raise RuntimeError("unbatched serve jobs failed")
+    del big
+    for t in trees:
+        t.close()
+    return {
+        "workload": "Poisson arrivals; 80% sampling jobs n log-uniform [1e2,1e8), N log-uniform [n,2^56], "
+                    "20% range queries on 8 resident trees (n=1e8, N log-uniform [1e8,2^56]) with 1e3..1e5 "
+                    f"expected hits; arena {args.serve_arena_gb} GB, 4 lanes, PCG64 seeds 4-6, 50-52",
+        "capacity": cap, "loads": loads,
+        "groups": stats["groups"], "max_group": stats["max_group_seen"], "peak_inflight": stats["peak_inflight"],
+        "peak_arena_gb": stats["peak_arena_bytes"] / 2**30,
+        "exact_vs_solo": f"{exact}/64 jobs bit-identical to their single calls",
+        "unbatched": {"jobs": m, "req_per_s": m / single_s,
+                      "note": "same jobs, one rs_sample / rs_tree_query call each, one stream"},
+        "speedup_vs_unbatched": capacity / (m / single_s),
+    }
+
+
 def run_ours(args):
     import torch
     import paper_1610_05141_gb300 as rs
@@ -378,10 +532,15 @@ def run_ours(args):
         e2e_wall_ms = 1000 * (time.perf_counter() - t0) / e2e_steps
         del host
         batch = None
+        serve = None
         if not args.no_batch:
             del out
             torch.cuda.empty_cache()
             batch = run_batch(rs, ctx, stream, args)
+        if not args.no_serve:
+            out = None
+            torch.cuda.empty_cache()
+            serve = run_serve(rs, ctx, stream, args)
     clk = clocks.summary(wall0, wall1)
 
     ms_per_step = ms_total / args.steps
@@ -416,6 +575,8 @@ def run_ours(args):
     }
     if batch is not None:
         line["batch"] = batch
+    if serve is not None:
+        line["serve"] = serve
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -436,6 +597,11 @@ def main():
     ap.add_argument("--batch-requests", type=int, default=100_000)
     ap.add_argument("--batch-runs", type=int, default=5)
     ap.add_argument("--unbatched-requests", type=int, default=3000)
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-seconds", type=float, default=3.0, help="length of each open-loop serving run")
+    ap.add_argument("--serve-capacity-jobs", type=int, default=4000)
+    ap.add_argument("--serve-unbatched-jobs", type=int, default=1000)
+    ap.add_argument("--serve-arena-gb", type=int, default=64)
     ap.add_argument("--n", type=int, default=None, help="smaller n (profiling cases only)")
     ap.add_argument("--log2N", type=int, default=None, help="smaller universe 2^log2N (profiling cases only)")
     args = ap.parse_args()
