@@ -11,14 +11,16 @@
 //
 // Three ways to compute them, all with the same result:
 //
-//  bucket path (the common case): candidates [0, k) are dropped into
-//    buckets of 8 entries addressed by their top bits (a shared-memory
-//    atomic add hands out the entry; a full bucket spills to a short side
-//    list).  A scan of the bucket counts gives every bucket its output
-//    offset; one lane per bucket sorts its keys with a 19-comparator network
-//    and stages them; a coalesced copy writes the leaf.  If a key repeats or
-//    a candidate was void, the first k candidates do not give k distinct
-//    values and the leaf goes to the probing path.
+//  bucket path (the common case): candidates [0, k) are generated once,
+//    kept in shared memory and counted per bucket (about one key per bucket
+//    on average, addressed by the top bits; 16-bit counts, no size limit).
+//    A scan of the counts gives every bucket its output offset; a second
+//    pass scatters the keys into bucket order; each key then finds its rank
+//    inside its bucket (four unrolled comparisons, a loop beyond), which is
+//    its output position; a coalesced copy writes the leaf and checks
+//    neighbours for repeats.  If a key repeats or a candidate was void, the
+//    first k candidates do not give k distinct values and the leaf goes to
+//    the probing path.
 //  bitmap path (complement leaves, and selections dense in a small range):
 //    an atomic OR sets bit v and tells whether it was already set; the
 //    read-out walks the bits in order.
@@ -44,10 +46,7 @@ constexpr uint32_t kHashCap = kLeafFastCap;         // largest selection of the 
 constexpr uint32_t kHashSlack = 64;                 // probing: slots past the end instead of wrap-around
 constexpr uint32_t kHashSlots = 2 * kHashCap + kHashSlack;
 constexpr uint32_t kBitmapBits = 32 * kHashSlots;  // largest leaf range of the bitmap path
-constexpr uint32_t kBucketWays = 8;                 // entries per bucket
-constexpr uint32_t kMaxBuckets = 2 * kHashCap / kBucketWays;
-constexpr uint32_t kSpillCap = 128;                 // side list of keys whose bucket was full
-constexpr uint32_t kWarpStage = 32 * kBucketWays + 32;   // outputs of one warp iteration (32 buckets)
+constexpr uint32_t kMaxBuckets = kHashCap + 64;   // bucket path: about one key per bucket
 
 template <typename KeyT>
 struct HashEmpty;
@@ -58,28 +57,28 @@ struct HashEmpty<uint64_t> { static constexpr uint64_t v = ~0ull; };
 
 template <typename KeyT, int NW>
 struct HashShared {
-    KeyT tab[kHashSlots];          // bucket entries / probing table / bitmap
-    KeyT wstage[NW][kWarpStage];   // per warp: the sorted keys of its current 32 buckets
-    uint32_t cnt[kMaxBuckets + 1]; // bucket counts, then their exclusive prefix
-    KeyT spill[kSpillCap];
-    KeyT spill_sorted[kSpillCap];
+    KeyT tab[kHashSlots];          // bucket path: keys (first k + 3), then keys in bucket order;
+                                   // probing table; bitmap; tallies
+    uint32_t cnt[kMaxBuckets / 2 + 1];   // bucket path: 16-bit counts, two per word, then offsets
     uint32_t scan_tmp[NW + 1];
     uint32_t warp_cnt[NW];
     uint32_t newcount[3];          // rounds: values added in round r go to newcount[r % 3]
     uint32_t topcount;             // probing, 32-bit keys: copies of 2^32-1 (it equals the empty mark)
     uint32_t overflow;             // probing ran past the slack
-    uint32_t nspill;
-    uint32_t flags;                // bucket path: 1 = void candidate, 2 = side list full
-    uint32_t nover;                // overfull buckets listed for the fix-up pass
-    uint32_t over[kSpillCap];
+    uint32_t flags;                // bucket path: 1 = void candidate
     uint64_t thr;                  // Lemire rejection threshold of the leaf
     uint64_t mult;                 // address multiplier of the current table
 };
 
 // Lemire rejection threshold for a leaf of size s: (2^32 - s) mod s for
-// 32-bit candidates, (2^64 - s) mod s for 64-bit ones.
+// 32-bit candidates (a 32-bit remainder), (2^64 - s) mod s for 64-bit ones.
 RS_DEV uint64_t lemire_threshold(uint64_t s) {
-    return s <= (1ull << 32) ? ((1ull << 32) - s) % s : (0ull - s) % s;
+    if (s == (1ull << 32)) return 0;
+    if (s < (1ull << 32)) {
+        const uint32_t s32 = (uint32_t)s;
+        return (0u - s32) % s32;
+    }
+    return (0ull - s) % s;
 }
 
 // Barrier over the NT threads of a leaf group (named barrier `ID`).
@@ -112,6 +111,21 @@ RS_DEV uint64_t slot_mult(uint64_t s, uint32_t T) {
     return (uint64_t)T >= s ? ~0ull : (uint64_t)(((unsigned __int128)T << 64) / s);
 }
 
+// A multiplier of the same kind computed by every thread on its own in
+// single precision, each step rounded down, so that mult <= T 2^width / s
+// and every slot stays below T.  Any such multiplier keeps the order of the
+// values, which is all the bucket path relies on.
+template <typename KeyT>
+RS_DEV uint64_t slot_mult_fast(uint64_t s, uint32_t T) {
+    const float q = __fdiv_rd((float)T, __ull2float_ru(s));   // <= T / s
+    if (sizeof(KeyT) == 4) {
+        const float m = __fmul_rd(q, 4294967296.0f);
+        return m >= 4294967295.0f ? 0xFFFFFFFFull : (uint64_t)__float2uint_rd(m);
+    }
+    const float m = __fmul_rd(q, 18446744073709551616.0f);
+    return m >= 18446744073709551615.0f ? ~0ull : __float2ull_rd(m);
+}
+
 RS_DEV uint32_t cas_key(uint32_t* p, uint32_t cmp, uint32_t val) { return atomicCAS(p, cmp, val); }
 RS_DEV uint64_t cas_key(uint64_t* p, uint64_t cmp, uint64_t val) {
     return (uint64_t)atomicCAS((unsigned long long*)p, (unsigned long long)cmp, (unsigned long long)val);
@@ -121,9 +135,9 @@ struct LeafRec {
     uint64_t lo, s, np, off, id;
 };
 
-// Walks the candidates [J, J+m) of the leaf's stream; calls f(v) for each
-// valid one and sets *void_seen if one was void.  32-bit words when
-// s <= 2^32, 64-bit values otherwise.
+// Walks the candidates [J, J+m) of the leaf's stream; calls f(rel, v) for
+// each valid one (rel = its index - J) and sets *void_seen if one was void.
+// 32-bit words when s <= 2^32, 64-bit values otherwise.
 template <int NT, typename F>
 RS_DEV void for_candidates(const LeafRec& r, uint64_t thr64, Key2 key, uint32_t tag, uint64_t J, uint32_t m,
                            uint32_t tid, bool* void_seen, F&& f) {
@@ -143,7 +157,7 @@ RS_DEV void for_candidates(const LeafRec& r, uint64_t thr64, Key2 key, uint32_t 
                 *void_seen = true;
                 return;
             }
-            f((uint64_t)(prod >> 32));
+            f(rel, (uint64_t)(prod >> 32));
         };
         for (uint32_t i = tid; i < nblk; i += 2 * NT) {
             const uint32_t i2 = i + NT;
@@ -179,28 +193,34 @@ RS_DEV void for_candidates(const LeafRec& r, uint64_t thr64, Key2 key, uint32_t 
                     *void_seen = true;
                     continue;
                 }
-                f(__umul64hi(xs[c], r.s));
+                f(rel, __umul64hi(xs[c], r.s));
             }
         }
     }
 }
 
-template <typename KeyT>
-RS_DEV void cmpswap(KeyT& a, KeyT& b) {
-    const KeyT lo = a < b ? a : b, hi = a < b ? b : a;
-    a = lo;
-    b = hi;
-}
-
-// Batcher's odd-even merge sort of 8 keys (19 comparators).
-template <typename KeyT>
-RS_DEV void sort8(KeyT (&x)[8]) {
-    cmpswap(x[0], x[1]); cmpswap(x[2], x[3]); cmpswap(x[4], x[5]); cmpswap(x[6], x[7]);
-    cmpswap(x[0], x[2]); cmpswap(x[1], x[3]); cmpswap(x[4], x[6]); cmpswap(x[5], x[7]);
-    cmpswap(x[1], x[2]); cmpswap(x[5], x[6]);
-    cmpswap(x[0], x[4]); cmpswap(x[1], x[5]); cmpswap(x[2], x[6]); cmpswap(x[3], x[7]);
-    cmpswap(x[2], x[4]); cmpswap(x[3], x[5]);
-    cmpswap(x[1], x[2]); cmpswap(x[3], x[4]); cmpswap(x[5], x[6]);
+// Exclusive prefix sums, in place, of the nb 16-bit counts packed two per
+// word in w[0 .. nb/2) (nb even).  Thread t owns Q consecutive words, Q odd
+// so that the threads' strided reads hit distinct banks.
+template <int NT>
+RS_DEV void scan_counts16(uint32_t* w, uint32_t nb, uint32_t* tmp, uint32_t tid) {
+    const uint32_t words = nb >> 1;
+    const uint32_t Q = ((words + NT - 1) / NT) | 1u;
+    const uint32_t w0 = min(tid * Q, words), w1 = min(w0 + Q, words);
+    uint32_t local = 0;
+    for (uint32_t i = w0; i < w1; ++i) {
+        const uint32_t x = w[i];
+        local += (x & 0xFFFFu) + (x >> 16);
+    }
+    uint32_t total;
+    uint32_t run = block_exclusive_scan<NT>(local, tmp, &total);
+    for (uint32_t i = w0; i < w1; ++i) {
+        const uint32_t x = w[i];
+        const uint32_t lo = run, hi = run + (x & 0xFFFFu);
+        w[i] = lo | (hi << 16);
+        run = hi + (x >> 16);
+    }
+    __syncthreads();
 }
 
 // Bucket path.  Returns true on success (leaf written), false if the leaf
@@ -208,121 +228,108 @@ RS_DEV void sort8(KeyT (&x)[8]) {
 template <typename KeyT, int NT, int BAR, bool WR>
 RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32>& sm, const LeafRec& r, Key2 key, uint32_t k,
                         uint64_t* __restrict__ dst, uint32_t tid) {
-    constexpr uint32_t W = kBucketWays;
     const uint32_t tag = WR ? TAG_LEAF_WR : TAG_LEAF_H;
-    const uint32_t nb = max(32u, ((2 * k + W - 1) / W + 31) & ~31u);
-    for (uint32_t i = tid; i <= nb; i += NT) sm.cnt[i] = 0;
-    if (tid == 0) {
-        sm.nspill = 0;
-        sm.flags = 0;
-        sm.nover = 0;
-        sm.mult = slot_mult<KeyT>(r.s, nb);
-        sm.thr = lemire_threshold(r.s);
-    }
+    const uint32_t nb = max(64u, (k + 63) & ~63u);   // even, <= kMaxBuckets
+    KeyT* A = sm.tab;                     // candidate j at A[j]; later the sorted leaf
+    KeyT* B = sm.tab + ((k + 3) & ~3u);   // keys in bucket order
+    uint32_t* cw = sm.cnt;                // count of bucket b: 16-bit half b & 1 of word b >> 1
+    const uint16_t* ch = reinterpret_cast<const uint16_t*>(sm.cnt);
+    for (uint32_t i = tid; i < nb / 2; i += NT) cw[i] = 0;
+    if (tid == 0) sm.flags = 0;
+    const uint64_t mult = slot_mult_fast<KeyT>(r.s, nb);
+    const uint64_t thr = lemire_threshold(r.s);
     group_sync<BAR, NT>();
-    const uint64_t mult = sm.mult, thr = sm.thr;
+    // pass 1: generate, keep, count per bucket
     bool void_seen = false;
-    for_candidates<NT>(r, thr, key, tag, 0, k, tid, &void_seen, [&](uint64_t v) {
+    for_candidates<NT>(r, thr, key, tag, 0, k, tid, &void_seen, [&](uint32_t j, uint64_t v) {
+        A[j] = (KeyT)v;
         const uint32_t b = hash_slot((KeyT)v, mult);
-        const uint32_t e = atomicAdd(&sm.cnt[b], 1u);
-        if (e < W) {
-            sm.tab[e * nb + b] = (KeyT)v;   // entry e of bucket b: transposed for conflict-free reads
-        } else {
-            const uint32_t o = atomicAdd(&sm.nspill, 1u);
-            if (o < kSpillCap) sm.spill[o] = (KeyT)v;
-            else atomicOr(&sm.flags, 2u);
-        }
+        atomicAdd(&cw[b >> 1], 1u << ((b & 1u) << 4));
     });
     if (void_seen) atomicOr(&sm.flags, 1u);
     group_sync<BAR, NT>();
-    const uint32_t flags = sm.flags;
-    const uint32_t nspill = min(sm.nspill, kSpillCap);
-    group_sync<BAR, NT>();   // everyone has read flags before the scan reuses scan_tmp
-    if (flags) return false;
-    // Warp 0 sorts the side list (by value, hence by bucket) while the block
-    // scans the counts; the scan's barriers publish it.
-    if (tid < 32) {
-        for (uint32_t i = tid; i < nspill; i += 32) {
-            const KeyT y = sm.spill[i];
-            uint32_t rank = 0;
-            for (uint32_t j = 0; j < nspill; ++j) {
-                const KeyT z = sm.spill[j];
-                rank += (z < y) || (z == y && j < i);
+    if (sm.flags) return false;   // read by all before anyone writes it again (several barriers away)
+    scan_counts16<NT>(cw, nb, sm.scan_tmp, tid);   // half b = first position of bucket b
+    // Passes 2, 3 and the copy take four independent keys per thread at a
+    // time so that their load -> address -> load chains overlap.
+    constexpr uint32_t U = 4;
+    // pass 2: scatter into bucket order; afterwards half b = end of bucket b
+    for (uint32_t j0 = tid; j0 < k; j0 += U * NT) {
+        KeyT x[U];
+        uint32_t b[U];
+#pragma unroll
+        for (uint32_t q = 0; q < U; ++q) {
+            x[q] = j0 + q * NT < k ? A[j0 + q * NT] : KeyT(0);
+            b[q] = hash_slot(x[q], mult);
+        }
+#pragma unroll
+        for (uint32_t q = 0; q < U; ++q) {
+            if (j0 + q * NT < k) {
+                const uint32_t sh = (b[q] & 1u) << 4;
+                B[(atomicAdd(&cw[b[q] >> 1], 1u << sh) >> sh) & 0xFFFFu] = x[q];
             }
-            sm.spill_sorted[rank] = y;
         }
     }
-    block_scan_counts<NT>(sm.cnt, nb, sm.scan_tmp);   // cnt[b] = offset of bucket b, cnt[nb] = k
-    // Each warp takes 32 consecutive buckets at a time, one per lane: sort,
-    // check for repeats, stage in the warp's buffer, then copy the run of
-    // output positions they cover with coalesced stores.
-    const uint32_t lane = tid & 31, warp = tid >> 5;
-    KeyT* ws = sm.wstage[warp];
-    const uint64_t base = r.lo + 1;
-    bool dup = false;
-    for (uint32_t b0 = warp * 32; b0 < nb; b0 += NT) {
-        const uint32_t b = b0 + lane;   // nb is a multiple of 32
-        const uint32_t q0 = sm.cnt[b0], q1 = sm.cnt[b0 + 32];
-        const bool direct = q1 - q0 > kWarpStage;   // too many spilled keys: write in place
-        const uint32_t p = sm.cnt[b], c = sm.cnt[b + 1] - p;
-        auto put = [&](uint32_t pos, KeyT v) {
-            if (direct) dst[pos] = base + v;
-            else ws[pos - q0] = v;
-        };
-        if (c > W) {
-            // overfull: the fix-up pass places this bucket with a whole warp
-            sm.over[atomicAdd(&sm.nover, 1u)] = b;
-        } else if (c > 0) {
-            KeyT x[8];
+    group_sync<BAR, NT>();
+    // pass 3: the rank of B[i] among its bucket's keys, ordered by (key,
+    // position in B), is its place in the sorted leaf
+    for (uint32_t i0 = tid; i0 < k; i0 += U * NT) {
+        KeyT x[U];
+        uint32_t s0[U], s1[U], rank[U];
 #pragma unroll
-            for (int t = 0; t < 8; ++t) x[t] = (uint32_t)t < c ? sm.tab[t * nb + b] : HashEmpty<KeyT>::v;
-            sort8(x);
+        for (uint32_t q = 0; q < U; ++q) {
+            const uint32_t i = i0 + q * NT;
+            x[q] = i < k ? B[i] : KeyT(0);
+            const uint32_t b = hash_slot(x[q], mult);
+            s0[q] = b ? ch[b - 1] : 0u;
+            s1[q] = i < k ? ch[b] : 0u;
+            rank[q] = s0[q];
+        }
 #pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                if ((uint32_t)t < c) {
-                    put(p + t, x[t]);
-                    if (t > 0 && x[t] == x[t - 1]) dup = true;
+        for (uint32_t u = 0; u < 4; ++u) {
+#pragma unroll
+            for (uint32_t q = 0; q < U; ++q) {
+                const uint32_t j = s0[q] + u;
+                if (j < s1[q]) {
+                    const KeyT y = B[j];
+                    rank[q] += (y < x[q]) || (y == x[q] && j < i0 + q * NT);
                 }
             }
         }
-        __syncwarp();
-        if (!direct) {
-            for (uint32_t o = lane; o < q1 - q0; o += 32) dst[q0 + o] = base + ws[o];
+#pragma unroll
+        for (uint32_t q = 0; q < U; ++q) {
+            for (uint32_t j = s0[q] + 4; j < s1[q]; ++j) {   // buckets of more than four keys
+                const KeyT y = B[j];
+                rank[q] += (y < x[q]) || (y == x[q] && j < i0 + q * NT);
+            }
         }
-        __syncwarp();
+#pragma unroll
+        for (uint32_t q = 0; q < U; ++q)
+            if (i0 + q * NT < k) A[rank[q]] = x[q];
     }
-    // The copy-outs above wrote placeholders over the ranges of overfull
-    // buckets; after this barrier the fix-up writes win.
     group_sync<BAR, NT>();
-    const uint32_t nover = sm.nover;   // at most one per spilled key, so <= kSpillCap
-    bool fail = false;
-    for (uint32_t o = warp; o < nover; o += NT / 32) {
-        const uint32_t b = sm.over[o];
-        const uint32_t p = sm.cnt[b], c = sm.cnt[b + 1] - p;
-        // the spilled keys of bucket b are a run of the sorted side list
-        uint32_t lo = 0, hi = nspill;
-        while (lo < hi) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (hash_slot(sm.spill_sorted[mid], mult) < b) lo = mid + 1; else hi = mid;
+    // copy out; without replacement a key equal to its successor is a repeat
+    const uint64_t base = r.lo + 1;
+    bool dup = false;
+    for (uint32_t i0 = tid; i0 < k; i0 += U * NT) {
+        KeyT x[U], y[U];
+#pragma unroll
+        for (uint32_t q = 0; q < U; ++q) {
+            const uint32_t i = i0 + q * NT;
+            x[q] = i < k ? A[i] : KeyT(0);
+            y[q] = (!WR && i + 1 < k) ? A[i + 1] : KeyT(0);
         }
-        if (c > 32) {   // more keys than lanes: leave the leaf to the probing path
-            fail = true;
-            continue;
+#pragma unroll
+        for (uint32_t q = 0; q < U; ++q) {
+            const uint32_t i = i0 + q * NT;
+            if (i < k) {
+                if (!WR && i + 1 < k && y[q] == x[q]) dup = true;
+                dst[i] = base + x[q];
+            }
         }
-        const bool has = lane < c;
-        KeyT y = HashEmpty<KeyT>::v;
-        if (has) y = lane < W ? sm.tab[lane * nb + b] : sm.spill_sorted[lo + lane - W];
-        uint32_t rank = 0;
-        for (uint32_t j = 0; j < c; ++j) {
-            const KeyT z = __shfl_sync(0xFFFFFFFFu, y, j);
-            rank += (z < y) || (z == y && j < lane);
-            if (has && z == y && j != lane) dup = true;
-        }
-        if (has) dst[p + rank] = base + y;
     }
-    if (WR) dup = false;
-    const bool any_fail = group_sync_or<BAR, NT>(dup || fail);
-    return !any_fail;   // on a repeat the probing path rewrites the whole leaf
+    if (WR) return true;
+    return !group_sync_or<BAR, NT>(dup);   // a repeat: the probing path rewrites the whole leaf
 }
 
 // Rounds of distinct insertion shared by the bitmap and probing paths:
@@ -343,7 +350,7 @@ RS_DEV bool distinct_rounds(uint32_t* newcount, const LeafRec& r, uint64_t thr, 
         }
         uint32_t added = 0;
         bool vs = false;
-        for_candidates<NT>(r, thr, key, tag, J, m, tid, &vs, [&](uint64_t v) { added += insert(v); });
+        for_candidates<NT>(r, thr, key, tag, J, m, tid, &vs, [&](uint32_t, uint64_t v) { added += insert(v); });
         if (added) atomicAdd(&newcount[round % 3], added);
         // Counter (round+1) % 3 was last read before the previous round's
         // barrier, which this thread has passed, and is next written after
