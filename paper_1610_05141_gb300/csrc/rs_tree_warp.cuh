@@ -12,7 +12,18 @@
 //    terms of short sums, ...), the whole warp evaluates them together, and
 //    each lane then assembles its acceptance test from the results in
 //    exactly the operations and order of the scalar definition
-//    (rs_deviates.cuh), so the results are the same bits.
+//    (rs_deviates.cuh), so the results are the same bits;
+//  - parallel trials: on levels with few nodes a node gets a group of G
+//    lanes, lane r of the group evaluating trial t + r.  Trial t of node v
+//    uses only Philox block (v, t), so trials are independent; the node
+//    takes the lowest accepted trial index, exactly the sequential loop's
+//    choice, after about one round instead of the slowest node's many;
+//  - parallel terms (tree_terms_warp, the smallest levels): an FP64 warp
+//    instruction costs the same whatever the number of active lanes, so a
+//    level with few nodes is bound by the length of one trial's instruction
+//    stream.  There the four log-factorial differences of a trial go to
+//    four lanes, which run one stream of the scalar dsd() side by side, and
+//    are summed in the scalar order after shuffles.
 #pragma once
 #include "rs_deviates.cuh"
 
@@ -70,12 +81,18 @@ RS_DEV double lfd_eval(uint64_t x, uint64_t y, const double* __restrict__ tab, L
     return (X + 0.5) * lp + D * L.next() - D + (stirling_tail(X) - stirling_tail(Y));
 }
 
+// Signed difference (dsd): the larger argument first, one call, then the
+// sign -- selects instead of two inlined calls, so that lanes whose
+// arguments come in opposite orders do not run both copies one after the
+// other.
 RS_DEV void sd_args(uint64_t x, uint64_t y, LfdArgs& A) {
-    if (x >= y) lfd_args(x, y, A);
-    else lfd_args(y, x, A);
+    const bool pos = x >= y;
+    lfd_args(pos ? x : y, pos ? y : x, A);
 }
 RS_DEV double sd_eval(uint64_t x, uint64_t y, const double* __restrict__ tab, LfdLogs& L) {
-    return x >= y ? lfd_eval(x, y, tab, L) : -lfd_eval(y, x, tab, L);
+    const bool pos = x >= y;
+    const double v = lfd_eval(pos ? x : y, pos ? y : x, tab, L);
+    return pos ? v : -v;
 }
 
 // Parameters of one node's ratio-of-uniforms loop (rs_deviates.cuh).
@@ -99,11 +116,11 @@ RS_DEV void write_children(NodeRec* __restrict__ rec, uint64_t v, const NodeRec&
 // no samples, a fast path, or inversion.
 template <bool WR>
 RS_DEV bool node_setup(NodeRec* __restrict__ rec, uint64_t v, Key2 key, const double* __restrict__ tab, int* status,
-                       RouNode* q) {
+                       RouNode* q, bool writer = true) {
     const NodeRec r = rec[v];
     const uint64_t K = r.S / 2;
     auto finish = [&](uint64_t L) {
-        write_children(rec, v, r, K, L);
+        if (writer) write_children(rec, v, r, K, L);
         return false;
     };
     if (r.c == 0) return finish(0);
@@ -165,39 +182,44 @@ RS_DEV bool node_setup(NodeRec* __restrict__ rec, uint64_t v, Key2 key, const do
     return true;
 }
 
-// Processes nodes v0 .. v0+count-1 (one level) with the calling warp.
-// `logs` is this warp's scratch of 32 * kLogSlots doubles in shared memory.
+// Processes nodes v0 .. v0+count-1 (one level) with the calling warp, G
+// lanes per node (G a power of two, 1 to 32).  `logs` is this warp's
+// scratch of 32 * kLogSlots doubles in shared memory.
 template <bool WR>
 RS_DEV void tree_batch_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t count, Key2 key,
-                            const double* __restrict__ tab, int* status, double* logs) {
+                            const double* __restrict__ tab, int* status, double* logs, uint32_t G = 1) {
     const uint32_t lane = threadIdx.x & 31;
-    const uint32_t lt_mask = (1u << lane) - 1u;
+    const uint32_t r = lane & (G - 1);         // trial offset inside the group
+    const uint32_t gbase = lane - r;           // the group's first lane
+    const uint32_t gmask = G == 32 ? 0xFFFFFFFFu : ((1u << G) - 1u) << gbase;
     double* mine = logs + lane * kLogSlots;
     RouNode q;
-    bool active = false;
+    bool active = false;                       // the same in all lanes of a group
     uint32_t next = 0;   // batch cursor (warp-uniform)
     for (;;) {
-        // refill free lanes, in order, until none is free or the batch is used up
+        // refill free groups, in order, until none is free or the batch is used up
         for (;;) {
-            const uint32_t freem = __ballot_sync(0xFFFFFFFFu, !active);
+            const uint32_t freem = __ballot_sync(0xFFFFFFFFu, !active && r == 0);
             if (freem == 0 || next >= count) break;
             const uint32_t take = min((uint32_t)__popc(freem), count - next);
-            const uint32_t rank = __popc(freem & lt_mask);
-            if (!active && rank < take) active = node_setup<WR>(rec, v0 + next + rank, key, tab, status, &q);
+            const uint32_t rank = __popc(freem & ((1u << gbase) - 1u));
+            if (!active && rank < take)
+                active = node_setup<WR>(rec, v0 + next + rank, key, tab, status, &q, r == 0);
             next += take;
         }
         if (__ballot_sync(0xFFFFFFFFu, active) == 0) break;
         // one trial per active lane: uniforms, candidate, logarithm arguments
+        const uint64_t t = (uint64_t)q.trial + r;   // this lane's trial
         double U = 1.0;
         uint64_t k = 0;
         bool inr = false;
         int nargs = 0;
         if (active) {
-            const uint4 blk = philox_block(q.trial, TAG_SPLIT, q.v, key);
+            const uint4 blk = philox_block((uint32_t)t, TAG_SPLIT, q.v, key);
             U = u_open(((uint64_t)blk.y << 32) | blk.x);
             const double V = v_closed(((uint64_t)blk.w << 32) | blk.z);
             const double X = q.alpha + q.h * (V - 0.5) / U;
-            inr = !(X < 0.0 || X >= q.top);
+            inr = !(X < 0.0 || X >= q.top) && t < kRouMaxTrials;
             if (inr) {
                 k = (uint64_t)X;
                 LfdArgs A{mine, 0};
@@ -251,37 +273,138 @@ RS_DEV void tree_batch_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
                 if (slot[j]) *slot[j] = x[j];
         }
         __syncwarp();
+        bool acc = false;
+        uint64_t L = 0;
+        if (active && inr) {
+            LfdLogs Lg{mine, 0};
+            const double lU = Lg.next();
+            double T;
+            if (WR) {
+                T = sd_eval(q.M, k, tab, Lg) + sd_eval(q.a - q.M, q.a - k, tab, Lg) +
+                    (double)((int64_t)k - (int64_t)q.M) * q.logr;
+            } else {
+                const uint64_t m = q.S - q.a - q.b;
+                T = sd_eval(q.M, k, tab, Lg) + sd_eval(q.a - q.M, q.a - k, tab, Lg) +
+                    sd_eval(q.b - q.M, q.b - k, tab, Lg) + sd_eval(m + q.M, m + k, tab, Lg);
+            }
+            if (2.0 * lU <= T) {
+                acc = true;
+                L = k;
+                if (!WR) {
+                    if (q.flipN) L = q.Kp - L;
+                    if (q.flipK) L = q.n_in - L;
+                }
+            }
+        }
+        // the group takes its lowest accepted trial
+        const uint32_t accm = __ballot_sync(0xFFFFFFFFu, acc) & gmask;
+        const uint64_t Lsel = __shfl_sync(0xFFFFFFFFu, L, accm ? __ffs(accm) - 1 : lane);
         if (active) {
             bool done = false;
-            uint64_t L = 0;
-            if (inr) {
-                LfdLogs Lg{mine, 0};
-                const double lU = Lg.next();
-                double T;
-                if (WR) {
-                    T = sd_eval(q.M, k, tab, Lg) + sd_eval(q.a - q.M, q.a - k, tab, Lg) +
-                        (double)((int64_t)k - (int64_t)q.M) * q.logr;
-                } else {
-                    const uint64_t m = q.S - q.a - q.b;
-                    T = sd_eval(q.M, k, tab, Lg) + sd_eval(q.a - q.M, q.a - k, tab, Lg) +
-                        sd_eval(q.b - q.M, q.b - k, tab, Lg) + sd_eval(m + q.M, m + k, tab, Lg);
-                }
-                if (2.0 * lU <= T) {
-                    done = true;
-                    L = k;
-                    if (!WR) {
-                        if (q.flipN) L = q.Kp - L;
-                        if (q.flipK) L = q.n_in - L;
-                    }
-                }
-            }
-            if (!done && ++q.trial >= kRouMaxTrials) {
-                set_status(status, RS_EITER);
+            uint64_t Lout = 0;
+            if (accm) {
                 done = true;
-                L = 0;
+                Lout = Lsel;
+            } else {
+                q.trial += G;
+                if (q.trial >= kRouMaxTrials) {
+                    if (r == 0) set_status(status, RS_EITER);
+                    done = true;
+                }
             }
             if (done) {
-                write_children(rec, q.v, NodeRec{q.lo, q.S, q.c, q.off}, q.K, L);
+                if (r == 0) write_children(rec, q.v, NodeRec{q.lo, q.S, q.c, q.off}, q.K, Lout);
+                active = false;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Nodes v0 .. v0+count-1 (count <= 32 / G) with G lanes per node, G a
+// multiple of 4: lane 4p + j of a node's group evaluates term j of trial
+// t + p (terms: the four differences of ln x! of the hypergeometric test, or
+// the two of the binomial one).  All lanes compute ln U; the four lanes of a
+// trial exchange their terms and reach the same decision.
+template <bool WR>
+RS_DEV void tree_terms_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t count, Key2 key,
+                            const double* __restrict__ tab, int* status, uint32_t G) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t r = lane & (G - 1);
+    const uint32_t gbase = lane - r;
+    const uint32_t gmask = G == 32 ? 0xFFFFFFFFu : ((1u << G) - 1u) << gbase;
+    const uint32_t p = r >> 2, j = r & 3u, tbase = lane & ~3u;
+    const uint32_t grp = lane / G;
+    RouNode q;
+    bool active = grp < count &&
+                  node_setup<WR>(rec, v0 + grp, key, tab, status, &q, r == 0);
+    while (__ballot_sync(0xFFFFFFFFu, active)) {
+        const uint64_t t = (uint64_t)q.trial + p;
+        double U = 1.0, T = 0.0, term = 0.0;
+        uint64_t k = 0;
+        bool inr = false;
+        if (active) {
+            const uint4 blk = philox_block((uint32_t)t, TAG_SPLIT, q.v, key);
+            U = u_open(((uint64_t)blk.y << 32) | blk.x);
+            const double V = v_closed(((uint64_t)blk.w << 32) | blk.z);
+            const double X = q.alpha + q.h * (V - 0.5) / U;
+            inr = !(X < 0.0 || X >= q.top) && t < kRouMaxTrials;
+            if (inr) k = (uint64_t)X;
+            // this lane's difference ln x! - ln y!, picked with selects so
+            // that all lanes run one copy of dlfdiff (dsd's sign rule after)
+            uint64_t x = 0, y = 0;
+            if (inr) {
+                if (WR) {
+                    x = j == 0 ? q.M : (j == 1 ? q.a - q.M : 0);
+                    y = j == 0 ? k : (j == 1 ? q.a - k : 0);
+                } else {
+                    const uint64_t m = q.S - q.a - q.b;
+                    const uint64_t base = j == 0 ? 0 : (j == 1 ? q.a : (j == 2 ? q.b : m));
+                    x = j == 0 ? q.M : (j == 3 ? base + q.M : base - q.M);
+                    y = j == 0 ? k : (j == 3 ? base + k : base - k);
+                }
+            }
+            const bool pos = x >= y;
+            const double v = dlfdiff(pos ? x : y, pos ? y : x, tab);
+            term = pos ? v : -v;
+        }
+        const double lU = dlog(U);
+        const double t0 = __shfl_sync(0xFFFFFFFFu, term, tbase);
+        const double t1 = __shfl_sync(0xFFFFFFFFu, term, tbase + 1);
+        const double t2 = __shfl_sync(0xFFFFFFFFu, term, tbase + 2);
+        const double t3 = __shfl_sync(0xFFFFFFFFu, term, tbase + 3);
+        bool acc = false;
+        uint64_t L = 0;
+        if (active && inr) {
+            if (WR) T = t0 + t1 + (double)((int64_t)k - (int64_t)q.M) * q.logr;
+            else T = t0 + t1 + t2 + t3;
+            if (2.0 * lU <= T) {
+                acc = true;
+                L = k;
+                if (!WR) {
+                    if (q.flipN) L = q.Kp - L;
+                    if (q.flipK) L = q.n_in - L;
+                }
+            }
+        }
+        // the group takes its lowest accepted trial
+        const uint32_t accm = __ballot_sync(0xFFFFFFFFu, acc) & gmask;
+        const uint64_t Lsel = __shfl_sync(0xFFFFFFFFu, L, accm ? __ffs(accm) - 1 : lane);
+        if (active) {
+            bool done = false;
+            uint64_t Lout = 0;
+            if (accm) {
+                done = true;
+                Lout = Lsel;
+            } else {
+                q.trial += G / 4;
+                if (q.trial >= kRouMaxTrials) {
+                    if (r == 0) set_status(status, RS_EITER);
+                    done = true;
+                }
+            }
+            if (done) {
+                if (r == 0) write_children(rec, q.v, NodeRec{q.lo, q.S, q.c, q.off}, q.K, Lout);
                 active = false;
             }
         }
