@@ -66,12 +66,15 @@ __global__ void __launch_bounds__(kTreeWarps * 32) tree_terms_kernel(NodeRec* __
 }
 
 // Lanes per node on a level of `nodes` nodes: the largest power of two up to
-// 32 that keeps nodes * G within about four warps per SM.  G >= 4: parallel
-// terms and trials; G = 2: parallel trials; G = 1: a node per lane.
+// 32 that keeps nodes * G within about four warps per SM, and at least 4
+// (four lanes share a trial) up to 512 nodes per SM.  G >= 4: parallel
+// terms and trials; G = 1: a node per lane with refill, which does the
+// least FP64 work per trial and wins once a level has more nodes than that.
 uint32_t lanes_per_node(uint64_t nodes, int sms) {
     const uint64_t target = (uint64_t)sms * 4 * 32;
     uint32_t G = 1;
     while (G < 32 && nodes * G * 2 <= target) G *= 2;
+    if (G < 4) G = nodes <= (uint64_t)sms * 512 ? 4 : 1;
     return G;
 }
 
