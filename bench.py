@@ -40,16 +40,18 @@ BYTES_PER_SAMPLE = 8
 WORKLOAD = "sorted sampling without replacement: n=1e9 distinct uint64 from 1..2^50, n0=4096 (2^18 leaves)"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_PATH = os.path.join(ROOT, "profiles", "leaf_kernel_traffic.json")
-LEAF_SOURCES = ["rs_leaf.cu", "rs_leaf.cuh", "rs_block.cuh", "rs_rng.cuh", "rs_common.cuh", "rs_internal.h"]
+LEAF_SOURCES = ["rs_leaf.cu", "rs_hash_leaf.cuh", "rs_big_leaf.cuh", "rs_leaf.cuh", "rs_block.cuh", "rs_rng.cuh",
+                "rs_common.cuh", "rs_internal.h"]
 
 
-def set_workload(n, log2N):
+def set_workload(n, log2N, n0=None):
     """Smaller cases of the same shape (used for ncu captures of a few GB)."""
-    global N_SAMPLES, UNIVERSE, WORKLOAD
-    if n is None and log2N is None:
+    global N_SAMPLES, UNIVERSE, WORKLOAD, N0
+    if n is None and log2N is None and n0 is None:
         return
     N_SAMPLES = n if n is not None else N_SAMPLES
     UNIVERSE = 2**log2N if log2N is not None else UNIVERSE
+    N0 = n0 if n0 is not None else N0
     WORKLOAD = (f"sorted sampling without replacement: n={N_SAMPLES} distinct uint64 from 1..2^{UNIVERSE.bit_length() - 1}"
                 f", n0={N0} (reduced case)")
 
@@ -604,8 +606,9 @@ def main():
     ap.add_argument("--serve-arena-gb", type=int, default=64)
     ap.add_argument("--n", type=int, default=None, help="smaller n (profiling cases only)")
     ap.add_argument("--log2N", type=int, default=None, help="smaller universe 2^log2N (profiling cases only)")
+    ap.add_argument("--n0", type=int, default=None, help="other leaf size (profiling cases only)")
     args = ap.parse_args()
-    set_workload(args.n, args.log2N)
+    set_workload(args.n, args.log2N, args.n0)
     if args.impl == "reference":
         run_reference(args)
     else:
