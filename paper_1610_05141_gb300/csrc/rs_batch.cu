@@ -257,13 +257,13 @@ uint64_t leaf_of_position(uint64_t N, int D, uint64_t pos) {
 }
 
 void GroupPlan::request_cost(const rs_request& q, uint64_t* up, uint64_t* work) {
-    *up = sizeof(BatchReq) + 16;
+    *up = sizeof(BatchReq);
     *work = 0;
     if (q.n == 0 || q.n0 == 0) return;
     const int D = plan_depth(q.n, q.N, q.n0);
     uint64_t items = 0;
     for (int l = 0; l < D; ++l) items += std::max<uint64_t>(1, (1ull << l) / kBatchTreeBatch);
-    *up += items * sizeof(BatchTreeItem);
+    *up += items * sizeof(BatchTreeItem) + (1ull << D) * sizeof(LeafDesc);
     *work = (2ull << D) * sizeof(NodeRec) + (1ull << D) * 4;
 }
 
@@ -324,9 +324,7 @@ void GroupPlan::build(const rs_request* reqs, uint64_t* const* out_ptrs, uint32_
         const uint64_t nleaves = 1ull << D;
         const uint64_t smax = (q.N >> D) + ((q.N & (nleaves - 1)) ? 1 : 0);
         Sub& G = groups_[group_of((int)q.kind, smax > (1ull << 32))];
-        if (G.p64.empty()) G.p64.push_back(0);
-        G.a32.push_back(r);
-        G.p64.push_back(G.p64.back() + nleaves);
+        for (uint64_t i = 0; i < nleaves; ++i) G.desc.push_back(LeafDesc{b.node_base + nleaves + i, r, (uint32_t)i});
         G.n1 += nleaves;
         if (q.kind != RS_KIND_B) bound = std::max<uint64_t>(bound, wr ? q.n : std::min<uint64_t>(q.n, smax - smax / 2));
     }
@@ -385,10 +383,7 @@ void GroupPlan::layout() {
     o_reqs_ = take(up, reqs_.size() * sizeof(BatchReq));
     o_levels_.clear();
     for (auto& lv : levels_) o_levels_.push_back(take(up, lv.size() * sizeof(BatchTreeItem)));
-    for (Sub& G : groups_) {
-        G.o_a32 = take(up, G.a32.size() * 4);
-        G.o_p64 = take(up, G.p64.size() * 8);
-    }
+    for (Sub& G : groups_) G.o_desc = take(up, G.desc.size() * sizeof(LeafDesc));
     o_qdesc_ = take(up, qdesc_.size() * sizeof(QueryDesc));
     for (Sub& G : qgroups_) {
         G.o_a32 = take(up, G.a32.size() * 4);
@@ -428,10 +423,7 @@ void GroupPlan::bind(unsigned char* up, unsigned char* work, void* big, unsigned
     put(o_reqs_, reqs_.data(), reqs_.size() * sizeof(BatchReq));
     for (size_t l = 0; l < levels_.size(); ++l)
         put(o_levels_[l], levels_[l].data(), levels_[l].size() * sizeof(BatchTreeItem));
-    for (const Sub& G : groups_) {
-        put(G.o_a32, G.a32.data(), G.a32.size() * 4);
-        put(G.o_p64, G.p64.data(), G.p64.size() * 8);
-    }
+    for (const Sub& G : groups_) put(G.o_desc, G.desc.data(), G.desc.size() * sizeof(LeafDesc));
     put(o_qdesc_, qdesc_.data(), qdesc_.size() * sizeof(QueryDesc));
     for (const Sub& G : qgroups_) {
         put(G.o_a32, G.a32.data(), G.a32.size() * 4);
@@ -461,9 +453,7 @@ int GroupPlan::issue(const double* tab, int sms, uint64_t* pool, int* status, cu
         for (int gi = 0; !rc && gi < 5; ++gi) {
             const Sub& G = groups_[gi];
             if (G.n1 == 0) continue;
-            BatchGroupView V{reqs, reinterpret_cast<const uint32_t*>(up_ + G.o_a32),
-                             reinterpret_cast<const uint64_t*>(up_ + G.o_p64), (uint32_t)G.a32.size(), G.n1,
-                             nodes, pool, status};
+            BatchGroupView V{reqs, reinterpret_cast<const LeafDesc*>(up_ + G.o_desc), G.n1, nodes, pool, status};
             rc = issue_leaves(V, G.kind, G.wide, reinterpret_cast<uint32_t*>(work_ + G.o_ovf1),
                               counters + counter_of(0, gi), big_, big_kmax_, per_sm_, sms, st, &nl);
         }

@@ -33,13 +33,17 @@ struct BatchTreeItem {
     uint64_t v0;
 };
 
-// The leaves of a group: requests req_of[0..m) in order, request req_of[i]
-// owning group leaves [prefix[i], prefix[i+1]).
+// Group leaf g: its node record nodes[node], request req, leaf index i of
+// that request (heap id 2^D + i).
+struct __align__(16) LeafDesc {
+    uint64_t node;
+    uint32_t req, i;
+};
+
+// The leaves of a group, one descriptor each (one load resolves a leaf).
 struct BatchGroupView {
     const BatchReq* reqs;
-    const uint32_t* req_of;
-    const uint64_t* prefix;
-    uint32_t m;
+    const LeafDesc* desc;
     uint64_t nleaves;
     NodeRec* nodes;
     uint64_t* pool;
@@ -65,17 +69,14 @@ RS_DEV uint32_t owner_of(const uint64_t* __restrict__ prefix, uint32_t m, uint64
 }
 
 RS_DEV ResolvedLeaf resolve_leaf(const BatchGroupView& G, uint64_t g) {
-    const uint32_t i = owner_of(G.prefix, G.m, g);
-    const uint32_t r = G.req_of[i];
-    const BatchReq q = G.reqs[r];
-    const uint64_t first = 1ull << q.D;
-    const uint64_t id = first + (g - G.prefix[i]);
+    const LeafDesc d = G.desc[g];
+    const BatchReq& q = G.reqs[d.req];
     ResolvedLeaf L;
-    L.rec = G.nodes[q.node_base + id];
-    L.id = id;
+    L.rec = G.nodes[d.node];
+    L.id = (1ull << q.D) + d.i;
     L.seed = q.seed;
     L.out = q.out_ptr ? q.out_ptr : G.pool + q.out_off;
-    L.status = G.status + r;
+    L.status = G.status + d.req;
     return L;
 }
 

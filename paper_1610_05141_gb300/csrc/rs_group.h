@@ -78,12 +78,13 @@ private:
     struct Sub {   // a leaf group (requests) or query subgroup, one kernel flavour
         int kind = 0;
         bool wide = false;
-        // requests: req_of/prefix; queries: bound items, then interior q_of/prefix
+        // requests: leaf descriptors; queries: bound items, then interior q_of/prefix
+        std::vector<LeafDesc> desc;
         std::vector<uint32_t> a32, b32;
         std::vector<uint64_t> p64;
         uint64_t n1 = 0, n2 = 0;          // leaves (requests) | boundary items, interior leaves (queries)
-        size_t o_a32 = 0, o_b32 = 0, o_p64 = 0;   // upload offsets
-        size_t o_ovf1 = 0, o_ovf2 = 0;            // work offsets
+        size_t o_desc = 0, o_a32 = 0, o_b32 = 0, o_p64 = 0;   // upload offsets
+        size_t o_ovf1 = 0, o_ovf2 = 0;                        // work offsets
     };
     std::vector<BatchReq> reqs_;
     std::vector<std::vector<BatchTreeItem>> levels_;

@@ -18,9 +18,12 @@
 //    pass scatters the keys into bucket order; each key then finds its rank
 //    inside its bucket (four unrolled comparisons, a loop beyond), which is
 //    its output position; a coalesced copy writes the leaf and checks
-//    neighbours for repeats.  If a key repeats or a candidate was void, the
-//    first k candidates do not give k distinct values and the leaf goes to
-//    the probing path.
+//    neighbours for repeats.  When the leaf size does not divide 2^32 (2^64)
+//    some candidates are void: candidates are then generated one Philox
+//    block per thread at a time and the valid ones numbered in index order
+//    with a block scan, so that exactly the first k valid ones are kept.  If
+//    a key repeats, the first k valid candidates do not give k distinct
+//    values and the leaf goes to the probing path.
 //  bitmap path (complement leaves, and selections dense in a small range):
 //    an atomic OR sets bit v and tells whether it was already set; the
 //    read-out walks the bits in order.
@@ -65,7 +68,6 @@ struct HashShared {
     uint32_t newcount[3];          // rounds: values added in round r go to newcount[r % 3]
     uint32_t topcount;             // probing, 32-bit keys: copies of 2^32-1 (it equals the empty mark)
     uint32_t overflow;             // probing ran past the slack
-    uint32_t flags;                // bucket path: 1 = void candidate
     uint64_t thr;                  // Lemire rejection threshold of the leaf
     uint64_t mult;                 // address multiplier of the current table
 };
@@ -235,20 +237,63 @@ RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32>& sm, const LeafRec& r, Key2 ke
     uint32_t* cw = sm.cnt;                // count of bucket b: 16-bit half b & 1 of word b >> 1
     const uint16_t* ch = reinterpret_cast<const uint16_t*>(sm.cnt);
     for (uint32_t i = tid; i < nb / 2; i += NT) cw[i] = 0;
-    if (tid == 0) sm.flags = 0;
     const uint64_t mult = slot_mult_fast<KeyT>(r.s, nb);
     const uint64_t thr = lemire_threshold(r.s);
     group_sync<BAR, NT>();
     // pass 1: generate, keep, count per bucket
-    bool void_seen = false;
-    for_candidates<NT>(r, thr, key, tag, 0, k, tid, &void_seen, [&](uint32_t j, uint64_t v) {
+    auto keep = [&](uint32_t j, uint64_t v) {
         A[j] = (KeyT)v;
         const uint32_t b = hash_slot((KeyT)v, mult);
         atomicAdd(&cw[b >> 1], 1u << ((b & 1u) << 4));
-    });
-    if (void_seen) atomicOr(&sm.flags, 1u);
-    group_sync<BAR, NT>();
-    if (sm.flags) return false;   // read by all before anyone writes it again (several barriers away)
+    };
+    if (thr == 0) {
+        // no candidate can be void: candidates [0, k) are the first k valid ones
+        bool void_seen = false;
+        for_candidates<NT>(r, thr, key, tag, 0, k, tid, &void_seen, keep);
+        group_sync<BAR, NT>();
+    } else {
+        // rounds of one Philox block per thread: the valid candidates of a
+        // round are numbered in index order by a block scan; the first k kept
+        const bool w32 = r.s <= (1ull << 32);
+        uint32_t got = 0;
+        for (uint64_t b0 = 0; got < k; b0 += NT) {
+            if (b0 >= (1ull << 32)) return false;   // the stream ran out: the probing path reports it
+            const uint64_t blk = b0 + tid;
+            uint64_t v[4] = {0, 0, 0, 0};
+            uint32_t valid = 0;
+            if (blk < (1ull << 32)) {
+                const uint4 w = philox_block((uint32_t)blk, tag, r.id, key);
+                if (w32) {
+                    const uint32_t s32 = (uint32_t)(r.s - 1), thr32 = (uint32_t)thr;
+                    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const uint64_t prod = (uint64_t)ws[c] * s32 + ws[c];   // w * s, exact
+                        v[c] = prod >> 32;
+                        valid |= ((uint32_t)prod >= thr32 ? 1u : 0u) << c;
+                    }
+                } else {
+                    const uint64_t xs[2] = {((uint64_t)w.y << 32) | w.x, ((uint64_t)w.w << 32) | w.z};
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        v[c] = __umul64hi(xs[c], r.s);
+                        valid |= (xs[c] * r.s >= thr ? 1u : 0u) << c;
+                    }
+                }
+            }
+            uint32_t total;
+            uint32_t rank = got + block_exclusive_scan<NT>((uint32_t)__popc(valid), sm.scan_tmp, &total);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if ((valid >> c) & 1u) {
+                    if (rank < k) keep(rank, v[c]);
+                    ++rank;
+                }
+            }
+            got += total;
+        }
+        group_sync<BAR, NT>();
+    }
     scan_counts16<NT>(cw, nb, sm.scan_tmp, tid);   // half b = first position of bucket b
     // Passes 2, 3 and the copy take four independent keys per thread at a
     // time so that their load -> address -> load chains overlap.

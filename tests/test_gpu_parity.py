@@ -62,6 +62,8 @@ H_CASES = [
     (100, 150, 16, 1),                  # depth capped by N
     (123457, 3906250 * 3 + 17, 21, 333),
     (8191, 2**20, 22, 8191),            # one leaf near the shared-memory capacity
+    (2 * 10**5, (2**31 + 12345) * 64, 31, 4096),   # leaves just above 2^31: half the candidates void
+    (4000, 2**61 + 999, 33, 4096),                 # one leaf, 64-bit candidates, an eighth void
 ]
 
 
@@ -84,6 +86,7 @@ WR_CASES = [
     (50, 3, 3, 4),
     (10**5, 2**62, 4, 4096),
     (77777, 10**9 + 7, 5, 100),
+    (10**5, (2**31 + 777) * 32, 6, 4096),   # half the candidates void
 ]
 
 
