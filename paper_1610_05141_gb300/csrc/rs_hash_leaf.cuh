@@ -22,8 +22,11 @@
 //    some candidates are void: candidates are then generated one Philox
 //    block per thread at a time and the valid ones numbered in index order
 //    with a block scan, so that exactly the first k valid ones are kept.  If
-//    a key repeats, the first k valid candidates do not give k distinct
-//    values and the leaf goes to the probing path.
+//    a key repeats (without replacement), the distinct values are kept and
+//    one warp draws the missing ones from the following candidates, each
+//    tested against the set (binary search) and against its batch, so that
+//    the set is still the first k distinct valid candidates; the two sorted
+//    lists are then merged into the output.
 //  bitmap path (complement leaves, and selections dense in a small range):
 //    an atomic OR sets bit v and tells whether it was already set; the
 //    read-out walks the bits in order.
@@ -68,6 +71,9 @@ struct HashShared {
     uint32_t newcount[3];          // rounds: values added in round r go to newcount[r % 3]
     uint32_t topcount;             // probing, 32-bit keys: copies of 2^32-1 (it equals the empty mark)
     uint32_t overflow;             // probing ran past the slack
+    uint64_t jnext;                // bucket path: index of the candidate after the k-th valid one
+    uint32_t nadded;               // bucket path: values drawn after a repeat
+    uint32_t repair_fail;
     uint64_t thr;                  // Lemire rejection threshold of the leaf
     uint64_t mult;                 // address multiplier of the current table
 };
@@ -225,6 +231,119 @@ RS_DEV void scan_counts16(uint32_t* w, uint32_t nb, uint32_t* tmp, uint32_t tid)
     __syncthreads();
 }
 
+// Candidate j of the leaf's stream (the same definition as for_candidates):
+// false if it is void.
+RS_DEV bool candidate_at(const LeafRec& r, uint64_t thr, Key2 key, uint32_t tag, uint64_t j, uint64_t* v) {
+    if (r.s <= (1ull << 32)) {
+        const uint4 w = philox_block((uint32_t)(j >> 2), tag, r.id, key);
+        const uint32_t c = (uint32_t)(j & 3);
+        const uint32_t x = c == 0 ? w.x : (c == 1 ? w.y : (c == 2 ? w.z : w.w));
+        const uint64_t prod = (uint64_t)x * (uint32_t)(r.s - 1) + x;
+        if ((uint32_t)prod < (uint32_t)thr) return false;
+        *v = prod >> 32;
+        return true;
+    }
+    const uint4 w = philox_block((uint32_t)(j >> 1), tag, r.id, key);
+    const uint64_t x = (j & 1) ? (((uint64_t)w.w << 32) | w.z) : (((uint64_t)w.y << 32) | w.x);
+    if (x * r.s < thr) return false;
+    *v = __umul64hi(x, r.s);
+    return true;
+}
+
+// Bucket path, leaves whose first k valid candidates repeat a value: A[0..k)
+// holds them sorted.  Keeps the d distinct values (B), draws the k - d
+// missing ones from candidates jnext, jnext+1, ... (a candidate counts if it
+// is valid and new), and writes the merged sorted leaf.  False if the stream
+// runs out (the probing path then reports it).
+template <typename KeyT, int NT, int BAR>
+RS_DEV bool bucket_repair(HashShared<KeyT, NT / 32>& sm, const LeafRec& r, Key2 key, uint32_t k, uint64_t thr,
+                          KeyT* A, KeyT* B, uint64_t* __restrict__ dst, uint32_t tid) {
+    // distinct values of the sorted A, in order, into B
+    const uint32_t Q = (k + NT - 1) / NT;
+    const uint32_t i0 = min(tid * Q, k), i1 = min(i0 + Q, k);
+    uint32_t local = 0;
+    for (uint32_t i = i0; i < i1; ++i) local += (i == 0 || A[i] != A[i - 1]) ? 1u : 0u;
+    uint32_t d;
+    uint32_t pos = block_exclusive_scan<NT>(local, sm.scan_tmp, &d);
+    for (uint32_t i = i0; i < i1; ++i)
+        if (i == 0 || A[i] != A[i - 1]) B[pos++] = A[i];
+    if (tid == 0) sm.repair_fail = 0;
+    group_sync<BAR, NT>();
+    // one warp draws the missing values, 32 candidates at a time, in index order
+    KeyT* NV = A;   // the new values (at most k - d)
+    const uint32_t need = k - d;
+    if (tid < 32) {
+        const uint32_t lane = tid;
+        const uint64_t jlimit = r.s > (1ull << 32) ? (1ull << 33) : (1ull << 34);
+        uint64_t J = sm.jnext;
+        uint32_t added = 0;
+        while (added < need) {
+            if (J + 32 > jlimit) {
+                if (lane == 0) sm.repair_fail = 1;
+                break;
+            }
+            uint64_t v64 = 0;
+            bool fresh = candidate_at(r, thr, key, TAG_LEAF_H, J + lane, &v64);
+            const KeyT v = (KeyT)v64;
+            if (fresh) {   // already in the set?
+                uint32_t lo = 0, hi = d;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (B[mid] < v) lo = mid + 1; else hi = mid;
+                }
+                if (lo < d && B[lo] == v) fresh = false;
+                for (uint32_t t = 0; t < added && fresh; ++t)
+                    if (NV[t] == v) fresh = false;
+            }
+            // an earlier lane of this batch drew the same value
+            const uint32_t same = __match_any_sync(0xFFFFFFFFu, (unsigned long long)v64) &
+                                  __ballot_sync(0xFFFFFFFFu, fresh);
+            if (fresh && (uint32_t)(__ffs(same) - 1) != lane) fresh = false;
+            const uint32_t keepm = __ballot_sync(0xFFFFFFFFu, fresh);
+            const uint32_t take = min((uint32_t)__popc(keepm), need - added);
+            const uint32_t rank = __popc(keepm & ((1u << lane) - 1u));
+            if (fresh && rank < take) NV[added + rank] = v;
+            added += take;
+            J += 32;
+            __syncwarp();
+        }
+    }
+    group_sync<BAR, NT>();
+    if (sm.repair_fail) return false;
+    // sort the new values (distinct) by counting, into the free end of B
+    KeyT* NS = B + d;
+    for (uint32_t t = tid; t < need; t += NT) {
+        const KeyT v = NV[t];
+        uint32_t rank = 0;
+        for (uint32_t u = 0; u < need; ++u) rank += NV[u] < v ? 1u : 0u;
+        NS[rank] = v;
+    }
+    group_sync<BAR, NT>();
+    // merge: each value's place is its index plus the number of values of the
+    // other list below it
+    const uint64_t base = r.lo + 1;
+    for (uint32_t i = tid; i < d; i += NT) {
+        const KeyT v = B[i];
+        uint32_t lo = 0, hi = need;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (NS[mid] < v) lo = mid + 1; else hi = mid;
+        }
+        dst[i + lo] = base + v;
+    }
+    for (uint32_t t = tid; t < need; t += NT) {
+        const KeyT v = NS[t];
+        uint32_t lo = 0, hi = d;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (B[mid] < v) lo = mid + 1; else hi = mid;
+        }
+        dst[t + lo] = base + v;
+    }
+    group_sync<BAR, NT>();
+    return true;
+}
+
 // Bucket path.  Returns true on success (leaf written), false if the leaf
 // must take the probing path (whatever was written is overwritten later).
 template <typename KeyT, int NT, int BAR, bool WR>
@@ -250,6 +369,7 @@ RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32>& sm, const LeafRec& r, Key2 ke
         // no candidate can be void: candidates [0, k) are the first k valid ones
         bool void_seen = false;
         for_candidates<NT>(r, thr, key, tag, 0, k, tid, &void_seen, keep);
+        if (tid == 0) sm.jnext = k;
         group_sync<BAR, NT>();
     } else {
         // rounds of one Philox block per thread: the valid candidates of a
@@ -287,6 +407,7 @@ RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32>& sm, const LeafRec& r, Key2 ke
             for (int c = 0; c < 4; ++c) {
                 if ((valid >> c) & 1u) {
                     if (rank < k) keep(rank, v[c]);
+                    if (rank == k - 1) sm.jnext = blk * (w32 ? 4 : 2) + c + 1;
                     ++rank;
                 }
             }
@@ -374,7 +495,8 @@ RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32>& sm, const LeafRec& r, Key2 ke
         }
     }
     if (WR) return true;
-    return !group_sync_or<BAR, NT>(dup);   // a repeat: the probing path rewrites the whole leaf
+    if (!group_sync_or<BAR, NT>(dup)) return true;
+    return bucket_repair<KeyT, NT, BAR>(sm, r, key, k, thr, A, B, dst, tid);   // rewrites the whole leaf
 }
 
 // Rounds of distinct insertion shared by the bitmap and probing paths:
