@@ -603,10 +603,36 @@ RS_DEV void bitmap_leaf(HashShared<KeyT, NT / 32>& sm, const LeafRec& r, Key2 ke
     group_sync<BAR, NT>();
     uint32_t base = 0;
     for (uint32_t i = 0; i < warp; ++i) base += sm.warp_cnt[i];
-    for (uint32_t w = w0; w < w1; ++w) {
-        const uint32_t bits = bits_of(w);
-        if ((bits >> lane) & 1u) dst[base + __popc(bits & ((1u << lane) - 1u))] = r.lo + 1 + (uint64_t)w * 32 + lane;
-        base += __popc(bits);
+    const uint32_t nout = comp ? (uint32_t)(r.s - k) : k;
+    if ((uint64_t)nout * 8 >= (uint64_t)words * 32) {
+        // dense: a word at a time, one bit per lane (coalesced stores)
+        for (uint32_t w = w0; w < w1; ++w) {
+            const uint32_t bits = bits_of(w);
+            if ((bits >> lane) & 1u)
+                dst[base + __popc(bits & ((1u << lane) - 1u))] = r.lo + 1 + (uint64_t)w * 32 + lane;
+            base += __popc(bits);
+        }
+    } else {
+        // sparse: 32 words at a time, one per lane; a warp scan of their bit
+        // counts places each lane's run of outputs
+        for (uint32_t wc = w0; wc < w1; wc += 32) {
+            const uint32_t w = wc + lane;
+            uint32_t bits = w < w1 ? bits_of(w) : 0u;
+            const uint32_t c = __popc(bits);
+            uint32_t incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= (uint32_t)o) incl += y;
+            }
+            uint32_t p = base + incl - c;
+            while (bits) {
+                const uint32_t t = (uint32_t)__ffs(bits) - 1u;
+                dst[p++] = r.lo + 1 + (uint64_t)w * 32 + t;
+                bits &= bits - 1u;
+            }
+            base += __shfl_sync(0xFFFFFFFFu, incl, 31);
+        }
     }
     group_sync<BAR, NT>();
 }
