@@ -55,6 +55,25 @@ __global__ void __launch_bounds__(kBatchTreeWarps * 32) batch_tree_kernel(const 
         tree_batch_warp<false>(nodes + q.node_base, e.v0, e.count, make_key(q.seed), tab, status + e.req, logs);
 }
 
+// A level whose items hold at most 8 nodes of one request: 32 / count lanes
+// per node, four lanes per trial (rs_tree_warp.cuh: tree_terms_warp).
+__global__ void __launch_bounds__(kBatchTreeWarps * 32) batch_terms_kernel(const BatchReq* __restrict__ reqs,
+                                                                           const BatchTreeItem* __restrict__ items,
+                                                                           uint32_t nitems, NodeRec* nodes,
+                                                                           const double* __restrict__ tab,
+                                                                           int* status) {
+    const uint32_t warp = threadIdx.x >> 5;
+    const uint32_t it = blockIdx.x * kBatchTreeWarps + warp;
+    if (it >= nitems) return;
+    const BatchTreeItem e = items[it];
+    const BatchReq q = reqs[e.req];
+    const uint32_t G = 32 / e.count;
+    if (q.kind == RS_KIND_WR)
+        tree_terms_warp<true>(nodes + q.node_base, e.v0, e.count, make_key(q.seed), tab, status + e.req, G);
+    else
+        tree_terms_warp<false>(nodes + q.node_base, e.v0, e.count, make_key(q.seed), tab, status + e.req, G);
+}
+
 // Leaf H / leaf WR over the leaves of a view, one block per leaf at a time;
 // leaves the shared-memory table cannot take go to the overflow list.
 template <typename KeyT, bool WR, class View>
@@ -446,8 +465,12 @@ int GroupPlan::issue(const double* tab, int sms, uint64_t* pool, int* status, cu
             const uint32_t n = (uint32_t)levels_[l].size();
             if (n == 0) continue;
             const auto* items = reinterpret_cast<const BatchTreeItem*>(up_ + o_levels_[l]);
-            batch_tree_kernel<<<(n + kBatchTreeWarps - 1) / kBatchTreeWarps, kBatchTreeWarps * 32, tree_smem, st>>>(
-                reqs, items, n, nodes, tab, status);
+            const unsigned blocks = (n + kBatchTreeWarps - 1) / kBatchTreeWarps;
+            // items of level l hold min(2^l, kBatchTreeBatch) nodes each
+            if ((1ull << l) <= 8)
+                batch_terms_kernel<<<blocks, kBatchTreeWarps * 32, 0, st>>>(reqs, items, n, nodes, tab, status);
+            else
+                batch_tree_kernel<<<blocks, kBatchTreeWarps * 32, tree_smem, st>>>(reqs, items, n, nodes, tab, status);
             ++nl;
         }
         for (int gi = 0; !rc && gi < 5; ++gi) {
