@@ -479,6 +479,9 @@ def run_ours(args):
         dist.barrier()
     rs.load()
     ctx = rs.rs_create(local)
+    if args.pipeline is not None:
+        log2_parts, blocks = (int(x) for x in args.pipeline.split(","))
+        rs.rs_set_pipeline(ctx, log2_parts, blocks)
     stream = torch.cuda.Stream()
     out = torch.empty(N_SAMPLES, dtype=torch.int64, device="cuda")
     seed = SEED + rank
@@ -607,6 +610,8 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="smaller n (profiling cases only)")
     ap.add_argument("--log2N", type=int, default=None, help="smaller universe 2^log2N (profiling cases only)")
     ap.add_argument("--n0", type=int, default=None, help="other leaf size (profiling cases only)")
+    ap.add_argument("--pipeline", default=None,
+                    help="LOG2_PARTS,LEAF_BLOCKS_PER_SM for rs_set_pipeline (default: the library's)")
     args = ap.parse_args()
     set_workload(args.n, args.log2N, args.n0)
     if args.impl == "reference":

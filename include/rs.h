@@ -303,6 +303,18 @@ int rs_set_leaf_capacity(rs_ctx* ctx, uint32_t cap);
 int rs_set_profiling(rs_ctx* ctx, int on);
 int rs_phase_totals(rs_ctx* ctx, double* tree_ms, double* leaf_ms, uint64_t* calls);
 
+/* Pipelining of deep split trees (depth >= log2_parts + 9): the subtrees
+ * under level log2_parts are built one after another on a second,
+ * highest-priority stream of the context, and the leaves of each run on the
+ * caller's stream as soon as its subtree is done, beside the FP64 work of
+ * the next subtrees, with at most leaf_blocks_per_sm leaf blocks per SM
+ * (0 = as many as fit) so that tree blocks can run beside them.  The
+ * output does not change.  log2_parts = 0 turns it off (the default: on
+ * GB300 the leaves keep the issue slots busy and the tree blocks beside them
+ * slow down more than the overlap gains).
+ * Errors: RS_EINVAL (log2_parts outside 0..6, negative blocks). */
+int rs_set_pipeline(rs_ctx* ctx, int log2_parts, int leaf_blocks_per_sm);
+
 /* Number of kernels this context has launched since it was created. */
 int rs_launch_count(rs_ctx* ctx, uint64_t* count);
 

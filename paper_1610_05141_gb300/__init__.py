@@ -83,6 +83,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "rs_set_profiling": (i32, [vp, i32]),
         "rs_phase_totals": (i32, [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(u64)]),
         "rs_launch_count": (i32, [vp, ctypes.POINTER(u64)]),
+        "rs_set_pipeline": (i32, [vp, i32, i32]),
         "rs_sample_static": (i32, [u64, u64, u64, u32, vp, vp]),
         "rs_batch_plan": (i32, [vp, vp, u32, ctypes.POINTER(vp)]),
         "rs_batch_run": (i32, [vp, vp, vp, vp]),
@@ -223,6 +224,10 @@ def rs_phase_totals(ctx: Context):
     t, l, c = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_uint64(0)
     _check(load().rs_phase_totals(ctx.handle, ctypes.byref(t), ctypes.byref(l), ctypes.byref(c)), "rs_phase_totals")
     return t.value, l.value, c.value
+
+
+def rs_set_pipeline(ctx: Context, log2_parts: int, leaf_blocks_per_sm: int = 3) -> int:
+    return _check(load().rs_set_pipeline(ctx.handle, log2_parts, leaf_blocks_per_sm), "rs_set_pipeline")
 
 
 def rs_launch_count(ctx: Context) -> int:

@@ -23,9 +23,22 @@ struct rs_ctx {
     uint64_t* words = nullptr;      // general scratch (Bernoulli chunk counts, leaf B positions)
     uint64_t words_cap = 0;
     uint32_t leaf_cap = 0;          // testing knob, 0 = default
+    // pipelining of deep trees: 2^pipe_log2 subtrees, each built on the tree
+    // stream while the caller's stream runs the leaves of the ones before
+    int pipe_log2 = 0;
+    int pipe_leaf_blocks = 3;       // leaf blocks per SM while tree work may run beside them (off by default:
+                                    // on GB300 the issue-bound leaves starve the tree blocks)
+    cudaStream_t tree_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr;
+    std::vector<cudaEvent_t> ev_part;
     bool profiling = false;
-    std::vector<cudaEvent_t> ev_pool;   // 3 events per profiled call: tree start, leaves start, end
+    struct PhaseRec {               // event indices of one profiled call
+        size_t start, tree_end, end;
+        std::vector<std::pair<size_t, size_t>> leaves;
+    };
+    std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
+    std::vector<PhaseRec> prof_calls;
     uint64_t launches = 0;
 };
 
@@ -69,20 +82,37 @@ int ensure(T*& ptr, uint64_t& cap, uint64_t need) {
     return RS_OK;
 }
 
-// Records event `which` (0, 1, 2) of the current profiled call; a new call
-// starts at which = 0.  Events are created on demand and reused.
-void record_phase(rs_ctx* ctx, int which, cudaStream_t st) {
-    const size_t idx = ctx->ev_used + (size_t)which;
-    while (ctx->ev_pool.size() <= idx) {
+// Records the next event of the profiling pool on `st` and returns its
+// index (events are created on demand and reused after rs_set_profiling).
+size_t record_event(rs_ctx* ctx, cudaStream_t st) {
+    while (ctx->ev_pool.size() <= ctx->ev_used) {
         cudaEvent_t e;
         if (cudaEventCreate(&e) != cudaSuccess) {
             ctx->profiling = false;
-            return;
+            return 0;
         }
         ctx->ev_pool.push_back(e);
     }
-    cudaEventRecord(ctx->ev_pool[idx], st);
-    if (which == 2) ctx->ev_used += 3;
+    cudaEventRecord(ctx->ev_pool[ctx->ev_used], st);
+    return ctx->ev_used++;
+}
+
+// The tree stream (highest priority) and its events, made on first use.
+int ensure_pipeline(rs_ctx* ctx, size_t parts) {
+    if (!ctx->tree_stream) {
+        int least = 0, greatest = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return RS_ECUDA;
+        if (cudaStreamCreateWithPriority(&ctx->tree_stream, cudaStreamNonBlocking, greatest) != cudaSuccess)
+            return RS_ECUDA;
+    }
+    if (!ctx->ev_fork && cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess)
+        return RS_ECUDA;
+    while (ctx->ev_part.size() < parts) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return RS_ECUDA;
+        ctx->ev_part.push_back(e);
+    }
+    return RS_OK;
 }
 
 int depth_of(uint64_t n, uint64_t N, uint32_t n0) {
@@ -111,7 +141,6 @@ int build_tree(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0, 
     int rc = ensure(ctx->nodes, ctx->nodes_cap, 2ull << D);
     if (rc) return rc;
     *D_out = D;
-    if (ctx->profiling) record_phase(ctx, 0, st);
     ctx->launches += 1 + (uint64_t)D;
     return cuda_rc(rs::launch_tree(ctx->nodes, n, N, seed, D, kind == RS_KIND_WR, ctx->tab, ctx->status, st));
 }
@@ -124,60 +153,105 @@ int sample_impl(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0,
     DeviceGuard g(ctx->device);
     if (!g.ok) return RS_ECUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int D;
-    rc = build_tree(ctx, n, N, seed, n0, kind, st, &D);
+    const int D = depth_of(n, N, n0);
+    if (D > rs::kMaxDepth) return RS_ECAPACITY;
+    rc = ensure(ctx->nodes, ctx->nodes_cap, 2ull << D);
     if (rc) return rc;
+    const bool wr = kind == RS_KIND_WR;
     const uint64_t nleaves = 1ull << D;
-    const uint64_t smax = (N >> D) + ((N & (nleaves - 1)) ? 1 : 0);
-    if (ctx->profiling) record_phase(ctx, 1, st);
-    if (kind == RS_KIND_B) {
-        rs::LeafBLaunch L{ctx->nodes + nleaves, nleaves, nleaves, seed, out, ctx->status, ctx->sms};
-        ctx->launches += 1;
-        rc = cuda_rc(rs::launch_leaves_b(L, st));
-        if (ctx->profiling) record_phase(ctx, 2, st);
-        return rc;
+    // Deep trees: the subtrees under level c are built one after another on
+    // the tree stream, and the leaves of each start on `st` as soon as its
+    // subtree is done, beside the FP64 work of the next subtrees.
+    const int c = (ctx->pipe_log2 > 0 && D >= ctx->pipe_log2 + 9) ? ctx->pipe_log2 : 0;
+    const uint64_t parts = 1ull << c, per_part = nleaves >> c;
+    if (c) {
+        rc = ensure_pipeline(ctx, parts);
+        if (rc) return rc;
     }
-    rc = ensure(ctx->ovf, ctx->ovf_cap, nleaves + 1);
+    size_t prof = 0;
+    if (ctx->profiling) {
+        ctx->prof_calls.emplace_back();
+        prof = ctx->prof_calls.size();
+        ctx->prof_calls[prof - 1].start = record_event(ctx, st);
+    }
+    if (c == 0) {
+        rc = cuda_rc(rs::launch_tree(ctx->nodes, n, N, seed, D, wr, ctx->tab, ctx->status, st));
+        ctx->launches += 1 + (uint64_t)D;
+        if (prof) ctx->prof_calls[prof - 1].tree_end = record_event(ctx, st);
+    } else {
+        cudaStream_t ts = ctx->tree_stream;
+        rc = cuda_rc(cudaEventRecord(ctx->ev_fork, st));
+        if (!rc) rc = cuda_rc(cudaStreamWaitEvent(ts, ctx->ev_fork, 0));
+        if (!rc) rc = cuda_rc(rs::launch_tree_top(ctx->nodes, n, N, seed, c, wr, ctx->tab, ctx->status, ts));
+        for (uint64_t j = 0; !rc && j < parts; ++j) {
+            rc = cuda_rc(rs::launch_tree_part(ctx->nodes, seed, D, c, j, wr, ctx->tab, ctx->status, ts));
+            if (!rc) rc = cuda_rc(cudaEventRecord(ctx->ev_part[j], ts));
+        }
+        ctx->launches += 1 + (uint64_t)c + parts * (uint64_t)(D - c);
+        if (prof) ctx->prof_calls[prof - 1].tree_end = record_event(ctx, ts);
+    }
     if (rc) return rc;
-    const uint32_t cap = ctx->leaf_cap ? std::min<uint32_t>(ctx->leaf_cap, rs::kLeafFastCap) : rs::kLeafFastCap;
-    // Largest selection any leaf can need: k <= n and, without replacement,
-    // k <= s/2 (the complement rule).
-    // A leaf also leaves the fast path when a complement does not fit the
-    // bitmap or a probe runs past the table: keep the general path ready
-    // whenever a leaf can hold more than a handful of values.
-    uint64_t bound = n;
-    if (kind != RS_KIND_WR) bound = std::min<uint64_t>(bound, smax - smax / 2);
+    const uint64_t smax = (N >> D) + ((N & (nleaves - 1)) ? 1 : 0);
+    rs::LeafLaunch L{};
     uint64_t big_kmax = 0;
-    if (bound > 64) {
-        big_kmax = std::min<uint64_t>(bound, rs::kBigLeafMax);
-        const uint64_t bytes = rs::big_pool_bytes(big_kmax);
-        if (ctx->big_pool_bytes < bytes) {
-            if (ctx->big_pool) cudaFree(ctx->big_pool);
-            ctx->big_pool = nullptr;
-            ctx->big_pool_bytes = 0;
-            cudaError_t e = cudaMalloc(&ctx->big_pool, bytes);
-            if (e != cudaSuccess) return cuda_rc(e);
-            ctx->big_pool_bytes = bytes;
+    if (kind != RS_KIND_B) {
+        rc = ensure(ctx->ovf, ctx->ovf_cap, nleaves + 1);
+        if (rc) return rc;
+        // Largest selection any leaf can need: k <= n and, without
+        // replacement, k <= s/2 (the complement rule).  A leaf also leaves
+        // the fast path when a complement does not fit the bitmap or a probe
+        // runs past the table: keep the general path ready whenever a leaf
+        // can hold more than a handful of values.
+        uint64_t bound = n;
+        if (!wr) bound = std::min<uint64_t>(bound, smax - smax / 2);
+        if (bound > 64) {
+            big_kmax = std::min<uint64_t>(bound, rs::kBigLeafMax);
+            const uint64_t bytes = rs::big_pool_bytes(big_kmax);
+            if (ctx->big_pool_bytes < bytes) {
+                if (ctx->big_pool) cudaFree(ctx->big_pool);
+                ctx->big_pool = nullptr;
+                ctx->big_pool_bytes = 0;
+                cudaError_t e = cudaMalloc(&ctx->big_pool, bytes);
+                if (e != cudaSuccess) return cuda_rc(e);
+                ctx->big_pool_bytes = bytes;
+            }
+        }
+        L.seed = seed;
+        L.smax = smax;
+        L.out = out;
+        L.status = ctx->status;
+        L.ovf_list = ctx->ovf;
+        L.ovf_count = ctx->ovf + nleaves;
+        L.big_pool = ctx->big_pool;
+        L.big_kmax = big_kmax;
+        L.cap = ctx->leaf_cap ? std::min<uint32_t>(ctx->leaf_cap, rs::kLeafFastCap) : rs::kLeafFastCap;
+        L.sms = ctx->sms;
+        L.with_replacement = wr;
+    }
+    for (uint64_t j = 0; !rc && j < parts; ++j) {
+        if (c) rc = cuda_rc(cudaStreamWaitEvent(st, ctx->ev_part[j], 0));
+        if (rc) break;
+        const size_t a = prof ? record_event(ctx, st) : 0;
+        const uint64_t first = j * per_part;
+        if (kind == RS_KIND_B) {
+            rs::LeafBLaunch LB{ctx->nodes + nleaves + first, per_part, nleaves + first, seed, out, ctx->status,
+                               ctx->sms};
+            ctx->launches += 1;
+            rc = cuda_rc(rs::launch_leaves_b(LB, st));
+        } else {
+            L.leaves = ctx->nodes + nleaves + first;
+            L.nleaves = per_part;
+            L.first_id = nleaves + first;
+            L.blocks_per_sm = (c && j + 1 < parts) ? ctx->pipe_leaf_blocks : 0;
+            ctx->launches += big_kmax ? 2 : 1;
+            rc = cuda_rc(rs::launch_leaves(L, st));
+        }
+        if (prof) {
+            const size_t b = record_event(ctx, st);
+            ctx->prof_calls[prof - 1].leaves.emplace_back(a, b);
+            ctx->prof_calls[prof - 1].end = b;
         }
     }
-    rs::LeafLaunch L{};
-    L.leaves = ctx->nodes + nleaves;
-    L.nleaves = nleaves;
-    L.first_id = nleaves;
-    L.seed = seed;
-    L.smax = smax;
-    L.out = out;
-    L.status = ctx->status;
-    L.ovf_list = ctx->ovf;
-    L.ovf_count = ctx->ovf + nleaves;
-    L.big_pool = ctx->big_pool;
-    L.big_kmax = big_kmax;
-    L.cap = cap;
-    L.sms = ctx->sms;
-    L.with_replacement = kind == RS_KIND_WR;
-    ctx->launches += big_kmax ? 2 : 1;
-    rc = cuda_rc(rs::launch_leaves(L, st));
-    if (ctx->profiling) record_phase(ctx, 2, st);
     return rc;
 }
 
@@ -237,6 +311,9 @@ int rs_destroy(rs_ctx* ctx) {
     cudaFree(ctx->big_pool);
     cudaFree(ctx->words);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->ev_part) cudaEventDestroy(e);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->tree_stream) cudaStreamDestroy(ctx->tree_stream);
     delete ctx;
     return rc;
 }
@@ -337,6 +414,7 @@ int rs_set_profiling(rs_ctx* ctx, int on) {
     if (!ctx) return RS_EINVAL;
     ctx->profiling = on != 0;
     ctx->ev_used = 0;
+    ctx->prof_calls.clear();
     return RS_OK;
 }
 
@@ -345,15 +423,27 @@ int rs_phase_totals(rs_ctx* ctx, double* tree_ms, double* leaf_ms, uint64_t* cal
     DeviceGuard g(ctx->device);
     *tree_ms = 0.0;
     *leaf_ms = 0.0;
-    *calls = ctx->ev_used / 3;
-    for (size_t i = 0; i + 2 < ctx->ev_used; i += 3) {
-        float t = 0.f, l = 0.f;
-        if (cudaEventSynchronize(ctx->ev_pool[i + 2]) != cudaSuccess) return RS_ECUDA;
-        if (cudaEventElapsedTime(&t, ctx->ev_pool[i], ctx->ev_pool[i + 1]) != cudaSuccess) return RS_ECUDA;
-        if (cudaEventElapsedTime(&l, ctx->ev_pool[i + 1], ctx->ev_pool[i + 2]) != cudaSuccess) return RS_ECUDA;
+    *calls = ctx->prof_calls.size();
+    for (const auto& c : ctx->prof_calls) {
+        float t = 0.f;
+        if (cudaEventSynchronize(ctx->ev_pool[c.end]) != cudaSuccess) return RS_ECUDA;
+        if (cudaEventSynchronize(ctx->ev_pool[c.tree_end]) != cudaSuccess) return RS_ECUDA;
+        if (cudaEventElapsedTime(&t, ctx->ev_pool[c.start], ctx->ev_pool[c.tree_end]) != cudaSuccess) return RS_ECUDA;
         *tree_ms += t;
-        *leaf_ms += l;
+        for (const auto& ab : c.leaves) {
+            float l = 0.f;
+            if (cudaEventElapsedTime(&l, ctx->ev_pool[ab.first], ctx->ev_pool[ab.second]) != cudaSuccess)
+                return RS_ECUDA;
+            *leaf_ms += l;
+        }
     }
+    return RS_OK;
+}
+
+int rs_set_pipeline(rs_ctx* ctx, int log2_parts, int leaf_blocks_per_sm) {
+    if (!ctx || log2_parts < 0 || log2_parts > 6 || leaf_blocks_per_sm < 0) return RS_EINVAL;
+    ctx->pipe_log2 = log2_parts;
+    ctx->pipe_leaf_blocks = leaf_blocks_per_sm;
     return RS_OK;
 }
 

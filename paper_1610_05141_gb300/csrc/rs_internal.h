@@ -26,6 +26,13 @@ cudaError_t launch_lf_table(double* tab, cudaStream_t st);
 // splits, else hypergeometric ones.
 cudaError_t launch_tree(NodeRec* rec, uint64_t n, uint64_t N, uint64_t seed, int D, bool with_replacement,
                         const double* tab, int* status, cudaStream_t st);
+// The root and levels 0 .. levels-1.
+cudaError_t launch_tree_top(NodeRec* rec, uint64_t n, uint64_t N, uint64_t seed, int levels, bool with_replacement,
+                            const double* tab, int* status, cudaStream_t st);
+// Levels c .. D-1 of the subtree under node 2^c + part (its nodes on level l
+// are 2^l + part 2^(l-c) .. + 2^(l-c) - 1); levels 0 .. c-1 must be done.
+cudaError_t launch_tree_part(NodeRec* rec, uint64_t seed, int D, int c, uint64_t part, bool with_replacement,
+                             const double* tab, int* status, cudaStream_t st);
 
 // Copies leaf records rec[2^D + i] to recs_out[4i .. 4i+3].
 cudaError_t launch_export_leaves(const NodeRec* leaves, uint64_t nleaves, uint64_t* recs_out, cudaStream_t st);
@@ -45,6 +52,7 @@ struct LeafLaunch {
     uint32_t cap;            // 0 = kLeafCap
     int sms;
     bool with_replacement;
+    int blocks_per_sm = 0;   // leaf-kernel blocks per SM, 0 = as many as fit
 };
 
 // Leaf H (or leaf WR) for every leaf, then the general path for the leaves

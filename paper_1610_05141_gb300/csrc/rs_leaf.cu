@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kBigThreads) big_leaf_kernel(LeafJob job, BigS
 // ---------------------------------------------------------------------------
 
 template <typename KeyT, bool WR>
-static cudaError_t launch_fast(const LeafJob& job, int sms, cudaStream_t st) {
+static cudaError_t launch_fast(const LeafJob& job, int sms, int per_sm_cap, cudaStream_t st) {
     const size_t smem = sizeof(HashShared<KeyT, kHashThreads / 32>);
     auto kern = leaf_kernel<KeyT, WR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -90,6 +90,7 @@ static cudaError_t launch_fast(const LeafJob& job, int sms, cudaStream_t st) {
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kHashThreads, smem);
     if (e != cudaSuccess) return e;
+    if (per_sm_cap > 0 && per_sm > per_sm_cap) per_sm = per_sm_cap;
     if (per_sm < 1) per_sm = 1;
     const uint64_t grid = std::min<uint64_t>(job.nleaves, (uint64_t)sms * per_sm);
     kern<<<(unsigned)grid, kHashThreads, smem, st>>>(job);
@@ -102,10 +103,11 @@ cudaError_t launch_leaves(const LeafLaunch& L, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(L.ovf_count, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
     const bool narrow = L.smax <= (1ull << 32);
+    const int cap = L.blocks_per_sm;
     if (L.with_replacement)
-        e = narrow ? launch_fast<uint32_t, true>(job, L.sms, st) : launch_fast<uint64_t, true>(job, L.sms, st);
+        e = narrow ? launch_fast<uint32_t, true>(job, L.sms, cap, st) : launch_fast<uint64_t, true>(job, L.sms, cap, st);
     else
-        e = narrow ? launch_fast<uint32_t, false>(job, L.sms, st) : launch_fast<uint64_t, false>(job, L.sms, st);
+        e = narrow ? launch_fast<uint32_t, false>(job, L.sms, cap, st) : launch_fast<uint64_t, false>(job, L.sms, cap, st);
     if (e != cudaSuccess) return e;
     if (L.big_kmax == 0) return cudaSuccess;   // no leaf can exceed the capacity
     BigScratch sc;

@@ -33,43 +33,42 @@ __global__ void tree_root_kernel(NodeRec* rec, uint64_t n, uint64_t N) {
 constexpr int kTreeWarps = 4;            // warps per block of the level kernel
 constexpr uint32_t kTreeBatch = 128;     // nodes per warp (lanes refill from it)
 
-// One level of the tree: each warp takes a batch of consecutive nodes, G
-// lanes per node.
+// Nodes first .. first+nodes-1 of one level: each warp takes a batch of
+// consecutive nodes, G lanes per node.
 template <bool WR>
-__global__ void __launch_bounds__(kTreeWarps * 32) tree_level_kernel(NodeRec* __restrict__ rec, int level,
-                                                                    uint32_t batch, uint32_t G, uint64_t seed,
-                                                                    const double* __restrict__ tab, int* status) {
+__global__ void __launch_bounds__(kTreeWarps * 32) tree_level_kernel(NodeRec* __restrict__ rec, uint64_t first,
+                                                                    uint64_t nodes, uint32_t batch, uint32_t G,
+                                                                    uint64_t seed, const double* __restrict__ tab,
+                                                                    int* status) {
     extern __shared__ double tree_logs[];
     const uint32_t warp = threadIdx.x >> 5;
-    const uint64_t nodes = 1ull << level;
     const uint64_t start = ((uint64_t)blockIdx.x * kTreeWarps + warp) * batch;
     if (start >= nodes) return;
     const uint64_t left = nodes - start;
     const uint32_t count = left < batch ? (uint32_t)left : batch;
-    tree_batch_warp<WR>(rec, nodes + start, count, make_key(seed), tab, status,
+    tree_batch_warp<WR>(rec, first + start, count, make_key(seed), tab, status,
                         tree_logs + warp * 32 * kLogSlots, G);
 }
 
-// A small level: G >= 4 lanes per node, parallel terms and trials.
+// Nodes of a small launch: G >= 4 lanes per node, parallel terms and trials.
 template <bool WR>
-__global__ void __launch_bounds__(kTreeWarps * 32) tree_terms_kernel(NodeRec* __restrict__ rec, int level,
-                                                                    uint32_t G, uint64_t seed,
+__global__ void __launch_bounds__(kTreeWarps * 32) tree_terms_kernel(NodeRec* __restrict__ rec, uint64_t first,
+                                                                    uint64_t nodes, uint32_t G, uint64_t seed,
                                                                     const double* __restrict__ tab, int* status) {
     const uint32_t warp = threadIdx.x >> 5;
-    const uint64_t nodes = 1ull << level;
     const uint32_t batch = 32 / G;
     const uint64_t start = ((uint64_t)blockIdx.x * kTreeWarps + warp) * batch;
     if (start >= nodes) return;
     const uint64_t left = nodes - start;
     const uint32_t count = left < batch ? (uint32_t)left : batch;
-    tree_terms_warp<WR>(rec, nodes + start, count, make_key(seed), tab, status, G);
+    tree_terms_warp<WR>(rec, first + start, count, make_key(seed), tab, status, G);
 }
 
-// Lanes per node on a level of `nodes` nodes: the largest power of two up to
-// 32 that keeps nodes * G within about four warps per SM, and at least 4
+// Lanes per node for a launch of `nodes` nodes: the largest power of two up
+// to 32 that keeps nodes * G within about four warps per SM, and at least 4
 // (four lanes share a trial) up to 512 nodes per SM.  G >= 4: parallel
 // terms and trials; G = 1: a node per lane with refill, which does the
-// least FP64 work per trial and wins once a level has more nodes than that.
+// least FP64 work per trial and wins once a launch has more nodes than that.
 uint32_t lanes_per_node(uint64_t nodes, int sms) {
     const uint64_t target = (uint64_t)sms * 4 * 32;
     uint32_t G = 1;
@@ -78,38 +77,60 @@ uint32_t lanes_per_node(uint64_t nodes, int sms) {
     return G;
 }
 
-cudaError_t launch_tree(NodeRec* rec, uint64_t n, uint64_t N, uint64_t seed, int D, bool with_replacement,
-                        const double* tab, int* status, cudaStream_t st) {
-    tree_root_kernel<<<1, 32, 0, st>>>(rec, n, N);
-    const size_t smem = (size_t)kTreeWarps * 32 * kLogSlots * sizeof(double);
+static int device_sms() {
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    for (int level = 0; level < D; ++level) {
-        const uint64_t nodes = 1ull << level;
-        // small levels: a group of G lanes per node runs trials in parallel;
-        // then one node per lane until the level has enough warps for every
-        // SM; beyond that, batches grow (up to kTreeBatch) and lanes refill
-        const uint32_t G = lanes_per_node(nodes, sms);
-        uint32_t batch;
-        if (G > 1) {
-            batch = 32 / G;
-        } else {
-            uint64_t per = nodes / ((uint64_t)sms * 2 * kTreeWarps);
-            per = std::max<uint64_t>(32, std::min<uint64_t>(kTreeBatch, per & ~31ull));
-            batch = (uint32_t)std::min<uint64_t>(per, nodes);
-        }
-        const uint64_t warps = (nodes + batch - 1) / batch;
-        const unsigned blocks = (unsigned)((warps + kTreeWarps - 1) / kTreeWarps);
-        if (G >= 4) {
-            if (with_replacement)
-                tree_terms_kernel<true><<<blocks, kTreeWarps * 32, 0, st>>>(rec, level, G, seed, tab, status);
-            else
-                tree_terms_kernel<false><<<blocks, kTreeWarps * 32, 0, st>>>(rec, level, G, seed, tab, status);
-        } else if (with_replacement) {
-            tree_level_kernel<true><<<blocks, kTreeWarps * 32, smem, st>>>(rec, level, batch, G, seed, tab, status);
-        } else {
-            tree_level_kernel<false><<<blocks, kTreeWarps * 32, smem, st>>>(rec, level, batch, G, seed, tab, status);
-        }
+    return sms;
+}
+
+// Splits nodes first .. first+nodes-1 (all on one level, parents done).
+static void launch_nodes(NodeRec* rec, uint64_t first, uint64_t nodes, uint64_t seed, bool wr, const double* tab,
+                         int* status, int sms, cudaStream_t st) {
+    const size_t smem = (size_t)kTreeWarps * 32 * kLogSlots * sizeof(double);
+    // small launches: a group of G lanes per node runs trials in parallel;
+    // then one node per lane until there are enough warps for every SM;
+    // beyond that, batches grow (up to kTreeBatch) and lanes refill
+    const uint32_t G = lanes_per_node(nodes, sms);
+    uint32_t batch;
+    if (G > 1) {
+        batch = 32 / G;
+    } else {
+        uint64_t per = nodes / ((uint64_t)sms * 2 * kTreeWarps);
+        per = std::max<uint64_t>(32, std::min<uint64_t>(kTreeBatch, per & ~31ull));
+        batch = (uint32_t)std::min<uint64_t>(per, nodes);
+    }
+    const uint64_t warps = (nodes + batch - 1) / batch;
+    const unsigned blocks = (unsigned)((warps + kTreeWarps - 1) / kTreeWarps);
+    if (G >= 4) {
+        if (wr) tree_terms_kernel<true><<<blocks, kTreeWarps * 32, 0, st>>>(rec, first, nodes, G, seed, tab, status);
+        else tree_terms_kernel<false><<<blocks, kTreeWarps * 32, 0, st>>>(rec, first, nodes, G, seed, tab, status);
+    } else if (wr) {
+        tree_level_kernel<true><<<blocks, kTreeWarps * 32, smem, st>>>(rec, first, nodes, batch, G, seed, tab, status);
+    } else {
+        tree_level_kernel<false><<<blocks, kTreeWarps * 32, smem, st>>>(rec, first, nodes, batch, G, seed, tab, status);
+    }
+}
+
+cudaError_t launch_tree(NodeRec* rec, uint64_t n, uint64_t N, uint64_t seed, int D, bool with_replacement,
+                        const double* tab, int* status, cudaStream_t st) {
+    return launch_tree_top(rec, n, N, seed, D, with_replacement, tab, status, st);
+}
+
+cudaError_t launch_tree_top(NodeRec* rec, uint64_t n, uint64_t N, uint64_t seed, int levels, bool with_replacement,
+                            const double* tab, int* status, cudaStream_t st) {
+    tree_root_kernel<<<1, 32, 0, st>>>(rec, n, N);
+    const int sms = device_sms();
+    for (int level = 0; level < levels; ++level)
+        launch_nodes(rec, 1ull << level, 1ull << level, seed, with_replacement, tab, status, sms, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tree_part(NodeRec* rec, uint64_t seed, int D, int c, uint64_t part, bool with_replacement,
+                             const double* tab, int* status, cudaStream_t st) {
+    const int sms = device_sms();
+    for (int level = c; level < D; ++level) {
+        const uint64_t per = 1ull << (level - c);
+        launch_nodes(rec, (1ull << level) + part * per, per, seed, with_replacement, tab, status, sms, st);
     }
     return cudaGetLastError();
 }

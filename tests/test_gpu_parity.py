@@ -202,3 +202,21 @@ def test_argument_errors(rs, ctx):
     assert rs.rs_sample(ctx, 1, 10, 1, 4, out.data_ptr() + 4, check=False) == rs.RS_EINVAL
     assert rs.rs_sample_with_replacement(ctx, 11, 10, 1, 4, out, check=False) == rs.RS_OK
     assert rs.rs_sync(ctx) == rs.RS_OK
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2])
+def test_pipelined_tree_matches_oracle(rs, ctx, oracle, kind):
+    """Subtrees built on the tree stream while earlier subtrees' leaves run:
+    the same output as the sequential schedule and as the oracle."""
+    n, seed, n0 = 4 * 10**6, 77 + kind, 1024         # depth 12: 8 subtrees of 512 leaves
+    N = 2**40 if kind == 1 else 2**50
+    call = {0: rs.rs_sample, 1: rs.rs_sample_with_replacement, 2: rs.rs_sample_b}[kind]
+    try:
+        rs.rs_set_pipeline(ctx, 3, 3)
+        got = run(rs, ctx, call, n, N, seed, n0)
+        rs.rs_set_pipeline(ctx, 0, 0)
+        seq = run(rs, ctx, call, n, N, seed, n0)
+    finally:
+        rs.rs_set_pipeline(ctx, 0, 3)
+    assert_same(got, seq, ("pipelined vs sequential", kind))
+    assert_same(got, oracle.sample(n, N, seed, n0, kind), (n, N, seed, n0, kind))
