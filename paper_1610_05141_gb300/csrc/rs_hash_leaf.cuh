@@ -366,9 +366,38 @@ RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32>& sm, const LeafRec& r, Key2 ke
         atomicAdd(&cw[b >> 1], 1u << ((b & 1u) << 4));
     };
     if (thr == 0) {
-        // no candidate can be void: candidates [0, k) are the first k valid ones
-        bool void_seen = false;
-        for_candidates<NT>(r, thr, key, tag, 0, k, tid, &void_seen, keep);
+        // No candidate can be void (the leaf size is a power of two 2^t, the
+        // only sizes that divide 2^32 or 2^64): candidates [0, k) are the
+        // first k valid ones and Lemire's map (w s) >> width is w >> (width - t).
+        const uint32_t t = 63u - (uint32_t)__clzll(r.s);
+        if (r.s <= (1ull << 32)) {
+            const uint32_t sh = 32u - t;   // 0 when s = 2^32
+            const uint32_t full = k >> 2;  // Philox blocks whose four words are all used
+            for (uint32_t i = tid; i < full; i += NT) {
+                const uint4 w = philox_block(i, tag, r.id, key);
+                keep(4 * i, sh < 32 ? (w.x >> sh) : 0u);
+                keep(4 * i + 1, sh < 32 ? (w.y >> sh) : 0u);
+                keep(4 * i + 2, sh < 32 ? (w.z >> sh) : 0u);
+                keep(4 * i + 3, sh < 32 ? (w.w >> sh) : 0u);
+            }
+            if (tid == 0 && (k & 3u)) {
+                const uint4 w = philox_block(full, tag, r.id, key);
+                const uint32_t ws[3] = {w.x, w.y, w.z};
+                for (uint32_t c = 0; c < (k & 3u); ++c) keep(4 * full + c, sh < 32 ? (ws[c] >> sh) : 0u);
+            }
+        } else {
+            const uint32_t sh = 64u - t;   // s > 2^32: 1 <= sh < 32
+            const uint32_t full = k >> 1;
+            for (uint32_t i = tid; i < full; i += NT) {
+                const uint4 w = philox_block(i, tag, r.id, key);
+                keep(2 * i, ((((uint64_t)w.y) << 32) | w.x) >> sh);
+                keep(2 * i + 1, ((((uint64_t)w.w) << 32) | w.z) >> sh);
+            }
+            if (tid == 0 && (k & 1u)) {
+                const uint4 w = philox_block(full, tag, r.id, key);
+                keep(2 * full, ((((uint64_t)w.y) << 32) | w.x) >> sh);
+            }
+        }
         if (tid == 0) sm.jnext = k;
         group_sync<BAR, NT>();
     } else {
@@ -438,64 +467,67 @@ RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32>& sm, const LeafRec& r, Key2 ke
     }
     group_sync<BAR, NT>();
     // pass 3: the rank of B[i] among its bucket's keys, ordered by (key,
-    // position in B), is its place in the sorted leaf
-    for (uint32_t i0 = tid; i0 < k; i0 += U * NT) {
-        KeyT x[U];
-        uint32_t s0[U], s1[U], rank[U];
-#pragma unroll
-        for (uint32_t q = 0; q < U; ++q) {
-            const uint32_t i = i0 + q * NT;
-            x[q] = i < k ? B[i] : KeyT(0);
-            const uint32_t b = hash_slot(x[q], mult);
-            s0[q] = b ? ch[b - 1] : 0u;
-            s1[q] = i < k ? ch[b] : 0u;
-            rank[q] = s0[q];
-        }
-#pragma unroll
-        for (uint32_t u = 0; u < 4; ++u) {
+    // position in B), is its place in the sorted leaf; it lies in the
+    // bucket's range, a few places from i, so the stores straight to the
+    // output stay nearly coalesced.  Without replacement, an equal key in the
+    // bucket is a repeat.  (The repair of repeats runs it again into A.)
+    const uint64_t base = r.lo + 1;
+    auto rank_pass = [&](bool to_out) {
+        bool dup = false;
+        for (uint32_t i0 = tid; i0 < k; i0 += U * NT) {
+            KeyT x[U];
+            uint32_t s0[U], s1[U], rank[U];
 #pragma unroll
             for (uint32_t q = 0; q < U; ++q) {
-                const uint32_t j = s0[q] + u;
-                if (j < s1[q]) {
-                    const KeyT y = B[j];
-                    rank[q] += (y < x[q]) || (y == x[q] && j < i0 + q * NT);
+                const uint32_t i = i0 + q * NT;
+                x[q] = i < k ? B[i] : KeyT(0);
+                const uint32_t b = hash_slot(x[q], mult);
+                s0[q] = b ? ch[b - 1] : 0u;
+                s1[q] = i < k ? ch[b] : 0u;
+                rank[q] = s0[q];
+            }
+            // four unrolled comparisons without branches: the load index is
+            // clamped into the leaf and the in-bucket test masks the result
+#pragma unroll
+            for (uint32_t u = 0; u < 4; ++u) {
+#pragma unroll
+                for (uint32_t q = 0; q < U; ++q) {
+                    const uint32_t j = s0[q] + u;
+                    const KeyT y = B[min(j, k - 1)];
+                    const uint32_t in = j < s1[q] ? 1u : 0u;
+                    const uint32_t lt = (y < x[q]) ? 1u : 0u;
+                    const uint32_t eq = (y == x[q]) ? 1u : 0u;
+                    const uint32_t before = j < i0 + q * NT ? 1u : 0u;
+                    rank[q] += in & (lt | (eq & before));
+                    if (!WR) dup |= (in & eq & (j != i0 + q * NT ? 1u : 0u)) != 0u;
                 }
             }
-        }
 #pragma unroll
-        for (uint32_t q = 0; q < U; ++q) {
-            for (uint32_t j = s0[q] + 4; j < s1[q]; ++j) {   // buckets of more than four keys
-                const KeyT y = B[j];
-                rank[q] += (y < x[q]) || (y == x[q] && j < i0 + q * NT);
+            for (uint32_t q = 0; q < U; ++q) {
+                for (uint32_t j = s0[q] + 4; j < s1[q]; ++j) {   // buckets of more than four keys
+                    const KeyT y = B[j];
+                    rank[q] += (y < x[q]) || (y == x[q] && j < i0 + q * NT);
+                    if (!WR && y == x[q] && j != i0 + q * NT) dup = true;
+                }
             }
-        }
 #pragma unroll
-        for (uint32_t q = 0; q < U; ++q)
-            if (i0 + q * NT < k) A[rank[q]] = x[q];
+            for (uint32_t q = 0; q < U; ++q)
+                if (i0 + q * NT < k) {
+                    if (to_out) dst[rank[q]] = base + x[q];
+                    else A[rank[q]] = x[q];
+                }
+        }
+        return dup;
+    };
+    const bool dup = rank_pass(true);
+    // (a barrier either way: the next leaf clears the counts this pass reads)
+    if (WR) {
+        group_sync<BAR, NT>();
+        return true;
     }
-    group_sync<BAR, NT>();
-    // copy out; without replacement a key equal to its successor is a repeat
-    const uint64_t base = r.lo + 1;
-    bool dup = false;
-    for (uint32_t i0 = tid; i0 < k; i0 += U * NT) {
-        KeyT x[U], y[U];
-#pragma unroll
-        for (uint32_t q = 0; q < U; ++q) {
-            const uint32_t i = i0 + q * NT;
-            x[q] = i < k ? A[i] : KeyT(0);
-            y[q] = (!WR && i + 1 < k) ? A[i + 1] : KeyT(0);
-        }
-#pragma unroll
-        for (uint32_t q = 0; q < U; ++q) {
-            const uint32_t i = i0 + q * NT;
-            if (i < k) {
-                if (!WR && i + 1 < k && y[q] == x[q]) dup = true;
-                dst[i] = base + x[q];
-            }
-        }
-    }
-    if (WR) return true;
     if (!group_sync_or<BAR, NT>(dup)) return true;
+    rank_pass(false);   // the sorted keys, repeats adjacent
+    group_sync<BAR, NT>();
     return bucket_repair<KeyT, NT, BAR>(sm, r, key, k, thr, A, B, dst, tid);   // rewrites the whole leaf
 }
 
