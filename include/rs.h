@@ -208,7 +208,12 @@ int rs_tree_destroy(rs_tree* tree);
  * machinery above: one launch per tree level across the group's requests,
  * one leaf kernel per leaf kind, the three query steps), so jobs that arrive
  * while other groups are running are admitted as slots and memory free up
- * and run alongside them on the device.  A job's result is exactly that of
+ * and run alongside them on the device.  Lane 0 runs at the highest stream
+ * priority and takes only small jobs (queries, samples of at most 2^20
+ * values) from anywhere in the queue; the other lanes take jobs in
+ * submission order, so large jobs are never passed over for ever; the
+ * lanes' leaf kernels use one block per leaf so that a small job's kernels
+ * do not wait for a large job's whole kernel.  A job's result is exactly that of
  * the corresponding single call (rs_sample / rs_sample_with_replacement /
  * rs_sample_b / rs_tree_query): samples depend on their own arguments only
  * (Sec. 4.5).  The paper has no serving layer; this is the library's. */

@@ -69,6 +69,11 @@ public:
     // Leaf-kernel blocks per SM for every leaf group (0 = occupancy limit).
     void set_blocks_per_sm(int per) { per_sm_ = per; }
 
+    // Leaf kernels with one block per leaf instead of a persistent grid, so
+    // that their blocks retire often and kernels of other streams (a
+    // server's other lanes) get SMs between them.
+    void set_persistent(bool p) { persistent_ = p; }
+
     // Upper bounds of what one request or query adds to a group.
     static void request_cost(const rs_request& q, uint64_t* up, uint64_t* work);
     static void query_cost(const TreeInfo& t, uint64_t a, uint64_t b, uint64_t* up, uint64_t* work);
@@ -104,6 +109,7 @@ private:
     void* big_ = nullptr;
     QueryRes* qres_ = nullptr;
     int per_sm_ = 0;
+    bool persistent_ = true;
 
     void layout();
 };

@@ -14,6 +14,13 @@
 // the values are) come back through the poll call; arena memory stays
 // reserved until the client releases the job.
 //
+// Lane 0 runs at the highest stream priority and takes only small jobs
+// (queries, and samples of at most kSmallJob values) from anywhere in the
+// queue; the other lanes take jobs in submission order whatever their size,
+// so that large jobs cannot be passed over for ever.  Leaf kernels of the
+// lanes use one block per leaf, so their blocks retire often and a small
+// job's kernels do not wait for a large job's whole kernel.
+//
 // Every job's values equal those of its single call: a sample depends on
 // its own (n, N, seed, n0) only (Sec. 4.5), a query on its tree's records.
 #include <chrono>
@@ -40,6 +47,8 @@ uint64_t tree_samples(const rs_tree* t);
 namespace {
 
 using Clock = std::chrono::steady_clock;
+
+constexpr uint64_t kSmallJob = 1ull << 20;   // samples of a job lane 0 takes
 
 int cuda_rc(cudaError_t e) {
     if (e == cudaSuccess) return RS_OK;
@@ -108,6 +117,7 @@ struct Job {
     int32_t status = RS_OK;
     uint64_t count = 0;
     bool done = false;
+    bool small = false;           // lane 0 may take it out of order
 };
 
 struct Lane {
@@ -193,18 +203,28 @@ bool retire(rs_server* S) {
     return any;
 }
 
-// Admits waiting jobs into an idle lane's group and issues it.
-bool launch(rs_server* S, Lane& L) {
+// Admits waiting jobs into an idle lane's group and issues it.  Lane 0
+// (small_only) takes the small jobs in queue order and skips the others; the
+// other lanes take the queue's head in order and stop at the first job that
+// does not fit.
+bool launch(rs_server* S, Lane& L, bool small_only) {
     std::vector<Job*> batch;
     {
         std::lock_guard<std::mutex> lock(S->mu);
         uint64_t up = rs::GroupPlan::kFixedCost, work = rs::GroupPlan::kFixedCost;
+        std::deque<uint64_t> skipped;
         while (!S->pending.empty() && S->inflight < S->cfg.max_inflight && batch.size() < S->cfg.max_group) {
             Job& j = S->jobs[S->pending.front()];
+            if (small_only && !j.small) {
+                if (skipped.size() >= S->cfg.max_group) break;   // bounded look-ahead
+                skipped.push_back(S->pending.front());
+                S->pending.pop_front();
+                continue;
+            }
             if (up + j.cost_up > L.up_cap || work + j.cost_work > L.work_cap) break;
             if (!j.spec.out_dev) {
                 uint64_t off = 0;
-                if (!S->arena.alloc(j.arena_bytes, &off)) break;   // wait for memory (FIFO)
+                if (!S->arena.alloc(j.arena_bytes, &off)) break;   // wait for memory
                 j.arena_off = off;
                 j.out = reinterpret_cast<uint64_t*>(S->arena_dev + off);
                 S->stats.peak_arena_bytes = std::max<uint64_t>(S->stats.peak_arena_bytes, S->arena.used());
@@ -214,6 +234,11 @@ bool launch(rs_server* S, Lane& L) {
             S->pending.pop_front();
             S->inflight++;
             batch.push_back(&j);
+        }
+        // skipped jobs go back to the front, in their order
+        while (!skipped.empty()) {
+            S->pending.push_front(skipped.back());
+            skipped.pop_back();
         }
         S->stats.peak_inflight = std::max<uint64_t>(S->stats.peak_inflight, S->inflight);
     }
@@ -248,6 +273,7 @@ bool launch(rs_server* S, Lane& L) {
     if (!rc && (L.plan.upload_bytes() > L.up_cap || L.plan.work_bytes() > L.work_cap)) rc = RS_ECAPACITY;
     uint64_t nl = 0;
     if (!rc) {
+        L.plan.set_persistent(false);
         L.plan.bind(L.up, L.work, L.big, L.img);
         rc = cuda_rc(cudaMemcpyAsync(L.up, L.img, L.plan.upload_bytes(), cudaMemcpyHostToDevice, L.st));
         if (!rc) rc = L.plan.issue(S->tab, S->sms, nullptr, L.status_dev, L.st, &nl);
@@ -288,12 +314,13 @@ void worker_main(rs_server* S) {
         }
         bool did = retire(S);
         bool busy = false;
-        for (Lane& L : S->lanes) {
+        for (size_t li = 0; li < S->lanes.size(); ++li) {
+            Lane& L = S->lanes[li];
             if (L.busy) {
                 busy = true;
                 continue;
             }
-            if (launch(S, L)) {
+            if (launch(S, L, li == 0 && S->lanes.size() > 1)) {
                 did = true;
                 busy = true;
             }
@@ -378,7 +405,10 @@ int rs_server_create(rs_ctx* ctx, const rs_server_config* cfg, rs_server** out) 
         if (rc) break;
         L.up_cap = c.lane_bytes / 4;
         L.work_cap = c.lane_bytes - L.up_cap;
-        rc = cuda_rc(cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking));
+        int least = 0, greatest = 0;
+        cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        const bool first = &L == &S->lanes[0];
+        rc = cuda_rc(cudaStreamCreateWithPriority(&L.st, cudaStreamNonBlocking, first ? greatest : least));
         if (!rc) rc = cuda_rc(cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming));
         if (!rc) rc = cuda_rc(cudaMalloc(&L.up, L.up_cap));
         if (!rc) rc = cuda_rc(cudaMalloc(&L.work, L.work_cap));
@@ -427,6 +457,7 @@ int rs_server_submit(rs_server* S, const rs_job* spec, uint64_t* ticket) {
             const rs_request q{spec->n, spec->N, spec->seed, 0, spec->n0, spec->kind};
             rs::GroupPlan::request_cost(q, &j.cost_up, &j.cost_work);
             values = spec->n;
+            j.small = spec->n <= kSmallJob;
         }
     } else if (immediate < 0) {
         const rs::TreeInfo* t = rs::tree_info(spec->tree);
@@ -437,6 +468,7 @@ int rs_server_submit(rs_server* S, const rs_job* spec, uint64_t* ticket) {
         else {
             rs::GroupPlan::query_cost(*t, lo, hi, &j.cost_up, &j.cost_work);
             values = spec->cap;
+            j.small = true;
         }
     }
     if (immediate < 0 && !spec->out_dev) {
