@@ -224,7 +224,8 @@ int sample_impl(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0,
         L.ovf_count = ctx->ovf + nleaves;
         L.big_pool = ctx->big_pool;
         L.big_kmax = big_kmax;
-        L.cap = ctx->leaf_cap ? std::min<uint32_t>(ctx->leaf_cap, rs::kLeafFastCap) : rs::kLeafFastCap;
+        L.cap = ctx->leaf_cap;
+        L.mean_count = n >> D;
         L.sms = ctx->sms;
         L.with_replacement = wr;
     }

@@ -50,9 +50,6 @@ namespace rs {
 
 constexpr uint32_t kHashCap = kLeafFastCap;         // largest selection of the shared-memory paths
 constexpr uint32_t kHashSlack = 64;                 // probing: slots past the end instead of wrap-around
-constexpr uint32_t kHashSlots = 2 * kHashCap + kHashSlack;
-constexpr uint32_t kBitmapBits = 32 * kHashSlots;  // largest leaf range of the bitmap path
-constexpr uint32_t kMaxBuckets = kHashCap + 64;   // bucket path: about one key per bucket
 
 template <typename KeyT>
 struct HashEmpty;
@@ -61,11 +58,17 @@ struct HashEmpty<uint32_t> { static constexpr uint32_t v = 0xFFFFFFFFu; };
 template <>
 struct HashEmpty<uint64_t> { static constexpr uint64_t v = ~0ull; };
 
-template <typename KeyT, int NW>
+// Shared memory of one leaf group: CAP is the largest selection of the
+// shared-memory paths (the table holds 2 CAP + slack keys).
+template <typename KeyT, int NW, uint32_t CAP = kHashCap>
 struct HashShared {
-    KeyT tab[kHashSlots];          // bucket path: keys (first k + 3), then keys in bucket order;
+    static constexpr uint32_t kCap = CAP;
+    static constexpr uint32_t kSlots = 2 * CAP + kHashSlack;
+    static constexpr uint32_t kBits = 32 * kSlots;        // largest leaf range of the bitmap path
+    static constexpr uint32_t kBuckets = CAP + 64;        // bucket path: about one key per bucket
+    KeyT tab[kSlots];              // bucket path: keys (first k + 3), then keys in bucket order;
                                    // probing table; bitmap; tallies
-    uint32_t cnt[kMaxBuckets / 2 + 1];   // bucket path: 16-bit counts, two per word, then offsets
+    uint32_t cnt[kBuckets / 2 + 1];      // bucket path: 16-bit counts, two per word, then offsets
     uint32_t scan_tmp[NW + 1];
     uint32_t warp_cnt[NW];
     uint32_t newcount[3];          // rounds: values added in round r go to newcount[r % 3]
@@ -255,8 +258,8 @@ RS_DEV bool candidate_at(const LeafRec& r, uint64_t thr, Key2 key, uint32_t tag,
 // missing ones from candidates jnext, jnext+1, ... (a candidate counts if it
 // is valid and new), and writes the merged sorted leaf.  False if the stream
 // runs out (the probing path then reports it).
-template <typename KeyT, int NT, int BAR>
-RS_DEV bool bucket_repair(HashShared<KeyT, NT / 32>& sm, const LeafRec& r, Key2 key, uint32_t k, uint64_t thr,
+template <typename KeyT, int NT, int BAR, uint32_t CAP>
+RS_DEV bool bucket_repair(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, Key2 key, uint32_t k, uint64_t thr,
                           KeyT* A, KeyT* B, uint64_t* __restrict__ dst, uint32_t tid) {
     // distinct values of the sorted A, in order, into B
     const uint32_t Q = (k + NT - 1) / NT;
@@ -346,11 +349,11 @@ RS_DEV bool bucket_repair(HashShared<KeyT, NT / 32>& sm, const LeafRec& r, Key2 
 
 // Bucket path.  Returns true on success (leaf written), false if the leaf
 // must take the probing path (whatever was written is overwritten later).
-template <typename KeyT, int NT, int BAR, bool WR>
-RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32>& sm, const LeafRec& r, Key2 key, uint32_t k,
+template <typename KeyT, int NT, int BAR, bool WR, uint32_t CAP = kHashCap>
+RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, Key2 key, uint32_t k,
                         uint64_t* __restrict__ dst, uint32_t tid) {
     const uint32_t tag = WR ? TAG_LEAF_WR : TAG_LEAF_H;
-    const uint32_t nb = max(64u, (k + 63) & ~63u);   // even, <= kMaxBuckets
+    const uint32_t nb = max(64u, (k + 63) & ~63u);   // even, <= kBuckets
     KeyT* A = sm.tab;                     // candidate j at A[j]; later the sorted leaf
     KeyT* B = sm.tab + ((k + 3) & ~3u);   // keys in bucket order
     uint32_t* cw = sm.cnt;                // count of bucket b: 16-bit half b & 1 of word b >> 1
@@ -528,7 +531,7 @@ RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32>& sm, const LeafRec& r, Key2 ke
     if (!group_sync_or<BAR, NT>(dup)) return true;
     rank_pass(false);   // the sorted keys, repeats adjacent
     group_sync<BAR, NT>();
-    return bucket_repair<KeyT, NT, BAR>(sm, r, key, k, thr, A, B, dst, tid);   // rewrites the whole leaf
+    return bucket_repair<KeyT, NT, BAR, CAP>(sm, r, key, k, thr, A, B, dst, tid);   // rewrites the whole leaf
 }
 
 // Rounds of distinct insertion shared by the bitmap and probing paths:
@@ -564,11 +567,11 @@ RS_DEV bool distinct_rounds(uint32_t* newcount, const LeafRec& r, uint64_t thr, 
     return true;
 }
 
-// Count path for dense leaves with replacement (s < kHashSlots): the first
+// Count path for dense leaves with replacement (s below the table size): the first
 // n' valid candidates are tallied per value; an exclusive scan of the tallies
 // gives each value's run of output positions.
-template <typename KeyT, int NT, int BAR>
-RS_DEV void count_leaf(HashShared<KeyT, NT / 32>& sm, const LeafRec& r, Key2 key, uint32_t k,
+template <typename KeyT, int NT, int BAR, uint32_t CAP>
+RS_DEV void count_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, Key2 key, uint32_t k,
                        uint64_t* __restrict__ dst, int* status, uint32_t tid) {
     uint32_t* h = reinterpret_cast<uint32_t*>(sm.tab);
     const uint32_t s = (uint32_t)r.s;
@@ -596,9 +599,9 @@ RS_DEV void count_leaf(HashShared<KeyT, NT / 32>& sm, const LeafRec& r, Key2 key
     group_sync<BAR, NT>();
 }
 
-// Bitmap path for leaves without replacement with s <= kBitmapBits.
-template <typename KeyT, int NT, int BAR>
-RS_DEV void bitmap_leaf(HashShared<KeyT, NT / 32>& sm, const LeafRec& r, Key2 key, uint32_t k, bool comp,
+// Bitmap path for leaves without replacement with s at most the table bits.
+template <typename KeyT, int NT, int BAR, uint32_t CAP>
+RS_DEV void bitmap_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, Key2 key, uint32_t k, bool comp,
                         uint64_t* __restrict__ dst, int* status, uint32_t tid) {
     constexpr int NW = NT / 32;
     const uint32_t lane = tid & 31, warp = tid >> 5;
@@ -670,8 +673,8 @@ RS_DEV void bitmap_leaf(HashShared<KeyT, NT / 32>& sm, const LeafRec& r, Key2 ke
 }
 
 // Probing path.  Returns false if a probe ran past the slack (general path).
-template <typename KeyT, int NT, int BAR, bool WR>
-RS_DEV bool probe_leaf(HashShared<KeyT, NT / 32>& sm, const LeafRec& r, Key2 key, uint32_t k,
+template <typename KeyT, int NT, int BAR, bool WR, uint32_t CAP>
+RS_DEV bool probe_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, Key2 key, uint32_t k,
                        uint64_t* __restrict__ dst, int* status, uint32_t tid) {
     constexpr int NW = NT / 32;
     constexpr KeyT E = HashEmpty<KeyT>::v;
@@ -768,27 +771,27 @@ RS_DEV bool probe_leaf(HashShared<KeyT, NT / 32>& sm, const LeafRec& r, Key2 key
 // false if the leaf must go to the general (global-memory) path, having
 // written nothing of use.  All NT threads of the group call it; tid is the
 // thread's index in the group.
-template <typename KeyT, int NT, int BAR, bool WR>
-RS_DEV bool hash_leaf(HashShared<KeyT, NT / 32>& sm, const LeafRec& r, Key2 key, uint64_t* __restrict__ out,
+template <typename KeyT, int NT, int BAR, bool WR, uint32_t CAP = kHashCap>
+RS_DEV bool hash_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, Key2 key, uint64_t* __restrict__ out,
                       int* status, uint32_t tid, uint32_t cap) {
     const bool comp = !WR && (r.np > r.s - r.np);
     const uint64_t k64 = comp ? r.s - r.np : r.np;
     if (k64 > cap) return false;
     const uint32_t k = (uint32_t)k64;
     uint64_t* dst = out + r.off;
-    const bool use_bitmap = !WR && r.s <= kBitmapBits && (comp || r.s <= 64ull * k);
+    const bool use_bitmap = !WR && r.s <= HashShared<KeyT, NT / 32, CAP>::kBits && (comp || r.s <= 64ull * k);
     if (comp && !use_bitmap) return false;
     if (k == 0 && !comp) return true;
-    if (WR && r.s < kHashSlots && r.s <= 64ull * k) {
-        count_leaf<KeyT, NT, BAR>(sm, r, key, k, dst, status, tid);
+    if (WR && r.s < HashShared<KeyT, NT / 32, CAP>::kSlots && r.s <= 64ull * k) {
+        count_leaf<KeyT, NT, BAR, CAP>(sm, r, key, k, dst, status, tid);
         return true;
     }
     if (use_bitmap) {
-        bitmap_leaf<KeyT, NT, BAR>(sm, r, key, k, comp, dst, status, tid);
+        bitmap_leaf<KeyT, NT, BAR, CAP>(sm, r, key, k, comp, dst, status, tid);
         return true;
     }
-    if (bucket_leaf<KeyT, NT, BAR, WR>(sm, r, key, k, dst, tid)) return true;
-    return probe_leaf<KeyT, NT, BAR, WR>(sm, r, key, k, dst, status, tid);
+    if (bucket_leaf<KeyT, NT, BAR, WR, CAP>(sm, r, key, k, dst, tid)) return true;
+    return probe_leaf<KeyT, NT, BAR, WR, CAP>(sm, r, key, k, dst, status, tid);
 }
 
 }  // namespace rs

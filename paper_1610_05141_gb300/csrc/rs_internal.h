@@ -49,10 +49,11 @@ struct LeafLaunch {
     uint32_t* ovf_count;
     void* big_pool;          // scratch of big_pool_bytes(big_kmax) bytes, or null when big_kmax = 0
     uint64_t big_kmax;
-    uint32_t cap;            // 0 = kLeafCap
+    uint32_t cap;            // testing knob: largest selection of the shared-memory paths, 0 = the kernel's
     int sms;
     bool with_replacement;
     int blocks_per_sm = 0;   // leaf-kernel blocks per SM, 0 = as many as fit
+    uint64_t mean_count = 0; // samples per leaf on average (picks the kernel's shape)
 };
 
 // Leaf H (or leaf WR) for every leaf, then the general path for the leaves

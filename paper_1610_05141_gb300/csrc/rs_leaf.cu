@@ -25,20 +25,26 @@ struct LeafJob {
     uint32_t cap;            // largest selection handled here
 };
 
+// Two shapes of the leaf kernel: 256 threads with room for 4,864 values
+// (leaves of about 4,096 samples, 4 blocks per SM), and 512 threads with
+// room for 9,728 (leaves of about 8,192, 2 blocks per SM): the same warps per
+// SM, half the per-leaf fixed costs per sample for the larger leaves.
 constexpr int kHashThreads = 256;
+constexpr int kLargeThreads = 512;
+constexpr uint32_t kLargeCap = 2 * kLeafFastCap;
 
 // One block per leaf at a time, persistent over the leaves; leaves the
 // shared-memory table cannot take go to the general path's list.
-template <typename KeyT, bool WR>
-__global__ void __launch_bounds__(kHashThreads) leaf_kernel(LeafJob job) {
+template <typename KeyT, bool WR, int NT, uint32_t CAP>
+__global__ void __launch_bounds__(NT) leaf_kernel(LeafJob job) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto& sm = *reinterpret_cast<HashShared<KeyT, kHashThreads / 32>*>(smem_raw);
+    auto& sm = *reinterpret_cast<HashShared<KeyT, NT / 32, CAP>*>(smem_raw);
     const Key2 key = make_key(job.seed);
     for (uint64_t leaf = blockIdx.x; leaf < job.nleaves; leaf += gridDim.x) {
         const NodeRec r = job.leaves[leaf];
         if (r.c == 0) continue;
         const LeafRec lr{r.lo, r.S, r.c, r.off, job.first_id + leaf};
-        if (!hash_leaf<KeyT, kHashThreads, 0, WR>(sm, lr, key, job.out, job.status, threadIdx.x, job.cap)) {
+        if (!hash_leaf<KeyT, NT, 0, WR, CAP>(sm, lr, key, job.out, job.status, threadIdx.x, job.cap)) {
             if (threadIdx.x == 0) job.ovf_list[atomicAdd(job.ovf_count, 1u)] = (uint32_t)leaf;
         }
     }
@@ -81,33 +87,41 @@ __global__ void __launch_bounds__(kBigThreads) big_leaf_kernel(LeafJob job, BigS
 // Host launchers.
 // ---------------------------------------------------------------------------
 
-template <typename KeyT, bool WR>
-static cudaError_t launch_fast(const LeafJob& job, int sms, int per_sm_cap, cudaStream_t st) {
-    const size_t smem = sizeof(HashShared<KeyT, kHashThreads / 32>);
-    auto kern = leaf_kernel<KeyT, WR>;
+template <typename KeyT, bool WR, int NT, uint32_t CAP>
+static cudaError_t launch_fast(LeafJob job, uint32_t cap_knob, int sms, int per_sm_cap, cudaStream_t st) {
+    job.cap = cap_knob ? std::min<uint32_t>(cap_knob, CAP) : CAP;
+    const size_t smem = sizeof(HashShared<KeyT, NT / 32, CAP>);
+    auto kern = leaf_kernel<KeyT, WR, NT, CAP>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kHashThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
     if (e != cudaSuccess) return e;
     if (per_sm_cap > 0 && per_sm > per_sm_cap) per_sm = per_sm_cap;
     if (per_sm < 1) per_sm = 1;
     const uint64_t grid = std::min<uint64_t>(job.nleaves, (uint64_t)sms * per_sm);
-    kern<<<(unsigned)grid, kHashThreads, smem, st>>>(job);
+    kern<<<(unsigned)grid, NT, smem, st>>>(job);
     return cudaGetLastError();
 }
 
+template <bool WR, int NT, uint32_t CAP>
+static cudaError_t launch_shape(const LeafJob& job, const LeafLaunch& L, cudaStream_t st) {
+    if (L.smax <= (1ull << 32)) return launch_fast<uint32_t, WR, NT, CAP>(job, L.cap, L.sms, L.blocks_per_sm, st);
+    return launch_fast<uint64_t, WR, NT, CAP>(job, L.cap, L.sms, L.blocks_per_sm, st);
+}
+
 cudaError_t launch_leaves(const LeafLaunch& L, cudaStream_t st) {
-    LeafJob job{L.leaves, L.nleaves, L.first_id, L.seed, L.out, L.status, L.ovf_list, L.ovf_count,
-                L.cap ? std::min<uint32_t>(L.cap, kHashCap) : kHashCap};
+    LeafJob job{L.leaves, L.nleaves, L.first_id, L.seed, L.out, L.status, L.ovf_list, L.ovf_count, 0};
     cudaError_t e = cudaMemsetAsync(L.ovf_count, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
-    const bool narrow = L.smax <= (1ull << 32);
-    const int cap = L.blocks_per_sm;
+    // leaves averaging well above the small shape's room take the large one
+    const bool large = L.mean_count * 20 > (uint64_t)kLeafFastCap * 17;
     if (L.with_replacement)
-        e = narrow ? launch_fast<uint32_t, true>(job, L.sms, cap, st) : launch_fast<uint64_t, true>(job, L.sms, cap, st);
+        e = large ? launch_shape<true, kLargeThreads, kLargeCap>(job, L, st)
+                  : launch_shape<true, kHashThreads, kLeafFastCap>(job, L, st);
     else
-        e = narrow ? launch_fast<uint32_t, false>(job, L.sms, cap, st) : launch_fast<uint64_t, false>(job, L.sms, cap, st);
+        e = large ? launch_shape<false, kLargeThreads, kLargeCap>(job, L, st)
+                  : launch_shape<false, kHashThreads, kLeafFastCap>(job, L, st);
     if (e != cudaSuccess) return e;
     if (L.big_kmax == 0) return cudaSuccess;   // no leaf can exceed the capacity
     BigScratch sc;

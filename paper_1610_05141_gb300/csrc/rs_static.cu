@@ -102,7 +102,8 @@ extern "C" int rs_sample_static(uint64_t n, uint64_t N, uint64_t seed, uint32_t 
     L.ovf_count = ovf + nleaves;
     L.big_pool = big;
     L.big_kmax = bound > 64 ? std::min<uint64_t>(bound, kStaticBigKeys) : 0;
-    L.cap = rs::kLeafFastCap;
+    L.cap = 0;
+    L.mean_count = 0;   // the small shape (the static scratch sizes follow it)
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return RS_ECUDA;
     L.sms = sms;

@@ -220,3 +220,19 @@ def test_pipelined_tree_matches_oracle(rs, ctx, oracle, kind):
         rs.rs_set_pipeline(ctx, 0, 3)
     assert_same(got, seq, ("pipelined vs sequential", kind))
     assert_same(got, oracle.sample(n, N, seed, n0, kind), (n, N, seed, n0, kind))
+
+
+@pytest.mark.parametrize("kind,N", [(0, 2**47), (0, 2**44), (0, 10**9 + 7), (1, 2**40), (0, 2**60)])
+def test_large_leaf_shape_matches_oracle(rs, ctx, oracle, kind, N):
+    """Leaves averaging about 6,000 samples take the 512-thread leaf kernel
+    with room for 9,728 values: every sampled leaf equals the oracle's."""
+    n, seed, n0 = 2 * 10**7, 91 + kind, 8192           # depth 12, ~4,900 samples per leaf
+    n, n0 = (6 * 10**7, 8192) if N == 2**47 else (n, n0)   # depth 13, ~7,300 per leaf
+    call = {0: rs.rs_sample, 1: rs.rs_sample_with_replacement}[kind]
+    got = run(rs, ctx, call, n, N, seed, n0)
+    recs, D = oracle.tree(n, N, seed, n0, kind)
+    rng = np.random.default_rng(seed)
+    for i in sorted(set(rng.integers(0, len(recs), 24).tolist()) | {0, len(recs) - 1}):
+        lo, s, c, off = (int(x) for x in recs[i])
+        want = oracle.leaf(seed, kind, D, i, recs[i])
+        assert_same(got[off:off + c], want, ("leaf", i, n, N, kind))
