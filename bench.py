@@ -9,8 +9,10 @@ deviates) + every leaf (selection, sort, write-out of 8 GB of uint64).
 
 Prints one JSON line.  `value` is samples/s over the device-timed steps
 (output buffer resident; the 8 GB output exceeds the 129 MB L2, so no flush
-is needed); `e2e` adds the device-to-host copy of each step's sample into
-pinned host memory.  `roofline` relates the leaf kernel's algorithmic write
+is needed); `e2e` is the same through rs_sample_to_host, which also copies
+each step's sample into pinned host memory (piece by piece while the next
+pieces are made).  `batch` and `serve` measure the batched and served paths
+against one call per request.  `roofline` relates the leaf kernel's algorithmic write
 bytes (8 B per sample) per launch to its CUDA-event duration on its own
 stream.  Under torchrun with N > 1, every rank runs an independent replica
 (seed + rank) on its own GPU: the path does not shard.
@@ -527,9 +529,8 @@ def run_ours(args):
         t0 = time.perf_counter()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(e2e_steps):
-            rs.rs_sample(ctx, N_SAMPLES, UNIVERSE, seed, N0, out, stream)
-            host.copy_(out, non_blocking=True)
+        for _ in range(e2e_steps):   # the sample goes to host memory piece by piece while it is made
+            rs.rs_sample_to_host(ctx, rs.RS_KIND_H, N_SAMPLES, UNIVERSE, seed, N0, out, host, stream)
         e1.record(stream)
         stream.synchronize()
         barrier()

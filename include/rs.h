@@ -93,6 +93,22 @@ int rs_sample_with_replacement(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t see
 int rs_sample_b(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0,
                 uint64_t* out_dev, void* stream);
 
+/* rs_sample / rs_sample_with_replacement / rs_sample_b (by `kind`, an
+ * RS_KIND_* value) with the sample also copied to host memory
+ * out_host[0..n) while it is produced: once the split tree is done the
+ * output is cut at eight leaf boundaries (a small read-back that waits for
+ * the tree), and each piece goes to the host on a second stream as soon as
+ * its leaves are written, while the next piece's leaves run.  out_dev: n
+ * device slots (the sample, as with rs_sample); out_host: n slots of
+ * page-locked host memory (cudaHostAlloc, torch's pin_memory) -- pageable
+ * memory works but the copies then do not overlap.  Returns before the
+ * copies finish; later work on `stream`, rs_sync and a synchronize of
+ * `stream` wait for them.  The paper has no counterpart (its GPU timings
+ * note that the transfer to the CPU dominated).  Errors: as rs_sample, and
+ * RS_EINVAL for a bad kind or a null out_host with n > 0. */
+int rs_sample_to_host(rs_ctx* ctx, int kind, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0,
+                      uint64_t* out_dev, uint64_t* out_host, void* stream);
+
 /* Leaf records of the split tree of (n, N, seed, n0): recs_dev[4i..4i+3] =
  * (lo, s, n', offset) of leaf i (0-based, left to right): leaf i covers the
  * 0-based positions [lo, lo+s), holds n' samples and writes them at

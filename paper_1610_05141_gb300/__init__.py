@@ -84,6 +84,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "rs_phase_totals": (i32, [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(u64)]),
         "rs_launch_count": (i32, [vp, ctypes.POINTER(u64)]),
         "rs_set_pipeline": (i32, [vp, i32, i32]),
+        "rs_sample_to_host": (i32, [vp, i32, u64, u64, u64, u32, vp, vp, vp]),
         "rs_sample_static": (i32, [u64, u64, u64, u32, vp, vp]),
         "rs_batch_plan": (i32, [vp, vp, u32, ctypes.POINTER(vp)]),
         "rs_batch_run": (i32, [vp, vp, vp, vp]),
@@ -186,6 +187,12 @@ def rs_sample_with_replacement(ctx: Context, n, N, seed, n0, out, stream=None, c
 def rs_sample_b(ctx: Context, n, N, seed, n0, out, stream=None, check=True) -> int:
     rc = load().rs_sample_b(ctx.handle, n, N, seed, n0, _ptr(out), _stream(stream))
     return _check(rc, "rs_sample_b") if check else rc
+
+
+def rs_sample_to_host(ctx: Context, kind, n, N, seed, n0, out, out_host, stream=None, check=True) -> int:
+    """out_host: a pinned torch CPU tensor (or a host address)."""
+    rc = load().rs_sample_to_host(ctx.handle, kind, n, N, seed, n0, _ptr(out), _ptr(out_host), _stream(stream))
+    return _check(rc, "rs_sample_to_host") if check else rc
 
 
 def rs_split_tree(ctx: Context, n, N, seed, n0, kind, recs, max_leaves, stream=None, check=True) -> int:

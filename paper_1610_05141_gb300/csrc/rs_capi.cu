@@ -31,6 +31,11 @@ struct rs_ctx {
     cudaStream_t tree_stream = nullptr;
     cudaEvent_t ev_fork = nullptr;
     std::vector<cudaEvent_t> ev_part;
+    // copies of the sample to host memory while it is produced
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_copied = nullptr;
+    uint64_t* bounds_dev = nullptr;     // output offsets at part boundaries
+    uint64_t* bounds_host = nullptr;    // pinned
     bool profiling = false;
     struct PhaseRec {               // event indices of one profiled call
         size_t start, tree_end, end;
@@ -97,6 +102,33 @@ size_t record_event(rs_ctx* ctx, cudaStream_t st) {
     return ctx->ev_used++;
 }
 
+constexpr int kCopyParts = 8;   // pieces of a sample copied to the host while the next ones are made
+
+// Output offsets of the first leaf of each of `parts` equal runs of leaves,
+// then n: the pieces of the output the leaves of each run write.
+__global__ void part_bounds_kernel(const rs::NodeRec* __restrict__ leaves, uint64_t per_part, uint32_t parts,
+                                   uint64_t n, uint64_t* __restrict__ bounds) {
+    const uint32_t j = threadIdx.x;
+    if (j < parts) bounds[j] = leaves[(uint64_t)j * per_part].off;
+    if (j == parts) bounds[j] = n;
+}
+
+int ensure_copy(rs_ctx* ctx, size_t parts) {
+    if (!ctx->copy_stream && cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return RS_ECUDA;
+    if (!ctx->ev_copied && cudaEventCreateWithFlags(&ctx->ev_copied, cudaEventDisableTiming) != cudaSuccess)
+        return RS_ECUDA;
+    if (!ctx->bounds_dev && cudaMalloc(&ctx->bounds_dev, 65 * sizeof(uint64_t)) != cudaSuccess) return RS_ENOMEM;
+    if (!ctx->bounds_host && cudaMallocHost(&ctx->bounds_host, 65 * sizeof(uint64_t)) != cudaSuccess)
+        return RS_ENOMEM;
+    while (ctx->ev_part.size() < parts) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return RS_ECUDA;
+        ctx->ev_part.push_back(e);
+    }
+    return RS_OK;
+}
+
 // The tree stream (highest priority) and its events, made on first use.
 int ensure_pipeline(rs_ctx* ctx, size_t parts) {
     if (!ctx->tree_stream) {
@@ -146,7 +178,7 @@ int build_tree(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0, 
 }
 
 int sample_impl(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0, int kind, uint64_t* out,
-                void* stream) {
+                void* stream, uint64_t* host_out = nullptr) {
     if (!ctx) return RS_EINVAL;
     int rc = check_sample_args(n, N, n0, kind == RS_KIND_WR, out);
     if (rc || n == 0) return rc;
@@ -162,10 +194,16 @@ int sample_impl(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0,
     // Deep trees: the subtrees under level c are built one after another on
     // the tree stream, and the leaves of each start on `st` as soon as its
     // subtree is done, beside the FP64 work of the next subtrees.
-    const int c = (ctx->pipe_log2 > 0 && D >= ctx->pipe_log2 + 9) ? ctx->pipe_log2 : 0;
-    const uint64_t parts = 1ull << c, per_part = nleaves >> c;
+    const int c = (!host_out && ctx->pipe_log2 > 0 && D >= ctx->pipe_log2 + 9) ? ctx->pipe_log2 : 0;
+    // copying to the host: the leaves run in pieces, each copied as soon as it is done
+    const int cc = host_out ? std::min(D, 3) : 0;
+    const uint64_t parts = 1ull << (c + cc), per_part = nleaves >> (c + cc);
     if (c) {
         rc = ensure_pipeline(ctx, parts);
+        if (rc) return rc;
+    }
+    if (host_out) {
+        rc = ensure_copy(ctx, parts);
         if (rc) return rc;
     }
     size_t prof = 0;
@@ -191,6 +229,15 @@ int sample_impl(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0,
         if (prof) ctx->prof_calls[prof - 1].tree_end = record_event(ctx, ts);
     }
     if (rc) return rc;
+    if (host_out) {
+        // where each piece of the output starts: known once the tree is done
+        part_bounds_kernel<<<1, 128, 0, st>>>(ctx->nodes + nleaves, per_part, (uint32_t)parts, n, ctx->bounds_dev);
+        ctx->launches += 1;
+        rc = cuda_rc(cudaMemcpyAsync(ctx->bounds_host, ctx->bounds_dev, (parts + 1) * sizeof(uint64_t),
+                                     cudaMemcpyDeviceToHost, st));
+        if (!rc) rc = cuda_rc(cudaStreamSynchronize(st));
+        if (rc) return rc;
+    }
     const uint64_t smax = (N >> D) + ((N & (nleaves - 1)) ? 1 : 0);
     rs::LeafLaunch L{};
     uint64_t big_kmax = 0;
@@ -252,6 +299,19 @@ int sample_impl(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0,
             ctx->prof_calls[prof - 1].leaves.emplace_back(a, b);
             ctx->prof_calls[prof - 1].end = b;
         }
+        if (!rc && host_out) {
+            const uint64_t b0 = ctx->bounds_host[j], b1 = ctx->bounds_host[j + 1];
+            rc = cuda_rc(cudaEventRecord(ctx->ev_part[j], st));
+            if (!rc) rc = cuda_rc(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_part[j], 0));
+            if (!rc && b1 > b0)
+                rc = cuda_rc(cudaMemcpyAsync(host_out + b0, out + b0, (b1 - b0) * sizeof(uint64_t),
+                                             cudaMemcpyDeviceToHost, ctx->copy_stream));
+        }
+    }
+    if (!rc && host_out) {
+        // later work on `stream` (and rs_sync) waits for the copies
+        rc = cuda_rc(cudaEventRecord(ctx->ev_copied, ctx->copy_stream));
+        if (!rc) rc = cuda_rc(cudaStreamWaitEvent(st, ctx->ev_copied, 0));
     }
     return rc;
 }
@@ -313,6 +373,10 @@ int rs_destroy(rs_ctx* ctx) {
     cudaFree(ctx->words);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : ctx->ev_part) cudaEventDestroy(e);
+    if (ctx->ev_copied) cudaEventDestroy(ctx->ev_copied);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    cudaFree(ctx->bounds_dev);
+    if (ctx->bounds_host) cudaFreeHost(ctx->bounds_host);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->tree_stream) cudaStreamDestroy(ctx->tree_stream);
     delete ctx;
@@ -336,6 +400,12 @@ int rs_sample_with_replacement(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t see
 
 int rs_sample_b(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0, uint64_t* out_dev, void* stream) {
     return sample_impl(ctx, n, N, seed, n0, RS_KIND_B, out_dev, stream);
+}
+
+int rs_sample_to_host(rs_ctx* ctx, int kind, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0, uint64_t* out_dev,
+                      uint64_t* out_host, void* stream) {
+    if (kind < RS_KIND_H || kind > RS_KIND_B || (n > 0 && !out_host)) return RS_EINVAL;
+    return sample_impl(ctx, n, N, seed, n0, kind, out_dev, stream, out_host);
 }
 
 int rs_split_tree(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0, int kind, uint64_t* recs_dev,

@@ -236,3 +236,20 @@ def test_large_leaf_shape_matches_oracle(rs, ctx, oracle, kind, N):
         lo, s, c, off = (int(x) for x in recs[i])
         want = oracle.leaf(seed, kind, D, i, recs[i])
         assert_same(got[off:off + c], want, ("leaf", i, n, N, kind))
+
+
+@pytest.mark.parametrize("kind,n,N,n0,pinned", [(0, 10**6, 10**9, 4096, True), (1, 10**6, 2**40, 4096, True),
+                                                (2, 10**5, 10**8, 4096, False), (0, 3000, 10**6, 4096, True),
+                                                (0, 6 * 10**6, 2**50, 1024, False)])
+def test_sample_to_host_matches_device_sample(rs, ctx, oracle, kind, n, N, n0, pinned):
+    """The sample copied to host memory piece by piece while it is made equals
+    the device sample and the oracle's."""
+    seed = 57 + kind
+    out = torch.full((n,), -1, dtype=torch.int64, device="cuda")
+    host = torch.full((n,), -1, dtype=torch.int64, pin_memory=pinned)
+    rs.rs_sample_to_host(ctx, kind, n, N, seed, n0, out, host)
+    assert rs.rs_sync(ctx) == rs.RS_OK
+    got = host.numpy().view(np.uint64)
+    assert np.array_equal(got, out.cpu().numpy().view(np.uint64))
+    if n <= 10**6:
+        assert_same(got, oracle.sample(n, N, seed, n0, kind), ("to host", kind, n, N))
