@@ -308,6 +308,62 @@ def run_batch(rs, ctx, stream, args):
     }
 
 
+def run_rows(rs, ctx, stream, args):
+    """The other rows of the method at their configurations' sizes: sampling
+    with replacement (n = 1e9 from 2^40, binomial splits), Algorithm B as the
+    base case (n = 1e9 from 2^50), and Bernoulli sampling of 2^36 positions
+    with p = 1e-4 and 1e-2 (whole range) and p = 0.5 (a chunk-aligned window
+    of 2^30 positions: the whole output would be 275 GB).  Device-timed
+    (CUDA events on the stream), a few steps each after one warm-up call."""
+    import torch
+    peak, _ = hbm_peak()
+    out = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, steps):
+        fn()
+        stream.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        stream.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    buf = torch.empty(10**9, dtype=torch.int64, device="cuda")
+    for name, call, N, steps in (("a5_with_replacement", rs.rs_sample_with_replacement, 2**40, args.row_steps),
+                                 ("a7_leaf_b", rs.rs_sample_b, 2**50, max(1, args.row_steps // 3))):
+        rs.rs_set_profiling(ctx, True)
+        ms = timed(lambda: call(ctx, 10**9, N, 3, N0, buf, stream), steps)
+        tree_ms, leaf_ms, calls = rs.rs_phase_totals(ctx)
+        rs.rs_set_profiling(ctx, False)
+        if rs.rs_sync(ctx, stream) != rs.RS_OK:
+            raise RuntimeError(f"{name} failed")
+        leaf = leaf_ms / calls
+        out[name] = {"workload": f"n=1e9 from 1..2^{N.bit_length() - 1}, n0={N0}", "ms_per_step": ms,
+                     "samples_per_s": 1e9 / (ms / 1000), "phases_ms": {"split_tree": tree_ms / calls, "leaves": leaf},
+                     "leaf_write_gbs": 8e9 / (leaf / 1000) / 1e9, "leaf_frac_of_hbm": 8e9 / (leaf / 1000) / 1e9 / peak}
+    bern = {}
+    for p, a, b in ((1e-4, 0, 2**36), (1e-2, 0, 2**36), (0.5, 0, 2**30)):
+        cap = buf.numel()
+        holder = {}
+
+        def call_b():
+            holder["rc"], holder["count"] = rs.rs_bernoulli(ctx, p, 2**36, 5, N0, a, b, buf, cap, stream, check=False)
+
+        ms = timed(call_b, args.row_steps)
+        if holder["rc"] != rs.RS_OK:
+            raise RuntimeError(f"bernoulli p={p} failed: {holder['rc']}")
+        cnt = holder["count"]
+        bern[f"p={p:g}"] = {"positions": b - a, "window": [a, b], "emitted": cnt, "ms_per_call": ms,
+                            "emitted_per_s": cnt / (ms / 1000), "positions_per_s": (b - a) / (ms / 1000),
+                            "write_gbs": 8 * cnt / (ms / 1000) / 1e9,
+                            "note": "whole call: count pass, scan, write pass, and the count read back"}
+    out["a6_bernoulli"] = {"N": 2**36, "n0": N0, "by_p": bern}
+    del buf
+    return out
+
+
 def _pct(x, q):
     return float(np.percentile(np.asarray(x, dtype=np.float64), q)) if len(x) else None
 
@@ -547,6 +603,11 @@ def run_ours(args):
             out = None
             torch.cuda.empty_cache()
             serve = run_serve(rs, ctx, stream, args)
+        rows = None
+        if not args.no_rows:
+            out = None
+            torch.cuda.empty_cache()
+            rows = run_rows(rs, ctx, stream, args)
     clk = clocks.summary(wall0, wall1)
 
     ms_per_step = ms_total / args.steps
@@ -583,6 +644,8 @@ def run_ours(args):
         line["batch"] = batch
     if serve is not None:
         line["serve"] = serve
+    if rows is not None:
+        line["rows"] = rows
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -604,6 +667,8 @@ def main():
     ap.add_argument("--batch-runs", type=int, default=5)
     ap.add_argument("--unbatched-requests", type=int, default=3000)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-rows", action="store_true", help="skip with-replacement, leaf B and Bernoulli")
+    ap.add_argument("--row-steps", type=int, default=6)
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="length of each open-loop serving run")
     ap.add_argument("--serve-capacity-jobs", type=int, default=4000)
     ap.add_argument("--serve-unbatched-jobs", type=int, default=1000)

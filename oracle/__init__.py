@@ -70,6 +70,7 @@ def _load():
             "or_v_closed": (dbl, [u64]),
             "or_candidate": (i32, [u64, u32, u64, u64, u64, p64]),
             "or_log": (dbl, [dbl]),
+            "or_log_table_entry": (None, [i32, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
             "or_log1p": (dbl, [dbl]),
             "or_exp": (dbl, [dbl]),
             "or_lf": (dbl, [u64]),
@@ -141,6 +142,13 @@ def candidate(seed, tag, node, s, j):
 
 
 # --- math ------------------------------------------------------------------
+
+def log_table_entry(i):
+    """Entry i of the logarithm's table: (RN(1/c), hi, lo) with hi + lo = -ln RN(1/c)."""
+    inv, hi, lo = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _load().or_log_table_entry(i, ctypes.byref(inv), ctypes.byref(hi), ctypes.byref(lo))
+    return inv.value, hi.value, lo.value
+
 
 def log(x):
     return float(_load().or_log(x))

@@ -125,14 +125,14 @@ int or_candidate(uint64_t seed, uint32_t tag, uint64_t id, uint64_t s, uint64_t 
 }
 
 /* ------------------------------------------------------------------------ */
-/* Project-owned FP64 math, used only through + - * / sqrt and integer ops  */
-/* so that two independent implementations agree bit for bit.               */
+/* Project-owned FP64 math, used only through + - * / sqrt, the fused       */
+/* multiply-add and integer ops (each IEEE correctly rounded), so that two  */
+/* independent implementations agree bit for bit.                          */
 /* ------------------------------------------------------------------------ */
 
 static double from_bits(uint64_t b) { double d; memcpy(&d, &b, 8); return d; }
 static uint64_t to_bits(double d) { uint64_t b; memcpy(&b, &d, 8); return b; }
 
-#define RT2     from_bits(0x3ff6a09e667f3bcdull)  /* double nearest sqrt(2)            */
 #define LN2_HI  from_bits(0x3fe62e42fee00000ull)  /* ln 2 truncated to 32 significant bits */
 #define LN2_LO  from_bits(0x3dea39ef35793c76ull)  /* RN(ln 2 - LN2_HI)                 */
 #define INV_LN2 from_bits(0x3ff71547652b82feull)  /* RN(1 / ln 2)                      */
@@ -140,38 +140,127 @@ static uint64_t to_bits(double d) { uint64_t b; memcpy(&b, &d, 8); return b; }
 #define HAT_D1  from_bits(0x3ffb72cd3f331398ull)  /* RN(2 sqrt(2/e))                   */
 #define HAT_D2  from_bits(0x3fecc3ebd3bc711aull)  /* RN(3 - 2 sqrt(3/e))               */
 
-/* Natural logarithm of a normal x > 0.  x = 2^e m with m in (sqrt2/2, sqrt2];
- * ln m = 2 atanh(s), s = (m-1)/(m+1), by the atanh Taylor series
- * s + s^3/3 + s^5/5 + ... truncated after s^25/25 (|s| < 0.1716). */
+/* Double-double arithmetic for building the logarithm table: error-free
+ * sums (Knuth) and products (by fused multiply-add), then renormalization. */
+typedef struct { double hi, lo; } dd_t;
+static dd_t dd_fast2(double a, double b) { double s = a + b; dd_t r = {s, b - (s - a)}; return r; }
+static dd_t dd_two_sum(double a, double b)
+{
+    double s = a + b;
+    double bb = s - a;
+    dd_t r = {s, (a - (s - bb)) + (b - bb)};
+    return r;
+}
+static dd_t dd_add(dd_t a, dd_t b)
+{
+    dd_t s = dd_two_sum(a.hi, b.hi);
+    double e = s.lo + (a.lo + b.lo);
+    return dd_fast2(s.hi, e);
+}
+static dd_t dd_mul(dd_t a, dd_t b)
+{
+    double p = a.hi * b.hi;
+    double e = fma(a.hi, b.hi, -p);
+    e = e + (a.hi * b.lo + a.lo * b.hi);
+    return dd_fast2(p, e);
+}
+/* a / b to double-double precision: three quotient digits. */
+static dd_t dd_div(dd_t a, dd_t b)
+{
+    double q1 = a.hi / b.hi;
+    dd_t t = dd_mul(b, (dd_t){q1, 0.0});
+    dd_t r = dd_add(a, (dd_t){-t.hi, -t.lo});
+    double q2 = r.hi / b.hi;
+    t = dd_mul(b, (dd_t){q2, 0.0});
+    r = dd_add(r, (dd_t){-t.hi, -t.lo});
+    double q3 = r.hi / b.hi;
+    dd_t q = dd_fast2(q1, q2);
+    return dd_add(q, (dd_t){q3, 0.0});
+}
+
+/* ln v for v in (1/2, 1] in double-double: 2 atanh(s), s = (v-1)/(v+1),
+ * sum over k < 36 of s^(2k+1)/(2k+1) (|s| <= 1/3: the first term left
+ * out is below 2^-110 relative). */
+static dd_t dd_log_unit(double v)
+{
+    dd_t s = dd_div((dd_t){v - 1.0, 0.0}, dd_two_sum(v, 1.0));
+    dd_t s2 = dd_mul(s, s);
+    dd_t term = s, sum = s;
+    for (int k = 1; k < 36; ++k) {
+        term = dd_mul(term, s2);
+        sum = dd_add(sum, dd_div(term, (dd_t){(double)(2 * k + 1), 0.0}));
+    }
+    dd_t r = {2.0 * sum.hi, 2.0 * sum.lo};
+    return r;
+}
+
+/* Table of the logarithm: mantissa interval i of [1, 2) (i = 1..126, width
+ * 2^-7) has centre c = 1 + (2i+1)/256, inv = RN(1/c) and L = -ln(inv) as a
+ * double-double; intervals 0 and 127 use c = 1 (see or_log). */
+static double log_inv[128], log_hi[128], log_lo[128];
+
+__attribute__((constructor)) static void build_log_table(void)
+{
+    for (int i = 0; i < 128; ++i) {
+        if (i == 0 || i == 127) {
+            log_inv[i] = 1.0;
+            log_hi[i] = 0.0;
+            log_lo[i] = 0.0;
+            continue;
+        }
+        double c = 1.0 + (double)(2 * i + 1) / 256.0;
+        double inv = 1.0 / c;
+        dd_t l = dd_log_unit(inv);
+        log_inv[i] = inv;
+        log_hi[i] = -l.hi;
+        log_lo[i] = -l.lo;
+    }
+}
+
+/* Entry i of the logarithm table (for tests): 1/c rounded, and -ln of it
+ * as a double-double. */
+void or_log_table_entry(int i, double* inv, double* hi, double* lo)
+{
+    *inv = log_inv[i & 127];
+    *hi = log_hi[i & 127];
+    *lo = log_lo[i & 127];
+}
+
+/* Natural logarithm of a normal x > 0.  x = 2^e m, m in [1, 2); the top 7
+ * bits of m pick an interval with centre c and inv = RN(1/c), and
+ * ln m = -ln(inv) + ln(1 + r), r = m inv - 1 (one fused multiply-add,
+ * |r| <= 2^-8), ln(1 + r) by its Taylor polynomial to r^8/8 (Horner with
+ * fused multiply-adds).  The two intervals next to 1 use c = 1 and r = m - 1
+ * (or m/2 - 1 with e + 1), exact, so that ln x near 1 keeps its relative
+ * accuracy; there |r| <= 2^-7. */
 double or_log(double x)
 {
     uint64_t bits = to_bits(x);
     int64_t e = (int64_t)((bits >> 52) & 0x7FF) - 1023;
+    int i = (int)((bits >> 45) & 0x7F);
     double m = from_bits((bits & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull);
-    if (m > RT2) { m = m * 0.5; e = e + 1; }
-    double f = m - 1.0;
-    double s = f / (2.0 + f);
-    double z = s * s;
-    double R = 1.0 / 25.0;
-    R = 1.0 / 23.0 + z * R;
-    R = 1.0 / 21.0 + z * R;
-    R = 1.0 / 19.0 + z * R;
-    R = 1.0 / 17.0 + z * R;
-    R = 1.0 / 15.0 + z * R;
-    R = 1.0 / 13.0 + z * R;
-    R = 1.0 / 11.0 + z * R;
-    R = 1.0 / 9.0 + z * R;
-    R = 1.0 / 7.0 + z * R;
-    R = 1.0 / 5.0 + z * R;
-    R = 1.0 / 3.0 + z * R;
-    R = z * R;
-    double t = s + s * R;
-    double logm = t + t;
+    double r;
+    if (i == 127) {
+        m = m * 0.5;
+        e = e + 1;
+        r = m - 1.0;
+    } else if (i == 0) {
+        r = m - 1.0;
+    } else {
+        r = fma(m, log_inv[i], -1.0);
+    }
+    double q = -1.0 / 8.0;
+    q = fma(q, r, 1.0 / 7.0);
+    q = fma(q, r, -1.0 / 6.0);
+    q = fma(q, r, 1.0 / 5.0);
+    q = fma(q, r, -1.0 / 4.0);
+    q = fma(q, r, 1.0 / 3.0);
+    q = fma(q, r, -0.5);
+    double p = fma(r * r, q, r);
     double de = (double)e;
-    return de * LN2_HI + (de * LN2_LO + logm);
+    return (de * LN2_HI + log_hi[i]) + ((de * LN2_LO + log_lo[i]) + p);
 }
 
-/* ln(1+z) for z > -1, Goldberg's correction: u = 1+z, ln(u) * z/(u-1). */
 double or_log1p(double z)
 {
     double u = 1.0 + z;

@@ -219,11 +219,12 @@ int blocks_per_sm(const void* kern, size_t smem, int threads) {
 // One leaf kernel (+ the general path) over the leaves of a view.
 template <class View>
 int issue_leaves(const View& V, int kind, bool wide, uint32_t* ovf, uint32_t* ovf_count, void* big,
-                 uint64_t big_kmax, int per_sm_cap, bool persistent, int sms, cudaStream_t st, uint64_t* nl) {
+                 uint64_t big_kmax, int per_sm_cap, bool persistent, const double* tab, int sms, cudaStream_t st,
+                 uint64_t* nl) {
     if (V.nleaves == 0) return RS_OK;
     if (kind == RS_KIND_B) {
         ++*nl;
-        return cuda_rc(launch_batch_leaves_b(V, sms, st));
+        return cuda_rc(launch_batch_leaves_b(V, tab, sms, st));
     }
     const bool wr = kind == RS_KIND_WR;
     void (*kern)(View, uint32_t*, uint32_t*, uint32_t);
@@ -479,7 +480,7 @@ int GroupPlan::issue(const double* tab, int sms, uint64_t* pool, int* status, cu
             if (G.n1 == 0) continue;
             BatchGroupView V{reqs, reinterpret_cast<const LeafDesc*>(up_ + G.o_desc), G.n1, nodes, pool, status};
             rc = issue_leaves(V, G.kind, G.wide, reinterpret_cast<uint32_t*>(work_ + G.o_ovf1),
-                              counters + counter_of(0, gi), big_, big_kmax_, per_sm_, persistent_, sms, st, &nl);
+                              counters + counter_of(0, gi), big_, big_kmax_, per_sm_, persistent_, tab, sms, st, &nl);
         }
     }
     if (!rc && Q_ > 0) {
@@ -489,7 +490,7 @@ int GroupPlan::issue(const double* tab, int sms, uint64_t* pool, int* status, cu
             if (G.n1 == 0) continue;
             QueryBoundView V{qd, qres_, reinterpret_cast<const uint32_t*>(up_ + G.o_a32), G.n1};
             rc = issue_leaves(V, G.kind, G.wide, reinterpret_cast<uint32_t*>(work_ + G.o_ovf1),
-                              counters + counter_of(1, gi), big_, big_kmax_, per_sm_, persistent_, sms, st, &nl);
+                              counters + counter_of(1, gi), big_, big_kmax_, per_sm_, persistent_, tab, sms, st, &nl);
         }
         if (!rc) {
             const unsigned grid = (unsigned)std::min<uint64_t>(Q_, (uint64_t)sms * 8);
@@ -506,7 +507,7 @@ int GroupPlan::issue(const double* tab, int sms, uint64_t* pool, int* status, cu
                              (uint32_t)G.b32.size(),
                              G.n2};
             rc = issue_leaves(V, G.kind, G.wide, reinterpret_cast<uint32_t*>(work_ + G.o_ovf2),
-                              counters + counter_of(2, gi), big_, big_kmax_, per_sm_, persistent_, sms, st, &nl);
+                              counters + counter_of(2, gi), big_, big_kmax_, per_sm_, persistent_, tab, sms, st, &nl);
         }
     }
     if (launches) *launches = nl;

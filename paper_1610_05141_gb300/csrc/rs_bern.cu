@@ -45,8 +45,8 @@ RS_DEV uint64_t warp_inclusive_sat(uint64_t x) {
 // chosen position (0-based) emit(k, pos) is called, k its index in the
 // range.  Returns the number of positions; *err is set if the stream ran out.
 template <typename Emit>
-RS_DEV uint64_t warp_walk(Key2 key, uint32_t tag, uint64_t id, double L, uint64_t start, uint64_t end, bool* err,
-                          Emit&& emit) {
+RS_DEV uint64_t warp_walk(Key2 key, uint32_t tag, uint64_t id, double L, uint64_t start, uint64_t end,
+                          const double* __restrict__ tab, bool* err, Emit&& emit) {
     const int lane = threadIdx.x & 31;
     const uint64_t cmax = end - start + 2;
     uint64_t base = start;   // a step of 1 lands on `base`
@@ -59,7 +59,7 @@ RS_DEV uint64_t warp_walk(Key2 key, uint32_t tag, uint64_t id, double L, uint64_
         uint64_t step = 0;
         if (!exhausted) {
             const double U = u_open(stream_value(key, tag, id, jl));
-            const double q = dlog(U) / L;
+            const double q = dlog(U, tab) / L;
             step = step_of(q, cmax, &stop);
         }
         const uint64_t incl = warp_inclusive_sat(step);
@@ -86,17 +86,18 @@ struct BernArgs {
     uint64_t* out;
     uint64_t cap;
     int* status;
+    const double* tab;
 };
 
 __global__ void bern_count_kernel(BernArgs A) {
-    const double L = dlog1p(-A.p);
+    const double L = dlog1p(-A.p, A.tab);
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
     for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < A.nchunks; w += warps) {
         const uint64_t i = A.first + w;
         const uint64_t start = i << A.chunk_log2;
         const uint64_t end = min(start + A.C, A.N);
         bool err;
-        const uint64_t c = warp_walk(A.key, TAG_BERN, i, L, start, end, &err, [](uint64_t, uint64_t) {});
+        const uint64_t c = warp_walk(A.key, TAG_BERN, i, L, start, end, A.tab, &err, [](uint64_t, uint64_t) {});
         if ((threadIdx.x & 31) == 0) {
             A.counts[w] = c;
             if (err) set_status(A.status, RS_EITER);
@@ -105,7 +106,7 @@ __global__ void bern_count_kernel(BernArgs A) {
 }
 
 __global__ void bern_write_kernel(BernArgs A) {
-    const double L = dlog1p(-A.p);
+    const double L = dlog1p(-A.p, A.tab);
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
     for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < A.nchunks; w += warps) {
         const uint64_t i = A.first + w;
@@ -116,7 +117,7 @@ __global__ void bern_write_kernel(BernArgs A) {
         uint64_t* out = A.out;
         const uint64_t cap = A.cap;
         bool err;
-        warp_walk(A.key, TAG_BERN, i, L, start, end, &err, [=](uint64_t k, uint64_t pos) {
+        warp_walk(A.key, TAG_BERN, i, L, start, end, A.tab, &err, [=](uint64_t k, uint64_t pos) {
             if (off + k < cap) out[off + k] = pos + 1;
         });
     }
@@ -232,6 +233,7 @@ cudaError_t launch_bernoulli(const BernLaunch& L, cudaStream_t st) {
     A.out = L.out;
     A.cap = L.cap;
     A.status = L.status;
+    A.tab = L.tab;
     const int threads = 256;
     const unsigned blocks = (unsigned)std::min<uint64_t>((L.nchunks * 32 + threads - 1) / threads,
                                                          (uint64_t)L.sms * 16);
@@ -283,7 +285,8 @@ RS_DEV uint64_t block_inclusive_sat(uint64_t x, LeafBShared& sm) {
 
 // Geometric-skip walk of [0, s) by the whole block; positions go to sm.pos
 // (up to the capacity).  Returns the count; sets sm.err on a run-out stream.
-RS_DEV uint64_t block_walk(Key2 key, uint32_t tag, uint64_t id, double L, uint64_t s, LeafBShared& sm) {
+RS_DEV uint64_t block_walk(Key2 key, uint32_t tag, uint64_t id, double L, uint64_t s, LeafBShared& sm,
+                           const double* __restrict__ tab) {
     const uint64_t cmax = s + 2;
     uint64_t base = 0, count = 0;
     for (uint64_t j = 0;; j += kLeafThreads) {
@@ -293,7 +296,7 @@ RS_DEV uint64_t block_walk(Key2 key, uint32_t tag, uint64_t id, double L, uint64
         uint64_t step = 0;
         if (!exhausted) {
             const double U = u_open(stream_value(key, tag, id, jt));
-            const double q = dlog(U) / L;
+            const double q = dlog(U, tab) / L;
             step = step_of(q, cmax, &stop);
         }
         if (threadIdx.x == 0) sm.first_bad = kLeafThreads;
@@ -319,11 +322,12 @@ struct LeafBArgs {
     Key2 key;
     uint64_t* out;
     int* status;
+    const double* tab;
 };
 
 // One leaf of Algorithm B, by the whole block.
 RS_DEV void leaf_b_one(LeafBShared& sm, const NodeRec& r, uint64_t id, Key2 key, uint64_t* __restrict__ out,
-                       int* status) {
+                       int* status, const double* __restrict__ tab) {
     if (r.c == 0) return;
     const double dn = (double)r.c;
     double rho = (dn + 3.0 * sqrt(dn) + 10.0) / (double)r.S;
@@ -339,9 +343,9 @@ RS_DEV void leaf_b_one(LeafBShared& sm, const NodeRec& r, uint64_t id, Key2 key,
         for (uint64_t i = threadIdx.x; i < fill; i += kLeafThreads) sm.pos[i] = i;
         __syncthreads();
     } else {
-        const double L = dlog1p(-rho);
+        const double L = dlog1p(-rho, tab);
         for (attempt = 0; attempt < 64; ++attempt) {
-            c = block_walk(key, TAG_LEAF_B + 256u * (uint32_t)attempt, id, L, r.S, sm);
+            c = block_walk(key, TAG_LEAF_B + 256u * (uint32_t)attempt, id, L, r.S, sm, tab);
             if (sm.err) break;
             if (c >= r.c) break;
         }
@@ -377,22 +381,22 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_b_kernel(LeafBArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     LeafBShared& sm = *reinterpret_cast<LeafBShared*>(smem_raw);
     for (uint64_t leaf = blockIdx.x; leaf < A.nleaves; leaf += gridDim.x)
-        leaf_b_one(sm, A.leaves[leaf], A.first_id + leaf, A.key, A.out, A.status);
+        leaf_b_one(sm, A.leaves[leaf], A.first_id + leaf, A.key, A.out, A.status, A.tab);
 }
 
 // Algorithm B leaves of a batch group or of range queries.
 template <class View>
-__global__ void __launch_bounds__(kLeafThreads) group_leaf_b_kernel(View G) {
+__global__ void __launch_bounds__(kLeafThreads) group_leaf_b_kernel(View G, const double* tab) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     LeafBShared& sm = *reinterpret_cast<LeafBShared*>(smem_raw);
     for (uint64_t g = blockIdx.x; g < G.nleaves; g += gridDim.x) {
         const ResolvedLeaf L = resolve_leaf(G, g);
-        leaf_b_one(sm, L.rec, L.id, make_key(L.seed), L.out, L.status);
+        leaf_b_one(sm, L.rec, L.id, make_key(L.seed), L.out, L.status, tab);
     }
 }
 
 template <class View>
-static cudaError_t launch_group_leaves_b(const View& G, int sms, cudaStream_t st) {
+static cudaError_t launch_group_leaves_b(const View& G, const double* tab, int sms, cudaStream_t st) {
     const size_t smem = sizeof(LeafBShared);
     auto kern = group_leaf_b_kernel<View>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -402,18 +406,18 @@ static cudaError_t launch_group_leaves_b(const View& G, int sms, cudaStream_t st
     if (e != cudaSuccess) return e;
     const uint64_t grid = std::min<uint64_t>(G.nleaves, (uint64_t)sms * std::max(per_sm, 1));
     if (grid == 0) return cudaSuccess;
-    kern<<<(unsigned)grid, kLeafThreads, smem, st>>>(G);
+    kern<<<(unsigned)grid, kLeafThreads, smem, st>>>(G, tab);
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_leaves_b(const BatchGroupView& G, int sms, cudaStream_t st) {
-    return launch_group_leaves_b(G, sms, st);
+cudaError_t launch_batch_leaves_b(const BatchGroupView& G, const double* tab, int sms, cudaStream_t st) {
+    return launch_group_leaves_b(G, tab, sms, st);
 }
-cudaError_t launch_batch_leaves_b(const QueryBoundView& G, int sms, cudaStream_t st) {
-    return launch_group_leaves_b(G, sms, st);
+cudaError_t launch_batch_leaves_b(const QueryBoundView& G, const double* tab, int sms, cudaStream_t st) {
+    return launch_group_leaves_b(G, tab, sms, st);
 }
-cudaError_t launch_batch_leaves_b(const QueryInnerView& G, int sms, cudaStream_t st) {
-    return launch_group_leaves_b(G, sms, st);
+cudaError_t launch_batch_leaves_b(const QueryInnerView& G, const double* tab, int sms, cudaStream_t st) {
+    return launch_group_leaves_b(G, tab, sms, st);
 }
 
 cudaError_t launch_leaves_b(const LeafBLaunch& L, cudaStream_t st) {
@@ -424,7 +428,7 @@ cudaError_t launch_leaves_b(const LeafBLaunch& L, cudaStream_t st) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, leaf_b_kernel, kLeafThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    LeafBArgs A{L.leaves, L.nleaves, L.first_id, make_key(L.seed), L.out, L.status};
+    LeafBArgs A{L.leaves, L.nleaves, L.first_id, make_key(L.seed), L.out, L.status, L.tab};
     const uint64_t grid = std::min<uint64_t>(L.nleaves, (uint64_t)L.sms * per_sm);
     leaf_b_kernel<<<(unsigned)grid, kLeafThreads, smem, st>>>(A);
     return cudaGetLastError();

@@ -283,7 +283,7 @@ int sample_impl(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0,
         const uint64_t first = j * per_part;
         if (kind == RS_KIND_B) {
             rs::LeafBLaunch LB{ctx->nodes + nleaves + first, per_part, nleaves + first, seed, out, ctx->status,
-                               ctx->sms};
+                               ctx->sms, ctx->tab};
             ctx->launches += 1;
             rc = cuda_rc(rs::launch_leaves_b(LB, st));
         } else {
@@ -348,7 +348,7 @@ int rs_create(rs_ctx** out, int device) {
     ctx->device = device;
     int rc = RS_OK;
     if (cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) rc = RS_ECUDA;
-    if (!rc) rc = cuda_rc(cudaMalloc(&ctx->tab, 256 * sizeof(double)));
+    if (!rc) rc = cuda_rc(cudaMalloc(&ctx->tab, rs::kTabWords * sizeof(double)));
     if (!rc) rc = cuda_rc(cudaMalloc(&ctx->status, sizeof(int)));
     if (!rc) rc = cuda_rc(cudaMemset(ctx->status, 0, sizeof(int)));
     if (!rc) rc = cuda_rc(rs::launch_lf_table(ctx->tab, 0));
@@ -445,7 +445,7 @@ int rs_bernoulli(rs_ctx* ctx, double p, uint64_t N, uint64_t seed, uint32_t n0, 
     int rc = ensure(ctx->words, ctx->words_cap, nchunks + 2 + rs::scan_scratch_words(nchunks));
     if (rc) return rc;
     rs::BernLaunch L{p, N, seed, c, first, nchunks, a, b, out_dev, cap, ctx->words, ctx->words + nchunks + 1,
-                     ctx->words + nchunks + 2, ctx->status, ctx->sms};
+                     ctx->words + nchunks + 2, ctx->status, ctx->sms, ctx->tab};
     rc = cuda_rc(rs::launch_bernoulli(L, st));
     if (rc) return rc;
     uint64_t total = 0;

@@ -20,6 +20,16 @@ struct __align__(16) NodeRec {
     uint64_t lo, S, c, off;
 };
 
+// The table the library's math reads (one per context, on the device):
+// ln i! for i < 256 (kTabLf), then for the 128 mantissa intervals of [1, 2)
+// the reciprocal of the interval's centre and minus its logarithm as a
+// double-double (kTabInv, kTabHi, kTabLo); see rs_math.cuh.
+constexpr int kTabLf = 0;
+constexpr int kTabInv = 256;
+constexpr int kTabHi = 384;
+constexpr int kTabLo = 512;
+constexpr int kTabWords = 640;
+
 // First error wins; later errors are dropped until the host clears the word.
 RS_DEV void set_status(int* status, int code) {
     if (code != RS_OK) atomicCAS(status, RS_OK, code);

@@ -65,7 +65,7 @@ RS_DEV int hypergeometric(Key2 key, uint64_t node, uint64_t n, uint64_t K, uint6
             const uint64_t k = (uint64_t)X;
             const double T = dsd(M, k, tab) + dsd(a - M, a - k, tab) + dsd(b - M, b - k, tab) +
                              dsd(S - a - b + M, S - a - b + k, tab);
-            if (2.0 * dlog(U) <= T) { y = k; done = true; break; }
+            if (2.0 * dlog(U, tab) <= T) { y = k; done = true; break; }
         }
     }
     if (!done) return RS_EITER;
@@ -82,7 +82,7 @@ RS_DEV int binomial(Key2 key, uint64_t node, uint64_t c, uint64_t K, uint64_t S,
     const double p = (double)K / (double)S;
     const double mu = (double)c * p;
     if (mu < 16.0) {
-        const double f0 = dexp((double)c * dlog1p(-p));
+        const double f0 = dexp((double)c * dlog1p(-p, tab));
         const double r = p / (1.0 - p);
         for (uint64_t rs = 0; rs < kInvMaxRestarts; ++rs) {
             double u = v_closed(stream_value(key, TAG_SPLIT, node, rs));
@@ -100,7 +100,7 @@ RS_DEV int binomial(Key2 key, uint64_t node, uint64_t c, uint64_t K, uint64_t S,
     const double h = RS_HAT_D1 * sqrt(var + 0.5) + RS_HAT_D2;
     const double alpha = mu + 0.5;
     const double r = p / (1.0 - p);
-    const double logr = (r == 1.0) ? 0.0 : dlog(r);
+    const double logr = (r == 1.0) ? 0.0 : dlog(r, tab);
     const uint64_t M = (uint64_t)(((unsigned __int128)(c + 1) * K) / S);
     const double top = (double)c + 1.0;
     for (uint64_t i = 0; i < kRouMaxTrials; ++i) {
@@ -111,7 +111,7 @@ RS_DEV int binomial(Key2 key, uint64_t node, uint64_t c, uint64_t K, uint64_t S,
         if (X < 0.0 || X >= top) continue;
         const uint64_t k = (uint64_t)X;
         const double T = dsd(M, k, tab) + dsd(c - M, c - k, tab) + (double)((int64_t)k - (int64_t)M) * logr;
-        if (2.0 * dlog(U) <= T) { out = k; return RS_OK; }
+        if (2.0 * dlog(U, tab) <= T) { out = k; return RS_OK; }
     }
     return RS_EITER;
 }

@@ -69,6 +69,7 @@ struct LeafBLaunch {
     uint64_t* out;
     int* status;
     int sms;
+    const double* tab;       // the context's table (its logarithm)
 };
 // Algorithm B leaves (positions of one attempt live in shared memory).
 cudaError_t launch_leaves_b(const LeafBLaunch& L, cudaStream_t st);
@@ -88,6 +89,7 @@ struct BernLaunch {
     uint64_t* scan_scratch;  // scan_scratch_words(nchunks) words
     int* status;
     int sms;
+    const double* tab;       // the context's table (its logarithm)
 };
 // Count pass, exclusive scan of the chunk counts, write pass.
 cudaError_t launch_bernoulli(const BernLaunch& L, cudaStream_t st);
@@ -97,8 +99,8 @@ struct BatchGroupView;
 struct QueryBoundView;
 struct QueryInnerView;
 // Algorithm B leaves of a batch group, or of range queries (rs_bern.cu).
-cudaError_t launch_batch_leaves_b(const BatchGroupView& G, int sms, cudaStream_t st);
-cudaError_t launch_batch_leaves_b(const QueryBoundView& G, int sms, cudaStream_t st);
-cudaError_t launch_batch_leaves_b(const QueryInnerView& G, int sms, cudaStream_t st);
+cudaError_t launch_batch_leaves_b(const BatchGroupView& G, const double* tab, int sms, cudaStream_t st);
+cudaError_t launch_batch_leaves_b(const QueryBoundView& G, const double* tab, int sms, cudaStream_t st);
+cudaError_t launch_batch_leaves_b(const QueryInnerView& G, const double* tab, int sms, cudaStream_t st);
 
 }  // namespace rs

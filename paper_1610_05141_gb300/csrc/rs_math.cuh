@@ -1,9 +1,9 @@
 // rs_math.cuh -- the sampler's own FP64 functions on the device.
 //
-// Built only from IEEE-exact operations (+ - * / sqrt, conversions, bit
-// manipulation) and compiled with -fmad=false, so the results are the same
-// bits on every IEEE machine that evaluates the same expressions in the same
-// order.  The split deviates (Sec. 3: hypergeometric, Sec. 4.6: binomial)
+// Built only from IEEE-exact operations (+ - * / sqrt, explicit fused
+// multiply-add, conversions, bit manipulation) and compiled with -fmad=false,
+// so the results are the same bits on every IEEE machine that evaluates the
+// same expressions in the same order.  The split deviates (Sec. 3: hypergeometric, Sec. 4.6: binomial)
 // and the geometric skips of Bernoulli sampling (Sec. 4.7) depend on them.
 #pragma once
 #include "rs_common.cuh"
@@ -15,7 +15,6 @@ RS_DEV uint64_t double_to_bits(double d) { return (uint64_t)__double_as_longlong
 
 // ln 2 split for exact range reduction: the high part keeps 32 significant
 // bits so k * LN2_HI is exact for |k| < 2^21.
-#define RS_RT2 bits_to_double(0x3ff6a09e667f3bcdull)      // nearest double to sqrt(2)
 #define RS_LN2_HI bits_to_double(0x3fe62e42fee00000ull)
 #define RS_LN2_LO bits_to_double(0x3dea39ef35793c76ull)
 #define RS_INV_LN2 bits_to_double(0x3ff71547652b82feull)
@@ -23,45 +22,108 @@ RS_DEV uint64_t double_to_bits(double d) { return (uint64_t)__double_as_longlong
 #define RS_HAT_D1 bits_to_double(0x3ffb72cd3f331398ull)   // 2 sqrt(2/e)
 #define RS_HAT_D2 bits_to_double(0x3fecc3ebd3bc711aull)   // 3 - 2 sqrt(3/e)
 
-// ln x for a normal x > 0: x = 2^e m with m in (sqrt2/2, sqrt2], and
-// ln m = 2 atanh(s), s = (m-1)/(m+1), from the series sum s^(2i+1)/(2i+1)
-// up to i = 12, evaluated by Horner's rule in z = s^2.
-RS_DEV double dlog(double x) {
+// Double-double arithmetic for building the table: error-free sums (Knuth)
+// and products (fused multiply-add), then renormalization.
+struct DD {
+    double hi, lo;
+};
+RS_DEV DD dd_fast2(double a, double b) {
+    const double s = a + b;
+    return DD{s, b - (s - a)};
+}
+RS_DEV DD dd_two_sum(double a, double b) {
+    const double s = a + b;
+    const double bb = s - a;
+    return DD{s, (a - (s - bb)) + (b - bb)};
+}
+RS_DEV DD dd_add(DD a, DD b) {
+    const DD s = dd_two_sum(a.hi, b.hi);
+    const double e = s.lo + (a.lo + b.lo);
+    return dd_fast2(s.hi, e);
+}
+RS_DEV DD dd_mul(DD a, DD b) {
+    const double p = a.hi * b.hi;
+    double e = __fma_rn(a.hi, b.hi, -p);
+    e = e + (a.hi * b.lo + a.lo * b.hi);
+    return dd_fast2(p, e);
+}
+// a / b to double-double precision: three quotient digits.
+RS_DEV DD dd_div(DD a, DD b) {
+    const double q1 = a.hi / b.hi;
+    DD t = dd_mul(b, DD{q1, 0.0});
+    DD r = dd_add(a, DD{-t.hi, -t.lo});
+    const double q2 = r.hi / b.hi;
+    t = dd_mul(b, DD{q2, 0.0});
+    r = dd_add(r, DD{-t.hi, -t.lo});
+    const double q3 = r.hi / b.hi;
+    const DD q = dd_fast2(q1, q2);
+    return dd_add(q, DD{q3, 0.0});
+}
+
+// Entry i of the logarithm table: interval i of [1, 2) (width 2^-7) has
+// centre c = 1 + (2i+1)/256 and inv = RN(1/c); -ln(inv) = -2 atanh(s),
+// s = (inv-1)/(inv+1), summed in double-double to s^71/71 (|s| <= 1/3).
+// Intervals 0 and 127 use c = 1 (see dlog).
+RS_DEV void build_log_entry(int i, double* tab) {
+    if (i == 0 || i == 127) {
+        tab[kTabInv + i] = 1.0;
+        tab[kTabHi + i] = 0.0;
+        tab[kTabLo + i] = 0.0;
+        return;
+    }
+    const double c = 1.0 + (double)(2 * i + 1) / 256.0;
+    const double inv = 1.0 / c;
+    const DD s = dd_div(DD{inv - 1.0, 0.0}, dd_two_sum(inv, 1.0));
+    const DD s2 = dd_mul(s, s);
+    DD term = s, sum = s;
+    for (int k = 1; k < 36; ++k) {
+        term = dd_mul(term, s2);
+        sum = dd_add(sum, dd_div(term, DD{(double)(2 * k + 1), 0.0}));
+    }
+    tab[kTabInv + i] = inv;
+    tab[kTabHi + i] = -(2.0 * sum.hi);
+    tab[kTabLo + i] = -(2.0 * sum.lo);
+}
+
+// ln x for a normal x > 0: x = 2^e m, m in [1, 2); the top 7 bits of m pick
+// an interval with centre c and inv = RN(1/c), and ln m = -ln(inv) +
+// ln(1 + r), r = m inv - 1 (one fused multiply-add, |r| <= 2^-8), ln(1 + r)
+// by its Taylor polynomial to r^8/8 (Horner with fused multiply-adds).  The
+// two intervals next to 1 use c = 1 and r = m - 1 (or m/2 - 1 with e + 1),
+// exact, so that ln x near 1 keeps its relative accuracy; there |r| <= 2^-7.
+RS_DEV double dlog(double x, const double* __restrict__ tab) {
     const uint64_t bits = double_to_bits(x);
     int64_t e = (int64_t)((bits >> 52) & 0x7FF) - 1023;
+    const int i = (int)((bits >> 45) & 0x7F);
     double m = bits_to_double((bits & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull);
-    if (m > RS_RT2) {
+    double r;
+    if (i == 127) {
         m = m * 0.5;
         e = e + 1;
+        r = m - 1.0;
+    } else if (i == 0) {
+        r = m - 1.0;
+    } else {
+        r = __fma_rn(m, __ldg(tab + kTabInv + i), -1.0);
     }
-    const double f = m - 1.0;
-    const double s = f / (2.0 + f);
-    const double z = s * s;
-    double R = 1.0 / 25.0;
-    R = 1.0 / 23.0 + z * R;
-    R = 1.0 / 21.0 + z * R;
-    R = 1.0 / 19.0 + z * R;
-    R = 1.0 / 17.0 + z * R;
-    R = 1.0 / 15.0 + z * R;
-    R = 1.0 / 13.0 + z * R;
-    R = 1.0 / 11.0 + z * R;
-    R = 1.0 / 9.0 + z * R;
-    R = 1.0 / 7.0 + z * R;
-    R = 1.0 / 5.0 + z * R;
-    R = 1.0 / 3.0 + z * R;
-    R = z * R;
-    const double t = s + s * R;
-    const double lm = t + t;
+    double q = -1.0 / 8.0;
+    q = __fma_rn(q, r, 1.0 / 7.0);
+    q = __fma_rn(q, r, -1.0 / 6.0);
+    q = __fma_rn(q, r, 1.0 / 5.0);
+    q = __fma_rn(q, r, -1.0 / 4.0);
+    q = __fma_rn(q, r, 1.0 / 3.0);
+    q = __fma_rn(q, r, -0.5);
+    const double p = __fma_rn(r * r, q, r);
     const double de = (double)e;
-    return de * RS_LN2_HI + (de * RS_LN2_LO + lm);
+    return (de * RS_LN2_HI + __ldg(tab + kTabHi + i)) + ((de * RS_LN2_LO + __ldg(tab + kTabLo + i)) + p);
 }
 
 // ln(1+z), z > -1: with u = 1+z rounded, ln(u) * (z / (u-1)) cancels the
 // rounding of u to first order (Goldberg 1991).
-RS_DEV double dlog1p(double z) {
+RS_DEV double dlog1p(double z, const double* __restrict__ tab) {
     const double u = 1.0 + z;
     if (u == 1.0) return z;
-    return dlog(u) * (z / (u - 1.0));
+    return dlog(u, tab) * (z / (u - 1.0));
 }
 
 // e^x for x in [-708, 0]: x = k ln2 + r with |r| <= ln2/2, e^r from its
@@ -98,7 +160,7 @@ RS_DEV double stirling_tail(double x) {
 RS_DEV double dlf(uint64_t x, const double* __restrict__ tab) {
     if (x < 256) return tab[x];
     const double X = (double)x;
-    return (X + 0.5) * dlog(X) - X + RS_HL2PI + stirling_tail(X);
+    return (X + 0.5) * dlog(X, tab) - X + RS_HL2PI + stirling_tail(X);
 }
 
 // ln x! - ln y! for x >= y without cancellation of the two large terms:
@@ -110,12 +172,12 @@ RS_DEV double dlfdiff(uint64_t x, uint64_t y, const double* __restrict__ tab) {
     if (x < 256) return tab[x] - tab[y];
     if (d <= 8) {
         double acc = 0.0;
-        for (uint64_t i = y + 1; i <= x; ++i) acc = acc + dlog((double)i);
+        for (uint64_t i = y + 1; i <= x; ++i) acc = acc + dlog((double)i, tab);
         return acc;
     }
     if (y < 256) return dlf(x, tab) - tab[y];
     const double X = (double)x, Y = (double)y, D = (double)d;
-    return (X + 0.5) * dlog1p(D / Y) + D * dlog(Y) - D + (stirling_tail(X) - stirling_tail(Y));
+    return (X + 0.5) * dlog1p(D / Y, tab) + D * dlog(Y, tab) - D + (stirling_tail(X) - stirling_tail(Y));
 }
 
 // Signed ln x! - ln y!.

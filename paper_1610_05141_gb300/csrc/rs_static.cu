@@ -23,7 +23,7 @@ namespace {
 constexpr int kStaticDepth = 16;                                // at most 2^16 leaves
 constexpr uint64_t kStaticNodes = 2ull << kStaticDepth;          // heap records 1 .. 2^17 - 1
 constexpr uint64_t kStaticBigKeys = 1ull << 16;                  // general-path pool
-constexpr uint64_t kTabBytes = 256 * sizeof(double);
+constexpr uint64_t kTabBytes = rs::kTabWords * sizeof(double);
 constexpr uint64_t kStatusBytes = 256;                           // status word, 256-byte slot
 constexpr uint64_t kNodeBytes = kStaticNodes * sizeof(rs::NodeRec);
 constexpr uint64_t kOvfBytes = (((1ull << kStaticDepth) + 1) * sizeof(uint32_t) + 255) & ~255ull;

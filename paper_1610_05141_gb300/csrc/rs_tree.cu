@@ -14,14 +14,22 @@
 
 namespace rs {
 
+// The context's table: first the logarithm's 128 entries (one thread
+// each), then, in a second launch (the logarithm reads its entries through
+// the read-only cache), ln i! for i < 256.
+__global__ void log_table_kernel(double* tab) {
+    if (blockIdx.x == 0 && threadIdx.x < 128) build_log_entry((int)threadIdx.x, tab);
+}
+
 __global__ void lf_table_kernel(double* tab) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    tab[0] = 0.0;
-    tab[1] = 0.0;
-    for (int i = 2; i < 256; ++i) tab[i] = tab[i - 1] + dlog((double)i);
+    tab[kTabLf + 0] = 0.0;
+    tab[kTabLf + 1] = 0.0;
+    for (int i = 2; i < 256; ++i) tab[kTabLf + i] = tab[kTabLf + i - 1] + dlog((double)i, tab);
 }
 
 cudaError_t launch_lf_table(double* tab, cudaStream_t st) {
+    log_table_kernel<<<1, 128, 0, st>>>(tab);
     lf_table_kernel<<<1, 1, 0, st>>>(tab);
     return cudaGetLastError();
 }

@@ -139,7 +139,7 @@ RS_DEV bool node_setup(NodeRec* __restrict__ rec, uint64_t v, Key2 key, const do
         q->h = RS_HAT_D1 * sqrt(var + 0.5) + RS_HAT_D2;
         q->alpha = mu + 0.5;
         const double rr = p / (1.0 - p);
-        q->logr = (rr == 1.0) ? 0.0 : dlog(rr);
+        q->logr = (rr == 1.0) ? 0.0 : dlog(rr, tab);
         q->M = (uint64_t)(((unsigned __int128)(c + 1) * K) / r.S);
         q->top = (double)c + 1.0;
         q->a = c;
@@ -267,7 +267,7 @@ RS_DEV void tree_batch_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
                 x[j] = slot[j] ? *slot[j] : 1.0;
             }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) x[j] = dlog(x[j]);
+            for (int j = 0; j < 4; ++j) x[j] = dlog(x[j], tab);
 #pragma unroll
             for (int j = 0; j < 4; ++j)
                 if (slot[j]) *slot[j] = x[j];
@@ -368,7 +368,7 @@ RS_DEV void tree_terms_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
             const double v = dlfdiff(pos ? x : y, pos ? y : x, tab);
             term = pos ? v : -v;
         }
-        const double lU = dlog(U);
+        const double lU = dlog(U, tab);
         const double t0 = __shfl_sync(0xFFFFFFFFu, term, tbase);
         const double t1 = __shfl_sync(0xFFFFFFFFu, term, tbase + 1);
         const double t2 = __shfl_sync(0xFFFFFFFFu, term, tbase + 2);

@@ -34,7 +34,6 @@ def test_constants_match_definitions():
     consts = dict(re.findall(r"#define (\w+)\s+from_bits\((0x[0-9a-f]+)ull\)", src))
     ln2 = mpmath.log(2)
     want = {
-        "RT2": mpmath.sqrt(2),
         "LN2_LO": None,   # checked below from LN2_HI
         "INV_LN2": 1 / ln2,
         "HL2PI": mpmath.log(2 * mpmath.pi) / 2,
@@ -76,6 +75,24 @@ def test_log_accuracy(oracle):
             continue
         worst = max(worst, _ulp_err(got, exact))
     assert worst <= 2, worst
+
+
+def test_log_table(oracle):
+    """Each interval of the logarithm's table: inv is the double nearest 1/c
+    for the interval's centre c, hi + lo is -ln(inv) to double-double
+    accuracy, hi is -ln(inv) rounded; the intervals next to 1 use c = 1."""
+    with mpmath.workprec(300):
+        for i in range(128):
+            inv, hi, lo = oracle.log_table_entry(i)
+            if i in (0, 127):
+                assert (inv, hi, lo) == (1.0, 0.0, 0.0)
+                continue
+            c = 1 + (2 * i + 1) / 256
+            assert inv == 1.0 / c
+            exact = -mpmath.log(mpmath.mpf(inv))
+            assert abs(mpmath.mpf(hi) + mpmath.mpf(lo) - exact) <= abs(exact) * mpmath.mpf(2) ** -100, i
+            assert hi == float(exact), i
+            assert abs(lo) <= math.ulp(hi) / 2
 
 
 def test_log_special_values(oracle):
