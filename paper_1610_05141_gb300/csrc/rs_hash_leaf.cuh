@@ -42,6 +42,8 @@
 // path only needs valid candidates, and the probing path orders equal keys
 // by slot.
 #pragma once
+#include <type_traits>
+
 #include "rs_block.cuh"
 #include "rs_internal.h"
 #include "rs_rng.cuh"
@@ -68,7 +70,7 @@ struct HashShared {
     static constexpr uint32_t kBuckets = CAP + 64;        // bucket path: about one key per bucket
     KeyT tab[kSlots];              // bucket path: keys (first k + 3), then keys in bucket order;
                                    // probing table; bitmap; tallies
-    uint32_t cnt[kBuckets / 2 + 1];      // bucket path: 16-bit counts, two per word, then offsets
+    alignas(16) uint32_t cnt[kBuckets / 2 + 1];   // bucket path: 16-bit counts, two per word, then offsets
     uint32_t scan_tmp[NW + 1];
     uint32_t warp_cnt[NW];
     uint32_t newcount[3];          // rounds: values added in round r go to newcount[r % 3]
@@ -77,6 +79,7 @@ struct HashShared {
     uint64_t jnext;                // bucket path: index of the candidate after the k-th valid one
     uint32_t nadded;               // bucket path: values drawn after a repeat
     uint32_t repair_fail;
+    uint32_t ranksum;              // bucket path: sum of the keys' ranks (k (k - 1) / 2 without ties)
     uint64_t thr;                  // Lemire rejection threshold of the leaf
     uint64_t mult;                 // address multiplier of the current table
 };
@@ -211,25 +214,48 @@ RS_DEV void for_candidates(const LeafRec& r, uint64_t thr64, Key2 key, uint32_t 
 }
 
 // Exclusive prefix sums, in place, of the nb 16-bit counts packed two per
-// word in w[0 .. nb/2) (nb even).  Thread t owns Q consecutive words, Q odd
-// so that the threads' strided reads hit distinct banks.
+// word in w[0 .. nb/2), nb a multiple of 64 and w 16-byte aligned.  Thread t
+// owns Q consecutive 16-byte groups (8 counts each), Q odd so that the
+// 16-byte accesses of a quarter warp fall in distinct banks.  Two barriers:
+// warp totals go to tmp[], then each warp adds those of the warps before it.
 template <int NT>
 RS_DEV void scan_counts16(uint32_t* w, uint32_t nb, uint32_t* tmp, uint32_t tid) {
-    const uint32_t words = nb >> 1;
-    const uint32_t Q = ((words + NT - 1) / NT) | 1u;
-    const uint32_t w0 = min(tid * Q, words), w1 = min(w0 + Q, words);
+    constexpr int NW = NT / 32;
+    uint4* g = reinterpret_cast<uint4*>(w);
+    const uint32_t groups = nb >> 3;
+    const uint32_t Q = ((groups + NT - 1) / NT) | 1u;
+    const uint32_t g0 = min(tid * Q, groups), g1 = min(g0 + Q, groups);
+    auto sum2 = [](uint32_t x) { return (x & 0xFFFFu) + (x >> 16); };
     uint32_t local = 0;
-    for (uint32_t i = w0; i < w1; ++i) {
-        const uint32_t x = w[i];
-        local += (x & 0xFFFFu) + (x >> 16);
+    for (uint32_t i = g0; i < g1; ++i) {
+        const uint4 x = g[i];
+        local += (sum2(x.x) + sum2(x.y)) + (sum2(x.z) + sum2(x.w));
     }
-    uint32_t total;
-    uint32_t run = block_exclusive_scan<NT>(local, tmp, &total);
-    for (uint32_t i = w0; i < w1; ++i) {
-        const uint32_t x = w[i];
+    const uint32_t lane = tid & 31, warp = tid >> 5;
+    uint32_t incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= (uint32_t)o) incl += y;
+    }
+    if (lane == 31) tmp[warp] = incl;
+    __syncthreads();
+    uint32_t run = incl - local;
+#pragma unroll
+    for (int u = 0; u < NW; ++u) run += (uint32_t)u < warp ? tmp[u] : 0u;
+    auto put = [&](uint32_t x) {   // the two counts of a word -> their first positions
         const uint32_t lo = run, hi = run + (x & 0xFFFFu);
-        w[i] = lo | (hi << 16);
         run = hi + (x >> 16);
+        return lo | (hi << 16);
+    };
+    for (uint32_t i = g0; i < g1; ++i) {
+        const uint4 x = g[i];
+        uint4 y;
+        y.x = put(x.x);
+        y.y = put(x.y);
+        y.z = put(x.z);
+        y.w = put(x.w);
+        g[i] = y;
     }
     __syncthreads();
 }
@@ -349,8 +375,9 @@ RS_DEV bool bucket_repair(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, 
 
 // Bucket path.  Returns true on success (leaf written), false if the leaf
 // must take the probing path (whatever was written is overwritten later).
-template <typename KeyT, int NT, int BAR, bool WR, uint32_t CAP = kHashCap>
-RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, Key2 key, uint32_t k,
+// K2 is Key2 or RoundKeys (the same generator, round keys precomputed).
+template <typename KeyT, int NT, int BAR, bool WR, uint32_t CAP = kHashCap, typename K2 = Key2>
+RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, const K2& key, uint32_t k,
                         uint64_t* __restrict__ dst, uint32_t tid) {
     const uint32_t tag = WR ? TAG_LEAF_WR : TAG_LEAF_H;
     const uint32_t nb = max(64u, (k + 63) & ~63u);   // even, <= kBuckets
@@ -359,9 +386,14 @@ RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, Ke
     uint32_t* cw = sm.cnt;                // count of bucket b: 16-bit half b & 1 of word b >> 1
     const uint16_t* ch = reinterpret_cast<const uint16_t*>(sm.cnt);
     for (uint32_t i = tid; i < nb / 2; i += NT) cw[i] = 0;
+    // B[k .. k+3) hold the largest key value: the rank pass's window of four
+    // may run past the end of the leaf, and reads past a key's bucket meet
+    // only larger keys (buckets are monotone in the key) or these
+    if (tid < 3) B[k + tid] = ~KeyT(0);
     const uint64_t mult = slot_mult_fast<KeyT>(r.s, nb);
     const uint64_t thr = lemire_threshold(r.s);
     group_sync<BAR, NT>();
+    if (tid == 0) sm.ranksum = 0;   // every read of the last leaf's sum came before this barrier
     // pass 1: generate, keep, count per bucket
     auto keep = [&](uint32_t j, uint64_t v) {
         A[j] = (KeyT)v;
@@ -376,12 +408,25 @@ RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, Ke
         if (r.s <= (1ull << 32)) {
             const uint32_t sh = 32u - t;   // 0 when s = 2^32
             const uint32_t full = k >> 2;  // Philox blocks whose four words are all used
+            auto count = [&](uint32_t v) {
+                const uint32_t b = hash_slot((KeyT)v, mult);
+                atomicAdd(&cw[b >> 1], 1u << ((b & 1u) << 4));
+            };
             for (uint32_t i = tid; i < full; i += NT) {
                 const uint4 w = philox_block(i, tag, r.id, key);
-                keep(4 * i, sh < 32 ? (w.x >> sh) : 0u);
-                keep(4 * i + 1, sh < 32 ? (w.y >> sh) : 0u);
-                keep(4 * i + 2, sh < 32 ? (w.z >> sh) : 0u);
-                keep(4 * i + 3, sh < 32 ? (w.w >> sh) : 0u);
+                const uint4 v = sh < 32 ? make_uint4(w.x >> sh, w.y >> sh, w.z >> sh, w.w >> sh) : make_uint4(0, 0, 0, 0);
+                if (sizeof(KeyT) == 4) {
+                    reinterpret_cast<uint4*>(A)[i] = v;   // one 16-byte store (A is 16-byte aligned)
+                } else {
+                    A[4 * i] = v.x;
+                    A[4 * i + 1] = v.y;
+                    A[4 * i + 2] = v.z;
+                    A[4 * i + 3] = v.w;
+                }
+                count(v.x);
+                count(v.y);
+                count(v.z);
+                count(v.w);
             }
             if (tid == 0 && (k & 3u)) {
                 const uint4 w = philox_block(full, tag, r.id, key);
@@ -472,11 +517,15 @@ RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, Ke
     // pass 3: the rank of B[i] among its bucket's keys, ordered by (key,
     // position in B), is its place in the sorted leaf; it lies in the
     // bucket's range, a few places from i, so the stores straight to the
-    // output stay nearly coalesced.  Without replacement, an equal key in the
-    // bucket is a repeat.  (The repair of repeats runs it again into A.)
+    // output stay nearly coalesced.  The first run counts only the smaller
+    // keys: equal keys then share a rank, which shows as a sum of ranks below
+    // k (k - 1) / 2.  Then, with replacement, a second run with the position
+    // tie-break rewrites the leaf; without, equal keys are repeats and the
+    // tie-break run writes the sorted keys to A for the repair.
     const uint64_t base = r.lo + 1;
-    auto rank_pass = [&](bool to_out) {
-        bool dup = false;
+    auto rank_pass = [&](auto ties_tag) {
+        constexpr bool ties = decltype(ties_tag)::value;
+        uint32_t rsum = 0;
         for (uint32_t i0 = tid; i0 < k; i0 += U * NT) {
             KeyT x[U];
             uint32_t s0[U], s1[U], rank[U];
@@ -489,48 +538,44 @@ RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, Ke
                 s1[q] = i < k ? ch[b] : 0u;
                 rank[q] = s0[q];
             }
-            // four unrolled comparisons without branches: the load index is
-            // clamped into the leaf and the in-bucket test masks the result
+            // a window of four from the bucket start, unrolled and without
+            // branches; longer buckets go on in a loop
 #pragma unroll
             for (uint32_t u = 0; u < 4; ++u) {
 #pragma unroll
                 for (uint32_t q = 0; q < U; ++q) {
                     const uint32_t j = s0[q] + u;
-                    const KeyT y = B[min(j, k - 1)];
-                    const uint32_t in = j < s1[q] ? 1u : 0u;
-                    const uint32_t lt = (y < x[q]) ? 1u : 0u;
-                    const uint32_t eq = (y == x[q]) ? 1u : 0u;
-                    const uint32_t before = j < i0 + q * NT ? 1u : 0u;
-                    rank[q] += in & (lt | (eq & before));
-                    if (!WR) dup |= (in & eq & (j != i0 + q * NT ? 1u : 0u)) != 0u;
+                    const KeyT y = B[j];
+                    if (!ties) rank[q] += y < x[q] ? 1u : 0u;
+                    else rank[q] += ((y < x[q]) || (y == x[q] && j < i0 + q * NT)) ? 1u : 0u;
                 }
             }
 #pragma unroll
             for (uint32_t q = 0; q < U; ++q) {
-                for (uint32_t j = s0[q] + 4; j < s1[q]; ++j) {   // buckets of more than four keys
+                for (uint32_t j = s0[q] + 4; j < s1[q]; ++j) {
                     const KeyT y = B[j];
-                    rank[q] += (y < x[q]) || (y == x[q] && j < i0 + q * NT);
-                    if (!WR && y == x[q] && j != i0 + q * NT) dup = true;
+                    if (!ties) rank[q] += y < x[q] ? 1u : 0u;
+                    else rank[q] += ((y < x[q]) || (y == x[q] && j < i0 + q * NT)) ? 1u : 0u;
                 }
             }
 #pragma unroll
             for (uint32_t q = 0; q < U; ++q)
                 if (i0 + q * NT < k) {
-                    if (to_out) dst[rank[q]] = base + x[q];
+                    rsum += rank[q];
+                    if (!ties || WR) dst[rank[q]] = base + x[q];
                     else A[rank[q]] = x[q];
                 }
         }
-        return dup;
+        return rsum;
     };
-    const bool dup = rank_pass(true);
-    // (a barrier either way: the next leaf clears the counts this pass reads)
-    if (WR) {
-        group_sync<BAR, NT>();
-        return true;
-    }
-    if (!group_sync_or<BAR, NT>(dup)) return true;
-    rank_pass(false);   // the sorted keys, repeats adjacent
+    const uint32_t rsum = __reduce_add_sync(0xFFFFFFFFu, rank_pass(std::false_type{}));
+    if ((tid & 31) == 0) atomicAdd(&sm.ranksum, rsum);
     group_sync<BAR, NT>();
+    // (a barrier either way: the next leaf clears the counts this pass reads)
+    if (sm.ranksum == (uint32_t)((uint64_t)k * (k - 1) / 2)) return true;
+    rank_pass(std::true_type{});
+    group_sync<BAR, NT>();
+    if (WR) return true;
     return bucket_repair<KeyT, NT, BAR, CAP>(sm, r, key, k, thr, A, B, dst, tid);   // rewrites the whole leaf
 }
 
@@ -771,8 +816,8 @@ RS_DEV bool probe_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, Key
 // false if the leaf must go to the general (global-memory) path, having
 // written nothing of use.  All NT threads of the group call it; tid is the
 // thread's index in the group.
-template <typename KeyT, int NT, int BAR, bool WR, uint32_t CAP = kHashCap>
-RS_DEV bool hash_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, Key2 key, uint64_t* __restrict__ out,
+template <typename KeyT, int NT, int BAR, bool WR, uint32_t CAP = kHashCap, typename K2 = Key2>
+RS_DEV bool hash_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, const K2& key, uint64_t* __restrict__ out,
                       int* status, uint32_t tid, uint32_t cap) {
     const bool comp = !WR && (r.np > r.s - r.np);
     const uint64_t k64 = comp ? r.s - r.np : r.np;

@@ -23,6 +23,7 @@ struct LeafJob {
     uint32_t* ovf_list;      // leaves left to the general path
     uint32_t* ovf_count;
     uint32_t cap;            // largest selection handled here
+    RoundKeys rk;            // the seed's Philox round keys
 };
 
 // Two shapes of the leaf kernel: 256 threads with room for 4,864 values
@@ -35,16 +36,17 @@ constexpr uint32_t kLargeCap = 2 * kLeafFastCap;
 
 // One block per leaf at a time, persistent over the leaves; leaves the
 // shared-memory table cannot take go to the general path's list.
+// The job is a __grid_constant__ parameter so that the Philox rounds read
+// their keys from the parameter bank.
 template <typename KeyT, bool WR, int NT, uint32_t CAP>
-__global__ void __launch_bounds__(NT) leaf_kernel(LeafJob job) {
+__global__ void __launch_bounds__(NT) leaf_kernel(const __grid_constant__ LeafJob job) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto& sm = *reinterpret_cast<HashShared<KeyT, NT / 32, CAP>*>(smem_raw);
-    const Key2 key = make_key(job.seed);
     for (uint64_t leaf = blockIdx.x; leaf < job.nleaves; leaf += gridDim.x) {
         const NodeRec r = job.leaves[leaf];
         if (r.c == 0) continue;
         const LeafRec lr{r.lo, r.S, r.c, r.off, job.first_id + leaf};
-        if (!hash_leaf<KeyT, NT, 0, WR, CAP>(sm, lr, key, job.out, job.status, threadIdx.x, job.cap)) {
+        if (!hash_leaf<KeyT, NT, 0, WR, CAP>(sm, lr, job.rk, job.out, job.status, threadIdx.x, job.cap)) {
             if (threadIdx.x == 0) job.ovf_list[atomicAdd(job.ovf_count, 1u)] = (uint32_t)leaf;
         }
     }
@@ -111,7 +113,8 @@ static cudaError_t launch_shape(const LeafJob& job, const LeafLaunch& L, cudaStr
 }
 
 cudaError_t launch_leaves(const LeafLaunch& L, cudaStream_t st) {
-    LeafJob job{L.leaves, L.nleaves, L.first_id, L.seed, L.out, L.status, L.ovf_list, L.ovf_count, 0};
+    LeafJob job{L.leaves, L.nleaves, L.first_id, L.seed, L.out, L.status, L.ovf_list, L.ovf_count, 0,
+                RoundKeys::of(L.seed)};
     cudaError_t e = cudaMemsetAsync(L.ovf_count, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
     // leaves averaging well above the small shape's room take the large one

@@ -33,6 +33,37 @@ RS_DEV uint4 philox_block(uint32_t t, uint32_t tag, uint64_t id, Key2 key) {
     return make_uint4(x0, x1, x2, x3);
 }
 
+// The same generator with its ten round keys worked out in advance.  A
+// kernel whose key is the same for every thread takes them as a kernel
+// parameter (__grid_constant__): each round then reads its key from the
+// parameter bank instead of bumping two registers.
+struct RoundKeys {
+    uint32_t k[20];   // round r: k[2r] = k0 + r 0x9E3779B9, k[2r+1] = k1 + r 0xBB67AE85 (mod 2^32)
+    RS_HD static RoundKeys of(uint64_t seed) {
+        RoundKeys rk;
+        const Key2 key = make_key(seed);
+        for (int r = 0; r < 10; ++r) {
+            rk.k[2 * r] = key.k0 + (uint32_t)r * 0x9E3779B9u;
+            rk.k[2 * r + 1] = key.k1 + (uint32_t)r * 0xBB67AE85u;
+        }
+        return rk;
+    }
+    RS_HD operator Key2() const { return Key2{k[0], k[1]}; }
+};
+
+RS_DEV uint4 philox_block(uint32_t t, uint32_t tag, uint64_t id, const RoundKeys& rk) {
+    uint32_t x0 = t, x1 = tag, x2 = (uint32_t)id, x3 = (uint32_t)(id >> 32);
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * x0;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * x2;
+        const uint32_t y0 = (uint32_t)(p1 >> 32) ^ x1 ^ rk.k[2 * r];
+        const uint32_t y2 = (uint32_t)(p0 >> 32) ^ x3 ^ rk.k[2 * r + 1];
+        x0 = y0; x1 = (uint32_t)p1; x2 = y2; x3 = (uint32_t)p0;
+    }
+    return make_uint4(x0, x1, x2, x3);
+}
+
 // 64-bit value j of a stream: words 2j and 2j+1 (low, high), block j/2.
 RS_DEV uint64_t stream_value(Key2 key, uint32_t tag, uint64_t id, uint64_t j) {
     uint4 b = philox_block((uint32_t)(j >> 1), tag, id, key);
