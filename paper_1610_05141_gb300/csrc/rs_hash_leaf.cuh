@@ -17,8 +17,9 @@
 //    A scan of the counts gives every bucket its output offset; a second
 //    pass scatters the keys into bucket order; each key then finds its rank
 //    inside its bucket (four unrolled comparisons, a loop beyond), which is
-//    its output position; a coalesced copy writes the leaf and checks
-//    neighbours for repeats.  When the leaf size does not divide 2^32 (2^64)
+//    its output position, and is written there.  Equal keys share a rank and
+//    so lower the sum of the ranks: a second run then breaks the ties by
+//    position.  When the leaf size does not divide 2^32 (2^64)
 //    some candidates are void: candidates are then generated one Philox
 //    block per thread at a time and the valid ones numbered in index order
 //    with a block scan, so that exactly the first k valid ones are kept.  If
@@ -50,6 +51,10 @@
 
 namespace rs {
 
+// The paths other than the bucket path's first run are compiled as calls of
+// their own, so that their registers do not weigh on the common case.
+#define RS_COLD __device__ __noinline__
+
 constexpr uint32_t kHashCap = kLeafFastCap;         // largest selection of the shared-memory paths
 constexpr uint32_t kHashSlack = 64;                 // probing: slots past the end instead of wrap-around
 
@@ -70,7 +75,8 @@ struct HashShared {
     static constexpr uint32_t kBuckets = CAP + 64;        // bucket path: about one key per bucket
     KeyT tab[kSlots];              // bucket path: keys (first k + 3), then keys in bucket order;
                                    // probing table; bitmap; tallies
-    alignas(16) uint32_t cnt[kBuckets / 2 + 1];   // bucket path: 16-bit counts, two per word, then offsets
+    alignas(16) uint32_t cnt[kBuckets / 2 + 5];   // bucket path: word 3 is zero; from word 4 on, 16-bit
+                                                  // counts, two per word, then offsets
     uint32_t scan_tmp[NW + 1];
     uint32_t warp_cnt[NW];
     uint32_t newcount[3];          // rounds: values added in round r go to newcount[r % 3]
@@ -214,22 +220,25 @@ RS_DEV void for_candidates(const LeafRec& r, uint64_t thr64, Key2 key, uint32_t 
 }
 
 // Exclusive prefix sums, in place, of the nb 16-bit counts packed two per
-// word in w[0 .. nb/2), nb a multiple of 64 and w 16-byte aligned.  Thread t
-// owns Q consecutive 16-byte groups (8 counts each), Q odd so that the
-// 16-byte accesses of a quarter warp fall in distinct banks.  Two barriers:
-// warp totals go to tmp[], then each warp adds those of the warps before it.
+// word in w[0 .. nb/2), nb a multiple of 64 and at most 24 NT, w 16-byte
+// aligned.  Thread t owns Q consecutive 16-byte groups (8 counts each), Q = 1
+// or 3 (odd, so that the 16-byte accesses of a quarter warp fall in distinct
+// banks), kept in registers between the two halves.  Two barriers: warp
+// totals go to tmp[], then each warp adds up those of the warps before it.
 template <int NT>
 RS_DEV void scan_counts16(uint32_t* w, uint32_t nb, uint32_t* tmp, uint32_t tid) {
-    constexpr int NW = NT / 32;
     uint4* g = reinterpret_cast<uint4*>(w);
     const uint32_t groups = nb >> 3;
-    const uint32_t Q = ((groups + NT - 1) / NT) | 1u;
-    const uint32_t g0 = min(tid * Q, groups), g1 = min(g0 + Q, groups);
+    const uint32_t Q = groups > NT ? 3u : 1u;
+    const uint32_t g0 = tid * Q;
     auto sum2 = [](uint32_t x) { return (x & 0xFFFFu) + (x >> 16); };
+    uint4 x[3];
     uint32_t local = 0;
-    for (uint32_t i = g0; i < g1; ++i) {
-        const uint4 x = g[i];
-        local += (sum2(x.x) + sum2(x.y)) + (sum2(x.z) + sum2(x.w));
+#pragma unroll
+    for (uint32_t q = 0; q < 3; ++q) {
+        x[q] = make_uint4(0, 0, 0, 0);
+        if (q < Q && g0 + q < groups) x[q] = g[g0 + q];
+        local += (sum2(x[q].x) + sum2(x[q].y)) + (sum2(x[q].z) + sum2(x[q].w));
     }
     const uint32_t lane = tid & 31, warp = tid >> 5;
     uint32_t incl = local;
@@ -240,22 +249,22 @@ RS_DEV void scan_counts16(uint32_t* w, uint32_t nb, uint32_t* tmp, uint32_t tid)
     }
     if (lane == 31) tmp[warp] = incl;
     __syncthreads();
-    uint32_t run = incl - local;
-#pragma unroll
-    for (int u = 0; u < NW; ++u) run += (uint32_t)u < warp ? tmp[u] : 0u;
-    auto put = [&](uint32_t x) {   // the two counts of a word -> their first positions
-        const uint32_t lo = run, hi = run + (x & 0xFFFFu);
-        run = hi + (x >> 16);
+    uint32_t run = incl - local + __reduce_add_sync(0xFFFFFFFFu, lane < warp ? tmp[lane] : 0u);
+    auto put = [&](uint32_t v) {   // the two counts of a word -> their first positions
+        const uint32_t lo = run, hi = run + (v & 0xFFFFu);
+        run = hi + (v >> 16);
         return lo | (hi << 16);
     };
-    for (uint32_t i = g0; i < g1; ++i) {
-        const uint4 x = g[i];
-        uint4 y;
-        y.x = put(x.x);
-        y.y = put(x.y);
-        y.z = put(x.z);
-        y.w = put(x.w);
-        g[i] = y;
+#pragma unroll
+    for (uint32_t q = 0; q < 3; ++q) {
+        if (q < Q && g0 + q < groups) {
+            uint4 y;
+            y.x = put(x[q].x);
+            y.y = put(x[q].y);
+            y.z = put(x[q].z);
+            y.w = put(x[q].w);
+            g[g0 + q] = y;
+        }
     }
     __syncthreads();
 }
@@ -285,7 +294,7 @@ RS_DEV bool candidate_at(const LeafRec& r, uint64_t thr, Key2 key, uint32_t tag,
 // is valid and new), and writes the merged sorted leaf.  False if the stream
 // runs out (the probing path then reports it).
 template <typename KeyT, int NT, int BAR, uint32_t CAP>
-RS_DEV bool bucket_repair(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, Key2 key, uint32_t k, uint64_t thr,
+RS_COLD bool bucket_repair(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, Key2 key, uint32_t k, uint64_t thr,
                           KeyT* A, KeyT* B, uint64_t* __restrict__ dst, uint32_t tid) {
     // distinct values of the sorted A, in order, into B
     const uint32_t Q = (k + NT - 1) / NT;
@@ -373,19 +382,104 @@ RS_DEV bool bucket_repair(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, 
     return true;
 }
 
+// Pass 3 of the bucket path over B (keys in bucket order, B[k .. k+3) the
+// largest key value) with bucket ends ch[] (ch[-1] = 0): each key's rank
+// among its bucket's keys is its place in the sorted leaf.  Without TIES the
+// rank counts the smaller keys only, and the key goes to dst[rank]; with
+// TIES equal keys are ordered by position in B, and the key goes to
+// dst[rank] (with replacement) or A[rank] (without, for the repair).
+// Returns the thread's sum of ranks.
+template <typename KeyT, int NT, bool TIES, bool WR>
+RS_DEV uint32_t rank_keys(const KeyT* B, KeyT* A, const uint16_t* ch, uint32_t k, uint64_t mult, uint64_t base,
+                          uint64_t* __restrict__ dst, uint32_t tid) {
+    constexpr uint32_t U = 4;   // keys per thread at a time, so that their load chains overlap
+    uint32_t rsum = 0;
+    // `full` tiles need no bounds tests
+    auto tile = [&](uint32_t i0, auto full_tag) {
+        constexpr bool full = decltype(full_tag)::value;
+        KeyT x[U];
+        uint32_t s0[U], s1[U], rank[U];
+#pragma unroll
+        for (uint32_t q = 0; q < U; ++q) {
+            const uint32_t i = i0 + q * NT;
+            const bool ok = full || i < k;
+            x[q] = ok ? B[i] : KeyT(0);
+            const uint32_t b = hash_slot(x[q], mult);
+            s0[q] = ch[(int)b - 1];
+            s1[q] = ok ? ch[b] : 0u;
+            rank[q] = s0[q];
+        }
+        // a window of four from the bucket start, unrolled and without
+        // branches: reads past the bucket meet only larger keys (buckets
+        // are monotone in the key) or the padding
+#pragma unroll
+        for (uint32_t u = 0; u < 4; ++u) {
+#pragma unroll
+            for (uint32_t q = 0; q < U; ++q) {
+                const uint32_t j = s0[q] + u;
+                const KeyT y = B[j];
+                if (!TIES) rank[q] += y < x[q] ? 1u : 0u;
+                else rank[q] += ((y < x[q]) || (y == x[q] && j < i0 + q * NT)) ? 1u : 0u;
+            }
+        }
+        // buckets of more than four keys: one loop for the U keys, reads
+        // past the leaf clamped to the padding
+        uint32_t extra = 0;
+#pragma unroll
+        for (uint32_t q = 0; q < U; ++q) extra = max(extra, s1[q] - min(s1[q], s0[q] + 4));
+        for (uint32_t e = 0; e < extra; ++e) {
+#pragma unroll
+            for (uint32_t q = 0; q < U; ++q) {
+                const uint32_t j = min(s0[q] + 4 + e, k + 2);
+                const KeyT y = B[j];
+                if (!TIES) rank[q] += y < x[q] ? 1u : 0u;
+                else rank[q] += ((y < x[q]) || (y == x[q] && j < i0 + q * NT)) ? 1u : 0u;
+            }
+        }
+#pragma unroll
+        for (uint32_t q = 0; q < U; ++q)
+            if (full || i0 + q * NT < k) {
+                rsum += rank[q];
+                if (!TIES || WR) dst[rank[q]] = base + x[q];
+                else A[rank[q]] = x[q];
+            }
+    };
+    uint32_t i0 = tid;
+    for (; i0 + (U - 1) * NT < k; i0 += U * NT) tile(i0, std::true_type{});
+    if (i0 < k) tile(i0, std::false_type{});
+    return rsum;
+}
+
+// The bucket path's leaves with equal keys (after the first rank run): the
+// tie-broken run rewrites the leaf (with replacement) or sorts the keys into
+// A for the repair of repeats (without).
+template <typename KeyT, int NT, int BAR, bool WR, uint32_t CAP>
+RS_COLD bool bucket_ties(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, Key2 key, uint32_t k, uint64_t thr,
+                         uint64_t mult, uint64_t* __restrict__ dst, uint32_t tid) {
+    KeyT* A = sm.tab;
+    KeyT* B = sm.tab + ((k + 3) & ~3u);
+    const uint16_t* ch = reinterpret_cast<const uint16_t*>(sm.cnt + 4);
+    rank_keys<KeyT, NT, true, WR>(B, A, ch, k, mult, r.lo + 1, dst, tid);
+    group_sync<BAR, NT>();
+    if (WR) return true;
+    return bucket_repair<KeyT, NT, BAR, CAP>(sm, r, key, k, thr, A, B, dst, tid);   // rewrites the whole leaf
+}
+
 // Bucket path.  Returns true on success (leaf written), false if the leaf
 // must take the probing path (whatever was written is overwritten later).
 // K2 is Key2 or RoundKeys (the same generator, round keys precomputed).
 template <typename KeyT, int NT, int BAR, bool WR, uint32_t CAP = kHashCap, typename K2 = Key2>
 RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, const K2& key, uint32_t k,
                         uint64_t* __restrict__ dst, uint32_t tid) {
+    static_assert(HashShared<KeyT, NT / 32, CAP>::kBuckets <= 24 * NT, "scan_counts16 takes at most 24 NT counts");
     const uint32_t tag = WR ? TAG_LEAF_WR : TAG_LEAF_H;
-    const uint32_t nb = max(64u, (k + 63) & ~63u);   // even, <= kBuckets
+    const uint32_t nb = max(64u, (k + 63) & ~63u);   // a multiple of 64, <= kBuckets
     KeyT* A = sm.tab;                     // candidate j at A[j]; later the sorted leaf
     KeyT* B = sm.tab + ((k + 3) & ~3u);   // keys in bucket order
-    uint32_t* cw = sm.cnt;                // count of bucket b: 16-bit half b & 1 of word b >> 1
-    const uint16_t* ch = reinterpret_cast<const uint16_t*>(sm.cnt);
-    for (uint32_t i = tid; i < nb / 2; i += NT) cw[i] = 0;
+    uint32_t* cw = sm.cnt + 4;            // count of bucket b: 16-bit half b & 1 of word b >> 1
+    const uint16_t* ch = reinterpret_cast<const uint16_t*>(cw);   // ch[-1] = 0, the high half of cnt[3]
+    for (uint32_t i = tid; i < nb / 8; i += NT) reinterpret_cast<uint4*>(cw)[i] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) sm.cnt[3] = 0;
     // B[k .. k+3) hold the largest key value: the rank pass's window of four
     // may run past the end of the leaf, and reads past a key's bucket meet
     // only larger keys (buckets are monotone in the key) or these
@@ -493,24 +587,33 @@ RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, co
         group_sync<BAR, NT>();
     }
     scan_counts16<NT>(cw, nb, sm.scan_tmp, tid);   // half b = first position of bucket b
-    // Passes 2, 3 and the copy take four independent keys per thread at a
-    // time so that their load -> address -> load chains overlap.
+    // Passes 2 and 3 take four independent keys per thread at a time so
+    // that their load -> address -> load chains overlap.
     constexpr uint32_t U = 4;
     // pass 2: scatter into bucket order; afterwards half b = end of bucket b
-    for (uint32_t j0 = tid; j0 < k; j0 += U * NT) {
-        KeyT x[U];
-        uint32_t b[U];
-#pragma unroll
-        for (uint32_t q = 0; q < U; ++q) {
-            x[q] = j0 + q * NT < k ? A[j0 + q * NT] : KeyT(0);
-            b[q] = hash_slot(x[q], mult);
+    auto scatter = [&](KeyT x) {
+        const uint32_t b = hash_slot(x, mult);
+        const uint32_t sh = (b & 1u) << 4;
+        B[(atomicAdd(&cw[b >> 1], 1u << sh) >> sh) & 0xFFFFu] = x;
+    };
+    if (sizeof(KeyT) == 4) {   // four keys per 16-byte load (the order within a bucket is free)
+        const uint32_t k4 = k >> 2;
+        for (uint32_t g = tid; g < k4; g += NT) {
+            const uint4 v = reinterpret_cast<const uint4*>(A)[g];
+            scatter((KeyT)v.x);
+            scatter((KeyT)v.y);
+            scatter((KeyT)v.z);
+            scatter((KeyT)v.w);
         }
+        for (uint32_t j = 4 * k4 + tid; j < k; j += NT) scatter(A[j]);
+    } else {
+        for (uint32_t j0 = tid; j0 < k; j0 += U * NT) {
+            KeyT x[U];
 #pragma unroll
-        for (uint32_t q = 0; q < U; ++q) {
-            if (j0 + q * NT < k) {
-                const uint32_t sh = (b[q] & 1u) << 4;
-                B[(atomicAdd(&cw[b[q] >> 1], 1u << sh) >> sh) & 0xFFFFu] = x[q];
-            }
+            for (uint32_t q = 0; q < U; ++q) x[q] = j0 + q * NT < k ? A[j0 + q * NT] : KeyT(0);
+#pragma unroll
+            for (uint32_t q = 0; q < U; ++q)
+                if (j0 + q * NT < k) scatter(x[q]);
         }
     }
     group_sync<BAR, NT>();
@@ -519,64 +622,14 @@ RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, co
     // bucket's range, a few places from i, so the stores straight to the
     // output stay nearly coalesced.  The first run counts only the smaller
     // keys: equal keys then share a rank, which shows as a sum of ranks below
-    // k (k - 1) / 2.  Then, with replacement, a second run with the position
-    // tie-break rewrites the leaf; without, equal keys are repeats and the
-    // tie-break run writes the sorted keys to A for the repair.
-    const uint64_t base = r.lo + 1;
-    auto rank_pass = [&](auto ties_tag) {
-        constexpr bool ties = decltype(ties_tag)::value;
-        uint32_t rsum = 0;
-        for (uint32_t i0 = tid; i0 < k; i0 += U * NT) {
-            KeyT x[U];
-            uint32_t s0[U], s1[U], rank[U];
-#pragma unroll
-            for (uint32_t q = 0; q < U; ++q) {
-                const uint32_t i = i0 + q * NT;
-                x[q] = i < k ? B[i] : KeyT(0);
-                const uint32_t b = hash_slot(x[q], mult);
-                s0[q] = b ? ch[b - 1] : 0u;
-                s1[q] = i < k ? ch[b] : 0u;
-                rank[q] = s0[q];
-            }
-            // a window of four from the bucket start, unrolled and without
-            // branches; longer buckets go on in a loop
-#pragma unroll
-            for (uint32_t u = 0; u < 4; ++u) {
-#pragma unroll
-                for (uint32_t q = 0; q < U; ++q) {
-                    const uint32_t j = s0[q] + u;
-                    const KeyT y = B[j];
-                    if (!ties) rank[q] += y < x[q] ? 1u : 0u;
-                    else rank[q] += ((y < x[q]) || (y == x[q] && j < i0 + q * NT)) ? 1u : 0u;
-                }
-            }
-#pragma unroll
-            for (uint32_t q = 0; q < U; ++q) {
-                for (uint32_t j = s0[q] + 4; j < s1[q]; ++j) {
-                    const KeyT y = B[j];
-                    if (!ties) rank[q] += y < x[q] ? 1u : 0u;
-                    else rank[q] += ((y < x[q]) || (y == x[q] && j < i0 + q * NT)) ? 1u : 0u;
-                }
-            }
-#pragma unroll
-            for (uint32_t q = 0; q < U; ++q)
-                if (i0 + q * NT < k) {
-                    rsum += rank[q];
-                    if (!ties || WR) dst[rank[q]] = base + x[q];
-                    else A[rank[q]] = x[q];
-                }
-        }
-        return rsum;
-    };
-    const uint32_t rsum = __reduce_add_sync(0xFFFFFFFFu, rank_pass(std::false_type{}));
+    // k (k - 1) / 2, and a second run breaks the ties.
+    const uint32_t rsum =
+        __reduce_add_sync(0xFFFFFFFFu, rank_keys<KeyT, NT, false, WR>(B, A, ch, k, mult, r.lo + 1, dst, tid));
     if ((tid & 31) == 0) atomicAdd(&sm.ranksum, rsum);
     group_sync<BAR, NT>();
     // (a barrier either way: the next leaf clears the counts this pass reads)
     if (sm.ranksum == (uint32_t)((uint64_t)k * (k - 1) / 2)) return true;
-    rank_pass(std::true_type{});
-    group_sync<BAR, NT>();
-    if (WR) return true;
-    return bucket_repair<KeyT, NT, BAR, CAP>(sm, r, key, k, thr, A, B, dst, tid);   // rewrites the whole leaf
+    return bucket_ties<KeyT, NT, BAR, WR, CAP>(sm, r, key, k, thr, mult, dst, tid);
 }
 
 // Rounds of distinct insertion shared by the bitmap and probing paths:
@@ -616,7 +669,7 @@ RS_DEV bool distinct_rounds(uint32_t* newcount, const LeafRec& r, uint64_t thr, 
 // n' valid candidates are tallied per value; an exclusive scan of the tallies
 // gives each value's run of output positions.
 template <typename KeyT, int NT, int BAR, uint32_t CAP>
-RS_DEV void count_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, Key2 key, uint32_t k,
+RS_COLD void count_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, Key2 key, uint32_t k,
                        uint64_t* __restrict__ dst, int* status, uint32_t tid) {
     uint32_t* h = reinterpret_cast<uint32_t*>(sm.tab);
     const uint32_t s = (uint32_t)r.s;
@@ -646,7 +699,7 @@ RS_DEV void count_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, Key
 
 // Bitmap path for leaves without replacement with s at most the table bits.
 template <typename KeyT, int NT, int BAR, uint32_t CAP>
-RS_DEV void bitmap_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, Key2 key, uint32_t k, bool comp,
+RS_COLD void bitmap_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, Key2 key, uint32_t k, bool comp,
                         uint64_t* __restrict__ dst, int* status, uint32_t tid) {
     constexpr int NW = NT / 32;
     const uint32_t lane = tid & 31, warp = tid >> 5;
@@ -719,7 +772,7 @@ RS_DEV void bitmap_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, Ke
 
 // Probing path.  Returns false if a probe ran past the slack (general path).
 template <typename KeyT, int NT, int BAR, bool WR, uint32_t CAP>
-RS_DEV bool probe_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, Key2 key, uint32_t k,
+RS_COLD bool probe_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, Key2 key, uint32_t k,
                        uint64_t* __restrict__ dst, int* status, uint32_t tid) {
     constexpr int NW = NT / 32;
     constexpr KeyT E = HashEmpty<KeyT>::v;

@@ -39,7 +39,7 @@ constexpr uint32_t kLargeCap = 2 * kLeafFastCap;
 // The job is a __grid_constant__ parameter so that the Philox rounds read
 // their keys from the parameter bank.
 template <typename KeyT, bool WR, int NT, uint32_t CAP>
-__global__ void __launch_bounds__(NT) leaf_kernel(const __grid_constant__ LeafJob job) {
+__global__ void __launch_bounds__(NT, 1024 / NT) leaf_kernel(const __grid_constant__ LeafJob job) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto& sm = *reinterpret_cast<HashShared<KeyT, NT / 32, CAP>*>(smem_raw);
     for (uint64_t leaf = blockIdx.x; leaf < job.nleaves; leaf += gridDim.x) {
