@@ -72,6 +72,8 @@ def _load():
             "or_log": (dbl, [dbl]),
             "or_log_table_entry": (None, [i32, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
             "or_log1p": (dbl, [dbl]),
+            "or_recip": (dbl, [dbl]),
+            "or_log1p_pos": (dbl, [dbl]),
             "or_exp": (dbl, [dbl]),
             "or_lf": (dbl, [u64]),
             "or_lfdiff": (dbl, [u64, u64]),
@@ -156,6 +158,14 @@ def log(x):
 
 def log1p(x):
     return float(_load().or_log1p(x))
+
+
+def recip(x):
+    return float(_load().or_recip(x))
+
+
+def log1p_pos(x):
+    return float(_load().or_log1p_pos(x))
 
 
 def exp(x):

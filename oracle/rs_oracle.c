@@ -12,11 +12,12 @@
  * the sampler, in the order the definition gives; nothing is blocked, fused
  * or reordered.  Build with -O2 -ffp-contract=off -fno-fast-math so that
  * every floating-point expression is evaluated exactly as written (IEEE
- * binary64, round to nearest, no fused multiply-add).
+ * binary64, round to nearest; a fused multiply-add only where fma() is
+ * written, single precision only where a (float) conversion is written).
  *
  * Where the paper fixes no detail (the RNG, the deviate algorithm, the
  * leaf draw order), the oracle takes the reading written out next to each
- * function; all readings are collected in the design doc.
+ * function.
  *
  * Parity status: everything here is pinned by the non-GPU tests against
  * known-answer vectors, libm/mpmath, exact rational probabilities, closed-form
@@ -268,6 +269,33 @@ double or_log1p(double z)
     return or_log(u) * (z / (u - 1.0));
 }
 
+/* 1/x for a positive x in [2^-60, 2^100]: a single-precision quotient of
+ * x rounded to single precision as the seed (relative error below 2^-23),
+ * then two Newton steps r <- r + r (1 - x r), each with two fused
+ * multiply-adds; the result is within about one ulp of 1/x.  It stands for
+ * a quotient wherever a correctly rounded one is not needed: Stirling's
+ * tail, the argument of ln(1 + z), the ratio-of-uniforms abscissa. */
+double or_recip(double x)
+{
+    double r = (double)(1.0f / (float)x);
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+}
+
+/* ln(1 + z) for z >= 0 without a division: u = 1 + z rounded, e = (1 + z)
+ * - u exactly (Knuth's two-sum), ln(1 + z) = ln u + ln(1 + e/u), and since
+ * |e/u| <= 2^-53 the last term is e/u to 2^-106 relative; e/u is taken as
+ * e times a single-precision 1/u. */
+double or_log1p_pos(double z)
+{
+    double u = 1.0 + z;
+    double bb = u - 1.0;
+    double e = (1.0 - (u - bb)) + (z - bb);
+    return or_log(u) + e * (double)(1.0f / (float)u);
+}
+
 /* e^x for x in [-708, 0]: k = round(x / ln 2), r = x - k ln 2 (split in two
  * parts), e^r by its Taylor series to r^13/13!, scaled by 2^k built from bits. */
 double or_exp(double x)
@@ -305,10 +333,10 @@ static void lf_init(void)
     lf_ready = 1;
 }
 
-/* Stirling correction 1/(12x) - 1/(360x^3) + 1/(1260x^5) - 1/(1680x^7). */
-static double stirling_tail(double x)
+/* Stirling correction 1/(12x) - 1/(360x^3) + 1/(1260x^5) - 1/(1680x^7),
+ * from r = 1/x (or_recip). */
+static double stirling_tail(double r)
 {
-    double r = 1.0 / x;
     double r2 = r * r;
     return r * (1.0 / 12.0 + r2 * (-1.0 / 360.0 + r2 * (1.0 / 1260.0 + r2 * (-1.0 / 1680.0))));
 }
@@ -318,10 +346,11 @@ double or_lf(uint64_t x)
     lf_init();
     if (x < 256) return lf_table[x];
     double X = (double)x;
-    return (X + 0.5) * or_log(X) - X + HL2PI + stirling_tail(X);
+    return (X + 0.5) * or_log(X) - X + HL2PI + stirling_tail(or_recip(X));
 }
 
-/* ln x! - ln y! for x >= y, written so that no large term cancels. */
+/* ln x! - ln y! for x >= y, written so that no large term cancels:
+ * (x + 1/2) ln(1 + d/y) + d ln y - d + tail(x) - tail(y), d = x - y. */
 double or_lfdiff(uint64_t x, uint64_t y)
 {
     lf_init();
@@ -335,7 +364,9 @@ double or_lfdiff(uint64_t x, uint64_t y)
     }
     if (y < 256) return or_lf(x) - lf_table[y];
     double X = (double)x, Y = (double)y, Dd = (double)d;
-    return (X + 0.5) * or_log1p(Dd / Y) + Dd * or_log(Y) - Dd + (stirling_tail(X) - stirling_tail(Y));
+    double rY = or_recip(Y);
+    double lp = or_log1p_pos(Dd * rY);
+    return (X + 0.5) * lp + Dd * or_log(Y) - Dd + (stirling_tail(or_recip(X)) - stirling_tail(rY));
 }
 
 /* Signed difference ln x! - ln y!. */
@@ -394,7 +425,7 @@ int or_hg(uint64_t seed, uint64_t id, uint64_t n, uint64_t K, uint64_t S, uint64
         for (uint64_t i = 0; i < (1ull << 20); ++i) {
             double U = or_u_open(or_value(seed, TAG_SPLIT, id, 2 * i));
             double V = or_v_closed(or_value(seed, TAG_SPLIT, id, 2 * i + 1));
-            double X = alpha + h * (V - 0.5) / U;
+            double X = alpha + h * (V - 0.5) * or_recip(U);
             if (X < 0.0 || X >= (double)a + 1.0) continue;
             uint64_t k = (uint64_t)X;
             double T = or_sd(M, k) + or_sd(a - M, a - k) + or_sd(b - M, b - k)
@@ -444,7 +475,7 @@ int or_bin(uint64_t seed, uint64_t id, uint64_t c, uint64_t K, uint64_t S, uint6
     for (uint64_t i = 0; i < (1ull << 20); ++i) {
         double U = or_u_open(or_value(seed, TAG_SPLIT, id, 2 * i));
         double V = or_v_closed(or_value(seed, TAG_SPLIT, id, 2 * i + 1));
-        double X = alpha + h * (V - 0.5) / U;
+        double X = alpha + h * (V - 0.5) * or_recip(U);
         if (X < 0.0 || X >= (double)c + 1.0) continue;
         uint64_t k = (uint64_t)X;
         double T = or_sd(M, k) + or_sd(c - M, c - k) + (double)((int64_t)k - (int64_t)M) * logr;
@@ -631,13 +662,16 @@ typedef void (*emit_fn)(void* ctx, uint64_t pos);
 static int64_t geometric_skips(uint64_t seed, uint32_t tag, uint64_t id, double p,
                                uint64_t start, uint64_t end, emit_fn emit, void* ctx)
 {
-    double L = or_log1p(-p);
+    /* Reading: the quotient ln U / ln(1-p) is taken as ln U times R =
+     * RN(1 / ln(1-p)), one division per range (within 2 ulp of the quotient);
+     * U = 1 gives skip 0 even where R overflows (p below 2^-1024). */
+    double R = 1.0 / or_log1p(-p);
     int64_t pos = (int64_t)start - 1;
     int64_t count = 0;
     for (uint64_t j = 0;; ++j) {
         if (j >= (1ull << 33)) return -1;
         double U = or_u_open(or_value(seed, tag, id, j));
-        double q = or_log(U) / L;
+        double q = (U == 1.0) ? 0.0 : or_log(U) * R;
         if (q >= 4611686018427387904.0) break;           /* 2^62 */
         pos = pos + (int64_t)floor(q) + 1;
         if (pos >= (int64_t)end) break;

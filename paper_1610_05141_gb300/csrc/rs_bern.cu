@@ -4,7 +4,9 @@
 // Geometric skips: with L = ln(1-p) and U uniform in (0,1], the skip
 // floor(ln U / L) is Geometric(p), so a Bernoulli(p) sample of a range is the
 // running sum of (skip + 1) while it stays inside the range (Sec. 2,
-// Algorithm B).  Draw j of a stream gives one skip.  A warp (Bernoulli
+// Algorithm B).  The quotient is taken as ln U times R = RN(1/L), one
+// division per range instead of one per draw (U = 1 gives skip 0 even where
+// R overflows).  Draw j of a stream gives one skip.  A warp (Bernoulli
 // chunks) or a block (leaf B) takes 32 or 512 consecutive draws at once and
 // turns them into positions with an integer prefix sum, which is exact, so
 // the positions are those of the sequential definition.  A draw with
@@ -31,6 +33,13 @@ RS_DEV uint64_t step_of(double q, uint64_t cmax, bool* stop) {
     return f < cmax ? f : cmax;
 }
 
+// q = ln U * R for the draw with 64-bit value x (U = u_open(x)); U = 1
+// (the top 53 bits of x all ones) gives 0.
+RS_DEV double skip_quotient(uint64_t x, double R, const double* __restrict__ tab) {
+    if ((x >> 11) == (1ull << 53) - 1) return 0.0;
+    return dlog(u_open(x), tab) * R;
+}
+
 RS_DEV uint64_t warp_inclusive_sat(uint64_t x) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -45,7 +54,7 @@ RS_DEV uint64_t warp_inclusive_sat(uint64_t x) {
 // chosen position (0-based) emit(k, pos) is called, k its index in the
 // range.  Returns the number of positions; *err is set if the stream ran out.
 template <typename Emit>
-RS_DEV uint64_t warp_walk(Key2 key, uint32_t tag, uint64_t id, double L, uint64_t start, uint64_t end,
+RS_DEV uint64_t warp_walk(Key2 key, uint32_t tag, uint64_t id, double R, uint64_t start, uint64_t end,
                           const double* __restrict__ tab, bool* err, Emit&& emit) {
     const int lane = threadIdx.x & 31;
     const uint64_t cmax = end - start + 2;
@@ -57,11 +66,7 @@ RS_DEV uint64_t warp_walk(Key2 key, uint32_t tag, uint64_t id, double L, uint64_
         const bool exhausted = jl >= kMaxDraws;
         bool stop = true;
         uint64_t step = 0;
-        if (!exhausted) {
-            const double U = u_open(stream_value(key, tag, id, jl));
-            const double q = dlog(U, tab) / L;
-            step = step_of(q, cmax, &stop);
-        }
+        if (!exhausted) step = step_of(skip_quotient(stream_value(key, tag, id, jl), R, tab), cmax, &stop);
         const uint64_t incl = warp_inclusive_sat(step);
         const bool ok = !stop && incl <= end - base;   // position base - 1 + incl < end
         const uint32_t bad = __ballot_sync(0xFFFFFFFFu, !ok);
@@ -90,14 +95,14 @@ struct BernArgs {
 };
 
 __global__ void bern_count_kernel(BernArgs A) {
-    const double L = dlog1p(-A.p, A.tab);
+    const double R = 1.0 / dlog1p(-A.p, A.tab);
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
     for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < A.nchunks; w += warps) {
         const uint64_t i = A.first + w;
         const uint64_t start = i << A.chunk_log2;
         const uint64_t end = min(start + A.C, A.N);
         bool err;
-        const uint64_t c = warp_walk(A.key, TAG_BERN, i, L, start, end, A.tab, &err, [](uint64_t, uint64_t) {});
+        const uint64_t c = warp_walk(A.key, TAG_BERN, i, R, start, end, A.tab, &err, [](uint64_t, uint64_t) {});
         if ((threadIdx.x & 31) == 0) {
             A.counts[w] = c;
             if (err) set_status(A.status, RS_EITER);
@@ -106,7 +111,7 @@ __global__ void bern_count_kernel(BernArgs A) {
 }
 
 __global__ void bern_write_kernel(BernArgs A) {
-    const double L = dlog1p(-A.p, A.tab);
+    const double R = 1.0 / dlog1p(-A.p, A.tab);
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
     for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < A.nchunks; w += warps) {
         const uint64_t i = A.first + w;
@@ -117,7 +122,7 @@ __global__ void bern_write_kernel(BernArgs A) {
         uint64_t* out = A.out;
         const uint64_t cap = A.cap;
         bool err;
-        warp_walk(A.key, TAG_BERN, i, L, start, end, A.tab, &err, [=](uint64_t k, uint64_t pos) {
+        warp_walk(A.key, TAG_BERN, i, R, start, end, A.tab, &err, [=](uint64_t k, uint64_t pos) {
             if (off + k < cap) out[off + k] = pos + 1;
         });
     }
@@ -285,7 +290,7 @@ RS_DEV uint64_t block_inclusive_sat(uint64_t x, LeafBShared& sm) {
 
 // Geometric-skip walk of [0, s) by the whole block; positions go to sm.pos
 // (up to the capacity).  Returns the count; sets sm.err on a run-out stream.
-RS_DEV uint64_t block_walk(Key2 key, uint32_t tag, uint64_t id, double L, uint64_t s, LeafBShared& sm,
+RS_DEV uint64_t block_walk(Key2 key, uint32_t tag, uint64_t id, double R, uint64_t s, LeafBShared& sm,
                            const double* __restrict__ tab) {
     const uint64_t cmax = s + 2;
     uint64_t base = 0, count = 0;
@@ -294,11 +299,7 @@ RS_DEV uint64_t block_walk(Key2 key, uint32_t tag, uint64_t id, double L, uint64
         const bool exhausted = jt >= kMaxDraws;
         bool stop = true;
         uint64_t step = 0;
-        if (!exhausted) {
-            const double U = u_open(stream_value(key, tag, id, jt));
-            const double q = dlog(U, tab) / L;
-            step = step_of(q, cmax, &stop);
-        }
+        if (!exhausted) step = step_of(skip_quotient(stream_value(key, tag, id, jt), R, tab), cmax, &stop);
         if (threadIdx.x == 0) sm.first_bad = kLeafThreads;
         const uint64_t incl = block_inclusive_sat(step, sm);
         const bool ok = !stop && incl <= s - base;
@@ -343,9 +344,9 @@ RS_DEV void leaf_b_one(LeafBShared& sm, const NodeRec& r, uint64_t id, Key2 key,
         for (uint64_t i = threadIdx.x; i < fill; i += kLeafThreads) sm.pos[i] = i;
         __syncthreads();
     } else {
-        const double L = dlog1p(-rho, tab);
+        const double R = 1.0 / dlog1p(-rho, tab);
         for (attempt = 0; attempt < 64; ++attempt) {
-            c = block_walk(key, TAG_LEAF_B + 256u * (uint32_t)attempt, id, L, r.S, sm, tab);
+            c = block_walk(key, TAG_LEAF_B + 256u * (uint32_t)attempt, id, R, r.S, sm, tab);
             if (sm.err) break;
             if (c >= r.c) break;
         }

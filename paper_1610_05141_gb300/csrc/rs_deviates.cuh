@@ -60,7 +60,7 @@ RS_DEV int hypergeometric(Key2 key, uint64_t node, uint64_t n, uint64_t K, uint6
             const uint4 blk = philox_block((uint32_t)i, TAG_SPLIT, node, key);
             const double U = u_open(((uint64_t)blk.y << 32) | blk.x);
             const double V = v_closed(((uint64_t)blk.w << 32) | blk.z);
-            const double X = alpha + h * (V - 0.5) / U;
+            const double X = alpha + h * (V - 0.5) * drecip(U);
             if (X < 0.0 || X >= top) continue;
             const uint64_t k = (uint64_t)X;
             const double T = dsd(M, k, tab) + dsd(a - M, a - k, tab) + dsd(b - M, b - k, tab) +
@@ -107,7 +107,7 @@ RS_DEV int binomial(Key2 key, uint64_t node, uint64_t c, uint64_t K, uint64_t S,
         const uint4 blk = philox_block((uint32_t)i, TAG_SPLIT, node, key);
         const double U = u_open(((uint64_t)blk.y << 32) | blk.x);
         const double V = v_closed(((uint64_t)blk.w << 32) | blk.z);
-        const double X = alpha + h * (V - 0.5) / U;
+        const double X = alpha + h * (V - 0.5) * drecip(U);
         if (X < 0.0 || X >= top) continue;
         const uint64_t k = (uint64_t)X;
         const double T = dsd(M, k, tab) + dsd(c - M, c - k, tab) + (double)((int64_t)k - (int64_t)M) * logr;

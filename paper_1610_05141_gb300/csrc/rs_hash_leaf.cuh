@@ -623,6 +623,9 @@ RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, co
     // output stay nearly coalesced.  The first run counts only the smaller
     // keys: equal keys then share a rank, which shows as a sum of ranks below
     // k (k - 1) / 2, and a second run breaks the ties.
+    // With replacement, a leaf of size s likely has equal keys once k^2 is
+    // about s (P(none) ~ exp(-k^2 / 2s)): it takes the tie-broken run at once.
+    if (WR && (uint64_t)k * k >= r.s / 2) return bucket_ties<KeyT, NT, BAR, WR, CAP>(sm, r, key, k, thr, mult, dst, tid);
     const uint32_t rsum =
         __reduce_add_sync(0xFFFFFFFFu, rank_keys<KeyT, NT, false, WR>(B, A, ch, k, mult, r.lo + 1, dst, tid));
     if ((tid & 31) == 0) atomicAdd(&sm.ranksum, rsum);

@@ -126,6 +126,37 @@ RS_DEV double dlog1p(double z, const double* __restrict__ tab) {
     return dlog(u, tab) * (z / (u - 1.0));
 }
 
+// 1/x for a positive x in [2^-60, 2^100]: the single-precision quotient of
+// x rounded to single precision as the seed (relative error below 2^-23),
+// then two Newton steps r <- r + r (1 - x r) with fused multiply-adds;
+// within about one ulp of 1/x.  Used where a correctly rounded quotient is
+// not needed (Stirling's tail, the argument of ln(1 + z), the ratio-of-
+// uniforms abscissa): an FP64 division costs several times as many FP64
+// instructions.
+RS_DEV double drecip(double x) {
+    double r = (double)__fdiv_rn(1.0f, __double2float_rn(x));
+    double e = __fma_rn(-x, r, 1.0);
+    r = __fma_rn(r, e, r);
+    e = __fma_rn(-x, r, 1.0);
+    return __fma_rn(r, e, r);
+}
+
+// ln(1 + z) for z >= 0 without a division: u = 1 + z rounded, e = (1 + z) - u
+// exactly (Knuth's two-sum), ln(1 + z) = ln u + e/u to 2^-106 relative
+// (|e/u| <= 2^-53), e/u taken as e times a single-precision 1/u.  The
+// logarithm of u is passed in (lnu = dlog(u)) so that callers may evaluate
+// it elsewhere.
+RS_DEV double log1p_pos_u(double z) { return 1.0 + z; }
+RS_DEV double log1p_pos_finish(double z, double lnu) {
+    const double u = 1.0 + z;
+    const double bb = u - 1.0;
+    const double e = (1.0 - (u - bb)) + (z - bb);
+    return lnu + e * (double)__fdiv_rn(1.0f, __double2float_rn(u));
+}
+RS_DEV double dlog1p_pos(double z, const double* __restrict__ tab) {
+    return log1p_pos_finish(z, dlog(log1p_pos_u(z), tab));
+}
+
 // e^x for x in [-708, 0]: x = k ln2 + r with |r| <= ln2/2, e^r from its
 // Taylor polynomial of degree 13, times 2^k assembled from the exponent bits.
 RS_DEV double dexp(double x) {
@@ -149,9 +180,9 @@ RS_DEV double dexp(double x) {
     return p * bits_to_double((uint64_t)(k + 1023) << 52);
 }
 
-// Tail of Stirling's series for ln x!: 1/(12x) - 1/(360x^3) + 1/(1260x^5) - 1/(1680x^7).
-RS_DEV double stirling_tail(double x) {
-    const double r = 1.0 / x;
+// Tail of Stirling's series for ln x!: 1/(12x) - 1/(360x^3) + 1/(1260x^5) -
+// 1/(1680x^7), from r = 1/x (drecip).
+RS_DEV double stirling_tail(double r) {
     const double r2 = r * r;
     return r * (1.0 / 12.0 + r2 * (-1.0 / 360.0 + r2 * (1.0 / 1260.0 + r2 * (-1.0 / 1680.0))));
 }
@@ -160,12 +191,12 @@ RS_DEV double stirling_tail(double x) {
 RS_DEV double dlf(uint64_t x, const double* __restrict__ tab) {
     if (x < 256) return tab[x];
     const double X = (double)x;
-    return (X + 0.5) * dlog(X, tab) - X + RS_HL2PI + stirling_tail(X);
+    return (X + 0.5) * dlog(X, tab) - X + RS_HL2PI + stirling_tail(drecip(X));
 }
 
 // ln x! - ln y! for x >= y without cancellation of the two large terms:
 // (x+1/2) ln(x/y) + (x-y) ln y - (x-y) + tail(x) - tail(y), with
-// ln(x/y) = ln1p((x-y)/y).  Short differences are summed directly.
+// ln(x/y) = ln(1 + (x-y)/y).  Short differences are summed directly.
 RS_DEV double dlfdiff(uint64_t x, uint64_t y, const double* __restrict__ tab) {
     const uint64_t d = x - y;
     if (d == 0) return 0.0;
@@ -177,7 +208,9 @@ RS_DEV double dlfdiff(uint64_t x, uint64_t y, const double* __restrict__ tab) {
     }
     if (y < 256) return dlf(x, tab) - tab[y];
     const double X = (double)x, Y = (double)y, D = (double)d;
-    return (X + 0.5) * dlog1p(D / Y, tab) + D * dlog(Y, tab) - D + (stirling_tail(X) - stirling_tail(Y));
+    const double rY = drecip(Y);
+    const double lp = dlog1p_pos(D * rY, tab);
+    return (X + 0.5) * lp + D * dlog(Y, tab) - D + (stirling_tail(drecip(X)) - stirling_tail(rY));
 }
 
 // Signed ln x! - ln y!.

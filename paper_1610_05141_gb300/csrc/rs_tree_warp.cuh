@@ -8,7 +8,7 @@
 //  - lane refill: a warp owns a batch of nodes; a lane whose node is done
 //    takes the next one, so trial counts no longer idle lanes;
 //  - cooperative logarithms: each ratio-of-uniforms trial first records the
-//    arguments of every logarithm it needs (ln U, ln Y, ln(1 + D/Y), the
+//    arguments of every logarithm it needs (ln U, ln Y, ln of 1 + D/Y, the
 //    terms of short sums, ...), the whole warp evaluates them together, and
 //    each lane then assembles its acceptance test from the results in
 //    exactly the operations and order of the scalar definition
@@ -58,8 +58,7 @@ RS_DEV void lfd_args(uint64_t x, uint64_t y, LfdArgs& A) {
         return;
     }
     const double Y = (double)y, D = (double)d;
-    const double u = 1.0 + D / Y;
-    if (u != 1.0) A.push(u);
+    A.push(log1p_pos_u(D * drecip(Y)));
     A.push(Y);
 }
 
@@ -73,12 +72,11 @@ RS_DEV double lfd_eval(uint64_t x, uint64_t y, const double* __restrict__ tab, L
         return acc;
     }
     const double X = (double)x;
-    if (y < 256) return ((X + 0.5) * L.next() - X + RS_HL2PI + stirling_tail(X)) - tab[y];
+    if (y < 256) return ((X + 0.5) * L.next() - X + RS_HL2PI + stirling_tail(drecip(X))) - tab[y];
     const double Y = (double)y, D = (double)d;
-    const double z = D / Y;
-    const double u = 1.0 + z;
-    const double lp = (u == 1.0) ? z : L.next() * (z / (u - 1.0));
-    return (X + 0.5) * lp + D * L.next() - D + (stirling_tail(X) - stirling_tail(Y));
+    const double rY = drecip(Y);
+    const double lp = log1p_pos_finish(D * rY, L.next());
+    return (X + 0.5) * lp + D * L.next() - D + (stirling_tail(drecip(X)) - stirling_tail(rY));
 }
 
 // Signed difference (dsd): the larger argument first, one call, then the
@@ -218,7 +216,7 @@ RS_DEV void tree_batch_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
             const uint4 blk = philox_block((uint32_t)t, TAG_SPLIT, q.v, key);
             U = u_open(((uint64_t)blk.y << 32) | blk.x);
             const double V = v_closed(((uint64_t)blk.w << 32) | blk.z);
-            const double X = q.alpha + q.h * (V - 0.5) / U;
+            const double X = q.alpha + q.h * (V - 0.5) * drecip(U);
             inr = !(X < 0.0 || X >= q.top) && t < kRouMaxTrials;
             if (inr) {
                 k = (uint64_t)X;
@@ -347,7 +345,7 @@ RS_DEV void tree_terms_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
             const uint4 blk = philox_block((uint32_t)t, TAG_SPLIT, q.v, key);
             U = u_open(((uint64_t)blk.y << 32) | blk.x);
             const double V = v_closed(((uint64_t)blk.w << 32) | blk.z);
-            const double X = q.alpha + q.h * (V - 0.5) / U;
+            const double X = q.alpha + q.h * (V - 0.5) * drecip(U);
             inr = !(X < 0.0 || X >= q.top) && t < kRouMaxTrials;
             if (inr) k = (uint64_t)X;
             // this lane's difference ln x! - ln y!, picked with selects so

@@ -115,6 +115,40 @@ def test_log1p_accuracy(oracle):
     assert worst <= 3, worst
 
 
+def test_recip_accuracy(oracle):
+    """1/x from a single-precision seed and two Newton steps: within 1 ulp
+    of the exact reciprocal over the range it serves (uniforms down to 2^-53,
+    integers up to 2^64)."""
+    rng = np.random.default_rng(6)
+    xs = [1.0, 2.0, 3.0, 0.1, 2.0**-53, 2.0**64, 1 + 2**-52, 2 - 2**-52, 12345.0, 2.0**32 - 1]
+    xs += list(np.exp(rng.uniform(math.log(2.0**-53), math.log(2.0**64), 3000)))
+    xs += [float(v) for v in rng.integers(1, 2**62, 1000)]
+    worst = 0
+    for x in xs:
+        got = oracle.recip(x)
+        worst = max(worst, _ulp_err(got, 1 / mpmath.mpf(x)))
+    assert worst <= 1, worst
+    # the seed alone is far from that: the Newton steps are doing the work
+    assert any(float(np.float32(1) / np.float32(x)) != oracle.recip(x) for x in xs[10:50])
+
+
+def test_log1p_pos_accuracy(oracle):
+    """ln(1 + z), z >= 0, by the table logarithm of the rounded 1 + z plus
+    the exact rounding error over 1 + z: within 2 ulp from z = 2^-70 (where
+    1 + z rounds to 1) to z = 2^40."""
+    rng = np.random.default_rng(7)
+    zs = [0.0, 2.0**-70, 2.0**-53, 2.0**-52, 1e-10, 2.0**-7, 0.5, 1.0, 3.0, 2.0**40]
+    zs += list(np.exp(rng.uniform(math.log(2.0**-70), math.log(2.0**40), 4000)))
+    worst = 0
+    for z in zs:
+        got = oracle.log1p_pos(z)
+        if z == 0.0:
+            assert got == 0.0
+            continue
+        worst = max(worst, _ulp_err(got, mpmath.log1p(mpmath.mpf(z))))
+    assert worst <= 2, worst
+
+
 def test_exp_accuracy(oracle):
     """or_exp within 2 ulp on its domain [-708, 0]."""
     rng = np.random.default_rng(3)
