@@ -120,7 +120,8 @@ int rs_split_tree(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n
 
 /* Bernoulli(p) sample of the positions 0..N-1 by independent chunks with
  * geometric skips (Sec. 4.7, Sec. 2 Algorithm B), restricted to the window
- * [a, b) of 0-based positions.  Chunks have 2^c positions, c the least value
+ * [a, b) of 0-based positions.  Scratch: the chunk counts, and the staging
+ * area of rs_set_bernoulli_staging.  Chunks have 2^c positions, c the least value
  * with 2^c p >= n0 (at most 62); a and b must be multiples of 2^c (b may also
  * equal N).  Writes the 1-based positions in increasing order to
  * out_dev[0..min(count, cap)) and the number in the window to *count_out
@@ -335,6 +336,16 @@ int rs_phase_totals(rs_ctx* ctx, double* tree_ms, double* leaf_ms, uint64_t* cal
  * slow down more than the overlap gains).
  * Errors: RS_EINVAL (log2_parts outside 0..6, negative blocks). */
 int rs_set_pipeline(rs_ctx* ctx, int log2_parts, int leaf_blocks_per_sm);
+
+/* Largest staging area (bytes) rs_bernoulli may keep, and its slots per
+ * chunk (0: mu + 8 sqrt(mu) + 64 for a chunk's expected count mu).  With
+ * staging each chunk is walked once and its positions staged (about 1.1
+ * times the output), then copied into place after the scan of the counts; a
+ * chunk with more positions than slots is walked again for the copy.
+ * Without (limit 0, an area above the limit, or an allocation that fails)
+ * each chunk is walked twice, once to count and once to write.  The output
+ * does not change.  Defaults: 16 GiB, 0.  Errors: RS_EINVAL. */
+int rs_set_bernoulli_staging(rs_ctx* ctx, uint64_t max_bytes, uint64_t slots_per_chunk);
 
 /* Number of kernels this context has launched since it was created. */
 int rs_launch_count(rs_ctx* ctx, uint64_t* count);

@@ -84,6 +84,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "rs_phase_totals": (i32, [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(u64)]),
         "rs_launch_count": (i32, [vp, ctypes.POINTER(u64)]),
         "rs_set_pipeline": (i32, [vp, i32, i32]),
+        "rs_set_bernoulli_staging": (i32, [vp, u64, u64]),
         "rs_sample_to_host": (i32, [vp, i32, u64, u64, u64, u32, vp, vp, vp]),
         "rs_sample_static": (i32, [u64, u64, u64, u32, vp, vp]),
         "rs_batch_plan": (i32, [vp, vp, u32, ctypes.POINTER(vp)]),
@@ -231,6 +232,11 @@ def rs_phase_totals(ctx: Context):
     t, l, c = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_uint64(0)
     _check(load().rs_phase_totals(ctx.handle, ctypes.byref(t), ctypes.byref(l), ctypes.byref(c)), "rs_phase_totals")
     return t.value, l.value, c.value
+
+
+def rs_set_bernoulli_staging(ctx: Context, max_bytes: int = 16 << 30, slots_per_chunk: int = 0) -> int:
+    return _check(load().rs_set_bernoulli_staging(ctx.handle, max_bytes, slots_per_chunk),
+                  "rs_set_bernoulli_staging")
 
 
 def rs_set_pipeline(ctx: Context, log2_parts: int, leaf_blocks_per_sm: int = 3) -> int:

@@ -82,6 +82,8 @@ RS_DEV uint64_t warp_walk(Key2 key, uint32_t tag, uint64_t id, double R, uint64_
 }
 
 struct BernArgs {
+    uint64_t* stage;
+    uint64_t stage_per;
     Key2 key;
     double p;
     uint64_t N, C;
@@ -126,6 +128,60 @@ __global__ void bern_write_kernel(BernArgs A) {
             if (off + k < cap) out[off + k] = pos + 1;
         });
     }
+}
+
+// One walk per chunk: positions to the chunk's staging slots (the first
+// stage_per of them), the count to counts[w].
+__global__ void bern_stage_kernel(BernArgs A) {
+    const double R = 1.0 / dlog1p(-A.p, A.tab);
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < A.nchunks; w += warps) {
+        const uint64_t i = A.first + w;
+        const uint64_t start = i << A.chunk_log2;
+        const uint64_t end = min(start + A.C, A.N);
+        uint64_t* slot = A.stage + w * A.stage_per;
+        const uint64_t per = A.stage_per;
+        bool err;
+        const uint64_t c = warp_walk(A.key, TAG_BERN, i, R, start, end, A.tab, &err, [=](uint64_t k, uint64_t pos) {
+            if (k < per) slot[k] = pos + 1;
+        });
+        if ((threadIdx.x & 31) == 0) {
+            A.counts[w] = c;
+            if (err) set_status(A.status, RS_EITER);
+        }
+    }
+}
+
+// A block per chunk: the staged positions go to their place in the output;
+// a chunk with more positions than its slots walks again with warp 0.
+__global__ void bern_copy_kernel(BernArgs A) {
+    const uint64_t w = blockIdx.x;
+    const uint64_t off = A.counts[w];
+    const uint64_t c = A.counts[w + 1] - off;
+    if (off >= A.cap) return;
+    const uint64_t n = min(c, A.cap - off);
+    if (c <= A.stage_per) {
+        const uint64_t* slot = A.stage + w * A.stage_per;
+        for (uint64_t k = threadIdx.x; k < n; k += blockDim.x) A.out[off + k] = slot[k];
+        return;
+    }
+    if (threadIdx.x >= 32) return;
+    const double R = 1.0 / dlog1p(-A.p, A.tab);
+    const uint64_t i = A.first + w;
+    const uint64_t start = i << A.chunk_log2;
+    const uint64_t end = min(start + A.C, A.N);
+    uint64_t* out = A.out;
+    const uint64_t cap = A.cap;
+    bool err;
+    warp_walk(A.key, TAG_BERN, i, R, start, end, A.tab, &err, [=](uint64_t k, uint64_t pos) {
+        if (off + k < cap) out[off + k] = pos + 1;
+    });
+}
+
+uint64_t bern_stage_per(double mu) {
+    const double v = ceil(mu + 8.0 * sqrt(mu) + 64.0);
+    const uint64_t s = v >= 9.0e18 ? (uint64_t)9e18 : (uint64_t)v;
+    return (s + 3) & ~3ull;
 }
 
 __global__ void fill_range_kernel(uint64_t* out, uint64_t a, uint64_t n) {
@@ -239,9 +295,29 @@ cudaError_t launch_bernoulli(const BernLaunch& L, cudaStream_t st) {
     A.cap = L.cap;
     A.status = L.status;
     A.tab = L.tab;
+    A.stage = L.stage;
+    A.stage_per = L.stage_per;
     const int threads = 256;
     const unsigned blocks = (unsigned)std::min<uint64_t>((L.nchunks * 32 + threads - 1) / threads,
                                                          (uint64_t)L.sms * 16);
+    if (L.stage) {
+        bern_stage_kernel<<<blocks, threads, 0, st>>>(A);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        e = scan_u64(L.counts, L.nchunks, L.scan_scratch, st);
+        if (e != cudaSuccess) return e;
+        for (uint64_t w0 = 0; w0 < L.nchunks; w0 += 65535u * 1024u) {   // grid x limit, in slices
+            BernArgs S = A;
+            const uint64_t m = std::min<uint64_t>(L.nchunks - w0, 65535u * 1024u);
+            S.counts = A.counts + w0;
+            S.first = A.first + w0;
+            S.stage = A.stage + w0 * A.stage_per;
+            bern_copy_kernel<<<(unsigned)m, 256, 0, st>>>(S);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+        return cudaMemcpyAsync(L.total, L.counts + L.nchunks, sizeof(uint64_t), cudaMemcpyDeviceToDevice, st);
+    }
     bern_count_kernel<<<blocks, threads, 0, st>>>(A);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

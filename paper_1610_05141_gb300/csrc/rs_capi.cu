@@ -22,6 +22,10 @@ struct rs_ctx {
     uint64_t big_pool_bytes = 0;
     uint64_t* words = nullptr;      // general scratch (Bernoulli chunk counts, leaf B positions)
     uint64_t words_cap = 0;
+    uint64_t* stage = nullptr;      // Bernoulli: positions staged per chunk by the single walk
+    uint64_t stage_cap = 0;
+    uint64_t stage_max_words = 1ull << 31;   // rs_set_bernoulli_staging
+    uint64_t stage_slots = 0;
     uint32_t leaf_cap = 0;          // testing knob, 0 = default
     // pipelining of deep trees: 2^pipe_log2 subtrees, each built on the tree
     // stream while the caller's stream runs the leaves of the ones before
@@ -371,6 +375,7 @@ int rs_destroy(rs_ctx* ctx) {
     cudaFree(ctx->ovf);
     cudaFree(ctx->big_pool);
     cudaFree(ctx->words);
+    cudaFree(ctx->stage);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : ctx->ev_part) cudaEventDestroy(e);
     if (ctx->ev_copied) cudaEventDestroy(ctx->ev_copied);
@@ -444,8 +449,17 @@ int rs_bernoulli(rs_ctx* ctx, double p, uint64_t N, uint64_t seed, uint32_t n0, 
     const uint64_t nchunks = ((b - 1) >> c) - first + 1;
     int rc = ensure(ctx->words, ctx->words_cap, nchunks + 2 + rs::scan_scratch_words(nchunks));
     if (rc) return rc;
+    // one walk per chunk with its positions staged (about 1.1 times the
+    // output), unless that needs more than the staging limit or cannot be
+    // allocated: then a count walk and a write walk
+    uint64_t* stage = nullptr;
+    const uint64_t per = ctx->stage_slots ? ctx->stage_slots : rs::bern_stage_per(ldexp(1.0, c) * p);
+    if (p < 1.0 && per <= ctx->stage_max_words / nchunks) {
+        if (ensure(ctx->stage, ctx->stage_cap, nchunks * per) == RS_OK) stage = ctx->stage;
+        else (void)cudaGetLastError();
+    }
     rs::BernLaunch L{p, N, seed, c, first, nchunks, a, b, out_dev, cap, ctx->words, ctx->words + nchunks + 1,
-                     ctx->words + nchunks + 2, ctx->status, ctx->sms, ctx->tab};
+                     ctx->words + nchunks + 2, ctx->status, ctx->sms, ctx->tab, stage, per};
     rc = cuda_rc(rs::launch_bernoulli(L, st));
     if (rc) return rc;
     uint64_t total = 0;
@@ -515,6 +529,13 @@ int rs_set_pipeline(rs_ctx* ctx, int log2_parts, int leaf_blocks_per_sm) {
     if (!ctx || log2_parts < 0 || log2_parts > 6 || leaf_blocks_per_sm < 0) return RS_EINVAL;
     ctx->pipe_log2 = log2_parts;
     ctx->pipe_leaf_blocks = leaf_blocks_per_sm;
+    return RS_OK;
+}
+
+int rs_set_bernoulli_staging(rs_ctx* ctx, uint64_t max_bytes, uint64_t slots_per_chunk) {
+    if (!ctx) return RS_EINVAL;
+    ctx->stage_max_words = max_bytes / sizeof(uint64_t);
+    ctx->stage_slots = slots_per_chunk;
     return RS_OK;
 }
 

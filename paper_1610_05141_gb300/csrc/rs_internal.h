@@ -90,10 +90,17 @@ struct BernLaunch {
     int* status;
     int sms;
     const double* tab;       // the context's table (its logarithm)
+    uint64_t* stage;         // nchunks * stage_per words, or null
+    uint64_t stage_per;      // staged positions per chunk
 };
-// Count pass, exclusive scan of the chunk counts, write pass.
+// With staging: one walk per chunk (positions staged, counted), exclusive
+// scan of the counts, copy to the output (a chunk above stage_per positions
+// walks again).  Without: count pass, scan, write pass.
 cudaError_t launch_bernoulli(const BernLaunch& L, cudaStream_t st);
 uint64_t scan_scratch_words(uint64_t n);
+// Staged positions per chunk for an expected count mu: mu + 8 sqrt(mu) + 64,
+// a multiple of 4.
+uint64_t bern_stage_per(double mu);
 
 struct BatchGroupView;
 struct QueryBoundView;

@@ -170,6 +170,24 @@ def test_bernoulli_matches_oracle(rs, ctx, oracle, p, N, seed, n0):
     assert_same(out[:cnt].cpu().numpy().view(np.uint64), want, (p, N))
 
 
+@pytest.mark.parametrize("limit,slots", [(0, 0), (16 << 30, 8), (16 << 30, 4000)])
+def test_bernoulli_two_walks_and_restaged_chunks(rs, ctx, oracle, limit, slots):
+    """Without staging (two walks per chunk), and with too few staging slots
+    for most chunks (those walk again for the copy): the same positions."""
+    try:
+        rs.rs_set_bernoulli_staging(ctx, limit, slots)
+        for p, N, seed, n0 in BERN_CASES[:4]:
+            want = oracle.bernoulli(p, N, seed, n0)
+            cap = len(want) + 16
+            out = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
+            rc, cnt = rs.rs_bernoulli(ctx, p, N, seed, n0, 0, N, out, cap)
+            assert rs.rs_sync(ctx) == rs.RS_OK
+            assert cnt == len(want)
+            assert_same(out[:cnt].cpu().numpy().view(np.uint64), want, (p, N, limit, slots))
+    finally:
+        rs.rs_set_bernoulli_staging(ctx)
+
+
 def test_bernoulli_windows_degenerate_and_capacity(rs, ctx, oracle):
     p, N, seed, n0 = 0.01, 10**7 + 123, 7, 1024
     C = 1 << oracle.bern_chunk_log2(p, n0)
