@@ -357,10 +357,10 @@ double or_lfdiff(uint64_t x, uint64_t y)
     uint64_t d = x - y;
     if (d == 0) return 0.0;
     if (x < 256) return lf_table[x] - lf_table[y];
-    if (d <= 8) {
-        double acc = 0.0;
-        for (uint64_t i = y + 1; i <= x; ++i) acc = acc + or_log((double)i);
-        return acc;
+    if (d <= 8) {   /* ln of the product y+1 .. x (below 2^512: no overflow) */
+        double prod = (double)(y + 1);
+        for (uint64_t i = y + 2; i <= x; ++i) prod = prod * (double)i;
+        return or_log(prod);
     }
     if (y < 256) return or_lf(x) - lf_table[y];
     double X = (double)x, Y = (double)y, Dd = (double)d;
@@ -398,7 +398,8 @@ int or_hg(uint64_t seed, uint64_t id, uint64_t n, uint64_t K, uint64_t S, uint64
     if (sN) n = S - n;
     uint64_t a = n < K ? n : K;
     uint64_t b = n < K ? K : n;
-    double mu = ((double)a * (double)b) / (double)S;
+    double rS = or_recip((double)S);
+    double mu = ((double)a * (double)b) * rS;
     uint64_t Y = 0;
     int found = 0;
     if (mu < 16.0) {
@@ -417,7 +418,7 @@ int or_hg(uint64_t seed, uint64_t id, uint64_t n, uint64_t K, uint64_t S, uint64
             }
         }
     } else {
-        double var = mu * ((double)(S - a) / (double)S) * ((double)(S - b) / (double)(S - 1));
+        double var = mu * ((double)(S - a) * rS) * ((double)(S - b) * or_recip((double)(S - 1)));
         double c = sqrt(var + 0.5);
         double h = HAT_D1 * c + HAT_D2;
         double alpha = mu + 0.5;

@@ -31,7 +31,8 @@ RS_DEV int hypergeometric(Key2 key, uint64_t node, uint64_t n, uint64_t K, uint6
     if (flipN) n = S - n;
     const uint64_t a = n < K ? n : K;
     const uint64_t b = n < K ? K : n;
-    const double mu = ((double)a * (double)b) / (double)S;
+    const double rS = drecip((double)S);
+    const double mu = ((double)a * (double)b) * rS;
     uint64_t y = 0;
     bool done = false;
     if (mu < 16.0) {
@@ -51,7 +52,7 @@ RS_DEV int hypergeometric(Key2 key, uint64_t node, uint64_t n, uint64_t K, uint6
             }
         }
     } else {
-        const double var = mu * ((double)(S - a) / (double)S) * ((double)(S - b) / (double)(S - 1));
+        const double var = mu * ((double)(S - a) * rS) * ((double)(S - b) * drecip((double)(S - 1)));
         const double h = RS_HAT_D1 * sqrt(var + 0.5) + RS_HAT_D2;
         const double alpha = mu + 0.5;
         const uint64_t M = (uint64_t)(((unsigned __int128)(a + 1) * (b + 1)) / (S + 2));

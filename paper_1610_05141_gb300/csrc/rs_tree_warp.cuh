@@ -29,27 +29,31 @@
 
 namespace rs {
 
-constexpr int kLogSlots = 40;   // logarithm arguments per lane per trial (at most 4 * 8 + 1)
+constexpr int kLogSlots = 16;   // per lane per trial: up to 9 logarithm arguments, then 4 saved reciprocals
 
 // Log-factorial difference lfdiff(x, y), x >= y, split in two halves: args()
 // lists the logarithm arguments it needs, eval() computes the value from
 // their logarithms, consumed in the same order.
+// Logarithm arguments fill a lane's slots from the front; reciprocals that
+// the evaluation needs again are saved from the back.
 struct LfdArgs {
     double* a;
-    int n;
+    int n, ns;
     RS_DEV void push(double v) { a[n++] = v; }
+    RS_DEV void save(double v) { a[kLogSlots - 1 - ns++] = v; }
 };
 struct LfdLogs {
     const double* l;
-    int n;
+    int n, ns;
     RS_DEV double next() { return l[n++]; }
+    RS_DEV double saved() { return l[kLogSlots - 1 - ns++]; }
 };
 
 RS_DEV void lfd_args(uint64_t x, uint64_t y, LfdArgs& A) {
     const uint64_t d = x - y;
     if (d == 0 || x < 256) return;
     if (d <= 8) {
-        for (uint64_t i = y + 1; i <= x; ++i) A.push((double)i);
+        A.push(short_product(x, y));
         return;
     }
     const double X = (double)x;
@@ -58,23 +62,21 @@ RS_DEV void lfd_args(uint64_t x, uint64_t y, LfdArgs& A) {
         return;
     }
     const double Y = (double)y, D = (double)d;
-    A.push(log1p_pos_u(D * drecip(Y)));
+    const double rY = drecip(Y);
+    A.push(log1p_pos_u(D * rY));
     A.push(Y);
+    A.save(rY);
 }
 
 RS_DEV double lfd_eval(uint64_t x, uint64_t y, const double* __restrict__ tab, LfdLogs& L) {
     const uint64_t d = x - y;
     if (d == 0) return 0.0;
     if (x < 256) return tab[x] - tab[y];
-    if (d <= 8) {
-        double acc = 0.0;
-        for (uint64_t i = y + 1; i <= x; ++i) acc = acc + L.next();
-        return acc;
-    }
+    if (d <= 8) return L.next();
     const double X = (double)x;
     if (y < 256) return ((X + 0.5) * L.next() - X + RS_HL2PI + stirling_tail(drecip(X))) - tab[y];
     const double Y = (double)y, D = (double)d;
-    const double rY = drecip(Y);
+    const double rY = L.saved();
     const double lp = log1p_pos_finish(D * rY, L.next());
     return (X + 0.5) * lp + D * L.next() - D + (stirling_tail(drecip(X)) - stirling_tail(rY));
 }
@@ -154,14 +156,15 @@ RS_DEV bool node_setup(NodeRec* __restrict__ rec, uint64_t v, Key2 key, const do
         if (q->flipN) n = S - n;
         const uint64_t a = n < Kh ? n : Kh;
         const uint64_t b = n < Kh ? Kh : n;
-        const double mu = ((double)a * (double)b) / (double)S;
+        const double rS = drecip((double)S);
+        const double mu = ((double)a * (double)b) * rS;
         if (mu < 16.0) {
             uint64_t L = 0;
             const int rc = hypergeometric(key, v, r.c, K, S, tab, L);
             if (rc != RS_OK) { set_status(status, rc); L = 0; }
             return finish(L);
         }
-        const double var = mu * ((double)(S - a) / (double)S) * ((double)(S - b) / (double)(S - 1));
+        const double var = mu * ((double)(S - a) * rS) * ((double)(S - b) * drecip((double)(S - 1)));
         q->h = RS_HAT_D1 * sqrt(var + 0.5) + RS_HAT_D2;
         q->alpha = mu + 0.5;
         q->M = (uint64_t)(((unsigned __int128)(a + 1) * (b + 1)) / (S + 2));
@@ -220,7 +223,7 @@ RS_DEV void tree_batch_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
             inr = !(X < 0.0 || X >= q.top) && t < kRouMaxTrials;
             if (inr) {
                 k = (uint64_t)X;
-                LfdArgs A{mine, 0};
+                LfdArgs A{mine, 0, 0};
                 A.push(U);
                 if (WR) {
                     sd_args(q.M, k, A);
@@ -274,7 +277,7 @@ RS_DEV void tree_batch_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
         bool acc = false;
         uint64_t L = 0;
         if (active && inr) {
-            LfdLogs Lg{mine, 0};
+            LfdLogs Lg{mine, 0, 0};
             const double lU = Lg.next();
             double T;
             if (WR) {
