@@ -78,6 +78,7 @@ def _load():
             "or_lf": (dbl, [u64]),
             "or_lfdiff": (dbl, [u64, u64]),
             "or_sd": (dbl, [u64, u64]),
+            "or_sd_fixed": (dbl, [u64, u64, dbl]),
             "or_hg": (i32, [u64, u64, u64, u64, u64, p64]),
             "or_bin": (i32, [u64, u64, u64, u64, u64, p64]),
             "or_depth": (i32, [u64, u64, u32]),
@@ -182,6 +183,10 @@ def lfdiff(x, y):
 
 def sd(x, y):
     return float(_load().or_sd(x, y))
+
+
+def sd_fixed(P, Q, lnP):
+    return float(_load().or_sd_fixed(P, Q, lnP))
 
 
 # --- deviates --------------------------------------------------------------

@@ -375,6 +375,46 @@ double or_sd(uint64_t x, uint64_t y)
     return x >= y ? or_lfdiff(x, y) : -or_lfdiff(y, x);
 }
 
+/* ln P! - ln Q! for the ratio-of-uniforms tests, where P is fixed for the
+ * node and lnP = or_log(P) (P >= 1; unused for P = 0) was computed once: the
+ * same branches as or_lfdiff on (max, min), except that ln of the larger
+ * argument is lnP when that is P, and ln of the smaller one in the
+ * cancellation-free form is lnP when that is P, else ln P - ln(P/Q). */
+double or_sd_fixed(uint64_t P, uint64_t Q, double lnP)
+{
+    lf_init();
+    int p_big = P >= Q;
+    uint64_t x = p_big ? P : Q, y = p_big ? Q : P, d = x - y;
+    double v;
+    if (d == 0) return 0.0;
+    if (x < 256) {
+        v = lf_table[x] - lf_table[y];
+    } else if (d <= 8) {
+        double prod = (double)(y + 1);
+        for (uint64_t i = y + 2; i <= x; ++i) prod = prod * (double)i;
+        v = or_log(prod);
+    } else {
+        double X = (double)x;
+        if (y < 256) {
+            double lx = p_big ? lnP : or_log(X);
+            v = ((X + 0.5) * lx - X + HL2PI + stirling_tail(or_recip(X))) - lf_table[y];
+        } else {
+            double Y = (double)y, Dd = (double)d;
+            double rY = or_recip(Y);
+            double lp = or_log1p_pos(Dd * rY);
+            double ly = p_big ? lnP - lp : lnP;
+            v = (X + 0.5) * lp + Dd * ly - Dd + (stirling_tail(or_recip(X)) - stirling_tail(rY));
+        }
+    }
+    return p_big ? v : -v;
+}
+
+/* ln P for or_sd_fixed. */
+static double log_fixed(uint64_t P)
+{
+    return or_log((double)(P > 0 ? P : 1));
+}
+
 /* ------------------------------------------------------------------------ */
 /* Random deviates for the splitting step.                                  */
 /* ------------------------------------------------------------------------ */
@@ -423,14 +463,17 @@ int or_hg(uint64_t seed, uint64_t id, uint64_t n, uint64_t K, uint64_t S, uint64
         double h = HAT_D1 * c + HAT_D2;
         double alpha = mu + 0.5;
         uint64_t M = (uint64_t)(((u128)(a + 1) * (u128)(b + 1)) / (u128)(S + 2));
+        uint64_t m = S - a - b;
+        /* the test's four differences have the fixed ends M, a-M, b-M, m+M */
+        double l0 = log_fixed(M), l1 = log_fixed(a - M), l2 = log_fixed(b - M), l3 = log_fixed(m + M);
         for (uint64_t i = 0; i < (1ull << 20); ++i) {
             double U = or_u_open(or_value(seed, TAG_SPLIT, id, 2 * i));
             double V = or_v_closed(or_value(seed, TAG_SPLIT, id, 2 * i + 1));
             double X = alpha + h * (V - 0.5) * or_recip(U);
             if (X < 0.0 || X >= (double)a + 1.0) continue;
             uint64_t k = (uint64_t)X;
-            double T = or_sd(M, k) + or_sd(a - M, a - k) + or_sd(b - M, b - k)
-                     + or_sd(S - a - b + M, S - a - b + k);
+            double T = or_sd_fixed(M, k, l0) + or_sd_fixed(a - M, a - k, l1) + or_sd_fixed(b - M, b - k, l2)
+                     + or_sd_fixed(m + M, m + k, l3);
             if (2.0 * or_log(U) <= T) { Y = k; found = 1; break; }
         }
     }
@@ -473,13 +516,14 @@ int or_bin(uint64_t seed, uint64_t id, uint64_t c, uint64_t K, uint64_t S, uint6
     double r = p / (1.0 - p);
     double logr = (r == 1.0) ? 0.0 : or_log(r);
     uint64_t M = (uint64_t)(((u128)(c + 1) * (u128)K) / (u128)S);
+    double l0 = log_fixed(M), l1 = log_fixed(c - M);
     for (uint64_t i = 0; i < (1ull << 20); ++i) {
         double U = or_u_open(or_value(seed, TAG_SPLIT, id, 2 * i));
         double V = or_v_closed(or_value(seed, TAG_SPLIT, id, 2 * i + 1));
         double X = alpha + h * (V - 0.5) * or_recip(U);
         if (X < 0.0 || X >= (double)c + 1.0) continue;
         uint64_t k = (uint64_t)X;
-        double T = or_sd(M, k) + or_sd(c - M, c - k) + (double)((int64_t)k - (int64_t)M) * logr;
+        double T = or_sd_fixed(M, k, l0) + or_sd_fixed(c - M, c - k, l1) + (double)((int64_t)k - (int64_t)M) * logr;
         if (2.0 * or_log(U) <= T) { *out = k; return OR_OK; }
     }
     return OR_EITER;

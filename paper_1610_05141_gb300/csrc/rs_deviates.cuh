@@ -56,7 +56,10 @@ RS_DEV int hypergeometric(Key2 key, uint64_t node, uint64_t n, uint64_t K, uint6
         const double h = RS_HAT_D1 * sqrt(var + 0.5) + RS_HAT_D2;
         const double alpha = mu + 0.5;
         const uint64_t M = (uint64_t)(((unsigned __int128)(a + 1) * (b + 1)) / (S + 2));
+        const uint64_t m = S - a - b;
         const double top = (double)a + 1.0;
+        const double l0 = log_fixed(M, tab), l1 = log_fixed(a - M, tab), l2 = log_fixed(b - M, tab),
+                     l3 = log_fixed(m + M, tab);
         for (uint64_t i = 0; i < kRouMaxTrials; ++i) {
             const uint4 blk = philox_block((uint32_t)i, TAG_SPLIT, node, key);
             const double U = u_open(((uint64_t)blk.y << 32) | blk.x);
@@ -64,8 +67,8 @@ RS_DEV int hypergeometric(Key2 key, uint64_t node, uint64_t n, uint64_t K, uint6
             const double X = alpha + h * (V - 0.5) * drecip(U);
             if (X < 0.0 || X >= top) continue;
             const uint64_t k = (uint64_t)X;
-            const double T = dsd(M, k, tab) + dsd(a - M, a - k, tab) + dsd(b - M, b - k, tab) +
-                             dsd(S - a - b + M, S - a - b + k, tab);
+            const double T = dsd_fixed(M, k, l0, tab) + dsd_fixed(a - M, a - k, l1, tab) +
+                             dsd_fixed(b - M, b - k, l2, tab) + dsd_fixed(m + M, m + k, l3, tab);
             if (2.0 * dlog(U, tab) <= T) { y = k; done = true; break; }
         }
     }
@@ -104,6 +107,7 @@ RS_DEV int binomial(Key2 key, uint64_t node, uint64_t c, uint64_t K, uint64_t S,
     const double logr = (r == 1.0) ? 0.0 : dlog(r, tab);
     const uint64_t M = (uint64_t)(((unsigned __int128)(c + 1) * K) / S);
     const double top = (double)c + 1.0;
+    const double l0 = log_fixed(M, tab), l1 = log_fixed(c - M, tab);
     for (uint64_t i = 0; i < kRouMaxTrials; ++i) {
         const uint4 blk = philox_block((uint32_t)i, TAG_SPLIT, node, key);
         const double U = u_open(((uint64_t)blk.y << 32) | blk.x);
@@ -111,7 +115,8 @@ RS_DEV int binomial(Key2 key, uint64_t node, uint64_t c, uint64_t K, uint64_t S,
         const double X = alpha + h * (V - 0.5) * drecip(U);
         if (X < 0.0 || X >= top) continue;
         const uint64_t k = (uint64_t)X;
-        const double T = dsd(M, k, tab) + dsd(c - M, c - k, tab) + (double)((int64_t)k - (int64_t)M) * logr;
+        const double T = dsd_fixed(M, k, l0, tab) + dsd_fixed(c - M, c - k, l1, tab) +
+                         (double)((int64_t)k - (int64_t)M) * logr;
         if (2.0 * dlog(U, tab) <= T) { out = k; return RS_OK; }
     }
     return RS_EITER;

@@ -223,4 +223,35 @@ RS_DEV double dsd(uint64_t x, uint64_t y, const double* __restrict__ tab) {
     return x >= y ? dlfdiff(x, y, tab) : -dlfdiff(y, x, tab);
 }
 
+// ln P! - ln Q! for the ratio-of-uniforms tests, P fixed for the node and
+// lnP = dlog(max(P, 1)) computed once: dlfdiff's branches on (max, min),
+// with ln of the larger argument = lnP when that is P, and ln of the smaller
+// one in the cancellation-free form = lnP when that is P, else ln P -
+// ln(P/Q).
+RS_DEV double dsd_fixed(uint64_t P, uint64_t Q, double lnP, const double* __restrict__ tab) {
+    const bool p_big = P >= Q;
+    const uint64_t x = p_big ? P : Q, y = p_big ? Q : P, d = x - y;
+    double v;
+    if (d == 0) return 0.0;
+    if (x < 256) {
+        v = tab[x] - tab[y];
+    } else if (d <= 8) {
+        v = dlog(short_product(x, y), tab);
+    } else {
+        const double X = (double)x;
+        if (y < 256) {
+            const double lx = p_big ? lnP : dlog(X, tab);
+            v = ((X + 0.5) * lx - X + RS_HL2PI + stirling_tail(drecip(X))) - tab[y];
+        } else {
+            const double Y = (double)y, D = (double)d;
+            const double rY = drecip(Y);
+            const double lp = dlog1p_pos(D * rY, tab);
+            const double ly = p_big ? lnP - lp : lnP;
+            v = (X + 0.5) * lp + D * ly - D + (stirling_tail(drecip(X)) - stirling_tail(rY));
+        }
+    }
+    return p_big ? v : -v;
+}
+RS_DEV double log_fixed(uint64_t P, const double* __restrict__ tab) { return dlog((double)(P > 0 ? P : 1), tab); }
+
 }  // namespace rs

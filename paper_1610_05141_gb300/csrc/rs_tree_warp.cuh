@@ -8,8 +8,9 @@
 //  - lane refill: a warp owns a batch of nodes; a lane whose node is done
 //    takes the next one, so trial counts no longer idle lanes;
 //  - cooperative logarithms: each ratio-of-uniforms trial first records the
-//    arguments of every logarithm it needs (ln U, ln Y, ln of 1 + D/Y, the
-//    terms of short sums, ...), the whole warp evaluates them together, and
+//    arguments of every logarithm it needs (ln U, ln of 1 + D/Y, of short
+//    products, and in a node's first round those of the differences' fixed
+//    ends), the whole warp evaluates them together, and
 //    each lane then assembles its acceptance test from the results in
 //    exactly the operations and order of the scalar definition
 //    (rs_deviates.cuh), so the results are the same bits;
@@ -81,20 +82,53 @@ RS_DEV double lfd_eval(uint64_t x, uint64_t y, const double* __restrict__ tab, L
     return (X + 0.5) * lp + D * L.next() - D + (stirling_tail(drecip(X)) - stirling_tail(rY));
 }
 
-// Signed difference (dsd): the larger argument first, one call, then the
-// sign -- selects instead of two inlined calls, so that lanes whose
-// arguments come in opposite orders do not run both copies one after the
-// other.
-RS_DEV void sd_args(uint64_t x, uint64_t y, LfdArgs& A) {
-    const bool pos = x >= y;
-    lfd_args(pos ? x : y, pos ? y : x, A);
+// The fixed-end difference dsd_fixed(P, Q, lnP) split the same way: one
+// call on (max, min) with the sign after, so that lanes whose arguments come
+// in opposite orders run one copy.
+RS_DEV void sdf_args(uint64_t P, uint64_t Q, LfdArgs& A) {
+    const bool p_big = P >= Q;
+    const uint64_t x = p_big ? P : Q, y = p_big ? Q : P, d = x - y;
+    if (d == 0 || x < 256) return;
+    if (d <= 8) {
+        A.push(short_product(x, y));
+        return;
+    }
+    if (y < 256) {
+        if (!p_big) A.push((double)x);
+        return;
+    }
+    const double rY = drecip((double)y);
+    A.push(log1p_pos_u((double)d * rY));
+    A.save(rY);
 }
-RS_DEV double sd_eval(uint64_t x, uint64_t y, const double* __restrict__ tab, LfdLogs& L) {
-    const bool pos = x >= y;
-    const double v = lfd_eval(pos ? x : y, pos ? y : x, tab, L);
-    return pos ? v : -v;
+RS_DEV double sdf_eval(uint64_t P, uint64_t Q, double lnP, const double* __restrict__ tab, LfdLogs& L) {
+    const bool p_big = P >= Q;
+    const uint64_t x = p_big ? P : Q, y = p_big ? Q : P, d = x - y;
+    double v;
+    if (d == 0) return 0.0;
+    if (x < 256) {
+        v = tab[x] - tab[y];
+    } else if (d <= 8) {
+        v = L.next();
+    } else {
+        const double X = (double)x;
+        if (y < 256) {
+            const double lx = p_big ? lnP : L.next();
+            v = ((X + 0.5) * lx - X + RS_HL2PI + stirling_tail(drecip(X))) - tab[y];
+        } else {
+            const double D = (double)d;
+            const double rY = L.saved();
+            const double lp = log1p_pos_finish(D * rY, L.next());
+            const double ly = p_big ? lnP - lp : lnP;
+            v = (X + 0.5) * lp + D * ly - D + (stirling_tail(drecip(X)) - stirling_tail(rY));
+        }
+    }
+    return p_big ? v : -v;
 }
 
+// The fixed ends of the test's differences: M and a - M (binomial), or M,
+// a - M, b - M and m + M with m = S - a - b (hypergeometric); the moving
+// ends replace M by the candidate k.
 // Parameters of one node's ratio-of-uniforms loop (rs_deviates.cuh).
 struct RouNode {
     uint64_t v;          // node id
@@ -102,9 +136,24 @@ struct RouNode {
     uint64_t a, b, M;    // hypergeometric: reduced draws/successes; binomial: a = c
     uint64_t n_in, Kp;   // un-reduction of the hypergeometric result
     double h, alpha, top, logr;
+    double lnP[4];       // ln of the fixed ends (lanes kernel), once per node
     uint32_t trial;
     bool flipN, flipK;
+    bool fresh;          // set up, fixed-end logarithms not yet taken
 };
+
+template <bool WR>
+RS_DEV uint64_t fixed_end(const RouNode& q, int j) {
+    if (WR) return j == 0 ? q.M : (j == 1 ? q.a - q.M : 0);
+    const uint64_t m = q.S - q.a - q.b;
+    return j == 0 ? q.M : (j == 1 ? q.a - q.M : (j == 2 ? q.b - q.M : m + q.M));
+}
+template <bool WR>
+RS_DEV uint64_t moving_end(const RouNode& q, int j, uint64_t k) {
+    if (WR) return j == 0 ? k : (j == 1 ? q.a - k : 0);
+    const uint64_t m = q.S - q.a - q.b;
+    return j == 0 ? k : (j == 1 ? q.a - k : (j == 2 ? q.b - k : m + k));
+}
 
 RS_DEV void write_children(NodeRec* __restrict__ rec, uint64_t v, const NodeRec& r, uint64_t K, uint64_t L) {
     rec[2 * v] = NodeRec{r.lo, K, L, r.off};
@@ -180,6 +229,7 @@ RS_DEV bool node_setup(NodeRec* __restrict__ rec, uint64_t v, Key2 key, const do
     q->off = r.off;
     q->K = K;
     q->trial = 0;
+    q->fresh = true;
     return true;
 }
 
@@ -215,7 +265,15 @@ RS_DEV void tree_batch_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
         uint64_t k = 0;
         bool inr = false;
         int nargs = 0;
+        constexpr int kTerms = WR ? 2 : 4;
         if (active) {
+            LfdArgs A{mine, 0, 0};
+            if (q.fresh)   // the fixed ends' logarithms go with this round's
+#pragma unroll
+                for (int j = 0; j < kTerms; ++j) {
+                    const uint64_t P = fixed_end<WR>(q, j);
+                    A.push((double)(P > 0 ? P : 1));
+                }
             const uint4 blk = philox_block((uint32_t)t, TAG_SPLIT, q.v, key);
             U = u_open(((uint64_t)blk.y << 32) | blk.x);
             const double V = v_closed(((uint64_t)blk.w << 32) | blk.z);
@@ -223,20 +281,11 @@ RS_DEV void tree_batch_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
             inr = !(X < 0.0 || X >= q.top) && t < kRouMaxTrials;
             if (inr) {
                 k = (uint64_t)X;
-                LfdArgs A{mine, 0, 0};
                 A.push(U);
-                if (WR) {
-                    sd_args(q.M, k, A);
-                    sd_args(q.a - q.M, q.a - k, A);
-                } else {
-                    const uint64_t m = q.S - q.a - q.b;
-                    sd_args(q.M, k, A);
-                    sd_args(q.a - q.M, q.a - k, A);
-                    sd_args(q.b - q.M, q.b - k, A);
-                    sd_args(m + q.M, m + k, A);
-                }
-                nargs = A.n;
+#pragma unroll
+                for (int j = 0; j < kTerms; ++j) sdf_args(fixed_end<WR>(q, j), moving_end<WR>(q, j, k), A);
             }
+            nargs = A.n;
         }
         __syncwarp();
         // the warp evaluates all logarithms together: item g of the
@@ -276,17 +325,22 @@ RS_DEV void tree_batch_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
         __syncwarp();
         bool acc = false;
         uint64_t L = 0;
+        LfdLogs Lg{mine, 0, 0};
+        if (active && q.fresh) {
+#pragma unroll
+            for (int j = 0; j < kTerms; ++j) q.lnP[j] = Lg.next();
+            q.fresh = false;
+        }
         if (active && inr) {
-            LfdLogs Lg{mine, 0, 0};
             const double lU = Lg.next();
             double T;
             if (WR) {
-                T = sd_eval(q.M, k, tab, Lg) + sd_eval(q.a - q.M, q.a - k, tab, Lg) +
+                T = sdf_eval(q.M, k, q.lnP[0], tab, Lg) + sdf_eval(q.a - q.M, q.a - k, q.lnP[1], tab, Lg) +
                     (double)((int64_t)k - (int64_t)q.M) * q.logr;
             } else {
                 const uint64_t m = q.S - q.a - q.b;
-                T = sd_eval(q.M, k, tab, Lg) + sd_eval(q.a - q.M, q.a - k, tab, Lg) +
-                    sd_eval(q.b - q.M, q.b - k, tab, Lg) + sd_eval(m + q.M, m + k, tab, Lg);
+                T = sdf_eval(q.M, k, q.lnP[0], tab, Lg) + sdf_eval(q.a - q.M, q.a - k, q.lnP[1], tab, Lg) +
+                    sdf_eval(q.b - q.M, q.b - k, q.lnP[2], tab, Lg) + sdf_eval(m + q.M, m + k, q.lnP[3], tab, Lg);
             }
             if (2.0 * lU <= T) {
                 acc = true;
@@ -339,6 +393,9 @@ RS_DEV void tree_terms_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
     RouNode q;
     bool active = grp < count &&
                   node_setup<WR>(rec, v0 + grp, key, tab, status, &q, r == 0);
+    // this lane's fixed end (term j) and its logarithm, once per node
+    const uint64_t P = active ? fixed_end<WR>(q, (int)j) : 0;
+    const double lnP = log_fixed(P, tab);
     while (__ballot_sync(0xFFFFFFFFu, active)) {
         const uint64_t t = (uint64_t)q.trial + p;
         double U = 1.0, T = 0.0, term = 0.0;
@@ -351,23 +408,11 @@ RS_DEV void tree_terms_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
             const double X = q.alpha + q.h * (V - 0.5) * drecip(U);
             inr = !(X < 0.0 || X >= q.top) && t < kRouMaxTrials;
             if (inr) k = (uint64_t)X;
-            // this lane's difference ln x! - ln y!, picked with selects so
-            // that all lanes run one copy of dlfdiff (dsd's sign rule after)
-            uint64_t x = 0, y = 0;
-            if (inr) {
-                if (WR) {
-                    x = j == 0 ? q.M : (j == 1 ? q.a - q.M : 0);
-                    y = j == 0 ? k : (j == 1 ? q.a - k : 0);
-                } else {
-                    const uint64_t m = q.S - q.a - q.b;
-                    const uint64_t base = j == 0 ? 0 : (j == 1 ? q.a : (j == 2 ? q.b : m));
-                    x = j == 0 ? q.M : (j == 3 ? base + q.M : base - q.M);
-                    y = j == 0 ? k : (j == 3 ? base + k : base - k);
-                }
-            }
-            const bool pos = x >= y;
-            const double v = dlfdiff(pos ? x : y, pos ? y : x, tab);
-            term = pos ? v : -v;
+            // this lane's difference ln P! - ln Q! (none: Q = P gives 0);
+            // the ends are picked with selects so that all lanes run one
+            // copy of dsd_fixed
+            const uint64_t Q = inr ? moving_end<WR>(q, (int)j, k) : P;
+            term = dsd_fixed(P, Q, lnP, tab);
         }
         const double lU = dlog(U, tab);
         const double t0 = __shfl_sync(0xFFFFFFFFu, term, tbase);

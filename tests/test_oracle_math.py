@@ -198,3 +198,28 @@ def test_lfdiff_accuracy(oracle):
             continue
         assert abs(mpmath.mpf(got) - exact) <= 1e-13 * abs(exact), (x, y, got, float(exact))
         assert oracle.sd(x, y) == got and oracle.sd(y, x) == -got
+
+
+def test_sd_fixed_accuracy(oracle):
+    """The ratio-of-uniforms differences with the node's ln P supplied: ln P! -
+    ln Q! to 1e-13 of the difference on every branch, with P the larger or
+    the smaller end, and equal to or_sd where no logarithm is reused."""
+    rng = np.random.default_rng(8)
+    pairs = [(5, 5), (10, 3), (3, 10), (255, 0), (0, 255), (300, 295), (295, 300), (1000, 255), (255, 1000),
+             (1000, 10), (10, 1000), (0, 7)]
+    for _ in range(400):
+        y = int(np.exp(rng.uniform(0, math.log(2**61))))
+        d = int(np.exp(rng.uniform(0, math.log(max(2, min(y, 2**40))))))
+        pairs += [(y + d, y), (y, y + d)]
+    for P, Q in pairs:
+        lnP = oracle.log(float(max(P, 1)))
+        got = oracle.sd_fixed(P, Q, lnP)
+        exact = _lf_exact(P) - _lf_exact(Q)
+        if P == Q:
+            assert got == 0.0
+            continue
+        assert abs(mpmath.mpf(got) - exact) <= 1e-13 * abs(exact), (P, Q, got, float(exact))
+        x, y = max(P, Q), min(P, Q)
+        if x < 256 or x - y <= 8:
+            assert got == oracle.sd(P, Q)
+
