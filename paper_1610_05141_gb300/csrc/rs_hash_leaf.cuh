@@ -131,9 +131,8 @@ RS_DEV uint64_t slot_mult(uint64_t s, uint32_t T) {
     return (uint64_t)T >= s ? ~0ull : (uint64_t)(((unsigned __int128)T << 64) / s);
 }
 
-// A multiplier of the same kind computed by every thread on its own in
-// single precision, each step rounded down, so that mult <= T 2^width / s
-// and every slot stays below T.  Any such multiplier keeps the order of the
+// A multiplier of the same kind computed in single precision, each step
+// rounded down, so that mult <= T 2^width / s and every slot stays below T.  Any such multiplier keeps the order of the
 // values, which is all the bucket path relies on.
 template <typename KeyT>
 RS_DEV uint64_t slot_mult_fast(uint64_t s, uint32_t T) {
@@ -484,9 +483,13 @@ RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, co
     // may run past the end of the leaf, and reads past a key's bucket meet
     // only larger keys (buckets are monotone in the key) or these
     if (tid < 3) B[k + tid] = ~KeyT(0);
-    const uint64_t mult = slot_mult_fast<KeyT>(r.s, nb);
-    const uint64_t thr = lemire_threshold(r.s);
+    if (tid == 0) {   // once per leaf; the last reads of these fields came before the last barrier
+        sm.mult = slot_mult_fast<KeyT>(r.s, nb);
+        sm.thr = lemire_threshold(r.s);
+    }
     group_sync<BAR, NT>();
+    const uint64_t mult = sm.mult;
+    const uint64_t thr = sm.thr;
     if (tid == 0) sm.ranksum = 0;   // every read of the last leaf's sum came before this barrier
     // pass 1: generate, keep, count per bucket
     auto keep = [&](uint32_t j, uint64_t v) {
