@@ -1,0 +1,103 @@
+"""Parity at the full sizes the benchmark times, in the same launch
+configuration (one call of the C ABI over the whole workload): the oracle
+cannot produce 10^9 values in seconds, so sampled parts of the output are
+recomputed one by one by the oracle (whole leaves, at the leaf records the
+oracle's own split tree gives), and the rest is checked by properties that
+hold at any size (order, range, count), on the device."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+SAMPLED_LEAVES = 40
+
+
+@pytest.fixture(scope="module")
+def rs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1610_05141_gb300 as rs
+    from paper_1610_05141_gb300 import build
+    build.build()
+    rs.load()
+    return rs
+
+
+@pytest.fixture(scope="module")
+def ctx(rs):
+    c = rs.rs_create(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def oracle():
+    import oracle as o
+    o.build()
+    return o
+
+
+def _check_leaves(got_dev, oracle, seed, kind, n, N, n0):
+    recs, D = oracle.tree(n, N, seed, n0, kind)
+    assert int(recs[-1][3]) + int(recs[-1][2]) == n
+    rng = np.random.default_rng(seed + 1000 * kind)
+    picks = set(rng.integers(0, len(recs), SAMPLED_LEAVES).tolist()) | {0, len(recs) // 2, len(recs) - 1}
+    for i in sorted(picks):
+        lo, s, c, off = (int(x) for x in recs[i])
+        want = oracle.leaf(seed, kind, D, i, recs[i])
+        got = got_dev[off:off + c].cpu().numpy().view(np.uint64)
+        if not np.array_equal(got, want):
+            bad = int(np.argmax(got != want))
+            raise AssertionError(f"leaf {i} of {len(recs)} (kind {kind}): first mismatch at {bad}: "
+                                 f"gpu {got[bad]} oracle {want[bad]}")
+
+
+@pytest.mark.parametrize("kind,n,N", [(0, 10**9, 2**50), (1, 10**9, 2**40), (2, 10**9, 2**50)])
+def test_full_size_samples(rs, ctx, oracle, kind, n, N):
+    """n = 1e9 sorted from 2^50 (Algorithm H leaves), with replacement from
+    2^40, and with Algorithm B leaves: sampled leaves equal the oracle's,
+    the whole output is sorted (strictly without replacement) inside 1..N."""
+    seed, n0 = 1, 4096
+    call = {0: rs.rs_sample, 1: rs.rs_sample_with_replacement, 2: rs.rs_sample_b}[kind]
+    out = torch.full((n,), -1, dtype=torch.int64, device="cuda")
+    call(ctx, n, N, seed, n0, out)
+    assert rs.rs_sync(ctx) == rs.RS_OK
+    assert int(out[0]) >= 1 and int(out[-1]) <= N
+    if kind == 1:
+        assert bool(torch.all(out[1:] >= out[:-1]))
+    else:
+        assert bool(torch.all(out[1:] > out[:-1]))
+    _check_leaves(out, oracle, seed, kind, n, N, n0)
+    del out
+    torch.cuda.empty_cache()
+
+
+def test_full_size_bernoulli(rs, ctx, oracle):
+    """Bernoulli p = 1e-2 over 2^36 positions, the whole range in one call:
+    the count is within 6 sigma of N p, positions increase strictly inside
+    1..N, and chunk-aligned slices equal the oracle's windows."""
+    p, N, seed, n0 = 1e-2, 2**36, 7, 4096
+    mean = N * p
+    cap = int(mean + 10 * np.sqrt(mean)) + 1024
+    out = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
+    rc, cnt = rs.rs_bernoulli(ctx, p, N, seed, n0, 0, N, out, cap)
+    assert rs.rs_sync(ctx) == rs.RS_OK
+    assert abs(cnt - mean) < 6 * np.sqrt(mean * (1 - p))
+    got = out[:cnt]
+    assert int(got[0]) >= 1 and int(got[-1]) <= N
+    assert bool(torch.all(got[1:] > got[:-1]))
+    C = 1 << oracle.bern_chunk_log2(p, n0)
+    nch = N // C
+    rng = np.random.default_rng(seed)
+    for c0 in sorted(set(rng.integers(0, nch - 2, 6).tolist()) | {0, nch - 2}):
+        a, b = c0 * C, (c0 + 2) * C
+        want = oracle.bernoulli(p, N, seed, n0, a, b)
+        lo = int(torch.searchsorted(got, torch.tensor([a + 1], dtype=torch.int64, device="cuda")))
+        sl = got[lo:lo + len(want)].cpu().numpy().view(np.uint64)
+        assert np.array_equal(sl, want), (a, b)
+        if lo + len(want) < cnt:
+            assert int(got[lo + len(want)]) > b
+    del out, got
+    torch.cuda.empty_cache()
