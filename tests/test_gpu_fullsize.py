@@ -101,3 +101,41 @@ def test_full_size_bernoulli(rs, ctx, oracle):
             assert int(got[lo + len(want)]) > b
     del out, got
     torch.cuda.empty_cache()
+
+
+def test_full_size_batch(rs, ctx, oracle):
+    """The 100,000-request batch the benchmark times (7.19e9 values), as a
+    graph-replayed run after the eager one and a tuning pass: every request
+    succeeds, every request's values increase strictly inside 1..N (checked
+    on the device), and sampled requests equal the oracle's samples."""
+    from paper_1610_05141_gb300.workloads import batch_requests
+    n, N, seeds, off, n0, total = batch_requests(R=100000)
+    kinds = np.zeros(len(n), dtype=np.uint32)
+    plan = rs.rs_batch_plan(ctx, rs.requests_array(n, N, seeds, off, n0, kinds))
+    pool = torch.full((total,), -1, dtype=torch.int64, device="cuda")
+    status = torch.empty(len(n), dtype=torch.int32, device="cuda")
+    try:
+        rs.rs_batch_run(plan, pool, status)
+        rs.rs_batch_tune(plan, pool, status)
+        rs.rs_batch_run(plan, pool, status)
+        torch.cuda.synchronize()
+        assert bool((status == 0).all())
+        # order inside each request: the value steps up everywhere except at a
+        # request's first value, which is at least 1; the last value of each
+        # request is at most its N
+        starts = torch.zeros(total, dtype=torch.bool, device="cuda")
+        starts[torch.as_tensor(off.astype(np.int64), device="cuda")] = True
+        step_ok = (pool[1:] > pool[:-1]) | starts[1:]
+        assert bool(step_ok.all()) and bool((pool[starts] >= 1).all())
+        last = torch.as_tensor((off + n - 1).astype(np.int64), device="cuda")
+        assert bool((pool[last] <= torch.as_tensor(N.astype(np.int64), device="cuda")).all())
+        rng = np.random.default_rng(20161017)
+        for i in sorted(set(rng.integers(0, len(n), 24).tolist()) | {0, len(n) - 1, int(np.argmax(n))}):
+            ni = int(n[i])
+            want = oracle.sample(ni, int(N[i]), int(seeds[i]), int(n0[i]), 0)
+            got = pool[int(off[i]):int(off[i]) + ni].cpu().numpy().view(np.uint64)
+            assert np.array_equal(got, want), (i, ni, int(N[i]))
+    finally:
+        plan.close()
+        del pool, status
+        torch.cuda.empty_cache()
