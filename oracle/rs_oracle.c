@@ -350,18 +350,16 @@ double or_lf(uint64_t x)
 }
 
 /* ln x! - ln y! for x >= y, written so that no large term cancels:
- * (x + 1/2) ln(1 + d/y) + d ln y - d + tail(x) - tail(y), d = x - y. */
+ * (x + 1/2) ln(1 + d/y) + d ln y - d + tail(x) - tail(y), d = x - y, for
+ * every d once y >= 256 (short differences included: ln(1 + d/y) keeps
+ * its relative accuracy for small d/y, and the tails' difference is far
+ * below the result's ulp). */
 double or_lfdiff(uint64_t x, uint64_t y)
 {
     lf_init();
     uint64_t d = x - y;
     if (d == 0) return 0.0;
     if (x < 256) return lf_table[x] - lf_table[y];
-    if (d <= 8) {   /* ln of the product y+1 .. x (below 2^512: no overflow) */
-        double prod = (double)(y + 1);
-        for (uint64_t i = y + 2; i <= x; ++i) prod = prod * (double)i;
-        return or_log(prod);
-    }
     if (y < 256) return or_lf(x) - lf_table[y];
     double X = (double)x, Y = (double)y, Dd = (double)d;
     double rY = or_recip(Y);
@@ -389,10 +387,6 @@ double or_sd_fixed(uint64_t P, uint64_t Q, double lnP)
     if (d == 0) return 0.0;
     if (x < 256) {
         v = lf_table[x] - lf_table[y];
-    } else if (d <= 8) {
-        double prod = (double)(y + 1);
-        for (uint64_t i = y + 2; i <= x; ++i) prod = prod * (double)i;
-        v = or_log(prod);
     } else {
         double X = (double)x;
         if (y < 256) {

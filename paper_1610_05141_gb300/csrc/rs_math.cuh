@@ -194,23 +194,13 @@ RS_DEV double dlf(uint64_t x, const double* __restrict__ tab) {
     return (X + 0.5) * dlog(X, tab) - X + RS_HL2PI + stirling_tail(drecip(X));
 }
 
-// y+1 .. x multiplied up, for x - y <= 8 (below 2^512): ln x! - ln y! is
-// its logarithm.
-RS_DEV double short_product(uint64_t x, uint64_t y) {
-    double prod = (double)(y + 1);
-    for (uint64_t i = y + 2; i <= x; ++i) prod = prod * (double)i;
-    return prod;
-}
-
 // ln x! - ln y! for x >= y without cancellation of the two large terms:
 // (x+1/2) ln(x/y) + (x-y) ln y - (x-y) + tail(x) - tail(y), with
-// ln(x/y) = ln(1 + (x-y)/y).  Short differences take the logarithm of the
-// product of their factors.
+// ln(x/y) = ln(1 + (x-y)/y), for every x - y once y >= 256.
 RS_DEV double dlfdiff(uint64_t x, uint64_t y, const double* __restrict__ tab) {
     const uint64_t d = x - y;
     if (d == 0) return 0.0;
     if (x < 256) return tab[x] - tab[y];
-    if (d <= 8) return dlog(short_product(x, y), tab);
     if (y < 256) return dlf(x, tab) - tab[y];
     const double X = (double)x, Y = (double)y, D = (double)d;
     const double rY = drecip(Y);
@@ -235,8 +225,6 @@ RS_DEV double dsd_fixed(uint64_t P, uint64_t Q, double lnP, const double* __rest
     if (d == 0) return 0.0;
     if (x < 256) {
         v = tab[x] - tab[y];
-    } else if (d <= 8) {
-        v = dlog(short_product(x, y), tab);
     } else {
         const double X = (double)x;
         if (y < 256) {

@@ -8,9 +8,9 @@
 //  - lane refill: a warp owns a batch of nodes; a lane whose node is done
 //    takes the next one, so trial counts no longer idle lanes;
 //  - cooperative logarithms: each ratio-of-uniforms trial first records the
-//    arguments of every logarithm it needs (ln U, ln of 1 + D/Y, of short
-//    products, and in a node's first round those of the differences' fixed
-//    ends), the whole warp evaluates them together, and
+//    arguments of every logarithm it needs (ln U, ln of 1 + D/Y, and in a
+//    node's first round those of the differences' fixed ends), the whole
+//    warp evaluates them together, and
 //    each lane then assembles its acceptance test from the results in
 //    exactly the operations and order of the scalar definition
 //    (rs_deviates.cuh), so the results are the same bits;
@@ -30,13 +30,11 @@
 
 namespace rs {
 
-constexpr int kLogSlots = 16;   // per lane per trial: up to 9 logarithm arguments, then 4 saved reciprocals
+constexpr int kLogSlots = 16;   // per lane per trial: up to 9 logarithm arguments, then up to 4 saved reciprocals
 
-// Log-factorial difference lfdiff(x, y), x >= y, split in two halves: args()
-// lists the logarithm arguments it needs, eval() computes the value from
-// their logarithms, consumed in the same order.
-// Logarithm arguments fill a lane's slots from the front; reciprocals that
-// the evaluation needs again are saved from the back.
+// A lane's slots for one trial: logarithm arguments fill them from the
+// front (the warp then replaces each by its logarithm); reciprocals that the
+// evaluation needs again are saved from the back.
 struct LfdArgs {
     double* a;
     int n, ns;
@@ -50,49 +48,15 @@ struct LfdLogs {
     RS_DEV double saved() { return l[kLogSlots - 1 - ns++]; }
 };
 
-RS_DEV void lfd_args(uint64_t x, uint64_t y, LfdArgs& A) {
-    const uint64_t d = x - y;
-    if (d == 0 || x < 256) return;
-    if (d <= 8) {
-        A.push(short_product(x, y));
-        return;
-    }
-    const double X = (double)x;
-    if (y < 256) {
-        A.push(X);
-        return;
-    }
-    const double Y = (double)y, D = (double)d;
-    const double rY = drecip(Y);
-    A.push(log1p_pos_u(D * rY));
-    A.push(Y);
-    A.save(rY);
-}
-
-RS_DEV double lfd_eval(uint64_t x, uint64_t y, const double* __restrict__ tab, LfdLogs& L) {
-    const uint64_t d = x - y;
-    if (d == 0) return 0.0;
-    if (x < 256) return tab[x] - tab[y];
-    if (d <= 8) return L.next();
-    const double X = (double)x;
-    if (y < 256) return ((X + 0.5) * L.next() - X + RS_HL2PI + stirling_tail(drecip(X))) - tab[y];
-    const double Y = (double)y, D = (double)d;
-    const double rY = L.saved();
-    const double lp = log1p_pos_finish(D * rY, L.next());
-    return (X + 0.5) * lp + D * L.next() - D + (stirling_tail(drecip(X)) - stirling_tail(rY));
-}
-
-// The fixed-end difference dsd_fixed(P, Q, lnP) split the same way: one
-// call on (max, min) with the sign after, so that lanes whose arguments come
-// in opposite orders run one copy.
+// The fixed-end difference dsd_fixed(P, Q, lnP) (rs_math.cuh) in two
+// halves: sdf_args lists the logarithm arguments it needs, sdf_eval computes
+// the value from their logarithms, consumed in the same order.  One call on
+// (max, min) with the sign after, so that lanes whose arguments come in
+// opposite orders run one copy.
 RS_DEV void sdf_args(uint64_t P, uint64_t Q, LfdArgs& A) {
     const bool p_big = P >= Q;
     const uint64_t x = p_big ? P : Q, y = p_big ? Q : P, d = x - y;
     if (d == 0 || x < 256) return;
-    if (d <= 8) {
-        A.push(short_product(x, y));
-        return;
-    }
     if (y < 256) {
         if (!p_big) A.push((double)x);
         return;
@@ -108,8 +72,6 @@ RS_DEV double sdf_eval(uint64_t P, uint64_t Q, double lnP, const double* __restr
     if (d == 0) return 0.0;
     if (x < 256) {
         v = tab[x] - tab[y];
-    } else if (d <= 8) {
-        v = L.next();
     } else {
         const double X = (double)x;
         if (y < 256) {
