@@ -12,7 +12,7 @@
 // the positions are those of the sequential definition.  A draw with
 // ln U / L >= 2^62 ends the range.
 #include "rs_batch.cuh"
-#include "rs_leaf.cuh"
+#include "rs_hash_leaf.cuh"
 #include "rs_math.cuh"
 
 namespace rs {
@@ -337,20 +337,26 @@ cudaError_t launch_bernoulli(const BernLaunch& L, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 
 constexpr uint32_t kLeafBCap = 8192;   // positions of one attempt
+constexpr int kLeafBThreads = 256;
 
+// PosT: 32-bit positions when no leaf exceeds 2^32 positions.
+template <typename PosT>
 struct LeafBShared {
-    uint64_t pos[kLeafBCap];
-    LeafShared<uint32_t> sel;
-    uint64_t warp_tot[kLeafThreads / 32];
+    PosT pos[kLeafBCap];              // the attempt's positions (offsets in the leaf), increasing
+    uint32_t drop[kLeafBCap / 32];    // removed indices, as bits
+    uint64_t warp_tot[kLeafBThreads / 32];
+    uint32_t warp_cnt[kLeafBThreads / 32];
+    uint32_t newcount[3];
     uint64_t last_incl;
     int first_bad;
     int err;
 };
 
 // Block-wide inclusive saturating scan of one value per thread.
-RS_DEV uint64_t block_inclusive_sat(uint64_t x, LeafBShared& sm) {
+template <int NT, typename Sm>
+RS_DEV uint64_t block_inclusive_sat(uint64_t x, Sm& sm) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int NW = kLeafThreads / 32;
+    constexpr int NW = NT / 32;
     uint64_t incl = warp_inclusive_sat(x);
     if (lane == 31) sm.warp_tot[warp] = incl;
     __syncthreads();
@@ -366,29 +372,30 @@ RS_DEV uint64_t block_inclusive_sat(uint64_t x, LeafBShared& sm) {
 
 // Geometric-skip walk of [0, s) by the whole block; positions go to sm.pos
 // (up to the capacity).  Returns the count; sets sm.err on a run-out stream.
-RS_DEV uint64_t block_walk(Key2 key, uint32_t tag, uint64_t id, double R, uint64_t s, LeafBShared& sm,
+template <int NT, typename PosT>
+RS_DEV uint64_t block_walk(Key2 key, uint32_t tag, uint64_t id, double R, uint64_t s, LeafBShared<PosT>& sm,
                            const double* __restrict__ tab) {
     const uint64_t cmax = s + 2;
     uint64_t base = 0, count = 0;
-    for (uint64_t j = 0;; j += kLeafThreads) {
+    for (uint64_t j = 0;; j += NT) {
         const uint64_t jt = j + threadIdx.x;
         const bool exhausted = jt >= kMaxDraws;
         bool stop = true;
         uint64_t step = 0;
         if (!exhausted) step = step_of(skip_quotient(stream_value(key, tag, id, jt), R, tab), cmax, &stop);
-        if (threadIdx.x == 0) sm.first_bad = kLeafThreads;
-        const uint64_t incl = block_inclusive_sat(step, sm);
+        if (threadIdx.x == 0) sm.first_bad = NT;
+        const uint64_t incl = block_inclusive_sat<NT>(step, sm);
         const bool ok = !stop && incl <= s - base;
         if (!ok) atomicMin(&sm.first_bad, (int)threadIdx.x);
-        if (threadIdx.x == kLeafThreads - 1) sm.last_incl = incl;
+        if (threadIdx.x == NT - 1) sm.last_incl = incl;
         __syncthreads();
         const int fb = sm.first_bad;
-        if ((int)threadIdx.x < fb && count + threadIdx.x < kLeafBCap) sm.pos[count + threadIdx.x] = base - 1 + incl;
+        if ((int)threadIdx.x < fb && count + threadIdx.x < kLeafBCap) sm.pos[count + threadIdx.x] = (PosT)(base - 1 + incl);
         if ((int)threadIdx.x == fb && exhausted) sm.err = 1;
         count += fb;
         const uint64_t last = sm.last_incl;
         __syncthreads();
-        if (fb < kLeafThreads) return count;
+        if (fb < NT) return count;
         base += last;
     }
 }
@@ -402,9 +409,16 @@ struct LeafBArgs {
     const double* tab;
 };
 
-// One leaf of Algorithm B, by the whole block.
-RS_DEV void leaf_b_one(LeafBShared& sm, const NodeRec& r, uint64_t id, Key2 key, uint64_t* __restrict__ out,
+// One leaf of Algorithm B, by the whole block: the walk (retried while
+// short), then the c - n' removed indices -- the first c - n' distinct valid
+// candidates of stream (FIXUP, id) over [0, c), Algorithm H on indices -- as
+// bits, and the kept positions written in order (a kept index's place is
+// the number of kept indices below it).
+template <int NT, typename PosT>
+RS_DEV void leaf_b_one(LeafBShared<PosT>& sm, const NodeRec& r, uint64_t id, Key2 key, uint64_t* __restrict__ out,
                        int* status, const double* __restrict__ tab) {
+    constexpr int NW = NT / 32;
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (r.c == 0) return;
     const double dn = (double)r.c;
     double rho = (dn + 3.0 * sqrt(dn) + 10.0) / (double)r.S;
@@ -412,78 +426,105 @@ RS_DEV void leaf_b_one(LeafBShared& sm, const NodeRec& r, uint64_t id, Key2 key,
     uint64_t c = 0;
     int attempt = 0;
     bool fail = false;
-    if (threadIdx.x == 0) sm.err = 0;
+    if (tid == 0) sm.err = 0;
     __syncthreads();
     if (rho == 1.0) {
         c = r.S;
         const uint64_t fill = c < kLeafBCap ? c : kLeafBCap;
-        for (uint64_t i = threadIdx.x; i < fill; i += kLeafThreads) sm.pos[i] = i;
+        for (uint64_t i = tid; i < fill; i += NT) sm.pos[i] = (PosT)i;
         __syncthreads();
     } else {
         const double R = 1.0 / dlog1p(-rho, tab);
         for (attempt = 0; attempt < 64; ++attempt) {
-            c = block_walk(key, TAG_LEAF_B + 256u * (uint32_t)attempt, id, R, r.S, sm, tab);
+            c = block_walk<NT>(key, TAG_LEAF_B + 256u * (uint32_t)attempt, id, R, r.S, sm, tab);
             if (sm.err) break;
             if (c >= r.c) break;
         }
         if (sm.err || attempt == 64) {
-            if (threadIdx.x == 0) set_status(status, RS_EITER);
+            if (tid == 0) set_status(status, RS_EITER);
             fail = true;
         }
     }
     if (!fail && c > kLeafBCap) {
-        if (threadIdx.x == 0) set_status(status, RS_ECAPACITY);
+        if (tid == 0) set_status(status, RS_ECAPACITY);
         fail = true;
     }
     if (fail) {
         __syncthreads();
         return;
     }
-    const uint32_t drop = (uint32_t)(c - r.c);
-    Draw<4> dr{Bounded32{c, (uint32_t)(((1ull << 32) - c) % c)}};
-    if (!select_leaf<uint32_t, 4, true>(sm.sel, dr, key, TAG_FIXUP, id, c, drop, status)) {
-        __syncthreads();
-        return;
-    }
+    const uint32_t cc = (uint32_t)c, drop = (uint32_t)(c - r.c);
+    const uint32_t words = (cc + 31) >> 5;
+    for (uint32_t i = tid; i < words; i += NT) sm.drop[i] = 0;
+    if (tid < 3) sm.newcount[tid] = 0;
+    __syncthreads();
+    const LeafRec fr{0, c, drop, 0, id};
+    const bool ok = distinct_rounds<NT, 0>(
+        sm.newcount, fr, lemire_threshold(c), key, TAG_FIXUP, drop, status, tid,
+        [&](uint64_t v) -> uint32_t {
+            const uint32_t bit = 1u << (v & 31);
+            return (atomicOr(&sm.drop[v >> 5], bit) & bit) ? 0u : 1u;
+        },
+        [] { return false; });
+    if (!ok) return;
+    // kept indices: each warp takes a contiguous run of words, one bit per
+    // lane of the current word so that the stores are coalesced
+    auto kept = [&](uint32_t w) {
+        uint32_t bits = ~sm.drop[w];
+        if (w * 32 + 32 > cc) bits &= (1u << (cc & 31)) - 1u;   // beyond the attempt
+        return bits;
+    };
+    const uint32_t per = (words + NW - 1) / NW;
+    const uint32_t w0 = min(warp * per, words), w1 = min(w0 + per, words);
+    uint32_t cnt = 0;
+    for (uint32_t w = w0 + lane; w < w1; w += 32) cnt += __popc(kept(w));
+    cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
+    if (lane == 0) sm.warp_cnt[warp] = cnt;
+    __syncthreads();
+    uint32_t base = 0;
+    for (uint32_t i = 0; i < warp; ++i) base += sm.warp_cnt[i];
     uint64_t* dst = out + r.off;
-    for (uint32_t i = threadIdx.x; i < c; i += kLeafThreads) {
-        const uint32_t below = lower_bound(sm.sel.keys, drop, i);
-        if (below < drop && sm.sel.keys[below] == i) continue;
-        dst[i - below] = r.lo + 1 + sm.pos[i];
+    const uint64_t lo1 = r.lo + 1;
+    for (uint32_t w = w0; w < w1; ++w) {
+        const uint32_t bits = kept(w);
+        if ((bits >> lane) & 1u) dst[base + __popc(bits & ((1u << lane) - 1u))] = lo1 + sm.pos[w * 32 + lane];
+        base += __popc(bits);
     }
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kLeafThreads) leaf_b_kernel(LeafBArgs A) {
+template <typename PosT>
+__global__ void __launch_bounds__(kLeafBThreads) leaf_b_kernel(LeafBArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    LeafBShared& sm = *reinterpret_cast<LeafBShared*>(smem_raw);
+    auto& sm = *reinterpret_cast<LeafBShared<PosT>*>(smem_raw);
     for (uint64_t leaf = blockIdx.x; leaf < A.nleaves; leaf += gridDim.x)
-        leaf_b_one(sm, A.leaves[leaf], A.first_id + leaf, A.key, A.out, A.status, A.tab);
+        leaf_b_one<kLeafBThreads>(sm, A.leaves[leaf], A.first_id + leaf, A.key, A.out, A.status, A.tab);
 }
 
-// Algorithm B leaves of a batch group or of range queries.
+// Algorithm B leaves of a batch group or of range queries (leaf sizes not
+// bounded in advance: 64-bit positions).
 template <class View>
-__global__ void __launch_bounds__(kLeafThreads) group_leaf_b_kernel(View G, const double* tab) {
+__global__ void __launch_bounds__(kLeafBThreads) group_leaf_b_kernel(View G, const double* tab) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    LeafBShared& sm = *reinterpret_cast<LeafBShared*>(smem_raw);
+    auto& sm = *reinterpret_cast<LeafBShared<uint64_t>*>(smem_raw);
     for (uint64_t g = blockIdx.x; g < G.nleaves; g += gridDim.x) {
         const ResolvedLeaf L = resolve_leaf(G, g);
-        leaf_b_one(sm, L.rec, L.id, make_key(L.seed), L.out, L.status, tab);
+        leaf_b_one<kLeafBThreads>(sm, L.rec, L.id, make_key(L.seed), L.out, L.status, tab);
     }
 }
 
 template <class View>
 static cudaError_t launch_group_leaves_b(const View& G, const double* tab, int sms, cudaStream_t st) {
-    const size_t smem = sizeof(LeafBShared);
+    const size_t smem = sizeof(LeafBShared<uint64_t>);
     auto kern = group_leaf_b_kernel<View>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 1;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLeafThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLeafBThreads, smem);
     if (e != cudaSuccess) return e;
     const uint64_t grid = std::min<uint64_t>(G.nleaves, (uint64_t)sms * std::max(per_sm, 1));
     if (grid == 0) return cudaSuccess;
-    kern<<<(unsigned)grid, kLeafThreads, smem, st>>>(G, tab);
+    kern<<<(unsigned)grid, kLeafBThreads, smem, st>>>(G, tab);
     return cudaGetLastError();
 }
 
@@ -497,18 +538,25 @@ cudaError_t launch_batch_leaves_b(const QueryInnerView& G, const double* tab, in
     return launch_group_leaves_b(G, tab, sms, st);
 }
 
-cudaError_t launch_leaves_b(const LeafBLaunch& L, cudaStream_t st) {
-    const size_t smem = sizeof(LeafBShared);
-    cudaError_t e = cudaFuncSetAttribute(leaf_b_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <typename PosT>
+static cudaError_t launch_leaves_b_t(const LeafBLaunch& L, cudaStream_t st) {
+    const size_t smem = sizeof(LeafBShared<PosT>);
+    auto kern = leaf_b_kernel<PosT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, leaf_b_kernel, kLeafThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLeafBThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     LeafBArgs A{L.leaves, L.nleaves, L.first_id, make_key(L.seed), L.out, L.status, L.tab};
     const uint64_t grid = std::min<uint64_t>(L.nleaves, (uint64_t)L.sms * per_sm);
-    leaf_b_kernel<<<(unsigned)grid, kLeafThreads, smem, st>>>(A);
+    kern<<<(unsigned)grid, kLeafBThreads, smem, st>>>(A);
     return cudaGetLastError();
+}
+
+cudaError_t launch_leaves_b(const LeafBLaunch& L, cudaStream_t st) {
+    if (L.smax <= (1ull << 32)) return launch_leaves_b_t<uint32_t>(L, st);
+    return launch_leaves_b_t<uint64_t>(L, st);
 }
 
 }  // namespace rs

@@ -287,7 +287,7 @@ int sample_impl(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0,
         const uint64_t first = j * per_part;
         if (kind == RS_KIND_B) {
             rs::LeafBLaunch LB{ctx->nodes + nleaves + first, per_part, nleaves + first, seed, out, ctx->status,
-                               ctx->sms, ctx->tab};
+                               ctx->sms, ctx->tab, smax};
             ctx->launches += 1;
             rc = cuda_rc(rs::launch_leaves_b(LB, st));
         } else {

@@ -70,6 +70,7 @@ struct LeafBLaunch {
     int* status;
     int sms;
     const double* tab;       // the context's table (its logarithm)
+    uint64_t smax;           // largest leaf size (32-bit positions up to 2^32)
 };
 // Algorithm B leaves (positions of one attempt live in shared memory).
 cudaError_t launch_leaves_b(const LeafBLaunch& L, cudaStream_t st);
