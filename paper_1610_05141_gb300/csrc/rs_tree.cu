@@ -58,13 +58,14 @@ __global__ void __launch_bounds__(kTreeWarps * 32) tree_level_kernel(NodeRec* __
                         tree_logs + warp * 32 * kLogSlots, G);
 }
 
-// Nodes of a small launch: G >= 4 lanes per node, parallel terms and trials.
+// Nodes of a small launch: G >= 4 lanes per node, parallel terms and trials;
+// a warp takes `batch` nodes (a multiple of 32 / G), its groups refilling.
 template <bool WR>
 __global__ void __launch_bounds__(kTreeWarps * 32) tree_terms_kernel(NodeRec* __restrict__ rec, uint64_t first,
-                                                                    uint64_t nodes, uint32_t G, uint64_t seed,
-                                                                    const double* __restrict__ tab, int* status) {
+                                                                    uint64_t nodes, uint32_t batch, uint32_t G,
+                                                                    uint64_t seed, const double* __restrict__ tab,
+                                                                    int* status) {
     const uint32_t warp = threadIdx.x >> 5;
-    const uint32_t batch = 32 / G;
     const uint64_t start = ((uint64_t)blockIdx.x * kTreeWarps + warp) * batch;
     if (start >= nodes) return;
     const uint64_t left = nodes - start;
@@ -101,7 +102,10 @@ static void launch_nodes(NodeRec* rec, uint64_t first, uint64_t nodes, uint64_t 
     const uint32_t G = lanes_per_node(nodes, sms);
     uint32_t batch;
     if (G > 1) {
-        batch = 32 / G;
+        // groups refill from batches of up to four nodes per group while
+        // that leaves about a dozen warps per SM
+        const uint64_t per_sm = nodes * G / ((uint64_t)sms * 12 * 32);
+        batch = (32 / G) * (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(4, per_sm));
     } else {
         uint64_t per = nodes / ((uint64_t)sms * 2 * kTreeWarps);
         per = std::max<uint64_t>(32, std::min<uint64_t>(kTreeBatch, per & ~31ull));
@@ -110,8 +114,8 @@ static void launch_nodes(NodeRec* rec, uint64_t first, uint64_t nodes, uint64_t 
     const uint64_t warps = (nodes + batch - 1) / batch;
     const unsigned blocks = (unsigned)((warps + kTreeWarps - 1) / kTreeWarps);
     if (G >= 4) {
-        if (wr) tree_terms_kernel<true><<<blocks, kTreeWarps * 32, 0, st>>>(rec, first, nodes, G, seed, tab, status);
-        else tree_terms_kernel<false><<<blocks, kTreeWarps * 32, 0, st>>>(rec, first, nodes, G, seed, tab, status);
+        if (wr) tree_terms_kernel<true><<<blocks, kTreeWarps * 32, 0, st>>>(rec, first, nodes, batch, G, seed, tab, status);
+        else tree_terms_kernel<false><<<blocks, kTreeWarps * 32, 0, st>>>(rec, first, nodes, batch, G, seed, tab, status);
     } else if (wr) {
         tree_level_kernel<true><<<blocks, kTreeWarps * 32, smem, st>>>(rec, first, nodes, batch, G, seed, tab, status);
     } else {

@@ -338,11 +338,13 @@ RS_DEV void tree_batch_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
     }
 }
 
-// Nodes v0 .. v0+count-1 (count <= 32 / G) with G lanes per node, G a
-// multiple of 4: lane 4p + j of a node's group evaluates term j of trial
-// t + p (terms: the four differences of ln x! of the hypergeometric test, or
-// the two of the binomial one).  All lanes compute ln U; the four lanes of a
-// trial exchange their terms and reach the same decision.
+// Nodes v0 .. v0+count-1 with G lanes per node, G a multiple of 4: lane
+// 4p + j of a node's group evaluates term j of trial t + p (terms: the four
+// differences of ln x! of the hypergeometric test, or the two of the
+// binomial one).  All lanes compute ln U; the four lanes of a trial exchange
+// their terms and reach the same decision.  The warp's 32 / G groups take the
+// nodes in order and a group whose node is done takes the next one, so that
+// the trial counts of a few nodes do not idle the rest of the warp.
 template <bool WR>
 RS_DEV void tree_terms_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t count, Key2 key,
                             const double* __restrict__ tab, int* status, uint32_t G) {
@@ -351,14 +353,28 @@ RS_DEV void tree_terms_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
     const uint32_t gbase = lane - r;
     const uint32_t gmask = G == 32 ? 0xFFFFFFFFu : ((1u << G) - 1u) << gbase;
     const uint32_t p = r >> 2, j = r & 3u, tbase = lane & ~3u;
-    const uint32_t grp = lane / G;
     RouNode q;
-    bool active = grp < count &&
-                  node_setup<WR>(rec, v0 + grp, key, tab, status, &q, r == 0);
-    // this lane's fixed end (term j) and its logarithm, once per node
-    const uint64_t P = active ? fixed_end<WR>(q, (int)j) : 0;
-    const double lnP = log_fixed(P, tab);
-    while (__ballot_sync(0xFFFFFFFFu, active)) {
+    bool active = false;   // the same in all lanes of a group
+    uint32_t next = 0;     // batch cursor (warp-uniform)
+    uint64_t P = 0;        // this lane's fixed end (term j) and its logarithm, once per node
+    double lnP = 0.0;
+    for (;;) {
+        // free groups take the next nodes, in order
+        for (;;) {
+            const uint32_t freem = __ballot_sync(0xFFFFFFFFu, !active && r == 0);
+            if (freem == 0 || next >= count) break;
+            const uint32_t take = min((uint32_t)__popc(freem), count - next);
+            const uint32_t rank = __popc(freem & ((1u << gbase) - 1u));
+            if (!active && rank < take) {
+                active = node_setup<WR>(rec, v0 + next + rank, key, tab, status, &q, r == 0);
+                if (active) {
+                    P = fixed_end<WR>(q, (int)j);
+                    lnP = log_fixed(P, tab);
+                }
+            }
+            next += take;
+        }
+        if (__ballot_sync(0xFFFFFFFFu, active) == 0) break;
         const uint64_t t = (uint64_t)q.trial + p;
         double U = 1.0, T = 0.0, term = 0.0;
         uint64_t k = 0;
