@@ -393,6 +393,11 @@ RS_DEV uint32_t rank_keys(const KeyT* B, KeyT* A, const uint16_t* ch, uint32_t k
                           uint64_t* __restrict__ dst, uint32_t tid) {
     constexpr uint32_t U = 4;   // keys per thread at a time, so that their load chains overlap
     uint32_t rsum = 0;
+    // (key, position) order; 32-bit keys compare as one 64-bit value
+    auto before = [](KeyT y, uint32_t j, KeyT x, uint32_t i) {
+        if (sizeof(KeyT) == 4) return (((uint64_t)y << 32) | j) < (((uint64_t)x << 32) | i);
+        return (y < x) || (y == x && j < i);
+    };
     // `full` tiles need no bounds tests
     auto tile = [&](uint32_t i0, auto full_tag) {
         constexpr bool full = decltype(full_tag)::value;
@@ -418,7 +423,7 @@ RS_DEV uint32_t rank_keys(const KeyT* B, KeyT* A, const uint16_t* ch, uint32_t k
                 const uint32_t j = s0[q] + u;
                 const KeyT y = B[j];
                 if (!TIES) rank[q] += y < x[q] ? 1u : 0u;
-                else rank[q] += ((y < x[q]) || (y == x[q] && j < i0 + q * NT)) ? 1u : 0u;
+                else rank[q] += before(y, j, x[q], i0 + q * NT) ? 1u : 0u;
             }
         }
         // buckets of more than four keys: one loop for the U keys, reads
@@ -432,7 +437,7 @@ RS_DEV uint32_t rank_keys(const KeyT* B, KeyT* A, const uint16_t* ch, uint32_t k
                 const uint32_t j = min(s0[q] + 4 + e, k + 2);
                 const KeyT y = B[j];
                 if (!TIES) rank[q] += y < x[q] ? 1u : 0u;
-                else rank[q] += ((y < x[q]) || (y == x[q] && j < i0 + q * NT)) ? 1u : 0u;
+                else rank[q] += before(y, j, x[q], i0 + q * NT) ? 1u : 0u;
             }
         }
 #pragma unroll
