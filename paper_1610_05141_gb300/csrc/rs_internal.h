@@ -8,9 +8,6 @@
 
 namespace rs {
 
-// Largest leaf selection of the shared-memory counting-sort machinery
-// (leaf B's repair step).
-constexpr uint32_t kLeafCap = 8192;
 // Largest leaf selection of the shared-memory table of leaf H / leaf WR.
 constexpr uint32_t kLeafFastCap = 4864;
 // Largest selection the general (global-memory) leaf path accepts.
