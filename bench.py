@@ -518,6 +518,18 @@ def run_serve(rs, ctx, stream, args):
     }
 
 
+def combine_over_ranks(dist, ms_per_step, e2e_step, launches, device):
+    """Replicas: the job's step time is the slowest rank's (max), its launch
+    count the sum over ranks."""
+    import torch
+    t = torch.tensor([ms_per_step, e2e_step], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    lt = torch.tensor([launches], dtype=torch.int64, device=device)
+    dist.all_reduce(lt)
+    ms, e2e = t.tolist()
+    return ms, e2e, int(lt.item())
+
+
 def run_ours(args):
     import torch
     import paper_1610_05141_gb300 as rs
@@ -613,12 +625,7 @@ def run_ours(args):
     ms_per_step = ms_total / args.steps
     e2e_step = max(e2e_ms, e2e_wall_ms)
     if dist is not None:
-        t = torch.tensor([ms_per_step, e2e_step], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_per_step, e2e_step = t.tolist()
-        lt = torch.tensor([launches], dtype=torch.int64, device="cuda")
-        dist.all_reduce(lt)
-        launches = int(lt.item())
+        ms_per_step, e2e_step, launches = combine_over_ranks(dist, ms_per_step, e2e_step, launches, "cuda")
     value = world * N_SAMPLES / (ms_per_step / 1000)
     leaf_avg_ms = leaf_ms / calls
     peak, peak_kind = hbm_peak()
@@ -673,7 +680,7 @@ def main():
     ap.add_argument("--serve-capacity-jobs", type=int, default=4000)
     ap.add_argument("--serve-unbatched-jobs", type=int, default=1000)
     ap.add_argument("--serve-arena-gb", type=int, default=64)
-    ap.add_argument("--n", type=int, default=None, help="smaller n (profiling cases only)")
+    ap.add_argument("--n", "--n-samples", dest="n", type=int, default=None, help="smaller n (profiling cases only)")
     ap.add_argument("--log2N", type=int, default=None, help="smaller universe 2^log2N (profiling cases only)")
     ap.add_argument("--n0", type=int, default=None, help="other leaf size (profiling cases only)")
     ap.add_argument("--pipeline", default=None,
