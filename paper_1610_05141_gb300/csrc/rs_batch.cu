@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kBatchTreeWarps * 32) batch_terms_kernel(const
 // Leaf H / leaf WR over the leaves of a view, one block per leaf at a time;
 // leaves the shared-memory table cannot take go to the overflow list.
 template <typename KeyT, bool WR, class View>
-__global__ void __launch_bounds__(kBatchLeafThreads) group_leaf_kernel(View G, uint32_t* ovf_list,
+__global__ void __launch_bounds__(kBatchLeafThreads, 4) group_leaf_kernel(View G, uint32_t* ovf_list,
                                                                        uint32_t* ovf_count, uint32_t cap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto& sm = *reinterpret_cast<HashShared<KeyT, kBatchLeafThreads / 32>*>(smem_raw);

@@ -469,6 +469,75 @@ RS_COLD bool bucket_ties(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, K
     return bucket_repair<KeyT, NT, BAR, CAP>(sm, r, key, k, thr, A, B, dst, tid);   // rewrites the whole leaf
 }
 
+// Pass 1 of the bucket path for leaves with void candidates (sizes that are
+// not powers of two): the first k valid candidates to A[0..k), counted per
+// bucket, sm.jnext set to the index after the k-th.  Rounds of up to q Philox
+// blocks per thread, contiguous so that a thread's candidates are in index
+// order: the values are staged in B (not yet in use), one block scan numbers
+// the valid ones in index order, and the first k are kept.  A round covers
+// the missing values plus an eighth, within B's room, so most leaves need one
+// round and one scan.  False if the stream runs out.
+template <typename KeyT, int NT, int BAR, uint32_t CAP, typename K2>
+RS_COLD bool void_leaf_pass1(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, const K2& key, uint32_t tag,
+                             uint32_t k, uint64_t thr, uint64_t mult, KeyT* A, KeyT* B, uint32_t* cw, uint32_t tid) {
+    auto keep = [&](uint32_t j, uint64_t v) {
+        A[j] = (KeyT)v;
+        const uint32_t b = hash_slot((KeyT)v, mult);
+        atomicAdd(&cw[b >> 1], 1u << ((b & 1u) << 4));
+    };
+    const bool w32 = r.s <= (1ull << 32);
+    const uint32_t cpb = w32 ? 4u : 2u;
+    const uint32_t qmax = 32u / cpb;   // a thread's candidates fit one 32-bit mask
+    const uint32_t room = HashShared<KeyT, NT / 32, CAP>::kSlots - ((k + 3) & ~3u);
+    uint32_t got = 0;
+    for (uint64_t b0 = 0; got < k;) {
+        if (b0 >= (1ull << 32)) return false;   // the stream ran out: the probing path reports it
+        const uint32_t m = k - got;
+        const uint32_t want = (m + m / 8 + 32 + cpb - 1) / cpb;
+        const uint32_t nbk = min(want, min(room / cpb, (uint32_t)NT * qmax));
+        const uint32_t q = (nbk + NT - 1) / NT;
+        const uint32_t t0 = tid * q;   // this thread's first block of the round
+        uint32_t mask = 0;
+        for (uint32_t u = 0; u < q; ++u) {
+            const uint64_t blk = b0 + t0 + u;
+            if (t0 + u >= nbk || blk >= (1ull << 32)) break;
+            const uint4 w = philox_block((uint32_t)blk, tag, r.id, key);
+            const uint32_t rel = (t0 + u) * cpb;
+            if (w32) {
+                const uint32_t s32 = (uint32_t)(r.s - 1), thr32 = (uint32_t)thr;
+                const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const uint64_t prod = (uint64_t)ws[c] * s32 + ws[c];   // w * s, exact
+                    B[rel + c] = (KeyT)(prod >> 32);
+                    mask |= ((uint32_t)prod >= thr32 ? 1u : 0u) << (u * 4 + c);
+                }
+            } else {
+                const uint64_t xs[2] = {((uint64_t)w.y << 32) | w.x, ((uint64_t)w.w << 32) | w.z};
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    B[rel + c] = (KeyT)__umul64hi(xs[c], r.s);
+                    mask |= (xs[c] * r.s >= thr ? 1u : 0u) << (u * 2 + c);
+                }
+            }
+        }
+        uint32_t total;
+        uint32_t rank = got + block_exclusive_scan<NT>((uint32_t)__popc(mask), sm.scan_tmp, &total);
+        while (mask && rank < k) {
+            const uint32_t p = (uint32_t)__ffs(mask) - 1u;
+            mask &= mask - 1u;
+            const uint32_t rel = t0 * cpb + p;
+            keep(rank, B[rel]);
+            if (rank == k - 1) sm.jnext = b0 * cpb + rel + 1;
+            ++rank;
+        }
+        got += total;
+        b0 += nbk;
+        if (got < k) group_sync<BAR, NT>();   // the next round stages over other threads' slots
+    }
+    return true;
+}
+
 // Bucket path.  Returns true on success (leaf written), false if the leaf
 // must take the probing path (whatever was written is overwritten later).
 // K2 is Key2 or RoundKeys (the same generator, round keys precomputed).
@@ -484,10 +553,6 @@ RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, co
     const uint16_t* ch = reinterpret_cast<const uint16_t*>(cw);   // ch[-1] = 0, the high half of cnt[3]
     for (uint32_t i = tid; i < nb / 8; i += NT) reinterpret_cast<uint4*>(cw)[i] = make_uint4(0, 0, 0, 0);
     if (tid == 0) sm.cnt[3] = 0;
-    // B[k .. k+3) hold the largest key value: the rank pass's window of four
-    // may run past the end of the leaf, and reads past a key's bucket meet
-    // only larger keys (buckets are monotone in the key) or these
-    if (tid < 3) B[k + tid] = ~KeyT(0);
     if (tid == 0) {   // once per leaf; the last reads of these fields came before the last barrier
         sm.mult = slot_mult_fast<KeyT>(r.s, nb);
         sm.thr = lemire_threshold(r.s);
@@ -551,49 +616,16 @@ RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, co
         if (tid == 0) sm.jnext = k;
         group_sync<BAR, NT>();
     } else {
-        // rounds of one Philox block per thread: the valid candidates of a
-        // round are numbered in index order by a block scan; the first k kept
-        const bool w32 = r.s <= (1ull << 32);
-        uint32_t got = 0;
-        for (uint64_t b0 = 0; got < k; b0 += NT) {
-            if (b0 >= (1ull << 32)) return false;   // the stream ran out: the probing path reports it
-            const uint64_t blk = b0 + tid;
-            uint64_t v[4] = {0, 0, 0, 0};
-            uint32_t valid = 0;
-            if (blk < (1ull << 32)) {
-                const uint4 w = philox_block((uint32_t)blk, tag, r.id, key);
-                if (w32) {
-                    const uint32_t s32 = (uint32_t)(r.s - 1), thr32 = (uint32_t)thr;
-                    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const uint64_t prod = (uint64_t)ws[c] * s32 + ws[c];   // w * s, exact
-                        v[c] = prod >> 32;
-                        valid |= ((uint32_t)prod >= thr32 ? 1u : 0u) << c;
-                    }
-                } else {
-                    const uint64_t xs[2] = {((uint64_t)w.y << 32) | w.x, ((uint64_t)w.w << 32) | w.z};
-#pragma unroll
-                    for (int c = 0; c < 2; ++c) {
-                        v[c] = __umul64hi(xs[c], r.s);
-                        valid |= (xs[c] * r.s >= thr ? 1u : 0u) << c;
-                    }
-                }
-            }
-            uint32_t total;
-            uint32_t rank = got + block_exclusive_scan<NT>((uint32_t)__popc(valid), sm.scan_tmp, &total);
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                if ((valid >> c) & 1u) {
-                    if (rank < k) keep(rank, v[c]);
-                    if (rank == k - 1) sm.jnext = blk * (w32 ? 4 : 2) + c + 1;
-                    ++rank;
-                }
-            }
-            got += total;
-        }
+        // leaves with void candidates: a call of its own (its registers stay
+        // out of the power-of-two path)
+        if (!void_leaf_pass1<KeyT, NT, BAR, CAP>(sm, r, key, tag, k, thr, mult, A, B, cw, tid)) return false;
         group_sync<BAR, NT>();
     }
+    // B[k .. k+3) hold the largest key value (after pass 1, which may stage
+    // candidates there): the rank pass's window of four may run past the end
+    // of the leaf, and reads past a key's bucket meet only larger keys
+    // (buckets are monotone in the key) or these
+    if (tid < 3) B[k + tid] = ~KeyT(0);
     scan_counts16<NT>(cw, nb, sm.scan_tmp, tid);   // half b = first position of bucket b
     // Passes 2 and 3 take four independent keys per thread at a time so
     // that their load -> address -> load chains overlap.
