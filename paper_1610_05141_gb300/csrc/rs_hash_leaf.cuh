@@ -20,9 +20,10 @@
 //    its output position, and is written there.  Equal keys share a rank and
 //    so lower the sum of the ranks: a second run then breaks the ties by
 //    position.  When the leaf size does not divide 2^32 (2^64)
-//    some candidates are void: candidates are then generated one Philox
-//    block per thread at a time and the valid ones numbered in index order
-//    with a block scan, so that exactly the first k valid ones are kept.  If
+//    some candidates are void: each thread then generates a contiguous run
+//    of Philox blocks, staged in shared memory, and one block scan numbers
+//    the valid ones in index order, so that exactly the first k valid ones
+//    are kept.  If
 //    a key repeats (without replacement), the distinct values are kept and
 //    one warp draws the missing ones from the following candidates, each
 //    tested against the set (binary search) and against its batch, so that
