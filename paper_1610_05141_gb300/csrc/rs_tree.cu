@@ -102,12 +102,13 @@ static void launch_nodes(NodeRec* rec, uint64_t first, uint64_t nodes, uint64_t 
     const uint32_t G = lanes_per_node(nodes, sms);
     uint32_t batch;
     if (G > 1) {
-        // groups refill from batches of up to four nodes per group while
-        // that leaves about a dozen warps per SM
-        const uint64_t per_sm = nodes * G / ((uint64_t)sms * 12 * 32);
-        batch = (32 / G) * (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(4, per_sm));
+        // groups refill from batches of up to eight nodes per group while
+        // that leaves about six warps per SM (measured best on GB300: the
+        // longer the batch, the less the last nodes' trials idle the warp)
+        const uint64_t per_sm = nodes * G / ((uint64_t)sms * 6 * 32);
+        batch = (32 / G) * (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(8, per_sm));
     } else {
-        uint64_t per = nodes / ((uint64_t)sms * 2 * kTreeWarps);
+        uint64_t per = nodes / ((uint64_t)sms * kTreeWarps);   // one block per SM before the cap
         per = std::max<uint64_t>(32, std::min<uint64_t>(kTreeBatch, per & ~31ull));
         batch = (uint32_t)std::min<uint64_t>(per, nodes);
     }
