@@ -12,7 +12,7 @@
 // Three ways to compute them, all with the same result:
 //
 //  bucket path (the common case): candidates [0, k) are generated once,
-//    kept in shared memory and counted per bucket (about one key per bucket
+//    kept in shared memory and counted per bucket (about 3/4 of a key per bucket
 //    on average, addressed by the top bits; 16-bit counts, no size limit).
 //    A scan of the counts gives every bucket its output offset; a second
 //    pass scatters the keys into bucket order; each key then finds its rank
@@ -73,7 +73,7 @@ struct HashShared {
     static constexpr uint32_t kCap = CAP;
     static constexpr uint32_t kSlots = 2 * CAP + kHashSlack;
     static constexpr uint32_t kBits = 32 * kSlots;        // largest leaf range of the bitmap path
-    static constexpr uint32_t kBuckets = CAP + 64;        // bucket path: about one key per bucket
+    static constexpr uint32_t kBuckets = CAP + 64;        // bucket path: at most this many buckets
     KeyT tab[kSlots];              // bucket path: keys (first k + 3), then keys in bucket order;
                                    // probing table; bitmap; tallies
     alignas(16) uint32_t cnt[kBuckets / 2 + 5];   // bucket path: word 3 is zero; from word 4 on, 16-bit
@@ -547,7 +547,9 @@ RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, co
                         uint64_t* __restrict__ dst, uint32_t tid) {
     static_assert(HashShared<KeyT, NT / 32, CAP>::kBuckets <= 24 * NT, "scan_counts16 takes at most 24 NT counts");
     const uint32_t tag = WR ? TAG_LEAF_WR : TAG_LEAF_H;
-    const uint32_t nb = max(64u, (k + 63) & ~63u);   // a multiple of 64, <= kBuckets
+    // buckets: about 3/4 of a key each (measured best on GB300 among 7/8 to
+    // 2 keys per bucket), a multiple of 64, at most kBuckets
+    const uint32_t nb = min(HashShared<KeyT, NT / 32, CAP>::kBuckets, max(64u, (k * 4 / 3 + 63) & ~63u));
     KeyT* A = sm.tab;                     // candidate j at A[j]; later the sorted leaf
     KeyT* B = sm.tab + ((k + 3) & ~3u);   // keys in bucket order
     uint32_t* cw = sm.cnt + 4;            // count of bucket b: 16-bit half b & 1 of word b >> 1
