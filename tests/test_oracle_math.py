@@ -182,10 +182,11 @@ def test_lf_accuracy(oracle):
 
 def test_lfdiff_accuracy(oracle):
     """ln x! - ln y! to a relative error below 1e-13 of the difference, for
-    every branch: table, short sums, small y, and the cancellation-free form
+    every branch: table, small y, and the cancellation-free form (short differences included)
     at x, y up to 2^62 (where a plain difference of ln x! would lose it)."""
     rng = np.random.default_rng(5)
-    pairs = [(5, 5), (10, 3), (255, 0), (300, 295), (300, 292), (300, 291), (1000, 255), (1000, 10)]
+    pairs = [(5, 5), (10, 3), (255, 0), (300, 295), (300, 292), (300, 291), (1000, 255), (1000, 10),
+             (257, 256), (10**6 + 1, 10**6), (10**6 + 8, 10**6), (2**40 + 1, 2**40), (2**61 + 3, 2**61)]
     for _ in range(600):
         y = int(np.exp(rng.uniform(0, math.log(2**61))))
         d = int(np.exp(rng.uniform(0, math.log(max(2, min(y, 2**40))))))
