@@ -312,9 +312,10 @@ def run_rows(rs, ctx, stream, args):
     """The other rows of the method at their configurations' sizes: sampling
     with replacement (n = 1e9 from 2^40, binomial splits), Algorithm B as the
     base case (n = 1e9 from 2^50), and Bernoulli sampling of 2^36 positions
-    with p = 1e-4 and 1e-2 (whole range) and p = 0.5 (a chunk-aligned window
-    of 2^30 positions: the whole output would be 275 GB).  Device-timed
-    (CUDA events on the stream), a few steps each after one warm-up call."""
+    with p = 1e-4 and 1e-2 (whole range in one call) and p = 0.5 (the whole
+    range as 8 chunk-aligned windows of 2^33 positions into one reusable
+    34 GB buffer: the whole output would be 275 GB).  Device-timed (CUDA
+    events on the stream), a few steps each after one warm-up call."""
     import torch
     peak, _ = hbm_peak()
     out = {}
@@ -344,21 +345,36 @@ def run_rows(rs, ctx, stream, args):
                      "samples_per_s": 1e9 / (ms / 1000), "phases_ms": {"split_tree": tree_ms / calls, "leaves": leaf},
                      "leaf_write_gbs": 8e9 / (leaf / 1000) / 1e9, "leaf_frac_of_hbm": 8e9 / (leaf / 1000) / 1e9 / peak}
     bern = {}
-    for p, a, b in ((1e-4, 0, 2**36), (1e-2, 0, 2**36), (0.5, 0, 2**30)):
+    for p, windows, steps in ((1e-4, 1, args.row_steps), (1e-2, 1, args.row_steps), (0.5, 8, 2)):
+        if windows > 1:   # p = 0.5: a 34 GB buffer reused by every window, and room to stage its positions
+            del buf
+            torch.cuda.empty_cache()
+            buf = torch.empty((1 << 32) + (1 << 20), dtype=torch.int64, device="cuda")
+            rs.rs_set_bernoulli_staging(ctx, 48 << 30)
         cap = buf.numel()
-        holder = {}
+        width = 2**36 // windows
+        holder = {"rc": rs.RS_OK, "count": 0}
 
         def call_b():
-            holder["rc"], holder["count"] = rs.rs_bernoulli(ctx, p, 2**36, 5, N0, a, b, buf, cap, stream, check=False)
+            total = 0
+            for w in range(windows):
+                rc, c = rs.rs_bernoulli(ctx, p, 2**36, 5, N0, w * width, (w + 1) * width, buf, cap, stream,
+                                        check=False)
+                if rc != rs.RS_OK:
+                    holder["rc"] = rc
+                total += c
+            holder["count"] = total
 
-        ms = timed(call_b, args.row_steps)
+        ms = timed(call_b, steps)
         if holder["rc"] != rs.RS_OK:
             raise RuntimeError(f"bernoulli p={p} failed: {holder['rc']}")
         cnt = holder["count"]
-        bern[f"p={p:g}"] = {"positions": b - a, "window": [a, b], "emitted": cnt, "ms_per_call": ms,
-                            "emitted_per_s": cnt / (ms / 1000), "positions_per_s": (b - a) / (ms / 1000),
+        bern[f"p={p:g}"] = {"positions": 2**36, "windows": windows, "emitted": cnt, "ms_per_call": ms,
+                            "emitted_per_s": cnt / (ms / 1000), "positions_per_s": 2**36 / (ms / 1000),
                             "write_gbs": 8 * cnt / (ms / 1000) / 1e9,
-                            "note": "whole call: count pass, scan, write pass, and the count read back"}
+                            "note": "whole range: per window one walk with staged positions, the scan of the "
+                                    "counts, the copy into place, and the count read back"}
+    rs.rs_set_bernoulli_staging(ctx)
     out["a6_bernoulli"] = {"N": 2**36, "n0": N0, "by_p": bern}
     del buf
     return out
