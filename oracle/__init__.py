@@ -91,6 +91,8 @@ def _load():
             "or_range_query": (i32, [u64, u64, u64, u32, i32, u64, u64, p64, u64, p64]),
             "or_bern_chunk_log2": (i32, [dbl, u32]),
             "or_bernoulli": (i32, [dbl, u64, u64, u32, u64, u64, p64, u64, p64]),
+            "or_bernoulli_size": (i32, [dbl, u64, u64, p64]),
+            "or_bernoulli_by_size": (i32, [dbl, u64, u64, u32, u64, u64, p64, u64, p64, p64]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -284,6 +286,28 @@ def bernoulli(p, N, seed, n0, a=0, b=None, cap=None):
     rc = _load().or_bernoulli(p, N, seed, n0, a, b, _p64(out), cap, ctypes.byref(cnt))
     _check(rc, "bernoulli")
     return out[: int(cnt.value)]
+
+
+def bernoulli_size(p, N, seed):
+    """BIN(N, p) deviate: the size of the Bernoulli sample drawn by its size."""
+    cnt = ctypes.c_uint64(0)
+    _check(_load().or_bernoulli_size(p, N, seed, ctypes.byref(cnt)), "bernoulli_size")
+    return int(cnt.value)
+
+
+def bernoulli_by_size(p, N, seed, n0, a=0, b=None, cap=None):
+    """1-based positions of the Bernoulli(p) sample of [0, N) drawn by its
+    size (a BIN(N, p) count, then that many positions without replacement),
+    within [a, b); returns (positions, total size)."""
+    if b is None:
+        b = N
+    if cap is None:
+        cap = int((b - a) * p + 20 * ((b - a) * p) ** 0.5 + 100)
+    out = np.zeros(max(cap, 1), dtype=np.uint64)
+    cnt, tot = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    rc = _load().or_bernoulli_by_size(p, N, seed, n0, a, b, _p64(out), cap, ctypes.byref(cnt), ctypes.byref(tot))
+    _check(rc, "bernoulli_by_size")
+    return out[: int(cnt.value)], int(tot.value)
 
 
 def bernoulli_rc(p, N, seed, n0, a, b, cap):

@@ -898,3 +898,47 @@ int or_bernoulli(double p, uint64_t N, uint64_t seed, uint32_t n0, uint64_t a, u
     *count = sink.got;
     return sink.got > cap ? OR_ECAPACITY : OR_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Bernoulli sampling by its size (Sec. 4.7, relation to Bernoulli          */
+/* sampling): the number of chosen positions follows BIN(N, p); drawing it  */
+/* first and then that many positions without replacement gives a          */
+/* Bernoulli(p) sample with no logarithm per position.                      */
+/* ------------------------------------------------------------------------ */
+
+/* The size: BIN(N, p) as the binomial deviate of stream (SPLIT, 0) -- a node
+ * id the split tree never uses.  Reading: p is taken as K / 2^62 with
+ * K = floor(p 2^62 + 1/2) (p 2^62 is exact in double; the rounding changes p
+ * by at most 2^-63); for p > 1/2 the size is N - BIN(N, K'/2^62) with K'
+ * from 1 - p (exact for p in [1/2, 1]), as or_bin takes K/S <= 1/2. */
+int or_bernoulli_size(double p, uint64_t N, uint64_t seed, uint64_t* count)
+{
+    *count = 0;
+    if (!(p >= 0.0 && p <= 1.0) || N > (1ull << 62)) return OR_EINVAL;
+    int flip = p > 0.5;
+    double q = flip ? 1.0 - p : p;
+    uint64_t K = (uint64_t)floor(q * 0x1p62 + 0.5);
+    uint64_t c = 0;
+    int rc = or_bin(seed, 0, N, K, 1ull << 62, &c);
+    if (rc) return rc;
+    *count = flip ? N - c : c;
+    return OR_OK;
+}
+
+/* The sample: the or_bernoulli_size positions drawn without replacement
+ * (or_sample, kind H, the same seed; the tree's nodes use ids from 1), as
+ * 1-based positions, restricted to the window [a, b) of 0-based positions
+ * (any ends) as a range query of that sample.  *total receives the size. */
+int or_bernoulli_by_size(double p, uint64_t N, uint64_t seed, uint32_t n0, uint64_t a, uint64_t b,
+                         uint64_t* out, uint64_t cap, uint64_t* count, uint64_t* total)
+{
+    *count = 0;
+    *total = 0;
+    if (n0 == 0 || a > b || b > N) return OR_EINVAL;
+    uint64_t n = 0;
+    int rc = or_bernoulli_size(p, N, seed, &n);
+    if (rc) return rc;
+    *total = n;
+    return or_range_query(n, N, seed, n0, 0, a + 1, b + 1, out, cap, count);
+}
+

@@ -82,3 +82,54 @@ def test_huge_universe_tiny_p(oracle):
     s = oracle.bernoulli(p, N, 5, 4096).astype(object)
     assert abs(len(s) - N * p) < 6 * math.sqrt(N * p)
     assert all(b > a for a, b in zip(s, s[1:])) and s[0] >= 1 and s[-1] <= N
+
+
+# ---- Bernoulli sampling by its size (Sec. 4.7, relation to Bernoulli sampling) ----
+
+@pytest.mark.parametrize("p,N", [(0.3, 20), (0.05, 40), (0.8, 15)])
+def test_size_is_binomial_exactly(oracle, p, N):
+    """The size of the sample is BIN(N, p): chi-square against the exact pmf
+    over 6000 seeds (p > 1/2 through the complement)."""
+    runs = 6000
+    sizes = np.array([oracle.bernoulli_size(p, N, s) for s in range(1, runs + 1)])
+    pmf = stats.binom.pmf(np.arange(N + 1), N, p)
+    keep = pmf * runs >= 5
+    obs = np.bincount(sizes, minlength=N + 1)
+    o = np.append(obs[keep], obs[~keep].sum())
+    e = np.append(pmf[keep] * runs, pmf[~keep].sum() * runs)
+    if e[-1] < 1e-9:
+        o, e = o[:-1], e[:-1]
+    chi2 = ((o - e) ** 2 / e).sum()
+    assert stats.chi2.sf(chi2, len(o) - 1) > 1e-4, (p, N, chi2)
+
+
+def test_size_moments_at_large_n(oracle):
+    """Mean and variance of BIN(2^40, 1e-3) over 400 seeds (ratio-of-uniforms
+    branch), and the degenerate p."""
+    N, p, runs = 2**40, 1e-3, 400
+    x = np.array([oracle.bernoulli_size(p, N, s) for s in range(1, runs + 1)], dtype=float)
+    mu, var = N * p, N * p * (1 - p)
+    assert abs(x.mean() - mu) < 5 * math.sqrt(var / runs)
+    assert 0.7 < x.var(ddof=1) / var < 1.4
+    assert oracle.bernoulli_size(0.0, 1000, 3) == 0 and oracle.bernoulli_size(1.0, 1000, 3) == 1000
+
+
+def test_by_size_positions(oracle):
+    """Each position is taken with probability p (chi-square over 2000
+    seeds), positions increase strictly inside 1..N, the window is a slice
+    of the whole, and the full window holds the whole size."""
+    p, N, runs = 0.3, 40, 2000
+    hits = np.zeros(N)
+    for s in range(1, runs + 1):
+        pos, tot = oracle.bernoulli_by_size(p, N, s, 4)
+        assert len(pos) == tot and np.all(np.diff(pos.astype(np.int64)) > 0) and (len(pos) == 0 or pos[0] >= 1)
+        hits[pos.astype(np.int64) - 1] += 1
+    e = runs * p
+    chi2 = (((hits - e) ** 2) / (e * (1 - p))).sum()
+    assert stats.chi2.sf(chi2, N) > 1e-4
+    full, tot = oracle.bernoulli_by_size(0.01, 10**7 + 3, 9, 1024)
+    assert len(full) == tot and abs(tot - 1e5) < 6 * math.sqrt(1e5)
+    for a, b in [(0, 12345), (777, 10**6 + 1), (5 * 10**6, 10**7 + 3), (10, 10)]:
+        got, tot2 = oracle.bernoulli_by_size(0.01, 10**7 + 3, 9, 1024, a, b)
+        assert tot2 == tot
+        assert np.array_equal(got, full[(full >= a + 1) & (full < b + 1)]), (a, b)
