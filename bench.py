@@ -376,6 +376,38 @@ def run_rows(rs, ctx, stream, args):
                                     "counts, the copy into place, and the count read back"}
     rs.rs_set_bernoulli_staging(ctx)
     out["a6_bernoulli"] = {"N": 2**36, "n0": N0, "by_p": bern}
+    # the next row (f2): Bernoulli sampling by its size (Sec. 4.7) -- the
+    # BIN(N, p) size, then the sample without replacement of that size; p =
+    # 0.5 as a resident split tree and 8 window queries into the same buffer
+    cap = buf.numel()
+    by_size = {}
+    for p, windows, steps in ((1e-4, 1, args.row_steps), (1e-2, 1, args.row_steps), (0.5, 8, 2)):
+        holder = {"count": 0}
+
+        def call_s():
+            if windows == 1:
+                rc, cnt, _ = rs.rs_bernoulli_by_size(ctx, p, 2**36, 5, N0, 0, 2**36, buf, cap, stream)
+                holder["count"] = cnt
+                return
+            n = rs.rs_bernoulli_size(ctx, p, 2**36, 5, stream)
+            tree = rs.rs_tree_create(ctx, n, 2**36, 5, N0, rs.RS_KIND_H, stream)
+            width = 2**36 // windows
+            total = 0
+            for w in range(windows):
+                _, c = rs.rs_tree_query(tree, w * width + 1, (w + 1) * width + 1, buf, cap, stream)
+                total += c
+            tree.close()
+            holder["count"] = total
+
+        ms = timed(call_s, steps)
+        if rs.rs_sync(ctx, stream) != rs.RS_OK:
+            raise RuntimeError(f"bernoulli by size p={p} failed")
+        cnt = holder["count"]
+        by_size[f"p={p:g}"] = {"positions": 2**36, "windows": windows, "emitted": cnt, "ms_per_call": ms,
+                               "emitted_per_s": cnt / (ms / 1000), "write_gbs": 8 * cnt / (ms / 1000) / 1e9,
+                               "note": "whole call: the size (read back), then rs_sample of that size, or the "
+                                       "split tree and one range query per window"}
+    out["f2_bernoulli_by_size"] = {"N": 2**36, "n0": N0, "by_p": by_size}
     del buf
     return out
 

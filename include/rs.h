@@ -337,6 +337,32 @@ int rs_phase_totals(rs_ctx* ctx, double* tree_ms, double* leaf_ms, uint64_t* cal
  * Errors: RS_EINVAL (log2_parts outside 0..6, negative blocks). */
 int rs_set_pipeline(rs_ctx* ctx, int log2_parts, int leaf_blocks_per_sm);
 
+/* Bernoulli sampling by its size (Sec. 4.7, relation to Bernoulli sampling:
+ * the number of chosen positions follows BIN(N, p); drawing it first and
+ * then that many positions without replacement needs no logarithm per
+ * position, which suits a GPU whose FP64 rate is low).  The size is the
+ * binomial deviate of stream (SPLIT, 0) with p taken as K / 2^62,
+ * K = floor(q 2^62 + 1/2), q = p for p <= 1/2 (else the size is N - BIN(N,
+ * K'/2^62) with q = 1 - p); the positions are the rs_sample sample of that
+ * size (kind H, the same seed, n0).  A different sample from rs_bernoulli's
+ * (the same distribution).
+ *
+ * rs_bernoulli_size: the size to *count_out (host memory); synchronizes
+ * `stream`.  Errors: RS_EINVAL (p outside [0, 1], N > 2^62), RS_ECUDA,
+ * RS_EITER.
+ *
+ * rs_bernoulli_by_size: the 1-based positions in the window [a, b) of
+ * 0-based positions (any ends), increasing, to out_dev[0..count); the window's
+ * count to *count_out and the whole size to *total_out (host memory).  The
+ * whole range (a = 0, b = N) runs rs_sample asynchronously on `stream` after
+ * the size is read; other windows build the split tree and run a range query
+ * (rs_tree_create / rs_tree_query, synchronous).  Errors: as rs_sample and
+ * rs_tree_query, RS_EINVAL (bad window, n0 = 0), RS_ECAPACITY (count > cap;
+ * the counts are still set). */
+int rs_bernoulli_size(rs_ctx* ctx, double p, uint64_t N, uint64_t seed, uint64_t* count_out, void* stream);
+int rs_bernoulli_by_size(rs_ctx* ctx, double p, uint64_t N, uint64_t seed, uint32_t n0, uint64_t a, uint64_t b,
+                         uint64_t* out_dev, uint64_t cap, uint64_t* count_out, uint64_t* total_out, void* stream);
+
 /* Largest staging area (bytes) rs_bernoulli may keep, and its slots per
  * chunk (0: mu + 8 sqrt(mu) + 64 for a chunk's expected count mu).  With
  * staging each chunk is walked once and its positions staged (about 1.1

@@ -85,6 +85,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "rs_launch_count": (i32, [vp, ctypes.POINTER(u64)]),
         "rs_set_pipeline": (i32, [vp, i32, i32]),
         "rs_set_bernoulli_staging": (i32, [vp, u64, u64]),
+        "rs_bernoulli_size": (i32, [vp, dbl, u64, u64, ctypes.POINTER(u64), vp]),
+        "rs_bernoulli_by_size": (i32, [vp, dbl, u64, u64, u32, u64, u64, vp, u64, ctypes.POINTER(u64),
+                                       ctypes.POINTER(u64), vp]),
         "rs_sample_to_host": (i32, [vp, i32, u64, u64, u64, u32, vp, vp, vp]),
         "rs_sample_static": (i32, [u64, u64, u64, u32, vp, vp]),
         "rs_batch_plan": (i32, [vp, vp, u32, ctypes.POINTER(vp)]),
@@ -209,6 +212,24 @@ def rs_bernoulli(ctx: Context, p, N, seed, n0, a, b, out, cap, stream=None, chec
     if check and rc != RS_OK:
         raise RSError(rc, "rs_bernoulli")
     return rc, cnt.value
+
+
+def rs_bernoulli_size(ctx: Context, p, N, seed, stream=None) -> int:
+    """BIN(N, p) size of the Bernoulli sample drawn by its size."""
+    cnt = ctypes.c_uint64(0)
+    _check(load().rs_bernoulli_size(ctx.handle, float(p), N, seed, ctypes.byref(cnt), _stream(stream)),
+           "rs_bernoulli_size")
+    return cnt.value
+
+
+def rs_bernoulli_by_size(ctx: Context, p, N, seed, n0, a, b, out, cap, stream=None, check=True):
+    """Returns (rc, count in [a, b), total size)."""
+    cnt, tot = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    rc = load().rs_bernoulli_by_size(ctx.handle, float(p), N, seed, n0, a, b, _ptr(out), cap, ctypes.byref(cnt),
+                                     ctypes.byref(tot), _stream(stream))
+    if check and rc != RS_OK:
+        raise RSError(rc, "rs_bernoulli_by_size")
+    return rc, cnt.value, tot.value
 
 
 def rs_sync(ctx: Context, stream=None) -> int:

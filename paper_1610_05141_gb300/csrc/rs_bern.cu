@@ -12,6 +12,7 @@
 // the positions are those of the sequential definition.  A draw with
 // ln U / L >= 2^62 ends the range.
 #include "rs_batch.cuh"
+#include "rs_deviates.cuh"
 #include "rs_hash_leaf.cuh"
 #include "rs_math.cuh"
 
@@ -182,6 +183,26 @@ uint64_t bern_stage_per(double mu) {
     const double v = ceil(mu + 8.0 * sqrt(mu) + 64.0);
     const uint64_t s = v >= 9.0e18 ? (uint64_t)9e18 : (uint64_t)v;
     return (s + 3) & ~3ull;
+}
+
+// The size of a Bernoulli(p) sample drawn by its size (Sec. 4.7): BIN(N,
+// K/2^62) from stream (SPLIT, 0), complemented to N - BIN when p > 1/2.
+__global__ void bern_size_kernel(uint64_t seed, uint64_t N, uint64_t K, int flip, const double* tab, uint64_t* out,
+                                 int* status) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    uint64_t c = 0;
+    const int rc = binomial(make_key(seed), 0, N, K, 1ull << 62, tab, c);
+    if (rc != RS_OK) {
+        set_status(status, rc);
+        c = 0;
+    }
+    *out = flip ? N - c : c;
+}
+
+cudaError_t launch_bernoulli_size(uint64_t seed, uint64_t N, uint64_t K, bool flip, const double* tab, uint64_t* out,
+                                  int* status, cudaStream_t st) {
+    bern_size_kernel<<<1, 32, 0, st>>>(seed, N, K, flip ? 1 : 0, tab, out, status);
+    return cudaGetLastError();
 }
 
 __global__ void fill_range_kernel(uint64_t* out, uint64_t a, uint64_t n) {

@@ -2,6 +2,7 @@
 //
 // Host side of the sampler: argument checks, the plan (tree depth), scratch
 // memory, and the launch sequence tree -> leaves on the caller's stream.
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -468,6 +469,56 @@ int rs_bernoulli(rs_ctx* ctx, double p, uint64_t N, uint64_t seed, uint32_t n0, 
     if (rc) return rc;
     *count_out = total;
     return total > cap ? RS_ECAPACITY : RS_OK;
+}
+
+int rs_bernoulli_size(rs_ctx* ctx, double p, uint64_t N, uint64_t seed, uint64_t* count_out, void* stream) {
+    if (!ctx || !count_out) return RS_EINVAL;
+    *count_out = 0;
+    if (!(p >= 0.0 && p <= 1.0) || N > (1ull << 62)) return RS_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RS_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // p as K / 2^62, K = floor(q 2^62 + 1/2) with q = p or 1 - p (whichever is at most 1/2)
+    const bool flip = p > 0.5;
+    const double q = flip ? 1.0 - p : p;
+    const uint64_t K = (uint64_t)floor(q * 0x1p62 + 0.5);
+    int rc = ensure(ctx->words, ctx->words_cap, 1);
+    if (rc) return rc;
+    rc = cuda_rc(rs::launch_bernoulli_size(seed, N, K, flip, ctx->tab, ctx->words, ctx->status, st));
+    ctx->launches += 1;
+    if (rc) return rc;
+    uint64_t c = 0;
+    rc = cuda_rc(cudaMemcpyAsync(&c, ctx->words, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    if (rc) return rc;
+    rc = rs_sync(ctx, stream);
+    if (rc) return rc;
+    *count_out = c;
+    return RS_OK;
+}
+
+int rs_bernoulli_by_size(rs_ctx* ctx, double p, uint64_t N, uint64_t seed, uint32_t n0, uint64_t a, uint64_t b,
+                         uint64_t* out_dev, uint64_t cap, uint64_t* count_out, uint64_t* total_out, void* stream) {
+    if (!ctx || !count_out || !total_out) return RS_EINVAL;
+    *count_out = 0;
+    *total_out = 0;
+    if (n0 == 0 || a > b || b > N) return RS_EINVAL;
+    if (cap > 0 && (!out_dev || ((uintptr_t)out_dev & 7))) return RS_EINVAL;
+    uint64_t n = 0;
+    int rc = rs_bernoulli_size(ctx, p, N, seed, &n, stream);
+    if (rc) return rc;
+    *total_out = n;
+    if (n == 0 || a == b) return RS_OK;
+    if (a == 0 && b == N) {   // the whole sample
+        *count_out = n;
+        if (n > cap) return RS_ECAPACITY;
+        return rs_sample(ctx, n, N, seed, n0, out_dev, stream);
+    }
+    rs_tree* tree = nullptr;
+    rc = rs_tree_create(ctx, n, N, seed, n0, RS_KIND_H, stream, &tree);
+    if (rc) return rc;
+    rc = rs_tree_query(tree, a + 1, b + 1, out_dev, cap, count_out, stream);
+    const int rd = rs_tree_destroy(tree);
+    return rc ? rc : rd;
 }
 
 int rs_sync(rs_ctx* ctx, void* stream) {

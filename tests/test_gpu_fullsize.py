@@ -139,3 +139,29 @@ def test_full_size_batch(rs, ctx, oracle):
         plan.close()
         del pool, status
         torch.cuda.empty_cache()
+
+
+def test_full_size_bernoulli_by_size(rs, ctx, oracle):
+    """Bernoulli p = 1e-2 over 2^36 positions drawn by its size, the whole
+    range in one call: the size equals the oracle's, positions increase
+    strictly inside 1..N, and slices at sampled windows equal the oracle's
+    range queries of the same sample."""
+    p, N, seed, n0 = 1e-2, 2**36, 7, 4096
+    tot = oracle.bernoulli_size(p, N, seed)
+    cap = tot + 1024
+    out = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
+    rc, cnt, tot2 = rs.rs_bernoulli_by_size(ctx, p, N, seed, n0, 0, N, out, cap)
+    assert rs.rs_sync(ctx) == rs.RS_OK
+    assert tot2 == tot and cnt == tot
+    got = out[:cnt]
+    assert int(got[0]) >= 1 and int(got[-1]) <= N and bool(torch.all(got[1:] > got[:-1]))
+    rng = np.random.default_rng(seed)
+    for a in sorted(int(x) for x in rng.integers(0, N - 2**22, 6)):
+        b = a + 2**22 + 12345
+        want, _ = oracle.bernoulli_by_size(p, N, seed, n0, a, b)
+        lo = int(torch.searchsorted(got, torch.tensor([a + 1], dtype=torch.int64, device="cuda")))
+        sl = got[lo:lo + len(want)].cpu().numpy().view(np.uint64)
+        assert np.array_equal(sl, want), (a, b)
+    del out, got
+    torch.cuda.empty_cache()
+

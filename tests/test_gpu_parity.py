@@ -210,6 +210,45 @@ def test_bernoulli_windows_degenerate_and_capacity(rs, ctx, oracle):
     assert rc == rs.RS_EINVAL
 
 
+SIZE_CASES = [(0.3, 1000, 1), (1e-2, 2**36, 7), (0.5, 2**36, 7), (0.8, 10**6, 3), (1e-15, 2**62, 5),
+              (0.0, 100, 1), (1.0, 100, 1), (0.5, 2**62, 9), (2e-6, 10**7, 4)]
+
+
+@pytest.mark.parametrize("p,N,seed", SIZE_CASES)
+def test_bernoulli_size_matches_oracle(rs, ctx, oracle, p, N, seed):
+    """The BIN(N, p) size of the sample drawn by its size: the device's
+    deviate equals the oracle's (inversion and ratio-of-uniforms, p > 1/2 by
+    the complement)."""
+    assert rs.rs_bernoulli_size(ctx, p, N, seed) == oracle.bernoulli_size(p, N, seed)
+
+
+BY_SIZE_CASES = [(0.3, 10**6 + 7, 8, 64), (1e-2, 2**24, 7, 4096), (0.5, 2**20, 7, 4096), (0.9, 5000, 9, 16),
+                 (1e-4, 2**30, 3, 4096)]
+
+
+@pytest.mark.parametrize("p,N,seed,n0", BY_SIZE_CASES)
+def test_bernoulli_by_size_matches_oracle(rs, ctx, oracle, p, N, seed, n0):
+    """Bernoulli sampling by its size: the whole range (rs_sample of the
+    size) and windows with any ends (range queries of that sample) equal the
+    oracle's, with the same counts."""
+    want, tot = oracle.bernoulli_by_size(p, N, seed, n0)
+    cap = len(want) + 16
+    out = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
+    rc, cnt, tot2 = rs.rs_bernoulli_by_size(ctx, p, N, seed, n0, 0, N, out, cap)
+    assert rs.rs_sync(ctx) == rs.RS_OK
+    assert tot2 == tot and cnt == len(want)
+    assert_same(out[:cnt].cpu().numpy().view(np.uint64), want, ("whole", p, N))
+    for a, b in [(0, N // 3), (N // 7 + 1, N // 2 + 3), (N - N // 5 - 1, N), (5, 5)]:
+        w, _ = oracle.bernoulli_by_size(p, N, seed, n0, a, b)
+        rc, cnt, tot3 = rs.rs_bernoulli_by_size(ctx, p, N, seed, n0, a, b, out, cap)
+        assert tot3 == tot and cnt == len(w), (a, b)
+        assert_same(out[:cnt].cpu().numpy().view(np.uint64), w, ("window", p, N, a, b))
+    rc, cnt, _ = rs.rs_bernoulli_by_size(ctx, p, N, seed, n0, 0, N, out, 3, check=False)
+    if tot > 3:
+        assert rc == rs.RS_ECAPACITY and cnt == tot
+    assert rs.rs_bernoulli_by_size(ctx, p, N, seed, n0, 7, 3, out, cap, check=False)[0] == rs.RS_EINVAL
+
+
 def test_argument_errors(rs, ctx):
     out = torch.empty(16, dtype=torch.int64, device="cuda")
     assert rs.rs_sample(ctx, 11, 10, 1, 4, out, check=False) == rs.RS_EINVAL
