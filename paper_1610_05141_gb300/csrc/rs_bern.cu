@@ -12,6 +12,7 @@
 // the positions are those of the sequential definition.  A draw with
 // ln U / L >= 2^62 ends the range.
 #include "rs_batch.cuh"
+#include "rs_bern.h"
 #include "rs_deviates.cuh"
 #include "rs_hash_leaf.cuh"
 #include "rs_math.cuh"

@@ -8,6 +8,7 @@
 #include <new>
 #include <vector>
 
+#include "rs_bern.h"
 #include "rs_internal.h"
 
 struct rs_ctx {

@@ -96,10 +96,6 @@ struct BernLaunch {
 // walks again).  Without: count pass, scan, write pass.
 cudaError_t launch_bernoulli(const BernLaunch& L, cudaStream_t st);
 uint64_t scan_scratch_words(uint64_t n);
-// One thread: *out = BIN(N, K / 2^62) of stream (SPLIT, 0) (N minus it when
-// flip); a failed deviate sets the status word and gives 0.
-cudaError_t launch_bernoulli_size(uint64_t seed, uint64_t N, uint64_t K, bool flip, const double* tab, uint64_t* out,
-                                  int* status, cudaStream_t st);
 // Staged positions per chunk for an expected count mu: mu + 8 sqrt(mu) + 64,
 // a multiple of 4.
 uint64_t bern_stage_per(double mu);
