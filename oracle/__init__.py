@@ -92,6 +92,9 @@ def _load():
             "or_bern_chunk_log2": (i32, [dbl, u32]),
             "or_bernoulli": (i32, [dbl, u64, u64, u32, u64, u64, p64, u64, p64]),
             "or_bernoulli_size": (i32, [dbl, u64, u64, p64]),
+            "or_union_key": (u64, [u64, u64]),
+            "or_union_counts": (i32, [p64, u32, u64, u64, p64]),
+            "or_union_sample": (i32, [p64, u32, u64, u64, u32, p64, p64]),
             "or_bernoulli_by_size": (i32, [dbl, u64, u64, u32, u64, u64, p64, u64, p64, p64]),
         }
         for name, (res, args) in sig.items():
@@ -308,6 +311,27 @@ def bernoulli_by_size(p, N, seed, n0, a=0, b=None, cap=None):
     rc = _load().or_bernoulli_by_size(p, N, seed, n0, a, b, _p64(out), cap, ctypes.byref(cnt), ctypes.byref(tot))
     _check(rc, "bernoulli_by_size")
     return out[: int(cnt.value)], int(tot.value)
+
+
+def union_key(seed, i):
+    return int(_load().or_union_key(seed, i))
+
+
+def union_counts(L, n, seed):
+    """Samples per segment of the union sample (binomial tree of HG splits)."""
+    L = np.ascontiguousarray(L, dtype=np.uint64)
+    counts = np.zeros(max(len(L), 1), dtype=np.uint64)
+    _check(_load().or_union_counts(_p64(L), len(L), n, seed, _p64(counts)), "union_counts")
+    return counts[: len(L)]
+
+
+def union_sample(L, n, seed, n0):
+    """(positions within their segments, segment after segment; counts)."""
+    L = np.ascontiguousarray(L, dtype=np.uint64)
+    out = np.zeros(max(n, 1), dtype=np.uint64)
+    counts = np.zeros(max(len(L), 1), dtype=np.uint64)
+    _check(_load().or_union_sample(_p64(L), len(L), n, seed, n0, _p64(out), _p64(counts)), "union_sample")
+    return out[:n], counts[: len(L)]
 
 
 def bernoulli_rc(p, N, seed, n0, a, b, cap):

@@ -942,3 +942,65 @@ int or_bernoulli_by_size(double p, uint64_t N, uint64_t seed, uint32_t n0, uint6
     return or_range_query(n, N, seed, n0, 0, a + 1, b + 1, out, cap, count);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Sampling from a union of uneven segments (Sec. 4.5, uneven distribution  */
+/* of the sampled universe): owner computes.                                */
+/* ------------------------------------------------------------------------ */
+
+/* Weyl step for the segments' keys: segment i samples with key
+ * seed + (i + 1) * W (mod 2^64), W odd, so the keys differ per segment. */
+static const uint64_t UNION_WEYL = 0x9E3779B97F4A7C15ull;
+
+uint64_t or_union_key(uint64_t seed, uint64_t i) { return seed + (i + 1) * UNION_WEYL; }
+
+/* Number of samples per segment.  Reading: the binomial tree of Sec. 4.5 over
+ * the p segments is the binary tree of power-of-two aligned ranges, padded to
+ * P = 2^ceil(log2 p) segments (the padding holds no elements): node v
+ * (heap-numbered, root 1) covers segments [i 2^h, (i+1) 2^h) and its element
+ * count is the sum of their sizes, added bottom-up; top-down, a node with c
+ * samples gives HG(c, L_left, L_left + L_right) of them to its left child --
+ * the hypergeometric deviate of stream (SPLIT, v) with the given seed -- and
+ * the rest to its right child.  counts[i] = the samples of segment i. */
+int or_union_counts(const uint64_t* L, uint32_t p, uint64_t n, uint64_t seed, uint64_t* counts)
+{
+    if (p == 0) return n == 0 ? OR_OK : OR_EINVAL;
+    uint64_t P = 1;
+    while (P < p) P <<= 1;
+    uint64_t* sum = (uint64_t*)calloc(2 * P, sizeof(uint64_t));
+    uint64_t* cnt = (uint64_t*)calloc(2 * P, sizeof(uint64_t));
+    if (!sum || !cnt) { free(sum); free(cnt); return OR_ENOMEM; }
+    int rc = OR_OK;
+    u128 total = 0;
+    for (uint32_t i = 0; i < p; ++i) { sum[P + i] = L[i]; total += L[i]; }
+    if (total > ((u128)1 << 62) || n > (uint64_t)total) rc = OR_EINVAL;
+    for (uint64_t v = P - 1; v >= 1 && rc == OR_OK; --v) sum[v] = sum[2 * v] + sum[2 * v + 1];
+    if (rc == OR_OK) cnt[1] = n;
+    for (uint64_t v = 1; v < P && rc == OR_OK; ++v) {
+        uint64_t left = 0;
+        rc = or_hg(seed, v, cnt[v], sum[2 * v], sum[v], &left);
+        cnt[2 * v] = left;
+        cnt[2 * v + 1] = cnt[v] - left;
+    }
+    for (uint32_t i = 0; i < p && rc == OR_OK; ++i) counts[i] = cnt[P + i];
+    free(sum);
+    free(cnt);
+    return rc;
+}
+
+/* The union's sample: segment i's counts[i] samples are the sample without
+ * replacement of that size from its L_i elements (or_sample, kind H, key
+ * or_union_key(seed, i), n0) as 1-based positions within the segment;
+ * segments follow each other in order in out[]. */
+int or_union_sample(const uint64_t* L, uint32_t p, uint64_t n, uint64_t seed, uint32_t n0, uint64_t* out,
+                    uint64_t* counts)
+{
+    if (n0 == 0) return OR_EINVAL;
+    int rc = or_union_counts(L, p, n, seed, counts);
+    uint64_t off = 0;
+    for (uint32_t i = 0; i < p && rc == OR_OK; ++i) {
+        rc = or_sample(counts[i], L[i], or_union_key(seed, i), n0, 0, out + off);
+        off += counts[i];
+    }
+    return rc;
+}
+
