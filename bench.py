@@ -408,6 +408,20 @@ def run_rows(rs, ctx, stream, args):
                                "note": "whole call: the size (read back), then rs_sample of that size, or the "
                                        "split tree and one range query per window"}
     out["f2_bernoulli_by_size"] = {"N": 2**36, "n0": N0, "by_p": by_size}
+    # the next row (f3): a sample of 1e8 from the union of 4096 segments of
+    # uneven sizes (Sec. 4.5): the count tree, then the segments' samples as
+    # one batch
+    from paper_1610_05141_gb300.workloads import union_segments
+    L = union_segments()
+    n_u = 10**8
+    ms_counts = timed(lambda: rs.rs_union_counts(ctx, L, n_u, 5, stream), args.row_steps)
+    ms_union = timed(lambda: rs.rs_union_sample(ctx, L, n_u, 5, N0, buf, stream), args.row_steps)
+    out["f3_union"] = {"workload": f"n=1e8 from the union of {len(L)} segments of sizes log-uniform in "
+                                   f"2^20..2^40 (total {int(L.sum()):.3e}), n0={N0}",
+                       "ms_per_call": ms_union, "samples_per_s": n_u / (ms_union / 1000),
+                       "count_tree_ms": ms_counts,
+                       "note": "whole call: sizes to the device, the count tree, counts read back, the "
+                               "segments' batch planned and run, statuses read back"}
     del buf
     return out
 

@@ -177,6 +177,37 @@ int rs_batch_destroy(rs_batchplan* plan);
 int rs_batch(rs_ctx* ctx, const rs_request* reqs_dev, uint32_t R, uint64_t* out_pool_dev,
              int32_t* status_dev, void* stream);
 
+/* ---- Union of uneven segments (Sec. 4.5) -------------------------------
+ * A universe made of p segments of sizes L[0..p) (the elements of segment i
+ * are its positions 1..L[i]); the sample is a uniform n-subset of the union.
+ * As with the paper's owners of uneven shares, the samples per segment come
+ * first, from a binary tree of hypergeometric splits over the segments
+ * (padded with empty segments to a power of two P; heap-numbered nodes, root
+ * 1, segment i at node P + i): node v's c samples give HG(c, sum of its left
+ * half's sizes, sum of its sizes) of stream (SPLIT, v), key seed, to the left
+ * child and the rest to the right child.  Then each segment with samples
+ * draws them alone (owner computes) as rs_sample(count_i, L[i],
+ * rs_union_key(seed, i), n0).  L_host: p host words, sum at most 2^62;
+ * p <= 2^24. */
+
+/* Segment i's key: seed + (i + 1) * 0x9E3779B97F4A7C15 (mod 2^64). */
+uint64_t rs_union_key(uint64_t seed, uint32_t i);
+
+/* The count tree on the device; counts_host[0..p) (host memory) receives the
+ * samples per segment.  Synchronizes `stream`.  Errors: RS_EINVAL (bad
+ * sizes, n above their sum), RS_ENOMEM, RS_ECUDA, RS_EITER. */
+int rs_union_counts(rs_ctx* ctx, const uint64_t* L_host, uint32_t p, uint64_t n, uint64_t seed,
+                    uint64_t* counts_host, void* stream);
+
+/* The union's sample: segment after segment, each segment's values as
+ * increasing positions within it (1..L[i]), at out_dev[0..n) (device memory,
+ * 8-byte aligned); counts_host[0..p) as rs_union_counts.  The segments' samples
+ * run as one batch (rs_batch_plan / rs_batch_run of the segments with
+ * samples).  Synchronizes `stream`.  Errors: as rs_union_counts and
+ * rs_batch_plan, RS_EINVAL for n0 = 0, and a request's status error. */
+int rs_union_sample(rs_ctx* ctx, const uint64_t* L_host, uint32_t p, uint64_t n, uint64_t seed, uint32_t n0,
+                    uint64_t* out_dev, uint64_t* counts_host, void* stream);
+
 /* ---- Resident trees and online sorted range queries -------------------
  * A resident tree holds, in device memory owned by the library, the leaf
  * records (range, count, output offset) of the split tree of one sample

@@ -88,6 +88,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "rs_bernoulli_size": (i32, [vp, dbl, u64, u64, ctypes.POINTER(u64), vp]),
         "rs_bernoulli_by_size": (i32, [vp, dbl, u64, u64, u32, u64, u64, vp, u64, ctypes.POINTER(u64),
                                        ctypes.POINTER(u64), vp]),
+        "rs_union_key": (u64, [u64, u32]),
+        "rs_union_counts": (i32, [vp, vp, u32, u64, u64, vp, vp]),
+        "rs_union_sample": (i32, [vp, vp, u32, u64, u64, u32, vp, vp, vp]),
         "rs_sample_to_host": (i32, [vp, i32, u64, u64, u64, u32, vp, vp, vp]),
         "rs_sample_static": (i32, [u64, u64, u64, u32, vp, vp]),
         "rs_batch_plan": (i32, [vp, vp, u32, ctypes.POINTER(vp)]),
@@ -230,6 +233,33 @@ def rs_bernoulli_by_size(ctx: Context, p, N, seed, n0, a, b, out, cap, stream=No
     if check and rc != RS_OK:
         raise RSError(rc, "rs_bernoulli_by_size")
     return rc, cnt.value, tot.value
+
+
+def rs_union_key(seed, i) -> int:
+    return int(load().rs_union_key(seed, i))
+
+
+def _segments(L):
+    import numpy as np
+    L = np.ascontiguousarray(L, dtype=np.uint64)
+    return L, np.zeros(max(len(L), 1), dtype=np.uint64)
+
+
+def rs_union_counts(ctx: Context, L, n, seed, stream=None):
+    """Samples per segment of a sample of n from the union of segments of sizes L."""
+    L, counts = _segments(L)
+    _check(load().rs_union_counts(ctx.handle, L.ctypes.data, len(L), n, seed, counts.ctypes.data, _stream(stream)),
+           "rs_union_counts")
+    return counts[: len(L)]
+
+
+def rs_union_sample(ctx: Context, L, n, seed, n0, out, stream=None):
+    """Writes the union's sample (segment after segment, positions within the
+    segment) to out[0..n); returns the counts per segment."""
+    L, counts = _segments(L)
+    _check(load().rs_union_sample(ctx.handle, L.ctypes.data, len(L), n, seed, n0, _ptr(out), counts.ctypes.data,
+                                  _stream(stream)), "rs_union_sample")
+    return counts[: len(L)]
 
 
 def rs_sync(ctx: Context, stream=None) -> int:

@@ -10,6 +10,7 @@
 
 #include "rs_bern.h"
 #include "rs_internal.h"
+#include "rs_union.h"
 
 struct rs_ctx {
     int device = 0;
@@ -519,6 +520,82 @@ int rs_bernoulli_by_size(rs_ctx* ctx, double p, uint64_t N, uint64_t seed, uint3
     if (rc) return rc;
     rc = rs_tree_query(tree, a + 1, b + 1, out_dev, cap, count_out, stream);
     const int rd = rs_tree_destroy(tree);
+    return rc ? rc : rd;
+}
+
+namespace {
+constexpr uint32_t kUnionMaxSegments = 1u << 24;
+constexpr uint64_t kUnionWeyl = 0x9E3779B97F4A7C15ull;
+
+// Validates the segments and runs the count tree; counts_host[i] = segment
+// i's count.  *total_out = the union's size.
+int union_counts(rs_ctx* ctx, const uint64_t* L_host, uint32_t p, uint64_t n, uint64_t seed,
+                 uint64_t* counts_host, cudaStream_t st) {
+    if (p > kUnionMaxSegments || (p > 0 && (!L_host || !counts_host))) return RS_EINVAL;
+    unsigned __int128 total = 0;
+    for (uint32_t i = 0; i < p; ++i) total += L_host[i];
+    if (total > ((unsigned __int128)1 << 62) || n > (uint64_t)total) return RS_EINVAL;
+    if (p == 0) return RS_OK;
+    int log2P = 0;
+    while ((1ull << log2P) < p) ++log2P;
+    const uint64_t P = 1ull << log2P;
+    int rc = ensure(ctx->words, ctx->words_cap, p + 4 * P);
+    if (rc) return rc;
+    uint64_t* L = ctx->words;
+    uint64_t* sum = L + p;
+    uint64_t* cnt = sum + 2 * P;
+    rc = cuda_rc(cudaMemcpyAsync(L, L_host, p * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+    if (rc) return rc;
+    rc = cuda_rc(rs::launch_union_counts(L, p, log2P, n, seed, sum, cnt, ctx->tab, ctx->status, st));
+    ctx->launches += 1 + 2 * (uint64_t)log2P;
+    if (rc) return rc;
+    rc = cuda_rc(cudaMemcpyAsync(counts_host, cnt + P, p * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    if (rc) return rc;
+    return rs_sync(ctx, st);
+}
+}  // namespace
+
+int rs_union_counts(rs_ctx* ctx, const uint64_t* L_host, uint32_t p, uint64_t n, uint64_t seed,
+                    uint64_t* counts_host, void* stream) {
+    if (!ctx) return RS_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RS_ECUDA;
+    return union_counts(ctx, L_host, p, n, seed, counts_host, static_cast<cudaStream_t>(stream));
+}
+
+uint64_t rs_union_key(uint64_t seed, uint32_t i) { return seed + ((uint64_t)i + 1) * kUnionWeyl; }
+
+int rs_union_sample(rs_ctx* ctx, const uint64_t* L_host, uint32_t p, uint64_t n, uint64_t seed, uint32_t n0,
+                    uint64_t* out_dev, uint64_t* counts_host, void* stream) {
+    if (!ctx || n0 == 0) return RS_EINVAL;
+    if (n > 0 && (!out_dev || ((uintptr_t)out_dev & 7))) return RS_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RS_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = union_counts(ctx, L_host, p, n, seed, counts_host, st);
+    if (rc || n == 0) return rc;
+    // one request per segment with samples, output segment after segment
+    std::vector<rs_request> req;
+    uint64_t off = 0;
+    for (uint32_t i = 0; i < p; ++i) {
+        if (counts_host[i])
+            req.push_back(rs_request{counts_host[i], L_host[i], rs_union_key(seed, i), off, n0, RS_KIND_H});
+        off += counts_host[i];
+    }
+    const uint32_t R = (uint32_t)req.size();
+    rs_batchplan* B = nullptr;
+    rc = rs_batch_plan(ctx, req.data(), R, &B);
+    if (rc) return rc;
+    // the count tree's scratch is free again: the requests' status words
+    int32_t* status = reinterpret_cast<int32_t*>(ctx->words);
+    rc = rs_batch_run(B, out_dev, status, st);
+    uint64_t per_run = 0;
+    if (!rc && !rs_batch_launch_count(B, &per_run)) ctx->launches += per_run;
+    std::vector<int32_t> sh(R);
+    if (!rc) rc = cuda_rc(cudaMemcpyAsync(sh.data(), status, R * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    if (!rc) rc = rs_sync(ctx, st);
+    const int rd = rs_batch_destroy(B);
+    for (uint32_t r = 0; !rc && r < R; ++r) rc = sh[r];
     return rc ? rc : rd;
 }
 

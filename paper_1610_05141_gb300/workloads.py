@@ -66,3 +66,11 @@ def serve_jobs(count: int, trees, seed: int = 5, query_frac: float = 0.2, log10_
     seeds = np.arange(5_000_000, 5_000_000 + count, dtype=np.uint64)
     return {"op": op, "n": n, "N": N, "seed": seeds, "tree": tree, "a": a.astype(np.uint64),
             "b": b.astype(np.uint64), "cap": cap}
+
+
+def union_segments(p: int = 4096, seed: int = 4, log2_min: float = 20.0, log2_max: float = 40.0):
+    """Segment sizes of a union: p sizes log-uniform in [2^log2_min, 2^log2_max]
+    (uneven shares, as the uneven distribution of the universe over owners)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    e = log2_min + (log2_max - log2_min) * rng.random(p)
+    return np.floor(np.exp2(e)).astype(np.uint64)
