@@ -93,6 +93,7 @@ def _load():
             "or_bernoulli": (i32, [dbl, u64, u64, u32, u64, u64, p64, u64, p64]),
             "or_bernoulli_size": (i32, [dbl, u64, u64, p64]),
             "or_union_key": (u64, [u64, u64]),
+            "or_peel_sample": (i32, [u64, u64, u64, u32, p64, p64, u64, p64]),
             "or_union_counts": (i32, [p64, u32, u64, u64, p64]),
             "or_union_sample": (i32, [p64, u32, u64, u64, u32, p64, p64]),
             "or_bernoulli_by_size": (i32, [dbl, u64, u64, u32, u64, u64, p64, u64, p64, p64]),
@@ -311,6 +312,16 @@ def bernoulli_by_size(p, N, seed, n0, a=0, b=None, cap=None):
     rc = _load().or_bernoulli_by_size(p, N, seed, n0, a, b, _p64(out), cap, ctypes.byref(cnt), ctypes.byref(tot))
     _check(rc, "bernoulli_by_size")
     return out[: int(cnt.value)], int(tot.value)
+
+
+def peel_sample(n, N, seed, n0):
+    """(the sample in increasing order, samples per peeled batch)."""
+    nb = min(N, 8 * (n // n0 + 1) + 1024) if N else 1
+    out = np.zeros(max(n, 1), dtype=np.uint64)
+    counts = np.zeros(max(nb, 1), dtype=np.uint64)
+    got = ctypes.c_uint64(0)
+    _check(_load().or_peel_sample(n, N, seed, n0, _p64(out), _p64(counts), nb, ctypes.byref(got)), "peel_sample")
+    return out[:n], counts[: got.value]
 
 
 def union_key(seed, i):

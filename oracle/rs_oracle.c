@@ -1004,3 +1004,49 @@ int or_union_sample(const uint64_t* L, uint32_t p, uint64_t n, uint64_t seed, ui
     return rc;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Online sorted sampling by peeling (Sec. 4.1, last paragraph: split off a */
+/* range of about N n0 / n positions at a time).                            */
+/* ------------------------------------------------------------------------ */
+
+/* The sample as its batches, in order.  With n_t samples left in the N_t
+ * positions after the first lo_t (n_0 = n, N_0 = N, lo_0 = 0), batch t
+ * (t = 0, 1, ...) peels the next m_t = ceil(N_t n0 / n_t) positions and
+ * takes c_t = HG(n_t, m_t, N_t) of the samples, the deviate of stream
+ * (SPLIT, t + 1); once m_t >= N_t the batch is the rest (m_t = N_t,
+ * c_t = n_t) and the last.  Batch t's values are leaf H of node t + 1 over
+ * [lo_t, lo_t + m_t) with c_t samples; lo_{t+1} = lo_t + m_t, N_{t+1} =
+ * N_t - m_t, n_{t+1} = n_t - c_t.  out[] receives the batches one after the
+ * other (the sample in increasing order), counts[t] = c_t, *nbatches the
+ * number of batches (at most max_batches, else OR_ECAPACITY). */
+int or_peel_sample(uint64_t n, uint64_t N, uint64_t seed, uint32_t n0, uint64_t* out, uint64_t* counts,
+                   uint64_t max_batches, uint64_t* nbatches)
+{
+    *nbatches = 0;
+    if (n0 == 0 || N > (1ull << 62) || n > N) return OR_EINVAL;
+    uint64_t nr = n, Nr = N, lo = 0, off = 0, t = 0;
+    while (nr > 0) {
+        if (t >= max_batches) return OR_ECAPACITY;
+        const u128 m128 = ((u128)Nr * n0 + nr - 1) / nr;
+        uint64_t m, c;
+        if (m128 >= Nr) {
+            m = Nr;
+            c = nr;
+        } else {
+            m = (uint64_t)m128;
+            int rc = or_hg(seed, t + 1, nr, m, Nr, &c);
+            if (rc) return rc;
+        }
+        int rc = or_leaf_h(seed, t + 1, lo, m, c, out + off);
+        if (rc) return rc;
+        counts[t] = c;
+        off += c;
+        lo += m;
+        Nr -= m;
+        nr -= c;
+        ++t;
+    }
+    *nbatches = t;
+    return OR_OK;
+}
+
