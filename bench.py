@@ -422,6 +422,31 @@ def run_rows(rs, ctx, stream, args):
                        "count_tree_ms": ms_counts,
                        "note": "whole call: sizes to the device, the count tree, counts read back, the "
                                "segments' batch planned and run, statuses read back"}
+    # the next row (f1): online sorted sampling by peeling (Sec. 4.1), n = 1e7
+    # from 2^50 in batches of about n0 = 4096 values
+    n_p, N_p = 10**7, 2**50
+    peel = {}
+    for B in (1, 256):
+        it = rs.rs_peel_create(ctx, n_p, N_p, 5, N0, B)
+        calls, made, t0 = 0, 0, time.perf_counter()
+        first = None
+        while True:
+            _, cnt, nb = it.next(buf, 1 << 21, stream)
+            if first is None:
+                first = (time.perf_counter() - t0) * 1e3
+            if nb == 0:
+                break
+            calls += 1
+            made += cnt
+            if B == 1 and calls == 400:
+                break
+        ms = (time.perf_counter() - t0) * 1e3
+        it.close()
+        peel[f"batches_per_call={B}"] = {"calls": calls, "values": made, "ms": ms, "ms_per_call": ms / calls,
+                                        "first_call_ms": first, "values_per_s": made / (ms / 1000)}
+    out["f1_peel"] = {"workload": f"n=1e7 from 1..2^50 in batches of about n0={N0}", "by_batches": peel,
+                      "note": "host wall time of synchronous calls: the chain of hypergeometric deviates "
+                              "(one thread), the counts read back, one leaf launch for the call's batches"}
     del buf
     return out
 

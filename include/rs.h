@@ -208,6 +208,44 @@ int rs_union_counts(rs_ctx* ctx, const uint64_t* L_host, uint32_t p, uint64_t n,
 int rs_union_sample(rs_ctx* ctx, const uint64_t* L_host, uint32_t p, uint64_t n, uint64_t seed, uint32_t n0,
                     uint64_t* out_dev, uint64_t* counts_host, void* stream);
 
+/* ---- Online sorted sampling by peeling (Sec. 4.1) ----------------------
+ * An iterator over a sample of n from 1..N in increasing order, in batches
+ * of about n0 values, each made in O(n0) work (the paper's constant delay
+ * per sample for constant n0).  With n_t samples left among the N_t
+ * positions after the first lo_t (n_0 = n, N_0 = N, lo_0 = 0), batch t
+ * (t = 0, 1, ...) splits off the next m_t = ceil(N_t n0 / n_t) positions and
+ * takes c_t = HG(n_t, m_t, N_t) of the samples, the deviate of stream
+ * (SPLIT, t + 1); once m_t >= N_t the batch is the rest (m_t = N_t,
+ * c_t = n_t) and the last.  Batch t's values are the leaf H values of node
+ * t + 1 over [lo_t, lo_t + m_t) with c_t samples (as in rs_sample's leaves).
+ * A different sample from rs_sample's with the same arguments, with the
+ * same distribution. */
+typedef struct rs_peel rs_peel;
+
+/* Creates the iterator (device state, room for max_batches batches per
+ * call, 1 <= max_batches <= 2^20).  It uses the context's table and must be
+ * destroyed before it.  Errors: RS_EINVAL (n > N, N > 2^62, n0 = 0, bad
+ * max_batches), RS_ENOMEM, RS_ECUDA. */
+int rs_peel_create(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0, uint32_t max_batches,
+                   rs_peel** it);
+
+/* Makes the next batches, as many as max_batches allows and whose values
+ * all fit in cap, and writes their values in increasing order to
+ * out_dev[0 .. *count_out) (device memory, 8-byte aligned); *batches_out =
+ * the batches made (batches may be empty).  After the last batch it returns
+ * RS_OK with 0 and 0.  Synchronizes `stream`.  Errors: RS_EINVAL,
+ * RS_ECAPACITY (not even the next batch fits: *count_out = its size, the
+ * state is unchanged), RS_ECUDA, RS_EITER; a device error stays with the
+ * iterator. */
+int rs_peel_next(rs_peel* it, uint64_t* out_dev, uint64_t cap, uint64_t* count_out, uint32_t* batches_out,
+                 void* stream);
+
+/* Samples and positions left and batches made so far.  Errors: RS_EINVAL. */
+int rs_peel_state(rs_peel* it, uint64_t* n_left, uint64_t* N_left, uint64_t* batches_done);
+
+/* Waits for the device and frees the iterator. */
+int rs_peel_destroy(rs_peel* it);
+
 /* ---- Resident trees and online sorted range queries -------------------
  * A resident tree holds, in device memory owned by the library, the leaf
  * records (range, count, output offset) of the split tree of one sample

@@ -89,6 +89,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "rs_bernoulli_by_size": (i32, [vp, dbl, u64, u64, u32, u64, u64, vp, u64, ctypes.POINTER(u64),
                                        ctypes.POINTER(u64), vp]),
         "rs_union_key": (u64, [u64, u32]),
+        "rs_peel_create": (i32, [vp, u64, u64, u64, u32, u32, ctypes.POINTER(vp)]),
+        "rs_peel_next": (i32, [vp, vp, u64, ctypes.POINTER(u64), ctypes.POINTER(u32), vp]),
+        "rs_peel_state": (i32, [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u64)]),
+        "rs_peel_destroy": (i32, [vp]),
         "rs_union_counts": (i32, [vp, vp, u32, u64, u64, vp, vp]),
         "rs_union_sample": (i32, [vp, vp, u32, u64, u64, u32, vp, vp, vp]),
         "rs_sample_to_host": (i32, [vp, i32, u64, u64, u64, u32, vp, vp, vp]),
@@ -260,6 +264,43 @@ def rs_union_sample(ctx: Context, L, n, seed, n0, out, stream=None):
     _check(load().rs_union_sample(ctx.handle, L.ctypes.data, len(L), n, seed, n0, _ptr(out), counts.ctypes.data,
                                   _stream(stream)), "rs_union_sample")
     return counts[: len(L)]
+
+
+class Peel:
+    """Iterator over a sample in increasing order, batch by batch (rs_peel_*)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def next(self, out, cap, stream=None, check=True):
+        """Returns (rc, values written, batches made)."""
+        cnt, nb = ctypes.c_uint64(0), ctypes.c_uint32(0)
+        rc = load().rs_peel_next(self.handle, _ptr(out), cap, ctypes.byref(cnt), ctypes.byref(nb), _stream(stream))
+        if check and rc != RS_OK:
+            raise RSError(rc, "rs_peel_next")
+        return rc, cnt.value, nb.value
+
+    def state(self):
+        a, b, c = ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
+        _check(load().rs_peel_state(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "rs_peel_state")
+        return a.value, b.value, c.value
+
+    def close(self):
+        if self.handle:
+            load().rs_peel_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rs_peel_create(ctx: Context, n, N, seed, n0, max_batches=256) -> Peel:
+    h = ctypes.c_void_p()
+    _check(load().rs_peel_create(ctx.handle, n, N, seed, n0, max_batches, ctypes.byref(h)), "rs_peel_create")
+    return Peel(h.value)
 
 
 def rs_sync(ctx: Context, stream=None) -> int:
