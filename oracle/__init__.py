@@ -93,6 +93,7 @@ def _load():
             "or_bernoulli": (i32, [dbl, u64, u64, u32, u64, u64, p64, u64, p64]),
             "or_bernoulli_size": (i32, [dbl, u64, u64, p64]),
             "or_union_key": (u64, [u64, u64]),
+            "or_points": (i32, [u64, u32, p64, u64, u32, p64]),
             "or_peel_sample": (i32, [u64, u64, u64, u32, p64, p64, u64, p64]),
             "or_union_counts": (i32, [p64, u32, u64, u64, p64]),
             "or_union_sample": (i32, [p64, u32, u64, u64, u32, p64, p64]),
@@ -322,6 +323,15 @@ def peel_sample(n, N, seed, n0):
     got = ctypes.c_uint64(0)
     _check(_load().or_peel_sample(n, N, seed, n0, _p64(out), _p64(counts), nb, ctypes.byref(got)), "peel_sample")
     return out[:n], counts[: got.value]
+
+
+def points(n, E, seed, n0):
+    """n points uniform in the box [0, E_0) x ... (with replacement), as an
+    (n, d) array of 0-based coordinates, leaf after leaf."""
+    E = np.ascontiguousarray(E, dtype=np.uint64)
+    out = np.zeros(max(n * len(E), 1), dtype=np.uint64)
+    _check(_load().or_points(n, len(E), _p64(E), seed, n0, _p64(out)), "points")
+    return out[: n * len(E)].reshape(n, len(E))
 
 
 def union_key(seed, i):

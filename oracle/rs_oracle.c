@@ -1050,3 +1050,103 @@ int or_peel_sample(uint64_t n, uint64_t N, uint64_t seed, uint32_t n0, uint64_t*
     return OR_OK;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Sampling with replacement from a d-dimensional box by bisection (Sec.    */
+/* 4.6, sampling in various spaces: random points in a rectangle).          */
+/* ------------------------------------------------------------------------ */
+
+#define OR_POINTS_MAXD 4
+
+typedef struct {
+    uint64_t seed;
+    uint32_t d;
+    int D;
+    uint64_t* out;     /* n * d coordinates */
+    uint64_t* tmp;     /* room for the largest leaf */
+    uint64_t off;      /* points written so far */
+} points_ctx;
+
+/* The dimension a box is halved along: the one of largest extent, the
+ * lowest such index on ties. */
+static uint32_t split_dim(const uint64_t* e, uint32_t d)
+{
+    uint32_t k = 0;
+    for (uint32_t j = 1; j < d; ++j)
+        if (e[j] > e[k]) k = j;
+    return k;
+}
+
+/* Node v is the box [o_k, o_k + e_k) in every dimension k and holds c
+ * points.  With ks = split_dim(e), its left child is the box with e_ks
+ * replaced by floor(e_ks / 2) and gets BIN(c, floor(e_ks / 2), e_ks) of the
+ * points (stream (SPLIT, v); the volumes are in that ratio); the right child
+ * is the rest of the box. */
+static int points_rec(points_ctx* P, uint64_t v, int level, const uint64_t* o, const uint64_t* e, uint64_t c)
+{
+    const uint32_t d = P->d;
+    if (level == P->D) {
+        if (c == 0) return OR_OK;
+        /* a leaf draws its points as indices into its box (row-major,
+         * dimension 0 most significant): leaf WR of the leaf's node over
+         * [0, volume), then each index decoded into coordinates */
+        uint64_t vol = 1;
+        for (uint32_t k = 0; k < d; ++k) vol *= e[k];
+        int rc = or_leaf_wr(P->seed, v, 0, vol, c, P->tmp);
+        if (rc) return rc;
+        for (uint64_t j = 0; j < c; ++j) {
+            uint64_t x = P->tmp[j] - 1;
+            uint64_t* pt = P->out + (P->off + j) * d;
+            for (uint32_t k = d; k-- > 0;) {
+                pt[k] = o[k] + x % e[k];
+                x /= e[k];
+            }
+        }
+        P->off += c;
+        return OR_OK;
+    }
+    const uint32_t ks = split_dim(e, d);
+    const uint64_t half = e[ks] / 2;
+    uint64_t cl = 0;
+    if (c > 0) {
+        int rc = or_bin(P->seed, v, c, half, e[ks], &cl);
+        if (rc) return rc;
+    }
+    uint64_t oc[OR_POINTS_MAXD], ec[OR_POINTS_MAXD];
+    for (uint32_t k = 0; k < d; ++k) { oc[k] = o[k]; ec[k] = e[k]; }
+    ec[ks] = half;
+    int rc = points_rec(P, 2 * v, level + 1, oc, ec, cl);
+    if (rc) return rc;
+    oc[ks] = o[ks] + half;
+    ec[ks] = e[ks] - half;
+    return points_rec(P, 2 * v + 1, level + 1, oc, ec, c - cl);
+}
+
+/* n points drawn uniformly and independently from the box [0, E_0) x ... x
+ * [0, E_{d-1}) (1 <= d <= 4, every E_k >= 1, volume V <= 2^62): the depth
+ * D is that of the one-dimensional tree with N = V (or_depth), the tree
+ * halves boxes as points_rec says, and out[] receives the leaves' points in
+ * heap order, d coordinates per point (0-based). */
+int or_points(uint64_t n, uint32_t d, const uint64_t* E, uint64_t seed, uint32_t n0, uint64_t* out)
+{
+    if (d == 0 || d > OR_POINTS_MAXD || n0 == 0) return OR_EINVAL;
+    u128 V = 1;
+    for (uint32_t k = 0; k < d; ++k) {
+        if (E[k] == 0) return OR_EINVAL;
+        V *= E[k];
+        if (V > ((u128)1 << 62)) return OR_EINVAL;
+    }
+    if (n == 0) return OR_OK;
+    points_ctx P;
+    P.seed = seed;
+    P.d = d;
+    P.D = or_depth(n, (uint64_t)V, n0);
+    P.out = out;
+    P.off = 0;
+    P.tmp = (uint64_t*)malloc(n * sizeof(uint64_t));
+    if (!P.tmp) return OR_ENOMEM;
+    uint64_t o[OR_POINTS_MAXD] = {0, 0, 0, 0};
+    int rc = points_rec(&P, 1, 0, o, E, n);
+    free(P.tmp);
+    return rc;
+}
+
