@@ -447,6 +447,17 @@ def run_rows(rs, ctx, stream, args):
     out["f1_peel"] = {"workload": f"n=1e7 from 1..2^50 in batches of about n0={N0}", "by_batches": peel,
                       "note": "host wall time of synchronous calls: the chain of hypergeometric deviates "
                               "(one thread), the counts read back, one leaf launch for the call's batches"}
+    # the next row (f4): 1e8 points uniform in the square [0, 2^31)^2, with
+    # replacement, by bisection (Sec. 4.6)
+    n_pts = 10**8
+    ms_pts = timed(lambda: rs.rs_points(ctx, [2**31, 2**31], n_pts, 5, N0, buf, stream), args.row_steps)
+    if rs.rs_sync(ctx, stream) != rs.RS_OK:
+        raise RuntimeError("points failed")
+    out["f4_points"] = {"workload": f"n=1e8 points in [0, 2^31)^2 with replacement, n0={N0}",
+                        "ms_per_call": ms_pts, "points_per_s": n_pts / (ms_pts / 1000),
+                        "write_gbs": 16 * n_pts / (ms_pts / 1000) / 1e9,
+                        "note": "whole call: box tree, leaf records and their largest volume and count (read "
+                                "back), leaf WR indices, decode to coordinates"}
     del buf
     return out
 

@@ -246,6 +246,28 @@ int rs_peel_state(rs_peel* it, uint64_t* n_left, uint64_t* N_left, uint64_t* bat
 /* Waits for the device and frees the iterator. */
 int rs_peel_destroy(rs_peel* it);
 
+/* ---- Sampling with replacement from a d-dimensional box (Sec. 4.6) -----
+ * n points drawn uniformly and independently from the integer box
+ * [0, E_0) x ... x [0, E_{d-1}) by bisection: the split tree of the
+ * one-dimensional sampler with replacement (depth as rs_sample's with N =
+ * the volume V), over boxes.  Node v (heap numbering, root 1 = the whole box
+ * with n points) halves its largest extent e (lowest dimension on ties):
+ * the lower half, extent floor(e/2), gets BIN(c, floor(e/2), e) of its c
+ * points (stream (SPLIT, v)), the upper half the rest.  Leaf box i (node
+ * 2^D + i) draws its points as row-major indices into itself (dimension 0
+ * most significant), as the with-replacement leaf of node 2^D + i over
+ * [0, its volume) (sorted), and writes their coordinates. */
+
+/* out_dev: n * d uint64 (device memory, 8-byte aligned), point j's 0-based
+ * coordinates at out_dev[j d .. j d + d); the points leaf after leaf, each
+ * leaf's in row-major order.  1 <= d <= 4, every E_k >= 1, V <= 2^62.
+ * Asynchronous after one wait for the tree (the leaves' largest volume and
+ * count pick the leaf kernel); device errors as rs_sync.  Errors:
+ * RS_EINVAL, RS_ECAPACITY (depth above the library's limit), RS_ENOMEM,
+ * RS_ECUDA. */
+int rs_points(rs_ctx* ctx, uint32_t d, const uint64_t* extents_host, uint64_t n, uint64_t seed, uint32_t n0,
+              uint64_t* out_dev, void* stream);
+
 /* ---- Resident trees and online sorted range queries -------------------
  * A resident tree holds, in device memory owned by the library, the leaf
  * records (range, count, output offset) of the split tree of one sample

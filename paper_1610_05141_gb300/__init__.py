@@ -89,6 +89,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "rs_bernoulli_by_size": (i32, [vp, dbl, u64, u64, u32, u64, u64, vp, u64, ctypes.POINTER(u64),
                                        ctypes.POINTER(u64), vp]),
         "rs_union_key": (u64, [u64, u32]),
+        "rs_points": (i32, [vp, u32, vp, u64, u64, u32, vp, vp]),
         "rs_peel_create": (i32, [vp, u64, u64, u64, u32, u32, ctypes.POINTER(vp)]),
         "rs_peel_next": (i32, [vp, vp, u64, ctypes.POINTER(u64), ctypes.POINTER(u32), vp]),
         "rs_peel_state": (i32, [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u64)]),
@@ -264,6 +265,13 @@ def rs_union_sample(ctx: Context, L, n, seed, n0, out, stream=None):
     _check(load().rs_union_sample(ctx.handle, L.ctypes.data, len(L), n, seed, n0, _ptr(out), counts.ctypes.data,
                                   _stream(stream)), "rs_union_sample")
     return counts[: len(L)]
+
+
+def rs_points(ctx: Context, E, n, seed, n0, out, stream=None):
+    """n points uniform in the box [0, E_0) x ... into out (n * d int64, point-major)."""
+    import numpy as np
+    E = np.ascontiguousarray(E, dtype=np.uint64)
+    _check(load().rs_points(ctx.handle, len(E), E.ctypes.data, n, seed, n0, _ptr(out), _stream(stream)), "rs_points")
 
 
 class Peel:

@@ -10,6 +10,7 @@
 
 #include "rs_bern.h"
 #include "rs_internal.h"
+#include "rs_points.h"
 #include "rs_union.h"
 
 struct rs_ctx {
@@ -25,6 +26,8 @@ struct rs_ctx {
     uint64_t big_pool_bytes = 0;
     uint64_t* words = nullptr;      // general scratch (Bernoulli chunk counts, leaf B positions)
     uint64_t words_cap = 0;
+    uint64_t* boxes = nullptr;      // box records of the multi-dimensional sampler
+    uint64_t boxes_cap = 0;         // words
     uint64_t* stage = nullptr;      // Bernoulli: positions staged per chunk by the single walk
     uint64_t stage_cap = 0;
     uint64_t stage_max_words = 1ull << 31;   // rs_set_bernoulli_staging
@@ -379,6 +382,7 @@ int rs_destroy(rs_ctx* ctx) {
     cudaFree(ctx->big_pool);
     cudaFree(ctx->words);
     cudaFree(ctx->stage);
+    cudaFree(ctx->boxes);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : ctx->ev_part) cudaEventDestroy(e);
     if (ctx->ev_copied) cudaEventDestroy(ctx->ev_copied);
@@ -597,6 +601,75 @@ int rs_union_sample(rs_ctx* ctx, const uint64_t* L_host, uint32_t p, uint64_t n,
     const int rd = rs_batch_destroy(B);
     for (uint32_t r = 0; !rc && r < R; ++r) rc = sh[r];
     return rc ? rc : rd;
+}
+
+int rs_points(rs_ctx* ctx, uint32_t d, const uint64_t* extents_host, uint64_t n, uint64_t seed, uint32_t n0,
+              uint64_t* out_dev, void* stream) {
+    if (!ctx || d == 0 || d > rs::kPointsMaxDim || !extents_host || n0 == 0) return RS_EINVAL;
+    if (n > 0 && (!out_dev || ((uintptr_t)out_dev & 7))) return RS_EINVAL;
+    rs::BoxExtents E{};
+    unsigned __int128 V = 1;
+    for (uint32_t k = 0; k < d; ++k) {
+        if (extents_host[k] == 0) return RS_EINVAL;
+        E.e[k] = extents_host[k];
+        V *= extents_host[k];
+        if (V > ((unsigned __int128)1 << 62)) return RS_EINVAL;
+    }
+    if (n == 0) return RS_OK;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return RS_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int D = depth_of(n, (uint64_t)V, n0);
+    if (D > rs::kMaxDepth) return RS_ECAPACITY;
+    const uint64_t nleaves = 1ull << D;
+    constexpr uint64_t kBoxWords = sizeof(rs::BoxRec) / sizeof(uint64_t);
+    int rc = ensure(ctx->boxes, ctx->boxes_cap, kBoxWords * 2 * nleaves);
+    if (!rc) rc = ensure(ctx->nodes, ctx->nodes_cap, nleaves);
+    if (!rc) rc = ensure(ctx->words, ctx->words_cap, n + 2);
+    if (!rc) rc = ensure(ctx->ovf, ctx->ovf_cap, nleaves + 1);
+    if (rc) return rc;
+    rs::BoxRec* boxes = reinterpret_cast<rs::BoxRec*>(ctx->boxes);
+    uint64_t* idx = ctx->words;
+    unsigned long long* stats = reinterpret_cast<unsigned long long*>(ctx->words + n);
+    rc = cuda_rc(rs::launch_points_tree(boxes, d, E, n, seed, D, ctx->tab, ctx->status, st));
+    if (!rc) rc = cuda_rc(cudaMemsetAsync(stats, 0, 2 * sizeof(uint64_t), st));
+    if (!rc) rc = cuda_rc(rs::launch_points_leaf_recs(boxes + nleaves, nleaves, d, ctx->nodes, stats, st));
+    ctx->launches += 2 + (uint64_t)D;
+    uint64_t sh[2] = {0, 0};
+    if (!rc) rc = cuda_rc(cudaMemcpyAsync(sh, stats, sizeof(sh), cudaMemcpyDeviceToHost, st));
+    if (!rc) rc = cuda_rc(cudaStreamSynchronize(st));
+    if (rc) return rc;
+    // the general path takes leaves above the shared-memory table's room
+    const uint64_t big_kmax = std::min<uint64_t>(std::max<uint64_t>(sh[1], 64), rs::kBigLeafMax);
+    const uint64_t bytes = rs::big_pool_bytes(big_kmax);
+    if (ctx->big_pool_bytes < bytes) {
+        if (ctx->big_pool) cudaFree(ctx->big_pool);
+        ctx->big_pool = nullptr;
+        ctx->big_pool_bytes = 0;
+        rc = cuda_rc(cudaMalloc(&ctx->big_pool, bytes));
+        if (rc) return rc;
+        ctx->big_pool_bytes = bytes;
+    }
+    rs::LeafLaunch L{};
+    L.leaves = ctx->nodes;
+    L.nleaves = nleaves;
+    L.first_id = nleaves;
+    L.seed = seed;
+    L.smax = sh[0];
+    L.out = idx;
+    L.status = ctx->status;
+    L.ovf_list = ctx->ovf;
+    L.ovf_count = ctx->ovf + nleaves;
+    L.big_pool = ctx->big_pool;
+    L.big_kmax = big_kmax;
+    L.cap = ctx->leaf_cap;
+    L.sms = ctx->sms;
+    L.with_replacement = true;
+    L.mean_count = n >> D;
+    rc = cuda_rc(rs::launch_leaves(L, st));
+    if (!rc) rc = cuda_rc(rs::launch_points_decode(boxes + nleaves, nleaves, d, idx, out_dev, ctx->sms, st));
+    ctx->launches += 3;
+    return rc;
 }
 
 int rs_sync(rs_ctx* ctx, void* stream) {
