@@ -361,9 +361,16 @@ def run_rows(rs, ctx, stream, args):
         stream.synchronize()
         return e0.elapsed_time(e1) / steps
 
+    rows = set(args.rows.split(","))
+
+    def want(name):
+        return name in rows
+
     buf = torch.empty(10**9, dtype=torch.int64, device="cuda")
     for name, call, N, steps in (("a5_with_replacement", rs.rs_sample_with_replacement, 2**40, args.row_steps),
                                  ("a7_leaf_b", rs.rs_sample_b, 2**50, max(1, args.row_steps // 3))):
+        if not want(name.split("_")[0]):
+            continue
         rs.rs_set_profiling(ctx, True)
         ms = timed(lambda: call(ctx, 10**9, N, 3, N0, buf, stream), steps)
         tree_ms, leaf_ms, calls = rs.rs_phase_totals(ctx)
@@ -374,120 +381,129 @@ def run_rows(rs, ctx, stream, args):
         out[name] = {"workload": f"n=1e9 from 1..2^{N.bit_length() - 1}, n0={N0}", "ms_per_step": ms,
                      "samples_per_s": 1e9 / (ms / 1000), "phases_ms": {"split_tree": tree_ms / calls, "leaves": leaf},
                      "leaf_write_gbs": 8e9 / (leaf / 1000) / 1e9, "leaf_frac_of_hbm": 8e9 / (leaf / 1000) / 1e9 / peak}
-    bern = {}
-    for p, windows, steps in ((1e-4, 1, args.row_steps), (1e-2, 1, args.row_steps), (0.5, 8, 2)):
-        if windows > 1:   # p = 0.5: a 34 GB buffer reused by every window, and room to stage its positions
+    if want("a6"):
+        bern = {}
+        for p, windows, steps in ((1e-4, 1, args.row_steps), (1e-2, 1, args.row_steps), (0.5, 8, 2)):
+            if windows > 1:   # p = 0.5: a 34 GB buffer reused by every window, and room to stage its positions
+                del buf
+                torch.cuda.empty_cache()
+                buf = torch.empty((1 << 32) + (1 << 20), dtype=torch.int64, device="cuda")
+                rs.rs_set_bernoulli_staging(ctx, 48 << 30)
+            cap = buf.numel()
+            width = 2**36 // windows
+            holder = {"rc": rs.RS_OK, "count": 0}
+
+            def call_b():
+                total = 0
+                for w in range(windows):
+                    rc, c = rs.rs_bernoulli(ctx, p, 2**36, 5, N0, w * width, (w + 1) * width, buf, cap, stream,
+                                            check=False)
+                    if rc != rs.RS_OK:
+                        holder["rc"] = rc
+                    total += c
+                holder["count"] = total
+
+            ms = timed(call_b, steps)
+            if holder["rc"] != rs.RS_OK:
+                raise RuntimeError(f"bernoulli p={p} failed: {holder['rc']}")
+            cnt = holder["count"]
+            bern[f"p={p:g}"] = {"positions": 2**36, "windows": windows, "emitted": cnt, "ms_per_call": ms,
+                                "emitted_per_s": cnt / (ms / 1000), "positions_per_s": 2**36 / (ms / 1000),
+                                "write_gbs": 8 * cnt / (ms / 1000) / 1e9,
+                                "note": "whole range: per window one walk with staged positions, the scan of the "
+                                        "counts, the copy into place, and the count read back"}
+        rs.rs_set_bernoulli_staging(ctx)
+        out["a6_bernoulli"] = {"N": 2**36, "n0": N0, "by_p": bern}
+    if want("f2"):
+        if buf.numel() < (1 << 32):   # p = 0.5: windows of 2^32 expected values
             del buf
             torch.cuda.empty_cache()
             buf = torch.empty((1 << 32) + (1 << 20), dtype=torch.int64, device="cuda")
-            rs.rs_set_bernoulli_staging(ctx, 48 << 30)
+        # the next row (f2): Bernoulli sampling by its size (Sec. 4.7) -- the
+        # BIN(N, p) size, then the sample without replacement of that size; p =
+        # 0.5 as a resident split tree and 8 window queries into the same buffer
         cap = buf.numel()
-        width = 2**36 // windows
-        holder = {"rc": rs.RS_OK, "count": 0}
+        by_size = {}
+        for p, windows, steps in ((1e-4, 1, args.row_steps), (1e-2, 1, args.row_steps), (0.5, 8, 2)):
+            holder = {"count": 0}
 
-        def call_b():
-            total = 0
-            for w in range(windows):
-                rc, c = rs.rs_bernoulli(ctx, p, 2**36, 5, N0, w * width, (w + 1) * width, buf, cap, stream,
-                                        check=False)
-                if rc != rs.RS_OK:
-                    holder["rc"] = rc
-                total += c
-            holder["count"] = total
+            def call_s():
+                if windows == 1:
+                    rc, cnt, _ = rs.rs_bernoulli_by_size(ctx, p, 2**36, 5, N0, 0, 2**36, buf, cap, stream)
+                    holder["count"] = cnt
+                    return
+                n = rs.rs_bernoulli_size(ctx, p, 2**36, 5, stream)
+                tree = rs.rs_tree_create(ctx, n, 2**36, 5, N0, rs.RS_KIND_H, stream)
+                width = 2**36 // windows
+                total = 0
+                for w in range(windows):
+                    _, c = rs.rs_tree_query(tree, w * width + 1, (w + 1) * width + 1, buf, cap, stream)
+                    total += c
+                tree.close()
+                holder["count"] = total
 
-        ms = timed(call_b, steps)
-        if holder["rc"] != rs.RS_OK:
-            raise RuntimeError(f"bernoulli p={p} failed: {holder['rc']}")
-        cnt = holder["count"]
-        bern[f"p={p:g}"] = {"positions": 2**36, "windows": windows, "emitted": cnt, "ms_per_call": ms,
-                            "emitted_per_s": cnt / (ms / 1000), "positions_per_s": 2**36 / (ms / 1000),
-                            "write_gbs": 8 * cnt / (ms / 1000) / 1e9,
-                            "note": "whole range: per window one walk with staged positions, the scan of the "
-                                    "counts, the copy into place, and the count read back"}
-    rs.rs_set_bernoulli_staging(ctx)
-    out["a6_bernoulli"] = {"N": 2**36, "n0": N0, "by_p": bern}
-    # the next row (f2): Bernoulli sampling by its size (Sec. 4.7) -- the
-    # BIN(N, p) size, then the sample without replacement of that size; p =
-    # 0.5 as a resident split tree and 8 window queries into the same buffer
-    cap = buf.numel()
-    by_size = {}
-    for p, windows, steps in ((1e-4, 1, args.row_steps), (1e-2, 1, args.row_steps), (0.5, 8, 2)):
-        holder = {"count": 0}
-
-        def call_s():
-            if windows == 1:
-                rc, cnt, _ = rs.rs_bernoulli_by_size(ctx, p, 2**36, 5, N0, 0, 2**36, buf, cap, stream)
-                holder["count"] = cnt
-                return
-            n = rs.rs_bernoulli_size(ctx, p, 2**36, 5, stream)
-            tree = rs.rs_tree_create(ctx, n, 2**36, 5, N0, rs.RS_KIND_H, stream)
-            width = 2**36 // windows
-            total = 0
-            for w in range(windows):
-                _, c = rs.rs_tree_query(tree, w * width + 1, (w + 1) * width + 1, buf, cap, stream)
-                total += c
-            tree.close()
-            holder["count"] = total
-
-        ms = timed(call_s, steps)
+            ms = timed(call_s, steps)
+            if rs.rs_sync(ctx, stream) != rs.RS_OK:
+                raise RuntimeError(f"bernoulli by size p={p} failed")
+            cnt = holder["count"]
+            by_size[f"p={p:g}"] = {"positions": 2**36, "windows": windows, "emitted": cnt, "ms_per_call": ms,
+                                   "emitted_per_s": cnt / (ms / 1000), "write_gbs": 8 * cnt / (ms / 1000) / 1e9,
+                                   "note": "whole call: the size (read back), then rs_sample of that size, or the "
+                                           "split tree and one range query per window"}
+        out["f2_bernoulli_by_size"] = {"N": 2**36, "n0": N0, "by_p": by_size}
+    if want("f3"):
+        # the next row (f3): a sample of 1e8 from the union of 4096 segments of
+        # uneven sizes (Sec. 4.5): the count tree, then the segments' samples as
+        # one batch
+        from paper_1610_05141_gb300.workloads import union_segments
+        L = union_segments()
+        n_u = 10**8
+        ms_counts = timed(lambda: rs.rs_union_counts(ctx, L, n_u, 5, stream), args.row_steps)
+        ms_union = timed(lambda: rs.rs_union_sample(ctx, L, n_u, 5, N0, buf, stream), args.row_steps)
+        out["f3_union"] = {"workload": f"n=1e8 from the union of {len(L)} segments of sizes log-uniform in "
+                                       f"2^20..2^40 (total {int(L.sum()):.3e}), n0={N0}",
+                           "ms_per_call": ms_union, "samples_per_s": n_u / (ms_union / 1000),
+                           "count_tree_ms": ms_counts,
+                           "note": "whole call: sizes to the device, the count tree, counts read back, the "
+                                   "segments' batch planned and run, statuses read back"}
+    if want("f1"):
+        # the next row (f1): online sorted sampling by peeling (Sec. 4.1), n = 1e7
+        # from 2^50 in batches of about n0 = 4096 values
+        n_p, N_p = 10**7, 2**50
+        peel = {}
+        for B in (1, 256):
+            it = rs.rs_peel_create(ctx, n_p, N_p, 5, N0, B)
+            calls, made, t0 = 0, 0, time.perf_counter()
+            first = None
+            while True:
+                _, cnt, nb = it.next(buf, 1 << 21, stream)
+                if first is None:
+                    first = (time.perf_counter() - t0) * 1e3
+                if nb == 0:
+                    break
+                calls += 1
+                made += cnt
+                if B == 1 and calls == 400:
+                    break
+            ms = (time.perf_counter() - t0) * 1e3
+            it.close()
+            peel[f"batches_per_call={B}"] = {"calls": calls, "values": made, "ms": ms, "ms_per_call": ms / calls,
+                                            "first_call_ms": first, "values_per_s": made / (ms / 1000)}
+        out["f1_peel"] = {"workload": f"n=1e7 from 1..2^50 in batches of about n0={N0}", "by_batches": peel,
+                          "note": "host wall time of synchronous calls: the chain of hypergeometric deviates "
+                                  "(one thread), the counts read back, one leaf launch for the call's batches"}
+    if want("f4"):
+        # the next row (f4): 1e8 points uniform in the square [0, 2^31)^2, with
+        # replacement, by bisection (Sec. 4.6)
+        n_pts = 10**8
+        ms_pts = timed(lambda: rs.rs_points(ctx, [2**31, 2**31], n_pts, 5, N0, buf, stream), args.row_steps)
         if rs.rs_sync(ctx, stream) != rs.RS_OK:
-            raise RuntimeError(f"bernoulli by size p={p} failed")
-        cnt = holder["count"]
-        by_size[f"p={p:g}"] = {"positions": 2**36, "windows": windows, "emitted": cnt, "ms_per_call": ms,
-                               "emitted_per_s": cnt / (ms / 1000), "write_gbs": 8 * cnt / (ms / 1000) / 1e9,
-                               "note": "whole call: the size (read back), then rs_sample of that size, or the "
-                                       "split tree and one range query per window"}
-    out["f2_bernoulli_by_size"] = {"N": 2**36, "n0": N0, "by_p": by_size}
-    # the next row (f3): a sample of 1e8 from the union of 4096 segments of
-    # uneven sizes (Sec. 4.5): the count tree, then the segments' samples as
-    # one batch
-    from paper_1610_05141_gb300.workloads import union_segments
-    L = union_segments()
-    n_u = 10**8
-    ms_counts = timed(lambda: rs.rs_union_counts(ctx, L, n_u, 5, stream), args.row_steps)
-    ms_union = timed(lambda: rs.rs_union_sample(ctx, L, n_u, 5, N0, buf, stream), args.row_steps)
-    out["f3_union"] = {"workload": f"n=1e8 from the union of {len(L)} segments of sizes log-uniform in "
-                                   f"2^20..2^40 (total {int(L.sum()):.3e}), n0={N0}",
-                       "ms_per_call": ms_union, "samples_per_s": n_u / (ms_union / 1000),
-                       "count_tree_ms": ms_counts,
-                       "note": "whole call: sizes to the device, the count tree, counts read back, the "
-                               "segments' batch planned and run, statuses read back"}
-    # the next row (f1): online sorted sampling by peeling (Sec. 4.1), n = 1e7
-    # from 2^50 in batches of about n0 = 4096 values
-    n_p, N_p = 10**7, 2**50
-    peel = {}
-    for B in (1, 256):
-        it = rs.rs_peel_create(ctx, n_p, N_p, 5, N0, B)
-        calls, made, t0 = 0, 0, time.perf_counter()
-        first = None
-        while True:
-            _, cnt, nb = it.next(buf, 1 << 21, stream)
-            if first is None:
-                first = (time.perf_counter() - t0) * 1e3
-            if nb == 0:
-                break
-            calls += 1
-            made += cnt
-            if B == 1 and calls == 400:
-                break
-        ms = (time.perf_counter() - t0) * 1e3
-        it.close()
-        peel[f"batches_per_call={B}"] = {"calls": calls, "values": made, "ms": ms, "ms_per_call": ms / calls,
-                                        "first_call_ms": first, "values_per_s": made / (ms / 1000)}
-    out["f1_peel"] = {"workload": f"n=1e7 from 1..2^50 in batches of about n0={N0}", "by_batches": peel,
-                      "note": "host wall time of synchronous calls: the chain of hypergeometric deviates "
-                              "(one thread), the counts read back, one leaf launch for the call's batches"}
-    # the next row (f4): 1e8 points uniform in the square [0, 2^31)^2, with
-    # replacement, by bisection (Sec. 4.6)
-    n_pts = 10**8
-    ms_pts = timed(lambda: rs.rs_points(ctx, [2**31, 2**31], n_pts, 5, N0, buf, stream), args.row_steps)
-    if rs.rs_sync(ctx, stream) != rs.RS_OK:
-        raise RuntimeError("points failed")
-    out["f4_points"] = {"workload": f"n=1e8 points in [0, 2^31)^2 with replacement, n0={N0}",
-                        "ms_per_call": ms_pts, "points_per_s": n_pts / (ms_pts / 1000),
-                        "write_gbs": 16 * n_pts / (ms_pts / 1000) / 1e9,
-                        "note": "whole call: box tree, leaf records and their largest volume and count (read "
-                                "back), leaf WR indices, decode to coordinates"}
+            raise RuntimeError("points failed")
+        out["f4_points"] = {"workload": f"n=1e8 points in [0, 2^31)^2 with replacement, n0={N0}",
+                            "ms_per_call": ms_pts, "points_per_s": n_pts / (ms_pts / 1000),
+                            "write_gbs": 16 * n_pts / (ms_pts / 1000) / 1e9,
+                            "note": "whole call: box tree, leaf records and their largest volume and count (read "
+                                    "back), leaf WR indices, decode to coordinates"}
     del buf
     return out
 
@@ -805,6 +821,8 @@ def main():
     ap.add_argument("--unbatched-requests", type=int, default=3000)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-rows", action="store_true", help="skip with-replacement, leaf B and Bernoulli")
+    ap.add_argument("--rows", default="a5,a7,a6,f2,f3,f1,f4",
+                    help="which of the other rows to run (comma-separated: a5,a7,a6,f2,f3,f1,f4)")
     ap.add_argument("--row-steps", type=int, default=6)
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="length of each open-loop serving run")
     ap.add_argument("--serve-capacity-jobs", type=int, default=4000)

@@ -16,10 +16,37 @@ namespace rs {
 constexpr uint64_t kRouMaxTrials = 1ull << 20;
 constexpr uint64_t kInvMaxRestarts = 64;
 
+// Warp-cooperative forms (WARP = true): every lane of a full warp calls with
+// the same arguments and gets the same result.  Inversion restart r and
+// ratio-of-uniforms trial i run on lane r mod 32 (i mod 32) in round r / 32
+// (i / 32); the result is that of the first restart or trial in index order
+// that succeeds, exactly as in the one-thread form, in about one trial's
+// latency instead of the expected number of trials' (GB300 issues an FP64
+// warp instruction at the same cost whatever its active lanes).
+template <bool WARP>
+struct TrialLanes {
+    static constexpr uint64_t step = WARP ? 32 : 1;
+    RS_DEV static uint64_t lane() { return WARP ? (threadIdx.x & 31u) : 0; }
+    // Among the lanes' outcomes (ok, value), the first lane's that succeeded.
+    RS_DEV static bool first(bool ok, uint64_t v, uint64_t& out) {
+        if constexpr (WARP) {
+            const unsigned acc = __ballot_sync(0xffffffffu, ok);
+            if (!acc) return false;
+            out = __shfl_sync(0xffffffffu, v, __ffs(acc) - 1);
+            return true;
+        } else {
+            if (ok) out = v;
+            return ok;
+        }
+    }
+};
+
 // HG(n, K, S): successes among n draws without replacement from S items
 // containing K successes.  Returns RS_OK or RS_EITER.
-RS_DEV int hypergeometric(Key2 key, uint64_t node, uint64_t n, uint64_t K, uint64_t S,
-                          const double* __restrict__ tab, uint64_t& out) {
+template <bool WARP>
+RS_DEV int hypergeometric_t(Key2 key, uint64_t node, uint64_t n, uint64_t K, uint64_t S,
+                            const double* __restrict__ tab, uint64_t& out) {
+    using TL = TrialLanes<WARP>;
     if (n == 0 || K == 0) { out = 0; return RS_OK; }
     if (K == S) { out = n; return RS_OK; }
     if (n == S) { out = K; return RS_OK; }
@@ -39,17 +66,21 @@ RS_DEV int hypergeometric(Key2 key, uint64_t node, uint64_t n, uint64_t K, uint6
         // Inversion from k = 0 with the pmf recurrence
         // f(k+1) = f(k) (a-k)(b-k) / ((k+1)(S-a-b+k+1)).
         const double f0 = dexp(dsd(S - b, S - a - b, tab) - dsd(S, S - a, tab));
-        for (uint64_t r = 0; r < kInvMaxRestarts && !done; ++r) {
+        for (uint64_t r0 = 0; r0 < kInvMaxRestarts && !done; r0 += TL::step) {
+            const uint64_t r = r0 + TL::lane();
             double u = v_closed(stream_value(key, TAG_SPLIT, node, r));
             double f = f0;
+            bool ok = false;
+            uint64_t yk = 0;
             for (uint64_t k = 0; k <= a; ++k) {
-                if (u < f) { y = k; done = true; break; }
+                if (u < f) { yk = k; ok = true; break; }
                 u = u - f;
                 f = (f * ((double)(a - k) * (double)(b - k))) / ((double)(k + 1) * (double)(S - a - b + k + 1));
                 // Once f underflows to 0 it stays 0 and u no longer changes, so
                 // this pass can only run past a: restart now (same outcome).
                 if (f == 0.0) break;
             }
+            done = TL::first(ok, yk, y);
         }
     } else {
         const double var = mu * ((double)(S - a) * rS) * ((double)(S - b) * drecip((double)(S - 1)));
@@ -60,16 +91,21 @@ RS_DEV int hypergeometric(Key2 key, uint64_t node, uint64_t n, uint64_t K, uint6
         const double top = (double)a + 1.0;
         const double l0 = log_fixed(M, tab), l1 = log_fixed(a - M, tab), l2 = log_fixed(b - M, tab),
                      l3 = log_fixed(m + M, tab);
-        for (uint64_t i = 0; i < kRouMaxTrials; ++i) {
+        for (uint64_t i0 = 0; i0 < kRouMaxTrials && !done; i0 += TL::step) {
+            const uint64_t i = i0 + TL::lane();
             const uint4 blk = philox_block((uint32_t)i, TAG_SPLIT, node, key);
             const double U = u_open(((uint64_t)blk.y << 32) | blk.x);
             const double V = v_closed(((uint64_t)blk.w << 32) | blk.z);
             const double X = alpha + h * (V - 0.5) * drecip(U);
-            if (X < 0.0 || X >= top) continue;
-            const uint64_t k = (uint64_t)X;
-            const double T = dsd_fixed(M, k, l0, tab) + dsd_fixed(a - M, a - k, l1, tab) +
-                             dsd_fixed(b - M, b - k, l2, tab) + dsd_fixed(m + M, m + k, l3, tab);
-            if (2.0 * dlog(U, tab) <= T) { y = k; done = true; break; }
+            bool ok = false;
+            uint64_t k = 0;
+            if (X >= 0.0 && X < top) {
+                k = (uint64_t)X;
+                const double T = dsd_fixed(M, k, l0, tab) + dsd_fixed(a - M, a - k, l1, tab) +
+                                 dsd_fixed(b - M, b - k, l2, tab) + dsd_fixed(m + M, m + k, l3, tab);
+                ok = 2.0 * dlog(U, tab) <= T;
+            }
+            done = TL::first(ok, k, y);
         }
     }
     if (!done) return RS_EITER;
@@ -80,23 +116,29 @@ RS_DEV int hypergeometric(Key2 key, uint64_t node, uint64_t n, uint64_t K, uint6
 }
 
 // BIN(c, p = K/S) with K/S <= 1/2.  Returns RS_OK or RS_EITER.
-RS_DEV int binomial(Key2 key, uint64_t node, uint64_t c, uint64_t K, uint64_t S,
-                    const double* __restrict__ tab, uint64_t& out) {
+template <bool WARP>
+RS_DEV int binomial_t(Key2 key, uint64_t node, uint64_t c, uint64_t K, uint64_t S,
+                      const double* __restrict__ tab, uint64_t& out) {
+    using TL = TrialLanes<WARP>;
     if (c == 0 || K == 0) { out = 0; return RS_OK; }
     const double p = (double)K / (double)S;
     const double mu = (double)c * p;
     if (mu < 16.0) {
         const double f0 = dexp((double)c * dlog1p(-p, tab));
         const double r = p / (1.0 - p);
-        for (uint64_t rs = 0; rs < kInvMaxRestarts; ++rs) {
-            double u = v_closed(stream_value(key, TAG_SPLIT, node, rs));
+        for (uint64_t q0 = 0; q0 < kInvMaxRestarts; q0 += TL::step) {
+            const uint64_t q = q0 + TL::lane();
+            double u = v_closed(stream_value(key, TAG_SPLIT, node, q));
             double f = f0;
+            bool ok = false;
+            uint64_t yk = 0;
             for (uint64_t k = 0; k <= c; ++k) {
-                if (u < f) { out = k; return RS_OK; }
+                if (u < f) { yk = k; ok = true; break; }
                 u = u - f;
                 f = (f * ((double)(c - k) * r)) / (double)(k + 1);
                 if (f == 0.0) break;
             }
+            if (TL::first(ok, yk, out)) return RS_OK;
         }
         return RS_EITER;
     }
@@ -108,18 +150,40 @@ RS_DEV int binomial(Key2 key, uint64_t node, uint64_t c, uint64_t K, uint64_t S,
     const uint64_t M = (uint64_t)(((unsigned __int128)(c + 1) * K) / S);
     const double top = (double)c + 1.0;
     const double l0 = log_fixed(M, tab), l1 = log_fixed(c - M, tab);
-    for (uint64_t i = 0; i < kRouMaxTrials; ++i) {
+    for (uint64_t i0 = 0; i0 < kRouMaxTrials; i0 += TL::step) {
+        const uint64_t i = i0 + TL::lane();
         const uint4 blk = philox_block((uint32_t)i, TAG_SPLIT, node, key);
         const double U = u_open(((uint64_t)blk.y << 32) | blk.x);
         const double V = v_closed(((uint64_t)blk.w << 32) | blk.z);
         const double X = alpha + h * (V - 0.5) * drecip(U);
-        if (X < 0.0 || X >= top) continue;
-        const uint64_t k = (uint64_t)X;
-        const double T = dsd_fixed(M, k, l0, tab) + dsd_fixed(c - M, c - k, l1, tab) +
-                         (double)((int64_t)k - (int64_t)M) * logr;
-        if (2.0 * dlog(U, tab) <= T) { out = k; return RS_OK; }
+        bool ok = false;
+        uint64_t k = 0;
+        if (X >= 0.0 && X < top) {
+            k = (uint64_t)X;
+            const double T = dsd_fixed(M, k, l0, tab) + dsd_fixed(c - M, c - k, l1, tab) +
+                             (double)((int64_t)k - (int64_t)M) * logr;
+            ok = 2.0 * dlog(U, tab) <= T;
+        }
+        if (TL::first(ok, k, out)) return RS_OK;
     }
     return RS_EITER;
+}
+
+RS_DEV int hypergeometric(Key2 key, uint64_t node, uint64_t n, uint64_t K, uint64_t S,
+                          const double* __restrict__ tab, uint64_t& out) {
+    return hypergeometric_t<false>(key, node, n, K, S, tab, out);
+}
+RS_DEV int hypergeometric_warp(Key2 key, uint64_t node, uint64_t n, uint64_t K, uint64_t S,
+                               const double* __restrict__ tab, uint64_t& out) {
+    return hypergeometric_t<true>(key, node, n, K, S, tab, out);
+}
+RS_DEV int binomial(Key2 key, uint64_t node, uint64_t c, uint64_t K, uint64_t S,
+                    const double* __restrict__ tab, uint64_t& out) {
+    return binomial_t<false>(key, node, c, K, S, tab, out);
+}
+RS_DEV int binomial_warp(Key2 key, uint64_t node, uint64_t c, uint64_t K, uint64_t S,
+                         const double* __restrict__ tab, uint64_t& out) {
+    return binomial_t<true>(key, node, c, K, S, tab, out);
 }
 
 }  // namespace rs

@@ -6,8 +6,9 @@
 // off the next m_t = ceil(N_t n0 / n_t) positions and takes HG(n_t, m_t, N_t)
 // of the samples (stream (SPLIT, t + 1)); once m_t >= N_t the batch is the
 // rest.  Its values are leaf H of node t + 1 over [lo_t, lo_t + m_t).  The
-// chain of deviates is sequential by definition: one thread walks it for the
-// batches of a call, then one leaf launch makes all their values.
+// chain of deviates is sequential by definition: one warp walks it for the
+// batches of a call (each deviate's trials spread over its lanes), then one
+// leaf launch makes all their values.
 #include <new>
 
 #include "rs_deviates.cuh"
@@ -27,7 +28,10 @@ struct PeelState {
 // batch that did not fit (0 if none), then the new state's n, N, t.
 __global__ void peel_chain_kernel(PeelState* st, uint32_t n0, uint64_t seed, uint32_t max_batches, uint64_t cap,
                                   NodeRec* rec, uint64_t* info, const double* __restrict__ tab, int* status) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    // one warp: the state is the same in every lane, the lanes share each
+    // deviate's trials, lane 0 writes
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+    const bool lead = threadIdx.x == 0;
     PeelState s = *st;
     const Key2 key = make_key(seed);
     uint64_t off = 0, maxm = 0, maxk = 0, need = 0;
@@ -40,9 +44,9 @@ __global__ void peel_chain_kernel(PeelState* st, uint32_t n0, uint64_t seed, uin
             c = s.n;
         } else {
             m = (uint64_t)m128;
-            const int rc = hypergeometric(key, s.t + 1, s.n, m, s.N, tab, c);
+            const int rc = hypergeometric_warp(key, s.t + 1, s.n, m, s.N, tab, c);
             if (rc != RS_OK) {
-                set_status(status, rc);
+                if (lead) set_status(status, rc);
                 break;
             }
         }
@@ -50,7 +54,7 @@ __global__ void peel_chain_kernel(PeelState* st, uint32_t n0, uint64_t seed, uin
             need = c;
             break;
         }
-        rec[b] = NodeRec{s.lo, m, c, off};
+        if (lead) rec[b] = NodeRec{s.lo, m, c, off};
         off += c;
         ++b;
         const uint64_t k = c < m - c ? c : m - c;
@@ -61,6 +65,7 @@ __global__ void peel_chain_kernel(PeelState* st, uint32_t n0, uint64_t seed, uin
         s.n -= c;
         s.t += 1;
     }
+    if (!lead) return;
     *st = s;
     info[0] = b;
     info[1] = off;

@@ -16,6 +16,8 @@
 namespace rs {
 
 constexpr int kPointsThreads = 128;
+// Levels of at most this many nodes take one warp per node.
+constexpr uint64_t kPointsWarpNodes = 1024;
 
 __global__ void box_root_kernel(BoxRec* rec, uint32_t d, BoxExtents E, uint64_t n) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -55,6 +57,39 @@ __global__ void __launch_bounds__(kPointsThreads) box_level_kernel(BoxRec* rec, 
     }
 }
 
+// The same for narrow levels: one warp per node, the deviate's trials spread
+// over the warp's lanes.
+__global__ void __launch_bounds__(kPointsThreads) box_level_warp_kernel(BoxRec* rec, uint64_t w, uint32_t d,
+                                                                        Key2 key, const double* __restrict__ tab,
+                                                                        int* status) {
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
+    for (uint64_t v = w + (uint64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; v < 2 * w; v += warps) {
+        const BoxRec r = rec[v];
+        uint32_t ks = 0;
+        for (uint32_t k = 1; k < d; ++k)
+            if (r.e[k] > r.e[ks]) ks = k;
+        const uint64_t half = r.e[ks] / 2;
+        uint64_t cl = 0;
+        int rc = RS_OK;
+        if (r.c > 0) rc = binomial_warp(key, v, r.c, half, r.e[ks], tab, cl);
+        if ((threadIdx.x & 31) == 0) {
+            if (rc != RS_OK) {
+                set_status(status, rc);
+                cl = 0;
+            }
+            BoxRec L = r, R = r;
+            L.e[ks] = half;
+            L.c = cl;
+            R.o[ks] = r.o[ks] + half;
+            R.e[ks] = r.e[ks] - half;
+            R.c = r.c - cl;
+            R.off = r.off + cl;
+            rec[2 * v] = L;
+            rec[2 * v + 1] = R;
+        }
+    }
+}
+
 __global__ void box_leaf_recs_kernel(const BoxRec* __restrict__ leaves, uint64_t nleaves, uint32_t d,
                                      NodeRec* __restrict__ nr, unsigned long long* stats) {
     unsigned long long mv = 0, mc = 0;
@@ -78,22 +113,51 @@ __global__ void box_leaf_recs_kernel(const BoxRec* __restrict__ leaves, uint64_t
     }
 }
 
+// Division by an extent e that stays fixed over a leaf, for dividends below
+// 2^62 (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", 1994, Thm. 4.2 with N = 62): with l = ceil(log2 e) and
+// m = ceil(2^(62+l) / e) < 2^64, floor(x / e) = floor(x m / 2^(62+l)) =
+// umulhi(x, m) >> (l - 2); powers of two by a shift.
+struct InvariantDiv {
+    uint64_t e, m;
+    uint32_t shift;
+    bool pow2;
+    RS_DEV void init(uint64_t ext) {
+        e = ext;
+        pow2 = (ext & (ext - 1)) == 0;
+        if (pow2) {
+            shift = 63 - __clzll(ext);
+            m = 0;
+        } else {
+            const uint32_t l = 64 - __clzll(ext - 1);
+            m = (uint64_t)((((unsigned __int128)1 << (62 + l)) - 1) / ext) + 1;
+            shift = l - 2;
+        }
+    }
+    RS_DEV uint64_t quot(uint64_t x) const { return pow2 ? x >> shift : __umul64hi(x, m) >> shift; }
+};
+
 // One block per leaf at a time: the leaf's points decoded by its threads.
 __global__ void __launch_bounds__(256) box_decode_kernel(const BoxRec* __restrict__ leaves, uint64_t nleaves,
                                                          uint32_t d, const uint64_t* __restrict__ idx,
                                                          uint64_t* __restrict__ out) {
+    __shared__ InvariantDiv div[kPointsMaxDim];
     for (uint64_t i = blockIdx.x; i < nleaves; i += gridDim.x) {
         const BoxRec r = leaves[i];
+        if (r.c == 0) continue;
+        if (threadIdx.x < d) div[threadIdx.x].init(r.e[threadIdx.x]);
+        __syncthreads();
         for (uint64_t j = threadIdx.x; j < r.c; j += blockDim.x) {
             uint64_t x = idx[r.off + j] - 1;
             uint64_t* pt = out + (r.off + j) * d;
             for (uint32_t k = d - 1; k > 0; --k) {
-                const uint64_t q = x / r.e[k];
+                const uint64_t q = div[k].quot(x);
                 pt[k] = r.o[k] + (x - q * r.e[k]);
                 x = q;
             }
             pt[0] = r.o[0] + x;
         }
+        __syncthreads();
     }
 }
 
@@ -106,8 +170,13 @@ cudaError_t launch_points_tree(BoxRec* rec, uint32_t d, const BoxExtents& E, uin
                                const double* tab, int* status, cudaStream_t st) {
     box_root_kernel<<<1, 32, 0, st>>>(rec, d, E, n);
     const Key2 key = make_key(seed);
-    for (int l = 0; l < D; ++l)
-        box_level_kernel<<<grid_of(1ull << l), kPointsThreads, 0, st>>>(rec, 1ull << l, d, key, tab, status);
+    for (int l = 0; l < D; ++l) {
+        const uint64_t w = 1ull << l;
+        if (w <= kPointsWarpNodes)
+            box_level_warp_kernel<<<grid_of(32 * w), kPointsThreads, 0, st>>>(rec, w, d, key, tab, status);
+        else
+            box_level_kernel<<<grid_of(w), kPointsThreads, 0, st>>>(rec, w, d, key, tab, status);
+    }
     return cudaGetLastError();
 }
 

@@ -52,6 +52,8 @@ CASES = [
     ([2**15] * 4, 100000, 5, 512),
     ([3, 1000003], 20000, 8, 100),
     ([2**16, 2**16], 20000000, 6, 4096),        # 2^13 leaves of 2^19 positions (32-bit keys)
+    ([2**31 - 1, 2**31 - 1], 300000, 13, 4096),  # odd extents near 2^31 in every leaf
+    ([3, 2**60 + 1], 100000, 14, 4096),         # odd extents near 2^55 after halving
 ]
 
 
