@@ -137,25 +137,56 @@ struct InvariantDiv {
     RS_DEV uint64_t quot(uint64_t x) const { return pow2 ? x >> shift : __umul64hi(x, m) >> shift; }
 };
 
-// One block per leaf at a time: the leaf's points decoded by its threads.
-__global__ void __launch_bounds__(256) box_decode_kernel(const BoxRec* __restrict__ leaves, uint64_t nleaves,
-                                                         uint32_t d, const uint64_t* __restrict__ idx,
-                                                         uint64_t* __restrict__ out) {
+constexpr int kDecodeThreads = 256;
+constexpr int kDecodeUnroll = 4;   // indices loaded per thread before any is decoded
+
+// One block per leaf at a time: the leaf's points decoded by its threads,
+// kDecodeUnroll loads in flight per thread; two-dimensional points as one
+// 16-byte store where the output allows.
+__global__ void __launch_bounds__(kDecodeThreads) box_decode_kernel(const BoxRec* __restrict__ leaves,
+                                                                    uint64_t nleaves, uint32_t d,
+                                                                    const uint64_t* __restrict__ idx,
+                                                                    uint64_t* __restrict__ out) {
     __shared__ InvariantDiv div[kPointsMaxDim];
+    const bool pair = d == 2 && ((uintptr_t)out & 15) == 0;
     for (uint64_t i = blockIdx.x; i < nleaves; i += gridDim.x) {
         const BoxRec r = leaves[i];
         if (r.c == 0) continue;
         if (threadIdx.x < d) div[threadIdx.x].init(r.e[threadIdx.x]);
         __syncthreads();
-        for (uint64_t j = threadIdx.x; j < r.c; j += blockDim.x) {
-            uint64_t x = idx[r.off + j] - 1;
-            uint64_t* pt = out + (r.off + j) * d;
-            for (uint32_t k = d - 1; k > 0; --k) {
-                const uint64_t q = div[k].quot(x);
-                pt[k] = r.o[k] + (x - q * r.e[k]);
-                x = q;
+        const uint64_t c = r.c, off = r.off, o0 = r.o[0], o1 = r.o[1], e1 = r.e[1];
+        for (uint64_t j0 = threadIdx.x; j0 < c; j0 += (uint64_t)kDecodeThreads * kDecodeUnroll) {
+            uint64_t xs[kDecodeUnroll];
+#pragma unroll
+            for (int u = 0; u < kDecodeUnroll; ++u) {
+                const uint64_t j = j0 + (uint64_t)u * kDecodeThreads;
+                xs[u] = j < c ? idx[off + j] - 1 : 0;
             }
-            pt[0] = r.o[0] + x;
+            if (pair) {
+                const InvariantDiv dv = div[1];
+#pragma unroll
+                for (int u = 0; u < kDecodeUnroll; ++u) {
+                    const uint64_t j = j0 + (uint64_t)u * kDecodeThreads;
+                    if (j >= c) break;
+                    const uint64_t q = dv.quot(xs[u]);
+                    *reinterpret_cast<ulonglong2*>(out + (off + j) * 2) =
+                        make_ulonglong2(o0 + q, o1 + (xs[u] - q * e1));
+                }
+                continue;
+            }
+#pragma unroll
+            for (int u = 0; u < kDecodeUnroll; ++u) {
+                const uint64_t j = j0 + (uint64_t)u * kDecodeThreads;
+                if (j >= c) break;
+                uint64_t x = xs[u];
+                uint64_t* pt = out + (off + j) * d;
+                for (uint32_t k = d - 1; k > 0; --k) {
+                    const uint64_t q = div[k].quot(x);
+                    pt[k] = r.o[k] + (x - q * r.e[k]);
+                    x = q;
+                }
+                pt[0] = r.o[0] + x;
+            }
         }
         __syncthreads();
     }
@@ -189,7 +220,7 @@ cudaError_t launch_points_leaf_recs(const BoxRec* leaves, uint64_t nleaves, uint
 cudaError_t launch_points_decode(const BoxRec* leaves, uint64_t nleaves, uint32_t d, const uint64_t* idx,
                                  uint64_t* out, int sms, cudaStream_t st) {
     const uint64_t grid = std::min<uint64_t>(nleaves, (uint64_t)sms * 8);
-    box_decode_kernel<<<(unsigned)(grid ? grid : 1), 256, 0, st>>>(leaves, nleaves, d, idx, out);
+    box_decode_kernel<<<(unsigned)(grid ? grid : 1), kDecodeThreads, 0, st>>>(leaves, nleaves, d, idx, out);
     return cudaGetLastError();
 }
 
