@@ -56,3 +56,12 @@ def test_plan_matches_oracle(lib_path, oracle):
     for n, N, n0 in [(0, 0, 1), (1, 1, 1), (4097, 10**9, 4096), (10**9, 2**40, 4096), (999, 1000, 3),
                      (2**62, 2**62, 1), (12345, 10**7, 100)]:
         assert rs.rs_plan(n, N, n0) == oracle.depth(n, N, n0)
+
+
+def test_binding_covers_every_declared_symbol():
+    """The Python binding gives every entry point of include/*.h its C
+    signature (argument marshalling only)."""
+    src = open(os.path.join(ROOT, "paper_1610_05141_gb300", "__init__.py")).read()
+    bound = set(re.findall(r'"(rs_\w+)":', src))
+    missing = [n for n in _declared() if n not in bound]
+    assert not missing, missing
