@@ -453,7 +453,7 @@ def run_rows(rs, ctx, stream, args):
         out["f2_bernoulli_by_size"] = {"N": 2**36, "n0": N0, "by_p": by_size}
     if want("f3"):
         # the next row (f3): a sample of 1e8 from the union of 4096 segments of
-        # uneven sizes (Sec. 4.5): the count tree, then the segments' samples as
+        # uneven sizes (Sec. 4.3): the count tree, then the segments' samples as
         # one batch
         from paper_1610_05141_gb300.workloads import union_segments
         L = union_segments()

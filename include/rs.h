@@ -177,7 +177,7 @@ int rs_batch_destroy(rs_batchplan* plan);
 int rs_batch(rs_ctx* ctx, const rs_request* reqs_dev, uint32_t R, uint64_t* out_pool_dev,
              int32_t* status_dev, void* stream);
 
-/* ---- Union of uneven segments (Sec. 4.5) -------------------------------
+/* ---- Union of uneven segments (Sec. 4.3) -------------------------------
  * A universe made of p segments of sizes L[0..p) (the elements of segment i
  * are its positions 1..L[i]); the sample is a uniform n-subset of the union.
  * As with the paper's owners of uneven shares, the samples per segment come

@@ -943,7 +943,7 @@ int or_bernoulli_by_size(double p, uint64_t N, uint64_t seed, uint32_t n0, uint6
 }
 
 /* ------------------------------------------------------------------------ */
-/* Sampling from a union of uneven segments (Sec. 4.5, uneven distribution  */
+/* Sampling from a union of uneven segments (Sec. 4.3, uneven distribution  */
 /* of the sampled universe): owner computes.                                */
 /* ------------------------------------------------------------------------ */
 
@@ -953,7 +953,7 @@ static const uint64_t UNION_WEYL = 0x9E3779B97F4A7C15ull;
 
 uint64_t or_union_key(uint64_t seed, uint64_t i) { return seed + (i + 1) * UNION_WEYL; }
 
-/* Number of samples per segment.  Reading: the binomial tree of Sec. 4.5 over
+/* Number of samples per segment.  Reading: the binomial tree of Sec. 4.3 over
  * the p segments is the binary tree of power-of-two aligned ranges, padded to
  * P = 2^ceil(log2 p) segments (the padding holds no elements): node v
  * (heap-numbered, root 1) covers segments [i 2^h, (i+1) 2^h) and its element

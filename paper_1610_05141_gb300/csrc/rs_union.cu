@@ -1,4 +1,4 @@
-// rs_union.cu -- sample counts of the segments of a union (Sec. 4.5, uneven
+// rs_union.cu -- sample counts of the segments of a union (Sec. 4.3, uneven
 // distribution of the universe over its owners).
 //
 // The paper's owners learn their share of the sample from a tree of

@@ -5,7 +5,7 @@
 namespace rs {
 
 // Samples per segment of a sample of n from the union of p segments of sizes
-// L[0..p) (Sec. 4.5): node sums of the binary tree over the segments padded
+// L[0..p) (Sec. 4.3): node sums of the binary tree over the segments padded
 // to P = 2^log2P (heap numbering, root 1, segment i at node P + i) are added
 // bottom-up into sum[1 .. 2P), then, top-down, node v's cnt[v] samples split
 // into HG(cnt[v], sum[2v], sum[v]) of stream (SPLIT, v) for its left child

@@ -1,4 +1,4 @@
-"""GPU parity of sampling from a union of uneven segments (Sec. 4.5): the
+"""GPU parity of sampling from a union of uneven segments (Sec. 4.3): the
 counts per segment from the device's tree of hypergeometric splits and the
 union's sample equal the oracle's, bit for bit, including empty segments,
 a single segment, segment counts that are not powers of two, n = 0 and

@@ -1,4 +1,4 @@
-"""Pins for sampling from a union of uneven segments (Sec. 4.5): the counts
+"""Pins for sampling from a union of uneven segments (Sec. 4.3): the counts
 per segment follow the multivariate hypergeometric law (exact pmf), the
 union's sample is a uniform n-subset of all the segments' elements (brute
 force over every subset of a tiny universe), and the degenerate cases
