@@ -408,6 +408,15 @@ const char* rs_strerror(int code);
  * does not change.  cap = 0 restores the default.  Errors: RS_EINVAL. */
 int rs_set_leaf_capacity(rs_ctx* ctx, uint32_t cap);
 
+/* Testing knob: on != 0 makes the split tree evaluate every ratio-of-uniforms
+ * acceptance test 2 ln U <= T (Sec. 3.1, Sec. 4.6) in FP64 as the definition
+ * states.  By default a single-precision evaluation with an error bound
+ * decides the trials whose two sides are further apart than the bound, and
+ * only the others are evaluated in FP64; the outcome of every test, and so
+ * the output, is the same either way.  Applies to the context's later
+ * sampling calls.  Errors: RS_EINVAL (null ctx). */
+int rs_set_exact_deviates(rs_ctx* ctx, int on);
+
 /* Phase timing (tracing): while on, every sampling call records CUDA events
  * on its stream around its split-tree phase and its leaf phase (no host
  * synchronization).  Turning it on clears the totals.  rs_phase_totals waits

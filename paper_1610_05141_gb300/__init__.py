@@ -80,6 +80,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "rs_sync": (i32, [vp, vp]),
         "rs_strerror": (ctypes.c_char_p, [i32]),
         "rs_set_leaf_capacity": (i32, [vp, u32]),
+        "rs_set_exact_deviates": (i32, [vp, i32]),
         "rs_set_profiling": (i32, [vp, i32]),
         "rs_phase_totals": (i32, [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(u64)]),
         "rs_launch_count": (i32, [vp, ctypes.POINTER(u64)]),
@@ -321,6 +322,10 @@ def rs_strerror(code: int) -> str:
 
 def rs_set_leaf_capacity(ctx: Context, cap: int) -> int:
     return _check(load().rs_set_leaf_capacity(ctx.handle, cap), "rs_set_leaf_capacity")
+
+
+def rs_set_exact_deviates(ctx: Context, on: bool) -> int:
+    return _check(load().rs_set_exact_deviates(ctx.handle, 1 if on else 0), "rs_set_exact_deviates")
 
 
 def rs_set_profiling(ctx: Context, on: bool) -> int:

@@ -33,6 +33,7 @@ struct rs_ctx {
     uint64_t stage_max_words = 1ull << 31;   // rs_set_bernoulli_staging
     uint64_t stage_slots = 0;
     uint32_t leaf_cap = 0;          // testing knob, 0 = default
+    bool guard = true;              // single-precision guard of the split tree's tests (rs_set_exact_deviates)
     // pipelining of deep trees: 2^pipe_log2 subtrees, each built on the tree
     // stream while the caller's stream runs the leaves of the ones before
     int pipe_log2 = 0;
@@ -184,7 +185,7 @@ int build_tree(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0, 
     if (rc) return rc;
     *D_out = D;
     ctx->launches += 1 + (uint64_t)D;
-    return cuda_rc(rs::launch_tree(ctx->nodes, n, N, seed, D, kind == RS_KIND_WR, ctx->tab, ctx->status, st));
+    return cuda_rc(rs::launch_tree(ctx->nodes, n, N, seed, D, kind == RS_KIND_WR, ctx->tab, ctx->status, st, ctx->guard));
 }
 
 int sample_impl(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0, int kind, uint64_t* out,
@@ -223,16 +224,16 @@ int sample_impl(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0,
         ctx->prof_calls[prof - 1].start = record_event(ctx, st);
     }
     if (c == 0) {
-        rc = cuda_rc(rs::launch_tree(ctx->nodes, n, N, seed, D, wr, ctx->tab, ctx->status, st));
+        rc = cuda_rc(rs::launch_tree(ctx->nodes, n, N, seed, D, wr, ctx->tab, ctx->status, st, ctx->guard));
         ctx->launches += 1 + (uint64_t)D;
         if (prof) ctx->prof_calls[prof - 1].tree_end = record_event(ctx, st);
     } else {
         cudaStream_t ts = ctx->tree_stream;
         rc = cuda_rc(cudaEventRecord(ctx->ev_fork, st));
         if (!rc) rc = cuda_rc(cudaStreamWaitEvent(ts, ctx->ev_fork, 0));
-        if (!rc) rc = cuda_rc(rs::launch_tree_top(ctx->nodes, n, N, seed, c, wr, ctx->tab, ctx->status, ts));
+        if (!rc) rc = cuda_rc(rs::launch_tree_top(ctx->nodes, n, N, seed, c, wr, ctx->tab, ctx->status, ts, ctx->guard));
         for (uint64_t j = 0; !rc && j < parts; ++j) {
-            rc = cuda_rc(rs::launch_tree_part(ctx->nodes, seed, D, c, j, wr, ctx->tab, ctx->status, ts));
+            rc = cuda_rc(rs::launch_tree_part(ctx->nodes, seed, D, c, j, wr, ctx->tab, ctx->status, ts, ctx->guard));
             if (!rc) rc = cuda_rc(cudaEventRecord(ctx->ev_part[j], ts));
         }
         ctx->launches += 1 + (uint64_t)c + parts * (uint64_t)(D - c);
@@ -750,6 +751,12 @@ int rs_launch_count(rs_ctx* ctx, uint64_t* count) {
 int rs_set_leaf_capacity(rs_ctx* ctx, uint32_t cap) {
     if (!ctx) return RS_EINVAL;
     ctx->leaf_cap = cap;
+    return RS_OK;
+}
+
+int rs_set_exact_deviates(rs_ctx* ctx, int on) {
+    if (!ctx) return RS_EINVAL;
+    ctx->guard = on == 0;
     return RS_OK;
 }
 

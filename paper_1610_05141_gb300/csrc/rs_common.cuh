@@ -23,12 +23,15 @@ struct __align__(16) NodeRec {
 // The table the library's math reads (one per context, on the device):
 // ln i! for i < 256 (kTabLf), then for the 128 mantissa intervals of [1, 2)
 // the reciprocal of the interval's centre and minus its logarithm as a
-// double-double (kTabInv, kTabHi, kTabLo); see rs_math.cuh.
+// double-double (kTabInv, kTabHi, kTabLo); see rs_math.cuh.  Then, from
+// double slot kTabF on, ln i! (i < 256) rounded to single precision, for
+// the single-precision guard of the ratio-of-uniforms test.
 constexpr int kTabLf = 0;
 constexpr int kTabInv = 256;
 constexpr int kTabHi = 384;
 constexpr int kTabLo = 512;
-constexpr int kTabWords = 640;
+constexpr int kTabF = 640;
+constexpr int kTabWords = 768;
 
 // First error wins; later errors are dropped until the host clears the word.
 RS_DEV void set_status(int* status, int code) {

@@ -20,16 +20,18 @@ cudaError_t launch_lf_table(double* tab, cudaStream_t st);
 
 // Split tree: writes node records 1 .. 2^(D+1)-1 of `rec` level by level;
 // the leaves are rec[2^D .. 2^(D+1)).  with_replacement selects binomial
-// splits, else hypergeometric ones.
+// splits, else hypergeometric ones.  guard = false evaluates every
+// ratio-of-uniforms test in FP64 (same output; the single-precision guard
+// of rs_math.cuh otherwise decides the trials far from the boundary).
 cudaError_t launch_tree(NodeRec* rec, uint64_t n, uint64_t N, uint64_t seed, int D, bool with_replacement,
-                        const double* tab, int* status, cudaStream_t st);
+                        const double* tab, int* status, cudaStream_t st, bool guard = true);
 // The root and levels 0 .. levels-1.
 cudaError_t launch_tree_top(NodeRec* rec, uint64_t n, uint64_t N, uint64_t seed, int levels, bool with_replacement,
-                            const double* tab, int* status, cudaStream_t st);
+                            const double* tab, int* status, cudaStream_t st, bool guard = true);
 // Levels c .. D-1 of the subtree under node 2^c + part (its nodes on level l
 // are 2^l + part 2^(l-c) .. + 2^(l-c) - 1); levels 0 .. c-1 must be done.
 cudaError_t launch_tree_part(NodeRec* rec, uint64_t seed, int D, int c, uint64_t part, bool with_replacement,
-                             const double* tab, int* status, cudaStream_t st);
+                             const double* tab, int* status, cudaStream_t st, bool guard = true);
 
 // Copies leaf records rec[2^D + i] to recs_out[4i .. 4i+3].
 cudaError_t launch_export_leaves(const NodeRec* leaves, uint64_t nleaves, uint64_t* recs_out, cudaStream_t st);

@@ -242,4 +242,76 @@ RS_DEV double dsd_fixed(uint64_t P, uint64_t Q, double lnP, const double* __rest
 }
 RS_DEV double log_fixed(uint64_t P, const double* __restrict__ tab) { return dlog((double)(P > 0 ? P : 1), tab); }
 
+// ---------------------------------------------------------------------------
+// Single-precision guard of the ratio-of-uniforms test.
+//
+// The test accepts a trial when 2 ln U <= T, T a signed sum of ln x! - ln y!
+// differences evaluated in FP64 as above.  The guard evaluates both sides in
+// single precision together with a bound on their error and decides only
+// when the two sides are further apart than the bound; otherwise the trial
+// is evaluated in FP64 exactly as the definition states.  So the outcome is
+// that of the FP64 test bit for bit, and the FP64 pipe (about 1/80 of the
+// single-precision rate on GB300) is used only by the trials near the
+// boundary.
+//
+// Error bound.  flfdiff returns F and a magnitude m (a sum of the absolute
+// values of the terms it combines, each at least as large as that term)
+// with |F - (ln x! - ln y!)| <= 8 2^-24 m: its inputs are rounded once to
+// single precision (relative 2^-24 each), single-precision logf and log1pf
+// are within 1 ulp (CUDA's documented bounds), each product, quotient and
+// sum adds 2^-24 of its result, the table entries are ln i! rounded once,
+// and the Stirling terms past 1/(12x) (below 1/(360 x^3) <= 2e-10 for
+// x >= 256) and the rounding of ln(2 pi)/2 are covered by the constants
+// added to m.  The left side 2 ln U is within 8 2^-24 (|2 ln U| + 2).  The
+// FP64 values of the definition are within 2^-45 of the same magnitudes.
+// The guard takes kGuardUlps = 64 (eight times the derivation's constant)
+// times 2^-24 times the summed magnitudes as its margin.
+constexpr float kGuardUlps = 64.0f;
+constexpr float kGuardEps = kGuardUlps * 5.9604645e-8f;   // kGuardUlps 2^-24
+
+// ln x! - ln y! for x >= y in single precision; *mag as above.  tf holds
+// ln i! (i < 256) rounded to single precision.
+RS_DEV float flfdiff(uint64_t x, uint64_t y, const float* __restrict__ tf, float* mag) {
+    const uint64_t d = x - y;
+    if (d == 0) {
+        *mag = 0.0f;
+        return 0.0f;
+    }
+    if (x < 256) {
+        const float a = tf[x], b = tf[y];
+        *mag = a + b;
+        return a - b;
+    }
+    const float X = __ull2float_rn(x), D = __ull2float_rn(d);
+    if (y < 256) {
+        // Stirling: (x + 1/2) ln x - x + ln(2 pi)/2 + 1/(12 x), less ln y!
+        const float A = (X + 0.5f) * logf(X);
+        const float ty = tf[y];
+        *mag = A + X + ty + 2.0f;
+        return ((A - X) + (0.9189385f + 0.083333336f * __frcp_rn(X))) - ty;
+    }
+    // (x + 1/2) ln(1 + d/y) + d ln y - d + (1/(12x) - 1/(12y))
+    const float Y = __ull2float_rn(y);
+    const float rY = __frcp_rn(Y);
+    const float A = (X + 0.5f) * log1pf(D * rY);
+    const float B = D * logf(Y);
+    *mag = A + B + D + 1.0f;
+    return ((A + B) - D) + 0.083333336f * (__frcp_rn(X) - rY);
+}
+
+// Signed ln P! - ln Q!.
+RS_DEV float fsd(uint64_t P, uint64_t Q, const float* __restrict__ tf, float* mag) {
+    return P >= Q ? flfdiff(P, Q, tf, mag) : -flfdiff(Q, P, tf, mag);
+}
+
+// The guard's decision for 2 ln U against T = tsum (magnitude tmag):
+// 1 accept, -1 reject, 0 too close to call.
+RS_DEV int guard_decide(double U, float tsum, float tmag) {
+    const float L = 2.0f * logf(__double2float_rn(U));
+    const float margin = kGuardEps * ((tmag + fabsf(L)) + 2.0f);
+    if (L + margin < tsum) return 1;
+    if (L - margin > tsum) return -1;
+    return 0;
+}
+
 }  // namespace rs

@@ -26,6 +26,8 @@ __global__ void lf_table_kernel(double* tab) {
     tab[kTabLf + 0] = 0.0;
     tab[kTabLf + 1] = 0.0;
     for (int i = 2; i < 256; ++i) tab[kTabLf + i] = tab[kTabLf + i - 1] + dlog((double)i, tab);
+    float* tf = reinterpret_cast<float*>(tab + kTabF);
+    for (int i = 0; i < 256; ++i) tf[i] = __double2float_rn(tab[kTabLf + i]);
 }
 
 cudaError_t launch_lf_table(double* tab, cudaStream_t st) {
@@ -47,7 +49,7 @@ template <bool WR>
 __global__ void __launch_bounds__(kTreeWarps * 32) tree_level_kernel(NodeRec* __restrict__ rec, uint64_t first,
                                                                     uint64_t nodes, uint32_t batch, uint32_t G,
                                                                     uint64_t seed, const double* __restrict__ tab,
-                                                                    int* status) {
+                                                                    int* status, bool guard) {
     extern __shared__ double tree_logs[];
     const uint32_t warp = threadIdx.x >> 5;
     const uint64_t start = ((uint64_t)blockIdx.x * kTreeWarps + warp) * batch;
@@ -55,7 +57,7 @@ __global__ void __launch_bounds__(kTreeWarps * 32) tree_level_kernel(NodeRec* __
     const uint64_t left = nodes - start;
     const uint32_t count = left < batch ? (uint32_t)left : batch;
     tree_batch_warp<WR>(rec, first + start, count, make_key(seed), tab, status,
-                        tree_logs + warp * 32 * kLogSlots, G);
+                        tree_logs + warp * 32 * kLogSlots, G, guard);
 }
 
 // Nodes of a small launch: G >= 4 lanes per node, parallel terms and trials;
@@ -64,13 +66,13 @@ template <bool WR>
 __global__ void __launch_bounds__(kTreeWarps * 32) tree_terms_kernel(NodeRec* __restrict__ rec, uint64_t first,
                                                                     uint64_t nodes, uint32_t batch, uint32_t G,
                                                                     uint64_t seed, const double* __restrict__ tab,
-                                                                    int* status) {
+                                                                    int* status, bool guard) {
     const uint32_t warp = threadIdx.x >> 5;
     const uint64_t start = ((uint64_t)blockIdx.x * kTreeWarps + warp) * batch;
     if (start >= nodes) return;
     const uint64_t left = nodes - start;
     const uint32_t count = left < batch ? (uint32_t)left : batch;
-    tree_terms_warp<WR>(rec, first + start, count, make_key(seed), tab, status, G);
+    tree_terms_warp<WR>(rec, first + start, count, make_key(seed), tab, status, G, guard);
 }
 
 // Lanes per node for a launch of `nodes` nodes: the largest power of two up
@@ -94,7 +96,7 @@ static int device_sms() {
 
 // Splits nodes first .. first+nodes-1 (all on one level, parents done).
 static void launch_nodes(NodeRec* rec, uint64_t first, uint64_t nodes, uint64_t seed, bool wr, const double* tab,
-                         int* status, int sms, cudaStream_t st) {
+                         int* status, int sms, cudaStream_t st, bool guard) {
     const size_t smem = (size_t)kTreeWarps * 32 * kLogSlots * sizeof(double);
     // small launches: a group of G lanes per node runs trials in parallel;
     // then one node per lane until there are enough warps for every SM;
@@ -115,35 +117,35 @@ static void launch_nodes(NodeRec* rec, uint64_t first, uint64_t nodes, uint64_t 
     const uint64_t warps = (nodes + batch - 1) / batch;
     const unsigned blocks = (unsigned)((warps + kTreeWarps - 1) / kTreeWarps);
     if (G >= 4) {
-        if (wr) tree_terms_kernel<true><<<blocks, kTreeWarps * 32, 0, st>>>(rec, first, nodes, batch, G, seed, tab, status);
-        else tree_terms_kernel<false><<<blocks, kTreeWarps * 32, 0, st>>>(rec, first, nodes, batch, G, seed, tab, status);
+        if (wr) tree_terms_kernel<true><<<blocks, kTreeWarps * 32, 0, st>>>(rec, first, nodes, batch, G, seed, tab, status, guard);
+        else tree_terms_kernel<false><<<blocks, kTreeWarps * 32, 0, st>>>(rec, first, nodes, batch, G, seed, tab, status, guard);
     } else if (wr) {
-        tree_level_kernel<true><<<blocks, kTreeWarps * 32, smem, st>>>(rec, first, nodes, batch, G, seed, tab, status);
+        tree_level_kernel<true><<<blocks, kTreeWarps * 32, smem, st>>>(rec, first, nodes, batch, G, seed, tab, status, guard);
     } else {
-        tree_level_kernel<false><<<blocks, kTreeWarps * 32, smem, st>>>(rec, first, nodes, batch, G, seed, tab, status);
+        tree_level_kernel<false><<<blocks, kTreeWarps * 32, smem, st>>>(rec, first, nodes, batch, G, seed, tab, status, guard);
     }
 }
 
 cudaError_t launch_tree(NodeRec* rec, uint64_t n, uint64_t N, uint64_t seed, int D, bool with_replacement,
-                        const double* tab, int* status, cudaStream_t st) {
-    return launch_tree_top(rec, n, N, seed, D, with_replacement, tab, status, st);
+                        const double* tab, int* status, cudaStream_t st, bool guard) {
+    return launch_tree_top(rec, n, N, seed, D, with_replacement, tab, status, st, guard);
 }
 
 cudaError_t launch_tree_top(NodeRec* rec, uint64_t n, uint64_t N, uint64_t seed, int levels, bool with_replacement,
-                            const double* tab, int* status, cudaStream_t st) {
+                            const double* tab, int* status, cudaStream_t st, bool guard) {
     tree_root_kernel<<<1, 32, 0, st>>>(rec, n, N);
     const int sms = device_sms();
     for (int level = 0; level < levels; ++level)
-        launch_nodes(rec, 1ull << level, 1ull << level, seed, with_replacement, tab, status, sms, st);
+        launch_nodes(rec, 1ull << level, 1ull << level, seed, with_replacement, tab, status, sms, st, guard);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tree_part(NodeRec* rec, uint64_t seed, int D, int c, uint64_t part, bool with_replacement,
-                             const double* tab, int* status, cudaStream_t st) {
+                             const double* tab, int* status, cudaStream_t st, bool guard) {
     const int sms = device_sms();
     for (int level = c; level < D; ++level) {
         const uint64_t per = 1ull << (level - c);
-        launch_nodes(rec, (1ull << level) + part * per, per, seed, with_replacement, tab, status, sms, st);
+        launch_nodes(rec, (1ull << level) + part * per, per, seed, with_replacement, tab, status, sms, st, guard);
     }
     return cudaGetLastError();
 }

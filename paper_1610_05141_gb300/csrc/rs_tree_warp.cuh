@@ -98,6 +98,7 @@ struct RouNode {
     uint64_t a, b, M;    // hypergeometric: reduced draws/successes; binomial: a = c
     uint64_t n_in, Kp;   // un-reduction of the hypergeometric result
     double h, alpha, top, logr;
+    float logrf;         // binomial: ln(p / (1 - p)) in single precision, for the guard
     double lnP[4];       // ln of the fixed ends (lanes kernel), once per node
     uint32_t trial;
     bool flipN, flipK;
@@ -151,6 +152,7 @@ RS_DEV bool node_setup(NodeRec* __restrict__ rec, uint64_t v, Key2 key, const do
         q->alpha = mu + 0.5;
         const double rr = p / (1.0 - p);
         q->logr = (rr == 1.0) ? 0.0 : dlog(rr, tab);
+        q->logrf = (rr == 1.0) ? 0.0f : logf(__double2float_rn(rr));
         q->M = (uint64_t)(((unsigned __int128)(c + 1) * K) / r.S);
         q->top = (double)c + 1.0;
         q->a = c;
@@ -200,11 +202,13 @@ RS_DEV bool node_setup(NodeRec* __restrict__ rec, uint64_t v, Key2 key, const do
 // scratch of 32 * kLogSlots doubles in shared memory.
 template <bool WR>
 RS_DEV void tree_batch_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t count, Key2 key,
-                            const double* __restrict__ tab, int* status, double* logs, uint32_t G = 1) {
+                            const double* __restrict__ tab, int* status, double* logs, uint32_t G = 1,
+                            bool guard = true) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t r = lane & (G - 1);         // trial offset inside the group
     const uint32_t gbase = lane - r;           // the group's first lane
     const uint32_t gmask = G == 32 ? 0xFFFFFFFFu : ((1u << G) - 1u) << gbase;
+    const float* tf = reinterpret_cast<const float*>(tab + kTabF);
     double* mine = logs + lane * kLogSlots;
     RouNode q;
     bool active = false;                       // the same in all lanes of a group
@@ -221,21 +225,17 @@ RS_DEV void tree_batch_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
             next += take;
         }
         if (__ballot_sync(0xFFFFFFFFu, active) == 0) break;
-        // one trial per active lane: uniforms, candidate, logarithm arguments
+        // one trial per active lane: uniforms, candidate, the guard, and for
+        // the trials it leaves open the logarithm arguments
         const uint64_t t = (uint64_t)q.trial + r;   // this lane's trial
         double U = 1.0;
         uint64_t k = 0;
         bool inr = false;
+        int dec = 0;
+        bool fresh_now = false;                    // this round takes the node's fixed-end logarithms
         int nargs = 0;
         constexpr int kTerms = WR ? 2 : 4;
         if (active) {
-            LfdArgs A{mine, 0, 0};
-            if (q.fresh)   // the fixed ends' logarithms go with this round's
-#pragma unroll
-                for (int j = 0; j < kTerms; ++j) {
-                    const uint64_t P = fixed_end<WR>(q, j);
-                    A.push((double)(P > 0 ? P : 1));
-                }
             const uint4 blk = philox_block((uint32_t)t, TAG_SPLIT, q.v, key);
             U = u_open(((uint64_t)blk.y << 32) | blk.x);
             const double V = v_closed(((uint64_t)blk.w << 32) | blk.z);
@@ -243,11 +243,38 @@ RS_DEV void tree_batch_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
             inr = !(X < 0.0 || X >= q.top) && t < kRouMaxTrials;
             if (inr) {
                 k = (uint64_t)X;
-                A.push(U);
+                if (guard) {
+                    float fm = 0.0f, ft = 0.0f;
 #pragma unroll
-                for (int j = 0; j < kTerms; ++j) sdf_args(fixed_end<WR>(q, j), moving_end<WR>(q, j, k), A);
+                    for (int j = 0; j < kTerms; ++j) {
+                        float m;
+                        ft += fsd(fixed_end<WR>(q, j), moving_end<WR>(q, j, k), tf, &m);
+                        fm += m;
+                    }
+                    if (WR) {
+                        const float dk = (float)((int64_t)k - (int64_t)q.M);
+                        const float rt = dk * q.logrf;
+                        ft += rt;
+                        fm += fabsf(rt) + fabsf(dk);
+                    }
+                    dec = guard_decide(U, ft, fm);
+                }
+                if (dec == 0) {
+                    LfdArgs A{mine, 0, 0};
+                    if (q.fresh) {   // the fixed ends' logarithms go with this round's
+                        fresh_now = true;
+#pragma unroll
+                        for (int j = 0; j < kTerms; ++j) {
+                            const uint64_t P = fixed_end<WR>(q, j);
+                            A.push((double)(P > 0 ? P : 1));
+                        }
+                    }
+                    A.push(U);
+#pragma unroll
+                    for (int j = 0; j < kTerms; ++j) sdf_args(fixed_end<WR>(q, j), moving_end<WR>(q, j, k), A);
+                    nargs = A.n;
+                }
             }
-            nargs = A.n;
         }
         __syncwarp();
         // the warp evaluates all logarithms together: item g of the
@@ -285,15 +312,15 @@ RS_DEV void tree_batch_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
                 if (slot[j]) *slot[j] = x[j];
         }
         __syncwarp();
-        bool acc = false;
+        bool acc = dec > 0;
         uint64_t L = 0;
         LfdLogs Lg{mine, 0, 0};
-        if (active && q.fresh) {
+        if (fresh_now) {
 #pragma unroll
             for (int j = 0; j < kTerms; ++j) q.lnP[j] = Lg.next();
             q.fresh = false;
         }
-        if (active && inr) {
+        if (active && inr && dec == 0) {
             const double lU = Lg.next();
             double T;
             if (WR) {
@@ -304,13 +331,13 @@ RS_DEV void tree_batch_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
                 T = sdf_eval(q.M, k, q.lnP[0], tab, Lg) + sdf_eval(q.a - q.M, q.a - k, q.lnP[1], tab, Lg) +
                     sdf_eval(q.b - q.M, q.b - k, q.lnP[2], tab, Lg) + sdf_eval(m + q.M, m + k, q.lnP[3], tab, Lg);
             }
-            if (2.0 * lU <= T) {
-                acc = true;
-                L = k;
-                if (!WR) {
-                    if (q.flipN) L = q.Kp - L;
-                    if (q.flipK) L = q.n_in - L;
-                }
+            acc = 2.0 * lU <= T;
+        }
+        if (acc) {
+            L = k;
+            if (!WR) {
+                if (q.flipN) L = q.Kp - L;
+                if (q.flipK) L = q.n_in - L;
             }
         }
         // the group takes its lowest accepted trial
@@ -347,17 +374,19 @@ RS_DEV void tree_batch_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
 // the trial counts of a few nodes do not idle the rest of the warp.
 template <bool WR>
 RS_DEV void tree_terms_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t count, Key2 key,
-                            const double* __restrict__ tab, int* status, uint32_t G) {
+                            const double* __restrict__ tab, int* status, uint32_t G, bool guard = true) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t r = lane & (G - 1);
     const uint32_t gbase = lane - r;
     const uint32_t gmask = G == 32 ? 0xFFFFFFFFu : ((1u << G) - 1u) << gbase;
     const uint32_t p = r >> 2, j = r & 3u, tbase = lane & ~3u;
+    const float* tf = reinterpret_cast<const float*>(tab + kTabF);
     RouNode q;
     bool active = false;   // the same in all lanes of a group
     uint32_t next = 0;     // batch cursor (warp-uniform)
-    uint64_t P = 0;        // this lane's fixed end (term j) and its logarithm, once per node
+    uint64_t P = 0;        // this lane's fixed end (term j); its logarithm once the node first needs FP64
     double lnP = 0.0;
+    bool haveLnP = false;
     for (;;) {
         // free groups take the next nodes, in order
         for (;;) {
@@ -369,15 +398,15 @@ RS_DEV void tree_terms_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
                 active = node_setup<WR>(rec, v0 + next + rank, key, tab, status, &q, r == 0);
                 if (active) {
                     P = fixed_end<WR>(q, (int)j);
-                    lnP = log_fixed(P, tab);
+                    haveLnP = false;
                 }
             }
             next += take;
         }
         if (__ballot_sync(0xFFFFFFFFu, active) == 0) break;
         const uint64_t t = (uint64_t)q.trial + p;
-        double U = 1.0, T = 0.0, term = 0.0;
-        uint64_t k = 0;
+        double U = 1.0;
+        uint64_t k = 0, Q = P;
         bool inr = false;
         if (active) {
             const uint4 blk = philox_block((uint32_t)t, TAG_SPLIT, q.v, key);
@@ -386,29 +415,54 @@ RS_DEV void tree_terms_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
             const double X = q.alpha + q.h * (V - 0.5) * drecip(U);
             inr = !(X < 0.0 || X >= q.top) && t < kRouMaxTrials;
             if (inr) k = (uint64_t)X;
-            // this lane's difference ln P! - ln Q! (none: Q = P gives 0);
-            // the ends are picked with selects so that all lanes run one
-            // copy of dsd_fixed
-            const uint64_t Q = inr ? moving_end<WR>(q, (int)j, k) : P;
-            term = dsd_fixed(P, Q, lnP, tab);
+            // this lane's difference ln P! - ln Q! (none: Q = P gives 0)
+            Q = inr ? moving_end<WR>(q, (int)j, k) : P;
         }
-        const double lU = dlog(U, tab);
-        const double t0 = __shfl_sync(0xFFFFFFFFu, term, tbase);
-        const double t1 = __shfl_sync(0xFFFFFFFFu, term, tbase + 1);
-        const double t2 = __shfl_sync(0xFFFFFFFFu, term, tbase + 2);
-        const double t3 = __shfl_sync(0xFFFFFFFFu, term, tbase + 3);
-        bool acc = false;
+        // the guard: the trial's four lanes sum their single-precision terms
+        int dec = 0;
+        if (guard) {
+            float fm;
+            float ft = fsd(P, Q, tf, &fm);
+            ft += __shfl_xor_sync(0xFFFFFFFFu, ft, 1);
+            fm += __shfl_xor_sync(0xFFFFFFFFu, fm, 1);
+            ft += __shfl_xor_sync(0xFFFFFFFFu, ft, 2);
+            fm += __shfl_xor_sync(0xFFFFFFFFu, fm, 2);
+            if (WR && active && inr) {
+                const float dk = (float)((int64_t)k - (int64_t)q.M);
+                const float rt = dk * q.logrf;
+                ft += rt;
+                fm += fabsf(rt) + fabsf(dk);
+            }
+            if (active && inr) dec = guard_decide(U, ft, fm);
+        }
+        // FP64, as the definition states, for the trials the guard left open
+        const bool need = active && inr && dec == 0;
+        bool acc = dec > 0;
+        if (__any_sync(0xFFFFFFFFu, need)) {
+            if (need && !haveLnP) {
+                lnP = log_fixed(P, tab);
+                haveLnP = true;
+            }
+            // the ends are picked with selects so that all lanes run one copy
+            const double term = dsd_fixed(P, need ? Q : P, lnP, tab);
+            const double lU = dlog(U, tab);
+            const double t0 = __shfl_sync(0xFFFFFFFFu, term, tbase);
+            const double t1 = __shfl_sync(0xFFFFFFFFu, term, tbase + 1);
+            const double t2 = __shfl_sync(0xFFFFFFFFu, term, tbase + 2);
+            const double t3 = __shfl_sync(0xFFFFFFFFu, term, tbase + 3);
+            if (need) {
+                double T;
+                if (WR) T = t0 + t1 + (double)((int64_t)k - (int64_t)q.M) * q.logr;
+                else T = t0 + t1 + t2 + t3;
+                acc = 2.0 * lU <= T;
+            }
+        }
         uint64_t L = 0;
-        if (active && inr) {
-            if (WR) T = t0 + t1 + (double)((int64_t)k - (int64_t)q.M) * q.logr;
-            else T = t0 + t1 + t2 + t3;
-            if (2.0 * lU <= T) {
-                acc = true;
-                L = k;
-                if (!WR) {
-                    if (q.flipN) L = q.Kp - L;
-                    if (q.flipK) L = q.n_in - L;
-                }
+        if (acc) {
+            L = k;
+            if (!WR) {
+                if (q.flipN) L = q.Kp - L;
+                if (q.flipK) L = q.n_in - L;
             }
         }
         // the group takes its lowest accepted trial

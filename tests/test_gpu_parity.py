@@ -149,6 +149,33 @@ def test_split_tree_matches_oracle(rs, ctx, oracle, n, N, seed, n0, kind):
     assert_same(got.ravel(), want.ravel(), (n, N, kind))
 
 
+GUARD_CASES = TREE_CASES + [
+    (7 * 10**8, 3 * 2**47 + 5, 11, 1000, 0),   # ragged sizes, deeper tree
+    (123456789, 987654321012, 12, 300, 1),
+    (2**40, 2**45, 13, 2**22, 0),              # a shallow tree of huge counts
+]
+
+
+@pytest.mark.parametrize("n,N,seed,n0,kind", GUARD_CASES)
+def test_split_tree_guard_equals_fp64(rs, n, N, seed, n0, kind):
+    """The single-precision guard of the ratio-of-uniforms tests only
+    decides trials far from the boundary: the whole tree is the same bits
+    with the guard and with every test evaluated in FP64."""
+    D = rs.rs_plan(n, N, n0)
+    recs = []
+    for exact in (False, True):
+        c = rs.rs_create(0)
+        try:
+            rs.rs_set_exact_deviates(c, exact)
+            r = torch.zeros(4 << D, dtype=torch.int64, device="cuda")
+            rs.rs_split_tree(c, n, N, seed, n0, kind, r, 1 << D)
+            assert rs.rs_sync(c) == rs.RS_OK
+            recs.append(r.cpu().numpy())
+        finally:
+            c.close()
+    assert np.array_equal(recs[0], recs[1]), (n, N, kind)
+
+
 BERN_CASES = [
     (1e-4, 2**28, 7, 4096),
     (1e-2, 2**24, 7, 4096),
