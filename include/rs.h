@@ -392,6 +392,13 @@ int rs_server_release(rs_server* server, uint64_t ticket);
 /* Counters since creation.  Errors: RS_EINVAL. */
 int rs_server_stats_get(rs_server* server, rs_server_stats* stats);
 
+/* Testing knob: the next `count` groups the server plans fail as if the host
+ * memory of their plan could not be allocated.  Their jobs finish with
+ * RS_ENOMEM (their arena memory stays reserved until released, like any
+ * finished job's); the server goes on with the jobs after them.
+ * Errors: RS_EINVAL (null server). */
+int rs_server_fail_next_plans(rs_server* server, uint32_t count);
+
 /* Stops the worker (jobs still queued are dropped), waits for the device,
  * frees everything. */
 int rs_server_destroy(rs_server* server);
@@ -416,6 +423,18 @@ int rs_set_leaf_capacity(rs_ctx* ctx, uint32_t cap);
  * the output, is the same either way.  Applies to the context's later
  * sampling calls.  Errors: RS_EINVAL (null ctx). */
 int rs_set_exact_deviates(rs_ctx* ctx, int on);
+
+/* Testing knob: lowers the iteration caps of the method's loops on the
+ * current device, for every context and call of the process: the
+ * ratio-of-uniforms trials and the inversion restarts of one split deviate
+ * (Sec. 3.1; defaults 2^20 and 64), the Philox blocks of one candidate or
+ * skip stream (default 2^32: 2^34 32-bit candidates, 2^33 64-bit values),
+ * and the attempts of one Algorithm B leaf (Sec. 2; default 64).  A value
+ * at or above the default (UINT64_MAX, say) keeps the default; 0 allows no
+ * trial, restart or attempt at all.  A loop that reaches its cap
+ * ends with the device status RS_EITER (no trap; rs_sync, the batch's and
+ * the server's statuses report it).  Errors: RS_ECUDA. */
+int rs_set_iteration_caps(uint64_t rou_trials, uint64_t inv_restarts, uint64_t stream_blocks, uint64_t b_attempts);
 
 /* Phase timing (tracing): while on, every sampling call records CUDA events
  * on its stream around its split-tree phase and its leaf phase (no host
@@ -491,6 +510,8 @@ int rs_launch_count(rs_ctx* ctx, uint64_t* count);
  *    returns the call's device status (RS_OK, RS_EITER, RS_ECAPACITY).
  *  - The first call on a device looks up the array's device address and
  *    builds its ln x! table: make that first call before any stream capture.
+ *    Both are kept for the life of the process, so the entry point must not
+ *    be called again after a cudaDeviceReset of that device.
  *  - Every call shares the array: calls that overlap on the GPU race. */
 int rs_sample_static(uint64_t n, uint64_t N, uint64_t seed, uint32_t n0, uint64_t* out_dev, void* stream);
 

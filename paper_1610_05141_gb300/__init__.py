@@ -81,6 +81,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "rs_strerror": (ctypes.c_char_p, [i32]),
         "rs_set_leaf_capacity": (i32, [vp, u32]),
         "rs_set_exact_deviates": (i32, [vp, i32]),
+        "rs_set_iteration_caps": (i32, [u64, u64, u64, u64]),
         "rs_set_profiling": (i32, [vp, i32]),
         "rs_phase_totals": (i32, [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(u64)]),
         "rs_launch_count": (i32, [vp, ctypes.POINTER(u64)]),
@@ -114,6 +115,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "rs_server_poll": (i32, [vp, ctypes.POINTER(Result), u32, ctypes.POINTER(u32), u32]),
         "rs_server_release": (i32, [vp, u64]),
         "rs_server_stats_get": (i32, [vp, ctypes.POINTER(ServerStats)]),
+        "rs_server_fail_next_plans": (i32, [vp, u32]),
         "rs_server_destroy": (i32, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -328,6 +330,13 @@ def rs_set_exact_deviates(ctx: Context, on: bool) -> int:
     return _check(load().rs_set_exact_deviates(ctx.handle, 1 if on else 0), "rs_set_exact_deviates")
 
 
+def rs_set_iteration_caps(rou_trials=None, inv_restarts=None, stream_blocks=None, b_attempts=None) -> int:
+    """Testing knob (current device, process-wide): None keeps a default."""
+    keep = (1 << 64) - 1
+    args = [keep if v is None else int(v) for v in (rou_trials, inv_restarts, stream_blocks, b_attempts)]
+    return _check(load().rs_set_iteration_caps(*args), "rs_set_iteration_caps")
+
+
 def rs_set_profiling(ctx: Context, on: bool) -> int:
     return _check(load().rs_set_profiling(ctx.handle, 1 if on else 0), "rs_set_profiling")
 
@@ -502,6 +511,10 @@ class Server:
 
     def release(self, ticket: int) -> None:
         _check(load().rs_server_release(self.handle, ticket), "rs_server_release")
+
+    def fail_next_plans(self, count: int) -> None:
+        """Testing knob: the next `count` group plans fail as if host memory ran out."""
+        _check(load().rs_server_fail_next_plans(self.handle, count), "rs_server_fail_next_plans")
 
     def stats(self) -> dict:
         s = ServerStats()

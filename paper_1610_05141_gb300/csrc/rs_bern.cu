@@ -21,7 +21,6 @@ namespace rs {
 
 constexpr uint64_t kSat = 1ull << 63;   // saturation of skip sums
 constexpr double kTwo62 = 4611686018427387904.0;
-constexpr uint64_t kMaxDraws = 1ull << 33;   // 2^32 Philox blocks of two values
 
 RS_DEV uint64_t sat_add(uint64_t a, uint64_t b) { return a > kSat - b ? kSat : a + b; }
 
@@ -65,7 +64,7 @@ RS_DEV uint64_t warp_walk(Key2 key, uint32_t tag, uint64_t id, double R, uint64_
     *err = false;
     for (uint64_t j = 0;; j += 32) {
         const uint64_t jl = j + lane;
-        const bool exhausted = jl >= kMaxDraws;
+        const bool exhausted = jl >= 2 * c_caps.stream_blocks;
         bool stop = true;
         uint64_t step = 0;
         if (!exhausted) step = step_of(skip_quotient(stream_value(key, tag, id, jl), R, tab), cmax, &stop);
@@ -401,7 +400,7 @@ RS_DEV uint64_t block_walk(Key2 key, uint32_t tag, uint64_t id, double R, uint64
     uint64_t base = 0, count = 0;
     for (uint64_t j = 0;; j += NT) {
         const uint64_t jt = j + threadIdx.x;
-        const bool exhausted = jt >= kMaxDraws;
+        const bool exhausted = jt >= 2 * c_caps.stream_blocks;
         bool stop = true;
         uint64_t step = 0;
         if (!exhausted) step = step_of(skip_quotient(stream_value(key, tag, id, jt), R, tab), cmax, &stop);
@@ -457,12 +456,12 @@ RS_DEV void leaf_b_one(LeafBShared<PosT>& sm, const NodeRec& r, uint64_t id, Key
         __syncthreads();
     } else {
         const double R = 1.0 / dlog1p(-rho, tab);
-        for (attempt = 0; attempt < 64; ++attempt) {
+        for (attempt = 0; (uint64_t)attempt < c_caps.b_attempts; ++attempt) {
             c = block_walk<NT>(key, TAG_LEAF_B + 256u * (uint32_t)attempt, id, R, r.S, sm, tab);
             if (sm.err) break;
             if (c >= r.c) break;
         }
-        if (sm.err || attempt == 64) {
+        if (sm.err || (uint64_t)attempt == c_caps.b_attempts) {
             if (tid == 0) set_status(status, RS_EITER);
             fail = true;
         }

@@ -109,7 +109,7 @@ RS_DEV bool big_select(const NodeRec& r, uint64_t id, Key2 key, uint64_t k, cons
                        int* status) {
     const uint32_t tag = WR ? TAG_LEAF_WR : TAG_LEAF_H;
     const bool wide = r.S > (1ull << 32);
-    const uint64_t jlimit = wide ? (1ull << 33) : (1ull << 34);
+    const uint64_t jlimit = (wide ? 2 : 4) * c_caps.stream_blocks;
     uint64_t d = 0, J = 0;
     while (d < k) {
         const uint64_t m = k - d;

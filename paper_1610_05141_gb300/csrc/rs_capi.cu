@@ -158,12 +158,7 @@ int ensure_pipeline(rs_ctx* ctx, size_t parts) {
     return RS_OK;
 }
 
-int depth_of(uint64_t n, uint64_t N, uint32_t n0) {
-    int D = 0;
-    while ((unsigned __int128)n > ((unsigned __int128)n0 << D)) ++D;
-    while (D > 0 && ((unsigned __int128)1 << D) > (unsigned __int128)N) --D;
-    return D;
-}
+int depth_of(uint64_t n, uint64_t N, uint32_t n0) { return rs::tree_depth(n, N, n0); }
 
 int check_sample_args(uint64_t n, uint64_t N, uint32_t n0, bool with_replacement, const void* out) {
     if (n0 == 0) return RS_EINVAL;
@@ -330,6 +325,20 @@ int sample_impl(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0,
 }  // namespace
 
 namespace rs {
+static std::vector<CapsWriter>& caps_writers() {
+    static std::vector<CapsWriter> v;
+    return v;
+}
+int register_caps_writer(CapsWriter w) {
+    caps_writers().push_back(w);
+    return 1;
+}
+int tree_depth(uint64_t n, uint64_t N, uint32_t n0) {
+    int D = 0;
+    while ((unsigned __int128)n > ((unsigned __int128)n0 << D)) ++D;
+    while (D > 0 && ((unsigned __int128)1 << D) > (unsigned __int128)N) --D;
+    return D;
+}
 // Accessors for the other translation units (the batch planner).
 int ctx_device(rs_ctx* ctx) { return ctx->device; }
 int ctx_sms(rs_ctx* ctx) { return ctx->sms; }
@@ -751,6 +760,16 @@ int rs_launch_count(rs_ctx* ctx, uint64_t* count) {
 int rs_set_leaf_capacity(rs_ctx* ctx, uint32_t cap) {
     if (!ctx) return RS_EINVAL;
     ctx->leaf_cap = cap;
+    return RS_OK;
+}
+
+int rs_set_iteration_caps(uint64_t rou_trials, uint64_t inv_restarts, uint64_t stream_blocks, uint64_t b_attempts) {
+    const rs::IterCaps def = RS_DEFAULT_CAPS;
+    auto pick = [](uint64_t v, uint64_t d) { return v > d ? d : v; };
+    const rs::IterCaps c{pick(rou_trials, def.rou_trials), pick(inv_restarts, def.inv_restarts),
+                         pick(stream_blocks, def.stream_blocks), pick(b_attempts, def.b_attempts)};
+    for (rs::CapsWriter w : rs::caps_writers())
+        if (w(c) != cudaSuccess) return RS_ECUDA;
     return RS_OK;
 }
 

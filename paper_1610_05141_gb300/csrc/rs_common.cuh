@@ -40,4 +40,26 @@ RS_DEV void set_status(int* status, int code) {
 
 RS_DEV uint64_t umulhi64(uint64_t a, uint64_t b) { return __umul64hi(a, b); }
 
+// Iteration caps of the method's loops: ratio-of-uniforms trials and
+// inversion restarts per deviate (Sec. 3.1), Philox blocks per candidate or
+// skip stream, Algorithm B attempts per leaf (Sec. 2).  The defaults are
+// the definition's; rs_set_iteration_caps lowers them so that tests can
+// reach the RS_EITER paths.
+struct IterCaps {
+    uint64_t rou_trials;
+    uint64_t inv_restarts;
+    uint64_t stream_blocks;
+    uint64_t b_attempts;
+};
+#define RS_DEFAULT_CAPS {1ull << 20, 64ull, 1ull << 32, 64ull}
+
+// Device code is compiled per translation unit: every unit holds its own
+// copy of the caps in constant memory and registers, when the library is
+// loaded, a host function that writes that copy on the current device.
+static __constant__ IterCaps c_caps = RS_DEFAULT_CAPS;
+using CapsWriter = cudaError_t (*)(const IterCaps&);
+int register_caps_writer(CapsWriter w);
+static cudaError_t write_caps_here(const IterCaps& c) { return cudaMemcpyToSymbol(c_caps, &c, sizeof(IterCaps)); }
+[[maybe_unused]] static const int caps_writer_registered = register_caps_writer(&write_caps_here);
+
 }  // namespace rs

@@ -13,9 +13,6 @@
 
 namespace rs {
 
-constexpr uint64_t kRouMaxTrials = 1ull << 20;
-constexpr uint64_t kInvMaxRestarts = 64;
-
 // Warp-cooperative forms (WARP = true): every lane of a full warp calls with
 // the same arguments and gets the same result.  Inversion restart r and
 // ratio-of-uniforms trial i run on lane r mod 32 (i mod 32) in round r / 32
@@ -66,13 +63,14 @@ RS_DEV int hypergeometric_t(Key2 key, uint64_t node, uint64_t n, uint64_t K, uin
         // Inversion from k = 0 with the pmf recurrence
         // f(k+1) = f(k) (a-k)(b-k) / ((k+1)(S-a-b+k+1)).
         const double f0 = dexp(dsd(S - b, S - a - b, tab) - dsd(S, S - a, tab));
-        for (uint64_t r0 = 0; r0 < kInvMaxRestarts && !done; r0 += TL::step) {
+        for (uint64_t r0 = 0; r0 < c_caps.inv_restarts && !done; r0 += TL::step) {
             const uint64_t r = r0 + TL::lane();
+            const bool in_cap = r < c_caps.inv_restarts;
             double u = v_closed(stream_value(key, TAG_SPLIT, node, r));
             double f = f0;
             bool ok = false;
             uint64_t yk = 0;
-            for (uint64_t k = 0; k <= a; ++k) {
+            for (uint64_t k = 0; k <= a && in_cap; ++k) {
                 if (u < f) { yk = k; ok = true; break; }
                 u = u - f;
                 f = (f * ((double)(a - k) * (double)(b - k))) / ((double)(k + 1) * (double)(S - a - b + k + 1));
@@ -91,7 +89,7 @@ RS_DEV int hypergeometric_t(Key2 key, uint64_t node, uint64_t n, uint64_t K, uin
         const double top = (double)a + 1.0;
         const double l0 = log_fixed(M, tab), l1 = log_fixed(a - M, tab), l2 = log_fixed(b - M, tab),
                      l3 = log_fixed(m + M, tab);
-        for (uint64_t i0 = 0; i0 < kRouMaxTrials && !done; i0 += TL::step) {
+        for (uint64_t i0 = 0; i0 < c_caps.rou_trials && !done; i0 += TL::step) {
             const uint64_t i = i0 + TL::lane();
             const uint4 blk = philox_block((uint32_t)i, TAG_SPLIT, node, key);
             const double U = u_open(((uint64_t)blk.y << 32) | blk.x);
@@ -99,7 +97,7 @@ RS_DEV int hypergeometric_t(Key2 key, uint64_t node, uint64_t n, uint64_t K, uin
             const double X = alpha + h * (V - 0.5) * drecip(U);
             bool ok = false;
             uint64_t k = 0;
-            if (X >= 0.0 && X < top) {
+            if (X >= 0.0 && X < top && i < c_caps.rou_trials) {
                 k = (uint64_t)X;
                 const double T = dsd_fixed(M, k, l0, tab) + dsd_fixed(a - M, a - k, l1, tab) +
                                  dsd_fixed(b - M, b - k, l2, tab) + dsd_fixed(m + M, m + k, l3, tab);
@@ -126,13 +124,13 @@ RS_DEV int binomial_t(Key2 key, uint64_t node, uint64_t c, uint64_t K, uint64_t 
     if (mu < 16.0) {
         const double f0 = dexp((double)c * dlog1p(-p, tab));
         const double r = p / (1.0 - p);
-        for (uint64_t q0 = 0; q0 < kInvMaxRestarts; q0 += TL::step) {
+        for (uint64_t q0 = 0; q0 < c_caps.inv_restarts; q0 += TL::step) {
             const uint64_t q = q0 + TL::lane();
             double u = v_closed(stream_value(key, TAG_SPLIT, node, q));
             double f = f0;
             bool ok = false;
             uint64_t yk = 0;
-            for (uint64_t k = 0; k <= c; ++k) {
+            for (uint64_t k = 0; k <= c && q < c_caps.inv_restarts; ++k) {
                 if (u < f) { yk = k; ok = true; break; }
                 u = u - f;
                 f = (f * ((double)(c - k) * r)) / (double)(k + 1);
@@ -150,7 +148,7 @@ RS_DEV int binomial_t(Key2 key, uint64_t node, uint64_t c, uint64_t K, uint64_t 
     const uint64_t M = (uint64_t)(((unsigned __int128)(c + 1) * K) / S);
     const double top = (double)c + 1.0;
     const double l0 = log_fixed(M, tab), l1 = log_fixed(c - M, tab);
-    for (uint64_t i0 = 0; i0 < kRouMaxTrials; i0 += TL::step) {
+    for (uint64_t i0 = 0; i0 < c_caps.rou_trials; i0 += TL::step) {
         const uint64_t i = i0 + TL::lane();
         const uint4 blk = philox_block((uint32_t)i, TAG_SPLIT, node, key);
         const double U = u_open(((uint64_t)blk.y << 32) | blk.x);
@@ -158,7 +156,7 @@ RS_DEV int binomial_t(Key2 key, uint64_t node, uint64_t c, uint64_t K, uint64_t 
         const double X = alpha + h * (V - 0.5) * drecip(U);
         bool ok = false;
         uint64_t k = 0;
-        if (X >= 0.0 && X < top) {
+        if (X >= 0.0 && X < top && i < c_caps.rou_trials) {
             k = (uint64_t)X;
             const double T = dsd_fixed(M, k, l0, tab) + dsd_fixed(c - M, c - k, l1, tab) +
                              (double)((int64_t)k - (int64_t)M) * logr;

@@ -312,7 +312,7 @@ RS_COLD bool bucket_repair(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r,
     const uint32_t need = k - d;
     if (tid < 32) {
         const uint32_t lane = tid;
-        const uint64_t jlimit = r.s > (1ull << 32) ? (1ull << 33) : (1ull << 34);
+        const uint64_t jlimit = (r.s > (1ull << 32) ? 2 : 4) * c_caps.stream_blocks;
         uint64_t J = sm.jnext;
         uint32_t added = 0;
         while (added < need) {
@@ -492,7 +492,7 @@ RS_COLD bool void_leaf_pass1(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& 
     const uint32_t room = HashShared<KeyT, NT / 32, CAP>::kSlots - ((k + 3) & ~3u);
     uint32_t got = 0;
     for (uint64_t b0 = 0; got < k;) {
-        if (b0 >= (1ull << 32)) return false;   // the stream ran out: the probing path reports it
+        if (b0 >= c_caps.stream_blocks) return false;   // the stream ran out: the probing path reports it
         const uint32_t m = k - got;
         const uint32_t want = (m + m / 8 + 32 + cpb - 1) / cpb;
         const uint32_t nbk = min(want, min(room / cpb, (uint32_t)NT * qmax));
@@ -686,7 +686,7 @@ RS_DEV bool distinct_rounds(uint32_t* newcount, const LeafRec& r, uint64_t thr, 
                             int* status, uint32_t tid, Insert&& insert, Abort&& aborted) {
     uint32_t d = 0, round = 0;
     uint64_t J = 0;
-    const uint64_t jlimit = r.s > (1ull << 32) ? (1ull << 33) : (1ull << 34);
+    const uint64_t jlimit = (r.s > (1ull << 32) ? 2 : 4) * c_caps.stream_blocks;
     while (d < k) {
         const uint32_t m = k - d;
         if (J + m > jlimit) {

@@ -15,6 +15,10 @@ constexpr uint64_t kBigLeafMax = 1ull << 22;
 // Deepest split tree the library builds (2^27 node records of 32 bytes).
 constexpr int kMaxDepth = 26;
 
+// Split-tree depth of (n, N, n0): the least D >= 0 with n <= n0 2^D, then
+// lowered until 2^D <= N (Algorithm P's fixed tree, Sec. 3.2 and Sec. 4.5).
+int tree_depth(uint64_t n, uint64_t N, uint32_t n0);
+
 // Builds the ln i! table (i < 256) on the device with the library's own log.
 cudaError_t launch_lf_table(double* tab, cudaStream_t st);
 

@@ -156,6 +156,7 @@ struct rs_server {
     std::deque<uint64_t> completed;            // not yet polled
     uint64_t next_ticket = 1;
     uint32_t inflight = 0;
+    uint32_t fail_plans = 0;   // testing knob: plans that fail as if host memory ran out
     rs_server_stats stats{};
     bool stop = false;
     std::thread worker;
@@ -265,7 +266,16 @@ bool launch(rs_server* S, Lane& L, bool small_only) {
     }
     const double t_launch = S->now_ms();
     int rc = RS_OK;
+    bool inject = false;
+    {
+        std::lock_guard<std::mutex> lock(S->mu);
+        if (S->fail_plans) {
+            S->fail_plans--;
+            inject = true;
+        }
+    }
     try {
+        if (inject) throw std::bad_alloc();
         L.plan.build(reqs.data(), outs.data(), (uint32_t)reqs.size(), qs.data(), (uint32_t)qs.size());
     } catch (const std::bad_alloc&) {
         rc = RS_ENOMEM;
@@ -534,6 +544,13 @@ int rs_server_release(rs_server* S, uint64_t ticket) {
         S->jobs.erase(it);
     }
     if (freed) S->cv_work.notify_one();
+    return RS_OK;
+}
+
+int rs_server_fail_next_plans(rs_server* S, uint32_t count) {
+    if (!S) return RS_EINVAL;
+    std::lock_guard<std::mutex> lock(S->mu);
+    S->fail_plans = count;
     return RS_OK;
 }
 

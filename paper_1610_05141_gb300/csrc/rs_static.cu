@@ -14,6 +14,9 @@
 //
 // The array is shared by every call in the process: calls that overlap on
 // the GPU (on different streams or host threads) race and must be avoided.
+// The device address and the table are looked up and built once per device
+// and kept for the life of the process: after a cudaDeviceReset the array's
+// contents are gone, so the entry point must not be used again after one.
 #include <mutex>
 
 #include "rs_internal.h"
@@ -56,13 +59,6 @@ int static_setup(int dev, cudaStream_t st, unsigned char** base) {
     return RS_OK;
 }
 
-int static_depth(uint64_t n, uint64_t N, uint32_t n0) {
-    int D = 0;
-    while ((unsigned __int128)n > ((unsigned __int128)n0 << D)) ++D;
-    while (D > 0 && ((unsigned __int128)1 << D) > (unsigned __int128)N) --D;
-    return D;
-}
-
 }  // namespace
 
 extern "C" int rs_sample_static(uint64_t n, uint64_t N, uint64_t seed, uint32_t n0, uint64_t* out_dev,
@@ -70,7 +66,7 @@ extern "C" int rs_sample_static(uint64_t n, uint64_t N, uint64_t seed, uint32_t 
     if (n0 == 0 || N > (1ull << 62) || (n > 0 && N == 0) || n > N) return RS_EINVAL;
     if (n > 0 && (out_dev == nullptr || ((uintptr_t)out_dev & 7))) return RS_EINVAL;
     if (n == 0) return RS_OK;
-    const int D = static_depth(n, N, n0);
+    const int D = rs::tree_depth(n, N, n0);   // the same depth as rs_sample's
     if (D > kStaticDepth) return RS_ECAPACITY;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RS_ECUDA;
@@ -103,7 +99,7 @@ extern "C" int rs_sample_static(uint64_t n, uint64_t N, uint64_t seed, uint32_t 
     L.big_pool = big;
     L.big_kmax = bound > 64 ? std::min<uint64_t>(bound, kStaticBigKeys) : 0;
     L.cap = 0;
-    L.mean_count = 0;   // the small shape (the static scratch sizes follow it)
+    L.mean_count = n >> D;   // picks the leaf kernel's shape as rs_sample does (both use shared memory only)
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return RS_ECUDA;
     L.sms = sms;

@@ -240,7 +240,7 @@ RS_DEV void tree_batch_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
             U = u_open(((uint64_t)blk.y << 32) | blk.x);
             const double V = v_closed(((uint64_t)blk.w << 32) | blk.z);
             const double X = q.alpha + q.h * (V - 0.5) * drecip(U);
-            inr = !(X < 0.0 || X >= q.top) && t < kRouMaxTrials;
+            inr = !(X < 0.0 || X >= q.top) && t < c_caps.rou_trials;
             if (inr) {
                 k = (uint64_t)X;
                 if (guard) {
@@ -351,7 +351,7 @@ RS_DEV void tree_batch_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
                 Lout = Lsel;
             } else {
                 q.trial += G;
-                if (q.trial >= kRouMaxTrials) {
+                if (q.trial >= c_caps.rou_trials) {
                     if (r == 0) set_status(status, RS_EITER);
                     done = true;
                 }
@@ -413,7 +413,7 @@ RS_DEV void tree_terms_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
             U = u_open(((uint64_t)blk.y << 32) | blk.x);
             const double V = v_closed(((uint64_t)blk.w << 32) | blk.z);
             const double X = q.alpha + q.h * (V - 0.5) * drecip(U);
-            inr = !(X < 0.0 || X >= q.top) && t < kRouMaxTrials;
+            inr = !(X < 0.0 || X >= q.top) && t < c_caps.rou_trials;
             if (inr) k = (uint64_t)X;
             // this lane's difference ln P! - ln Q! (none: Q = P gives 0)
             Q = inr ? moving_end<WR>(q, (int)j, k) : P;
@@ -476,7 +476,7 @@ RS_DEV void tree_terms_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
                 Lout = Lsel;
             } else {
                 q.trial += G / 4;
-                if (q.trial >= kRouMaxTrials) {
+                if (q.trial >= c_caps.rou_trials) {
                     if (r == 0) set_status(status, RS_EITER);
                     done = true;
                 }
