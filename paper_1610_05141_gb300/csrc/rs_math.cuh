@@ -254,19 +254,20 @@ RS_DEV double log_fixed(uint64_t P, const double* __restrict__ tab) { return dlo
 // single-precision rate on GB300) is used only by the trials near the
 // boundary.
 //
-// Error bound.  flfdiff returns F and a magnitude m (a sum of the absolute
-// values of the terms it combines, each at least as large as that term)
-// with |F - (ln x! - ln y!)| <= 8 2^-24 m: its inputs are rounded once to
-// single precision (relative 2^-24 each), single-precision logf and log1pf
-// are within 1 ulp (CUDA's documented bounds), each product, quotient and
-// sum adds 2^-24 of its result, the table entries are ln i! rounded once,
-// and the Stirling terms past 1/(12x) (below 1/(360 x^3) <= 2e-10 for
-// x >= 256) and the rounding of ln(2 pi)/2 are covered by the constants
-// added to m.  The left side 2 ln U is within 8 2^-24 (|2 ln U| + 2).  The
-// FP64 values of the definition are within 2^-45 of the same magnitudes.
-// The guard takes kGuardUlps = 64 (eight times the derivation's constant)
-// times 2^-24 times the summed magnitudes as its margin.
-constexpr float kGuardUlps = 64.0f;
+// Error bound (u = 2^-24).  flfdiff returns F and a magnitude m (a sum of
+// the absolute values of the terms it combines, each at least as large as
+// that term) with |F - (ln x! - ln y!)| <= 12 u m: its inputs are rounded
+// once to single precision, each product, reciprocal and sum adds u of its
+// result, single-precision logf and log1pf are within 1 ulp (CUDA's
+// documented bounds; ln(1 + z) then keeps 6 u relative), the table entries
+// are ln i! rounded once, and the Stirling terms past 1/(12x) (below
+// 1/(360 x^3) <= 2e-10 for x >= 256) and the rounding of ln(2 pi)/2 are
+// covered by the constants added to m.  A sum of four such terms is within
+// 15 u of the summed magnitudes; the left side 2 ln U within 4 u (|2 ln U|
+// + 1); the FP64 values of the definition within 2^-45 of the same
+// magnitudes.  The guard takes kGuardUlps = 24 times u times the summed
+// magnitudes (plus |2 ln U| + 2) as its margin.
+constexpr float kGuardUlps = 24.0f;
 constexpr float kGuardEps = kGuardUlps * 5.9604645e-8f;   // kGuardUlps 2^-24
 
 // ln x! - ln y! for x >= y in single precision; *mag as above.  tf holds
@@ -304,10 +305,42 @@ RS_DEV float fsd(uint64_t P, uint64_t Q, const float* __restrict__ tf, float* ma
     return P >= Q ? flfdiff(P, Q, tf, mag) : -flfdiff(Q, P, tf, mag);
 }
 
+// Single-precision guard of the ratio-of-uniforms abscissa.  The definition
+// evaluates X = alpha + h (V - 1/2) / U in FP64; a trial is rejected when X
+// lies outside [0, top), else its candidate is k = floor(X).  alpha_f and
+// h_f are the node's parameters from the same formulas in single precision:
+// each input rounded once (relative u = 2^-24), each product, reciprocal and
+// sum once, sqrtf correctly rounded, so alpha_f is within 7 u alpha and h_f
+// within 14 u h; with Uf and Vf the uniforms rounded once, |X_f - X| <=
+// u (8 alpha + 11 h / U), and the FP64 X is within 2^-50 (alpha + h / U) of
+// the same value.  The guard takes 16 u (alpha + h / U + 1) as its margin
+// and settles the trial only when no boundary (0, top, an integer) lies
+// within it.  Returns 1 (X in [0, top), *k = floor(X)), -1 (outside:
+// rejected) or 0 (too close to call).
+constexpr float kXGuardEps = 16.0f * 5.9604645e-8f;
+RS_DEV int guard_abscissa(float alpha_f, float h_f, float top_f, float Uf, float Vf, uint64_t* k) {
+    const float hu = h_f * __frcp_rn(Uf);
+    const float X = alpha_f + hu * (Vf - 0.5f);
+    const float E = kXGuardEps * ((alpha_f + hu) + 1.0f);
+    // top_f is the integer top rounded once to single precision
+    const float top_lo = top_f * (1.0f - 2.4e-7f), top_hi = top_f * (1.0f + 2.4e-7f);
+    if (X + E < 0.0f || X - E >= top_hi) return -1;
+    if (X - E < 0.0f || X + E >= top_lo) return 0;
+    const float lo = floorf(X - E);
+    if (lo != floorf(X + E)) return 0;
+    *k = (uint64_t)lo;
+    return 1;
+}
+
+// The uniforms of a 64-bit value rounded once to single precision: U in
+// (0, 1] and V in [0, 1) of rs_rng.cuh, without FP64 operations.
+RS_DEV float u_open_f(uint64_t x) { return __ull2float_rn((x >> 11) + 1) * 1.1102230e-16f; }
+RS_DEV float v_closed_f(uint64_t x) { return __ull2float_rn(x >> 11) * 1.1102230e-16f; }
+
 // The guard's decision for 2 ln U against T = tsum (magnitude tmag):
 // 1 accept, -1 reject, 0 too close to call.
-RS_DEV int guard_decide(double U, float tsum, float tmag) {
-    const float L = 2.0f * logf(__double2float_rn(U));
+RS_DEV int guard_decide(float Uf, float tsum, float tmag) {
+    const float L = 2.0f * logf(Uf);
     const float margin = kGuardEps * ((tmag + fabsf(L)) + 2.0f);
     if (L + margin < tsum) return 1;
     if (L - margin > tsum) return -1;

@@ -9,6 +9,8 @@
 // no samples draws nothing.  Depth D is fixed in advance (as in Algorithm P's
 // tree over PEs and the p' >> p jobs of Sec. 4.5), so the tree, and with it
 // the sample, does not depend on how the work is scheduled.
+#include <cooperative_groups.h>
+
 #include "rs_internal.h"
 #include "rs_tree_warp.cuh"
 
@@ -75,6 +77,40 @@ __global__ void __launch_bounds__(kTreeWarps * 32) tree_terms_kernel(NodeRec* __
     tree_terms_warp<WR>(rec, first + start, count, make_key(seed), tab, status, G, guard);
 }
 
+// The root and the top `levels` levels in one cooperative launch (one block
+// of kTreeWarps warps per SM, all resident): level l's 2^l nodes are spread
+// over the grid's warps, a group of G lanes per node running trials in
+// parallel, and the grid synchronizes between levels.  These levels hold few
+// nodes each, so their time is the latency of one node's chain of FP64
+// operations; one launch instead of one per level saves the launches and
+// the cold start of each.
+constexpr int kTopFused = 12;   // levels of the fused launch, at most
+
+template <bool WR>
+__global__ void __launch_bounds__(kTreeWarps * 32) tree_top_kernel(NodeRec* __restrict__ rec, uint64_t n, uint64_t N,
+                                                                  int levels, uint64_t seed,
+                                                                  const double* __restrict__ tab, int* status,
+                                                                  bool guard) {
+    namespace cg = cooperative_groups;
+    cg::grid_group grid = cg::this_grid();
+    if (blockIdx.x == 0 && threadIdx.x == 0) rec[1] = NodeRec{0, N, n, 0};
+    grid.sync();
+    const uint64_t W = (uint64_t)gridDim.x * kTreeWarps;
+    const uint64_t w = (uint64_t)blockIdx.x * kTreeWarps + (threadIdx.x >> 5);
+    for (int level = 0; level < levels; ++level) {
+        const uint64_t nodes = 1ull << level;
+        uint32_t G = 32;
+        while (G > 4 && nodes * G > W * 32) G >>= 1;
+        const uint64_t groups = 32 / G;   // nodes a warp holds at once
+        const uint64_t per = groups * ((nodes + W * groups - 1) / (W * groups));
+        const uint64_t start = w * per;
+        if (start < nodes)
+            tree_terms_warp<WR>(rec, nodes + start, (uint32_t)min(per, nodes - start), make_key(seed), tab, status, G,
+                                guard);
+        grid.sync();
+    }
+}
+
 // Lanes per node for a launch of `nodes` nodes: the largest power of two up
 // to 32 that keeps nodes * G within about four warps per SM, and at least 4
 // (four lanes share a trial) up to 512 nodes per SM.  G >= 4: parallel
@@ -131,11 +167,37 @@ cudaError_t launch_tree(NodeRec* rec, uint64_t n, uint64_t N, uint64_t seed, int
     return launch_tree_top(rec, n, N, seed, D, with_replacement, tab, status, st, guard);
 }
 
+// Whether the device takes cooperative launches of the fused top kernel
+// (one block per SM).
+static bool top_fusable() {
+    int dev = 0, coop = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return false;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tree_top_kernel<false>, kTreeWarps * 32, 0) !=
+            cudaSuccess || per_sm < 1)
+        return false;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tree_top_kernel<true>, kTreeWarps * 32, 0) !=
+            cudaSuccess || per_sm < 1)
+        return false;
+    return true;
+}
+
 cudaError_t launch_tree_top(NodeRec* rec, uint64_t n, uint64_t N, uint64_t seed, int levels, bool with_replacement,
                             const double* tab, int* status, cudaStream_t st, bool guard) {
-    tree_root_kernel<<<1, 32, 0, st>>>(rec, n, N);
     const int sms = device_sms();
-    for (int level = 0; level < levels; ++level)
+    static const bool fusable = top_fusable();
+    int level = 0;
+    if (fusable && levels > 1) {
+        int fused = levels < kTopFused ? levels : kTopFused;
+        void* args[] = {&rec, &n, &N, &fused, &seed, &tab, &status, &guard};
+        const void* kern = with_replacement ? (const void*)tree_top_kernel<true> : (const void*)tree_top_kernel<false>;
+        const cudaError_t e = cudaLaunchCooperativeKernel(kern, dim3(sms), dim3(kTreeWarps * 32), args, 0, st);
+        if (e != cudaSuccess) return e;
+        level = fused;
+    } else {
+        tree_root_kernel<<<1, 32, 0, st>>>(rec, n, N);
+    }
+    for (; level < levels; ++level)
         launch_nodes(rec, 1ull << level, 1ull << level, seed, with_replacement, tab, status, sms, st, guard);
     return cudaGetLastError();
 }

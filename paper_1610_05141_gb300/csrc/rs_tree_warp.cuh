@@ -97,13 +97,45 @@ struct RouNode {
     uint64_t lo, S, c, off, K;
     uint64_t a, b, M;    // hypergeometric: reduced draws/successes; binomial: a = c
     uint64_t n_in, Kp;   // un-reduction of the hypergeometric result
-    double h, alpha, top, logr;
+    double mu, h, alpha, top, logr;   // FP64 parameters, as defined (set up when a trial first needs them)
+    float fa, fh, ftop;  // alpha, h, top in single precision, for the guards
     float logrf;         // binomial: ln(p / (1 - p)) in single precision, for the guard
     double lnP[4];       // ln of the fixed ends (lanes kernel), once per node
     uint32_t trial;
     bool flipN, flipK;
     bool fresh;          // set up, fixed-end logarithms not yet taken
+    bool have64;         // h, alpha, top, logr are set
 };
+
+// The hat's constants 2 sqrt(2/e) and 3 - 2 sqrt(3/e) in single precision.
+constexpr float kHatD1f = 1.71552777f;
+constexpr float kHatD2f = 0.898916162f;
+
+// The node's FP64 parameters exactly as the definition computes them
+// (rs_deviates.cuh).
+template <bool WR>
+RS_DEV void setup64(RouNode* q, const double* __restrict__ tab) {
+    if (WR) {
+        const double p = (double)q->K / (double)q->S;
+        const double mu = (double)q->a * p;
+        const double var = mu * (1.0 - p);
+        q->mu = mu;
+        q->h = RS_HAT_D1 * sqrt(var + 0.5) + RS_HAT_D2;
+        q->alpha = mu + 0.5;
+        const double rr = p / (1.0 - p);
+        q->logr = (rr == 1.0) ? 0.0 : dlog(rr, tab);
+    } else {
+        const uint64_t S = q->S, a = q->a, b = q->b;
+        const double rS = drecip((double)S);
+        const double mu = ((double)a * (double)b) * rS;
+        const double var = mu * ((double)(S - a) * rS) * ((double)(S - b) * drecip((double)(S - 1)));
+        q->mu = mu;
+        q->h = RS_HAT_D1 * sqrt(var + 0.5) + RS_HAT_D2;
+        q->alpha = mu + 0.5;
+    }
+    q->top = (double)q->a + 1.0;
+    q->have64 = true;
+}
 
 template <bool WR>
 RS_DEV uint64_t fixed_end(const RouNode& q, int j) {
@@ -125,36 +157,34 @@ RS_DEV void write_children(NodeRec* __restrict__ rec, uint64_t v, const NodeRec&
 
 // Prepares node v.  Returns true if the node needs ratio-of-uniforms trials
 // (state in *q); otherwise the node is finished here (children written):
-// no samples, a fast path, or inversion.
+// no samples, a fast path, or inversion.  The choice between inversion and
+// ratio-of-uniforms (mean below 16) is taken from the single-precision mean
+// when that is clear of 16 by its error bound (6 2^-24 relative), else from
+// the FP64 mean as defined.  The FP64 parameters are set up here when
+// eager64, else by the first trial that needs them.
 template <bool WR>
 RS_DEV bool node_setup(NodeRec* __restrict__ rec, uint64_t v, Key2 key, const double* __restrict__ tab, int* status,
-                       RouNode* q, bool writer = true) {
-    const NodeRec r = rec[v];
+                       RouNode* q, bool writer = true, bool eager64 = true) {
+    // written by the level before, possibly by another SM of the same launch
+    // (the fused top levels): read past this SM's L1
+    const ulonglong2* pr = reinterpret_cast<const ulonglong2*>(rec + v);
+    const ulonglong2 r0 = __ldcg(pr), r1 = __ldcg(pr + 1);
+    const NodeRec r{r0.x, r0.y, r1.x, r1.y};
     const uint64_t K = r.S / 2;
     auto finish = [&](uint64_t L) {
         if (writer) write_children(rec, v, r, K, L);
         return false;
     };
     if (r.c == 0) return finish(0);
+    float muf;
     if (WR) {
         const uint64_t c = r.c;
         if (K == 0) return finish(0);
-        const double p = (double)K / (double)r.S;
-        const double mu = (double)c * p;
-        if (mu < 16.0) {
-            uint64_t L = 0;
-            const int rc = binomial(key, v, c, K, r.S, tab, L);
-            if (rc != RS_OK) { set_status(status, rc); L = 0; }
-            return finish(L);
-        }
-        const double var = mu * (1.0 - p);
-        q->h = RS_HAT_D1 * sqrt(var + 0.5) + RS_HAT_D2;
-        q->alpha = mu + 0.5;
-        const double rr = p / (1.0 - p);
-        q->logr = (rr == 1.0) ? 0.0 : dlog(rr, tab);
-        q->logrf = (rr == 1.0) ? 0.0f : logf(__double2float_rn(rr));
+        const float pf = __ull2float_rn(K) * __frcp_rn(__ull2float_rn(r.S));
+        muf = __ull2float_rn(c) * pf;
+        q->fh = kHatD1f * sqrtf(muf * (1.0f - pf) + 0.5f) + kHatD2f;
+        q->logrf = (2 * K == r.S) ? 0.0f : logf(pf / (1.0f - pf));
         q->M = (uint64_t)(((unsigned __int128)(c + 1) * K) / r.S);
-        q->top = (double)c + 1.0;
         q->a = c;
     } else {
         uint64_t n = r.c, Kh = K;
@@ -169,19 +199,12 @@ RS_DEV bool node_setup(NodeRec* __restrict__ rec, uint64_t v, Key2 key, const do
         if (q->flipN) n = S - n;
         const uint64_t a = n < Kh ? n : Kh;
         const uint64_t b = n < Kh ? Kh : n;
-        const double rS = drecip((double)S);
-        const double mu = ((double)a * (double)b) * rS;
-        if (mu < 16.0) {
-            uint64_t L = 0;
-            const int rc = hypergeometric(key, v, r.c, K, S, tab, L);
-            if (rc != RS_OK) { set_status(status, rc); L = 0; }
-            return finish(L);
-        }
-        const double var = mu * ((double)(S - a) * rS) * ((double)(S - b) * drecip((double)(S - 1)));
-        q->h = RS_HAT_D1 * sqrt(var + 0.5) + RS_HAT_D2;
-        q->alpha = mu + 0.5;
+        const float rSf = __frcp_rn(__ull2float_rn(S));
+        muf = (__ull2float_rn(a) * __ull2float_rn(b)) * rSf;
+        const float varf = (muf * (__ull2float_rn(S - a) * rSf)) *
+                           (__ull2float_rn(S - b) * __frcp_rn(__ull2float_rn(S - 1)));
+        q->fh = kHatD1f * sqrtf(varf + 0.5f) + kHatD2f;
         q->M = (uint64_t)(((unsigned __int128)(a + 1) * (b + 1)) / (S + 2));
-        q->top = (double)a + 1.0;
         q->a = a;
         q->b = b;
         q->Kp = Kh;
@@ -194,6 +217,23 @@ RS_DEV bool node_setup(NodeRec* __restrict__ rec, uint64_t v, Key2 key, const do
     q->K = K;
     q->trial = 0;
     q->fresh = true;
+    q->have64 = false;
+    q->fa = muf + 0.5f;
+    q->ftop = __ull2float_rn(q->a + 1);
+    // inversion below a mean of 16 (the FP64 mean decides when the single
+    // one is within its error of 16)
+    bool inversion = muf < 15.99f;
+    if (!inversion && muf <= 16.01f) {
+        setup64<WR>(q, tab);
+        inversion = q->mu < 16.0;
+    }
+    if (inversion) {
+        uint64_t L = 0;
+        const int rc = WR ? binomial(key, v, r.c, K, r.S, tab, L) : hypergeometric(key, v, r.c, K, r.S, tab, L);
+        if (rc != RS_OK) { set_status(status, rc); L = 0; }
+        return finish(L);
+    }
+    if (eager64 && !q->have64) setup64<WR>(q, tab);
     return true;
 }
 
@@ -221,14 +261,13 @@ RS_DEV void tree_batch_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
             const uint32_t take = min((uint32_t)__popc(freem), count - next);
             const uint32_t rank = __popc(freem & ((1u << gbase) - 1u));
             if (!active && rank < take)
-                active = node_setup<WR>(rec, v0 + next + rank, key, tab, status, &q, r == 0);
+                active = node_setup<WR>(rec, v0 + next + rank, key, tab, status, &q, r == 0, !guard);
             next += take;
         }
         if (__ballot_sync(0xFFFFFFFFu, active) == 0) break;
         // one trial per active lane: uniforms, candidate, the guard, and for
         // the trials it leaves open the logarithm arguments
         const uint64_t t = (uint64_t)q.trial + r;   // this lane's trial
-        double U = 1.0;
         uint64_t k = 0;
         bool inr = false;
         int dec = 0;
@@ -237,12 +276,19 @@ RS_DEV void tree_batch_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
         constexpr int kTerms = WR ? 2 : 4;
         if (active) {
             const uint4 blk = philox_block((uint32_t)t, TAG_SPLIT, q.v, key);
-            U = u_open(((uint64_t)blk.y << 32) | blk.x);
-            const double V = v_closed(((uint64_t)blk.w << 32) | blk.z);
-            const double X = q.alpha + q.h * (V - 0.5) * drecip(U);
-            inr = !(X < 0.0 || X >= q.top) && t < c_caps.rou_trials;
+            const uint64_t ux = ((uint64_t)blk.y << 32) | blk.x;
+            const uint64_t vx = ((uint64_t)blk.w << 32) | blk.z;
+            const float Uf = u_open_f(ux);
+            int xd = guard ? guard_abscissa(q.fa, q.fh, q.ftop, Uf, v_closed_f(vx), &k) : 0;
+            if (xd == 0) {   // the abscissa in FP64, as defined
+                if (!q.have64) setup64<WR>(&q, tab);
+                const double U = u_open(ux), V = v_closed(vx);
+                const double X = q.alpha + q.h * (V - 0.5) * drecip(U);
+                xd = (X < 0.0 || X >= q.top) ? -1 : 1;
+                if (xd > 0) k = (uint64_t)X;
+            }
+            inr = xd > 0 && t < c_caps.rou_trials;
             if (inr) {
-                k = (uint64_t)X;
                 if (guard) {
                     float fm = 0.0f, ft = 0.0f;
 #pragma unroll
@@ -257,9 +303,10 @@ RS_DEV void tree_batch_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
                         ft += rt;
                         fm += fabsf(rt) + fabsf(dk);
                     }
-                    dec = guard_decide(U, ft, fm);
+                    dec = guard_decide(Uf, ft, fm);
                 }
                 if (dec == 0) {
+                    if (WR && !q.have64) setup64<WR>(&q, tab);   // ln(p / (1 - p)) as defined
                     LfdArgs A{mine, 0, 0};
                     if (q.fresh) {   // the fixed ends' logarithms go with this round's
                         fresh_now = true;
@@ -269,7 +316,7 @@ RS_DEV void tree_batch_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
                             A.push((double)(P > 0 ? P : 1));
                         }
                     }
-                    A.push(U);
+                    A.push(u_open(ux));
 #pragma unroll
                     for (int j = 0; j < kTerms; ++j) sdf_args(fixed_end<WR>(q, j), moving_end<WR>(q, j, k), A);
                     nargs = A.n;
@@ -387,6 +434,9 @@ RS_DEV void tree_terms_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
     uint64_t P = 0;        // this lane's fixed end (term j); its logarithm once the node first needs FP64
     double lnP = 0.0;
     bool haveLnP = false;
+    // few nodes per launch (the top of the tree): latency, not the FP64 rate,
+    // bounds the launch, so the FP64 set-up and logarithms start at once
+    const bool eager = !guard || G >= 16;
     for (;;) {
         // free groups take the next nodes, in order
         for (;;) {
@@ -395,29 +445,37 @@ RS_DEV void tree_terms_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
             const uint32_t take = min((uint32_t)__popc(freem), count - next);
             const uint32_t rank = __popc(freem & ((1u << gbase) - 1u));
             if (!active && rank < take) {
-                active = node_setup<WR>(rec, v0 + next + rank, key, tab, status, &q, r == 0);
+                active = node_setup<WR>(rec, v0 + next + rank, key, tab, status, &q, r == 0, eager);
                 if (active) {
                     P = fixed_end<WR>(q, (int)j);
-                    haveLnP = false;
+                    haveLnP = eager;
+                    if (eager) lnP = log_fixed(P, tab);
                 }
             }
             next += take;
         }
         if (__ballot_sync(0xFFFFFFFFu, active) == 0) break;
         const uint64_t t = (uint64_t)q.trial + p;
-        double U = 1.0;
-        uint64_t k = 0, Q = P;
-        bool inr = false;
+        uint64_t ux = 0, k = 0, Q = P;   // ux: the value of U
+        float Uf = 1.0f;
+        int xd = 0;   // 1: X in [0, top), k = floor(X); -1: rejected; 0: not settled
         if (active) {
             const uint4 blk = philox_block((uint32_t)t, TAG_SPLIT, q.v, key);
-            U = u_open(((uint64_t)blk.y << 32) | blk.x);
-            const double V = v_closed(((uint64_t)blk.w << 32) | blk.z);
-            const double X = q.alpha + q.h * (V - 0.5) * drecip(U);
-            inr = !(X < 0.0 || X >= q.top) && t < c_caps.rou_trials;
-            if (inr) k = (uint64_t)X;
-            // this lane's difference ln P! - ln Q! (none: Q = P gives 0)
-            Q = inr ? moving_end<WR>(q, (int)j, k) : P;
+            ux = ((uint64_t)blk.y << 32) | blk.x;
+            const uint64_t vx = ((uint64_t)blk.w << 32) | blk.z;
+            Uf = u_open_f(ux);
+            if (guard) xd = guard_abscissa(q.fa, q.fh, q.ftop, Uf, v_closed_f(vx), &k);
+            if (xd == 0) {   // the abscissa in FP64, as defined
+                if (!q.have64) setup64<WR>(&q, tab);
+                const double U = u_open(ux), V = v_closed(vx);
+                const double X = q.alpha + q.h * (V - 0.5) * drecip(U);
+                xd = (X < 0.0 || X >= q.top) ? -1 : 1;
+                if (xd > 0) k = (uint64_t)X;
+            }
         }
+        const bool inr = active && xd > 0 && t < c_caps.rou_trials;
+        // this lane's difference ln P! - ln Q! (none: Q = P gives 0)
+        if (active) Q = inr ? moving_end<WR>(q, (int)j, k) : P;
         // the guard: the trial's four lanes sum their single-precision terms
         int dec = 0;
         if (guard) {
@@ -433,7 +491,7 @@ RS_DEV void tree_terms_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
                 ft += rt;
                 fm += fabsf(rt) + fabsf(dk);
             }
-            if (active && inr) dec = guard_decide(U, ft, fm);
+            if (active && inr) dec = guard_decide(Uf, ft, fm);
         }
         // FP64, as the definition states, for the trials the guard left open
         const bool need = active && inr && dec == 0;
@@ -443,9 +501,10 @@ RS_DEV void tree_terms_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
                 lnP = log_fixed(P, tab);
                 haveLnP = true;
             }
+            if (WR && need && !q.have64) setup64<WR>(&q, tab);   // ln(p / (1 - p)) as defined
             // the ends are picked with selects so that all lanes run one copy
             const double term = dsd_fixed(P, need ? Q : P, lnP, tab);
-            const double lU = dlog(U, tab);
+            const double lU = dlog(u_open(ux), tab);
             const double t0 = __shfl_sync(0xFFFFFFFFu, term, tbase);
             const double t1 = __shfl_sync(0xFFFFFFFFu, term, tbase + 1);
             const double t2 = __shfl_sync(0xFFFFFFFFu, term, tbase + 2);
