@@ -38,17 +38,43 @@ constexpr uint32_t kLargeCap = 2 * kLeafFastCap;
 // shared-memory table cannot take go to the general path's list.
 // The job is a __grid_constant__ parameter so that the Philox rounds read
 // their keys from the parameter bank.
+// Copies a leaf record (32 bytes) into shared memory asynchronously.
+RS_DEV void prefetch_record(NodeRec* dst, const NodeRec* src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n\t"
+                 "cp.async.cg.shared.global [%2], [%3], 16;\n\t"
+                 "cp.async.commit_group;" ::"r"(d), "l"(src), "r"(d + 16),
+                 "l"(reinterpret_cast<const unsigned char*>(src) + 16)
+                 : "memory");
+}
+RS_DEV void prefetch_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 template <typename KeyT, bool WR, int NT, uint32_t CAP>
 __global__ void __launch_bounds__(NT, 1024 / NT) leaf_kernel(const __grid_constant__ LeafJob job) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto& sm = *reinterpret_cast<HashShared<KeyT, NT / 32, CAP>*>(smem_raw);
-    for (uint64_t leaf = blockIdx.x; leaf < job.nleaves; leaf += gridDim.x) {
-        const NodeRec r = job.leaves[leaf];
-        if (r.c == 0) continue;
-        const LeafRec lr{r.lo, r.S, r.c, r.off, job.first_id + leaf};
-        if (!hash_leaf<KeyT, NT, 0, WR, CAP>(sm, lr, job.rk, job.out, job.status, threadIdx.x, job.cap)) {
-            if (threadIdx.x == 0) job.ovf_list[atomicAdd(job.ovf_count, 1u)] = (uint32_t)leaf;
+    // the next leaf's record is copied in (thread 0, cp.async) while this
+    // leaf runs; the wait and a barrier at the end of the leaf make it visible
+    __shared__ __align__(16) NodeRec recbuf[2];
+    if (blockIdx.x >= job.nleaves) return;
+    if (threadIdx.x == 0) {
+        prefetch_record(&recbuf[0], &job.leaves[blockIdx.x]);
+        prefetch_wait();
+    }
+    __syncthreads();
+    uint32_t par = 0;
+    for (uint64_t leaf = blockIdx.x; leaf < job.nleaves; leaf += gridDim.x, par ^= 1u) {
+        const NodeRec r = recbuf[par];
+        if (threadIdx.x == 0 && leaf + gridDim.x < job.nleaves)
+            prefetch_record(&recbuf[par ^ 1u], &job.leaves[leaf + gridDim.x]);
+        if (r.c != 0) {
+            const LeafRec lr{r.lo, r.S, r.c, r.off, job.first_id + leaf};
+            if (!hash_leaf<KeyT, NT, 0, WR, CAP>(sm, lr, job.rk, job.out, job.status, threadIdx.x, job.cap)) {
+                if (threadIdx.x == 0) job.ovf_list[atomicAdd(job.ovf_count, 1u)] = (uint32_t)leaf;
+            }
         }
+        if (threadIdx.x == 0) prefetch_wait();
+        __syncthreads();
     }
 }
 
