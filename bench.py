@@ -88,7 +88,7 @@ def leaf_traffic():
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle samples every 200 ms while running."""
+    """nvidia-smi clock/throttle samples every 50 ms while running."""
 
     FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -104,7 +104,7 @@ class ClockSampler:
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -329,8 +329,9 @@ def run_batch(rs, ctx, stream, args):
         "requests": len(n), "samples": total, "ms_per_run": batch_ms,
         "req_per_s": len(n) / (batch_ms / 1000), "samples_per_s": total / (batch_ms / 1000),
         "write_gbs": 8 * total / (batch_ms / 1000) / 1e9,
-        "latency_ms": {"p50": batch_ms, "p99": batch_ms,
-                       "note": "every request of a run completes with the run"},
+        "request_latency_ms": batch_ms,
+        "request_latency_note": "a run is one graph replay: every request's values are complete when the run "
+                                "ends, so each request's latency is the run's time (no per-request spread)",
         "kernel_launches_per_run": launches, "plan_s": plan_s,
         "unbatched": {"requests": m, "req_per_s": m / (single_ms / 1000),
                       "batched_same_requests_req_per_s": m / (slice_ms / 1000),
@@ -787,7 +788,9 @@ def run_ours(args):
                      "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs)",
                      "traffic": leaf_traffic()},
         "e2e": {"value": world * N_SAMPLES / (e2e_step / 1000), "unit": "samples/s", "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": BYTES_PER_SAMPLE * N_SAMPLES, "ms_per_step": e2e_step},
+                "d2h_bytes_per_step": BYTES_PER_SAMPLE * N_SAMPLES, "ms_per_step": e2e_step,
+                "h2d_note": "a step's inputs are four scalars (n, N, seed, n0) passed by value: there is no input "
+                            "array to copy; the whole sample is copied to pinned host memory"},
         "gpu_launches": launches,
         "clocks": clk,
     }
@@ -808,6 +811,36 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_tree_only(args):
+    """The split tree of the workload alone (rs_split_tree into a record
+    buffer of 32 B per leaf), device-timed: a small footprint for profiling
+    the tree kernels."""
+    import torch
+    import paper_1610_05141_gb300 as rs
+    from paper_1610_05141_gb300 import build as rs_build
+    rs_build.build()
+    rs.load()
+    ctx = rs.rs_create(0)
+    D = rs.rs_plan(N_SAMPLES, UNIVERSE, N0)
+    recs = torch.zeros(4 << D, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for k in range(args.warmup):
+            rs.rs_split_tree(ctx, N_SAMPLES, UNIVERSE, SEED + k, N0, 0, recs, 1 << D, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(args.steps):
+            rs.rs_split_tree(ctx, N_SAMPLES, UNIVERSE, SEED + k, N0, 0, recs, 1 << D, stream)
+        e1.record(stream)
+        stream.synchronize()
+    rc = rs.rs_sync(ctx, stream)
+    if rc != rs.RS_OK:
+        raise RuntimeError(f"device status {rc}: {rs.strerror(rc)}")
+    print(json.dumps({"metric": "split tree ms", "value": e0.elapsed_time(e1) / max(args.steps, 1), "unit": "ms",
+                      "higher_is_better": False, "config": {"workload": WORKLOAD, "depth": D}}))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -818,7 +851,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-requests measurement")
     ap.add_argument("--batch-requests", type=int, default=100_000)
     ap.add_argument("--batch-runs", type=int, default=5)
-    ap.add_argument("--unbatched-requests", type=int, default=3000)
+    ap.add_argument("--unbatched-requests", type=int, default=10000)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-rows", action="store_true", help="skip with-replacement, leaf B and Bernoulli")
     ap.add_argument("--rows", default="a5,a7,a6,f2,f3,f1,f4",
@@ -831,11 +864,14 @@ def main():
     ap.add_argument("--n", "--n-samples", dest="n", type=int, default=None, help="smaller n (profiling cases only)")
     ap.add_argument("--log2N", type=int, default=None, help="smaller universe 2^log2N (profiling cases only)")
     ap.add_argument("--n0", type=int, default=None, help="other leaf size (profiling cases only)")
+    ap.add_argument("--tree-only", action="store_true", help="time the split tree alone (profiling)")
     ap.add_argument("--pipeline", default=None,
                     help="LOG2_PARTS,LEAF_BLOCKS_PER_SM for rs_set_pipeline (default: the library's)")
     args = ap.parse_args()
     set_workload(args.n, args.log2N, args.n0)
-    if args.impl == "reference":
+    if args.tree_only:
+        run_tree_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
