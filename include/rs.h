@@ -416,12 +416,15 @@ const char* rs_strerror(int code);
 int rs_set_leaf_capacity(rs_ctx* ctx, uint32_t cap);
 
 /* Testing knob: on != 0 makes the split tree evaluate every ratio-of-uniforms
- * acceptance test 2 ln U <= T (Sec. 3.1, Sec. 4.6) in FP64 as the definition
- * states.  By default a single-precision evaluation with an error bound
- * decides the trials whose two sides are further apart than the bound, and
- * only the others are evaluated in FP64; the outcome of every test, and so
- * the output, is the same either way.  Applies to the context's later
- * sampling calls.  Errors: RS_EINVAL (null ctx). */
+ * acceptance test 2 ln U <= T (Sec. 3.1, Sec. 4.6), and Bernoulli sampling
+ * and Algorithm B leaves every geometric skip floor(ln U / ln(1 - p)) (Sec. 2
+ * Algorithm B, Sec. 4.7), in FP64 as the definition states.  By default an
+ * evaluation in single precision (and, for the skips, a fixed-point
+ * logarithm) with a proven error bound decides the cases further from the
+ * decision's boundary than the bound, and only the others are evaluated in
+ * FP64; every outcome, and so the output, is the same either way.  Applies
+ * to the context's later rs_sample*, rs_bernoulli* and rs_sample_b calls.
+ * Errors: RS_EINVAL (null ctx). */
 int rs_set_exact_deviates(rs_ctx* ctx, int on);
 
 /* Testing knob: lowers the iteration caps of the method's loops on the

@@ -41,6 +41,77 @@ RS_DEV double skip_quotient(uint64_t x, double R, const double* __restrict__ tab
     return dlog(u_open(x), tab) * R;
 }
 
+// The skip of one draw decided without FP64 where that is safe.  The
+// definition floors q64 = RN(dlog(U) R) (skip_quotient); here, with
+// A = -qlog_u57(m) (U = m 2^-53, |A 2^-57 - |ln U|| <= 2^-55):
+// - Lh + Lm = A 2^-57 (1 - tau), 0 <= tau < 2^-47: the top 48 of A's 63
+//   bits as two exact singles;
+// - rh + rl = |R| (1 + rho), |rho| <= 2^-48;
+// - p = RN(Lh rh) and e = fma(Lh, rh, -p) + (Lh rl + Lm rh), whose roundings
+//   stay below 2^-45 p; the dropped Lm rl is below 2^-48 p; so
+//   |p + e - |ln U| |R|| <= |R| 2^-55 + p 2^-44.3;
+// - dlog is within 2 ulp of ln U and the product is rounded once, so
+//   |q64 - |ln U| |R|| <= 2^-50.6 q64;
+// - r = RN((p - floor(p)) + e), p - floor(p) exact, rounds by 2^-24 |r|.
+// Hence |floor(p) + r - q64| <= b / 2 for b = (|r| + 1) 2^-23 + p 2^-43 +
+// |R| 2^-54, and when floor(r - b) = floor(r + b) (rounded outward) that is
+// floor(q64 - floor(p)).  Otherwise, or for p >= 2^61 (where the range's
+// end test of 2^62 could be near), the draw takes the FP64 definition.  The
+// skips, and so the sample, are the definition's in every case.
+struct SkipParams {
+    double R;        // RN(1 / ln(1 - p)), negative
+    float rh, rl;    // |R| as an unevaluated sum of two singles
+    float rb;        // |R| 2^-54, rounded up
+    bool fast;       // the single-precision decision may be taken
+};
+
+RS_DEV SkipParams skip_params(double R, bool guard) {
+    SkipParams s;
+    s.R = R;
+    const double a = -R;
+    s.fast = guard && a > 0.0 && a < 1e30;   // huge or infinite |R| (p near 0) takes FP64 only
+    s.rh = __double2float_rn(s.fast ? a : 0.0);
+    s.rl = __double2float_rn(s.fast ? a - (double)s.rh : 0.0);
+    s.rb = __double2float_ru(s.fast ? a * 0x1p-54 : 0.0);
+    return s;
+}
+
+// Skip + 1 of the draw with 64-bit value x; false if it must take FP64.
+RS_DEV bool skip_fast(uint64_t x, const SkipParams& sp, const double* __restrict__ tab, uint64_t* step) {
+    const uint64_t m = (x >> 11) + 1;
+    if (m == (1ull << 53)) {   // U = 1: skip 0, as in skip_quotient
+        *step = 1;
+        return true;
+    }
+    const int64_t A = -qlog_u57(m, tab);   // below 2^62.2 (|ln U| <= 53 ln 2)
+    if (A <= 0) return false;
+    const int lz = __clzll(A);
+    const uint64_t nn = (uint64_t)A << lz;
+    const float Lh = (float)(uint32_t)(nn >> 40) * __int_as_float((110 - lz) << 23);              // * 2^(-17-lz)
+    const float Lm = (float)((uint32_t)(nn >> 16) & 0xFFFFFFu) * __int_as_float((86 - lz) << 23);  // * 2^(-41-lz)
+    const float p = Lh * sp.rh;
+    const float e = __fmaf_rn(Lh, sp.rh, -p) + (Lh * sp.rl + Lm * sp.rh);
+    if (!(p < 0x1p61f)) return false;
+    const float fl = floorf(p);
+    const float r = (p - fl) + e;
+    const float b = (fabsf(r) + 1.0f) * 0x1p-23f + p * 0x1p-43f + sp.rb;
+    const float klo = floorf(__fadd_rd(r, -b));
+    if (klo != floorf(__fadd_ru(r, b))) return false;
+    *step = __float2ull_rz(fl) + (uint64_t)__float2ll_rz(klo) + 1;
+    return true;
+}
+
+// Skip + 1 of one draw (or 0 with *stop), by skip_fast where it decides.
+RS_DEV uint64_t draw_step(uint64_t x, const SkipParams& sp, uint64_t cmax, bool* stop,
+                          const double* __restrict__ tab) {
+    uint64_t s;
+    if (sp.fast && skip_fast(x, sp, tab, &s)) {
+        *stop = false;
+        return s < cmax ? s : cmax;
+    }
+    return step_of(skip_quotient(x, sp.R, tab), cmax, stop);
+}
+
 RS_DEV uint64_t warp_inclusive_sat(uint64_t x) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -51,34 +122,86 @@ RS_DEV uint64_t warp_inclusive_sat(uint64_t x) {
     return x;
 }
 
+// The draws a lane (or a thread) takes per round of a walk: V consecutive
+// draws from V/2 Philox blocks (block b gives draws 2b and 2b + 1, as in
+// stream_value), so that no block is computed twice and a round's scan is
+// shared by V draws.
+constexpr int kWalkV = 4;
+
+// Steps of draws j0 .. j0 + V - 1 (j0 even): step[q] (0 for a draw that
+// ends the range), bit q of *endm set for a draw that ends the range or lies
+// past the stream, bit q of *exhm for a draw past the stream.
+template <int V>
+RS_DEV void draw_steps(Key2 key, uint32_t tag, uint64_t id, const SkipParams& sp, uint64_t j0, uint64_t cmax,
+                       const double* __restrict__ tab, uint64_t (&step)[V], uint32_t* endm, uint32_t* exhm) {
+    uint32_t em = 0, xm = 0;
+#pragma unroll
+    for (int h = 0; h < V / 2; ++h) {
+        const uint64_t blk = (j0 >> 1) + h;
+        bool s0 = true, s1 = true;
+        step[2 * h] = 0;
+        step[2 * h + 1] = 0;
+        if (blk < c_caps.stream_blocks) {
+            const uint4 w = philox_block((uint32_t)blk, tag, id, key);
+            step[2 * h] = draw_step(((uint64_t)w.y << 32) | w.x, sp, cmax, &s0, tab);
+            step[2 * h + 1] = draw_step(((uint64_t)w.w << 32) | w.z, sp, cmax, &s1, tab);
+        } else {
+            xm |= 3u << (2 * h);
+        }
+        em |= (s0 ? 1u : 0u) << (2 * h);
+        em |= (s1 ? 1u : 0u) << (2 * h + 1);
+    }
+    *endm = em;
+    *exhm = xm;
+}
+
 // One warp walks the positions [start, end) with stream (tag, id): for each
 // chosen position (0-based) emit(k, pos) is called, k its index in the
 // range.  Returns the number of positions; *err is set if the stream ran out.
+// Draw k of a round (lane k / V) lands on base - 1 plus the saturating sum of
+// the round's steps up to k; the first draw that ends the range, lies past
+// the stream or lands at or past `end` ends the walk.
 template <typename Emit>
-RS_DEV uint64_t warp_walk(Key2 key, uint32_t tag, uint64_t id, double R, uint64_t start, uint64_t end,
+RS_DEV uint64_t warp_walk(Key2 key, uint32_t tag, uint64_t id, const SkipParams& sp, uint64_t start, uint64_t end,
                           const double* __restrict__ tab, bool* err, Emit&& emit) {
+    constexpr int V = kWalkV;
     const int lane = threadIdx.x & 31;
     const uint64_t cmax = end - start + 2;
     uint64_t base = start;   // a step of 1 lands on `base`
     uint64_t count = 0;
     *err = false;
-    for (uint64_t j = 0;; j += 32) {
-        const uint64_t jl = j + lane;
-        const bool exhausted = jl >= 2 * c_caps.stream_blocks;
-        bool stop = true;
-        uint64_t step = 0;
-        if (!exhausted) step = step_of(skip_quotient(stream_value(key, tag, id, jl), R, tab), cmax, &stop);
-        const uint64_t incl = warp_inclusive_sat(step);
-        const bool ok = !stop && incl <= end - base;   // position base - 1 + incl < end
-        const uint32_t bad = __ballot_sync(0xFFFFFFFFu, !ok);
-        const int first_bad = bad ? __ffs(bad) - 1 : 32;
-        if (lane < first_bad) emit(count + lane, base - 1 + incl);
-        count += first_bad;
-        if (first_bad < 32) {
-            *err = __shfl_sync(0xFFFFFFFFu, exhausted, first_bad);
-            return count;
+    for (uint64_t j = 0;; j += 32 * V) {
+        uint64_t step[V];
+        uint32_t endm, exhm;
+        draw_steps<V>(key, tag, id, sp, j + (uint64_t)V * lane, cmax, tab, step, &endm, &exhm);
+        uint64_t loc[V];   // the lane's own running sums
+        loc[0] = step[0];
+#pragma unroll
+        for (int q = 1; q < V; ++q) loc[q] = sat_add(loc[q - 1], step[q]);
+        const uint64_t lincl = warp_inclusive_sat(loc[V - 1]);
+        uint64_t excl = __shfl_up_sync(0xFFFFFFFFu, lincl, 1);
+        if (lane == 0) excl = 0;
+        const uint64_t room = end - base;   // a draw fits while its sum is at most this
+        uint32_t badm = endm;
+#pragma unroll
+        for (int q = 0; q < V; ++q)
+            if (sat_add(excl, loc[q]) > room) badm |= 1u << q;
+        const uint32_t lanes_bad = __ballot_sync(0xFFFFFFFFu, badm != 0);
+        int first_bad = 32 * V;
+        if (lanes_bad) {
+            const int fl = __ffs(lanes_bad) - 1;
+            const int qb = __ffs(__shfl_sync(0xFFFFFFFFu, badm, fl)) - 1;
+            first_bad = fl * V + qb;
+            *err = (__shfl_sync(0xFFFFFFFFu, exhm, fl) >> qb) & 1u;
         }
-        base = base + __shfl_sync(0xFFFFFFFFu, incl, 31);
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            const int k = lane * V + q;
+            if (k < first_bad) emit(count + k, base - 1 + sat_add(excl, loc[q]));
+        }
+        count += first_bad;
+        if (first_bad < 32 * V) return count;
+        base = base + __shfl_sync(0xFFFFFFFFu, lincl, 31);
     }
 }
 
@@ -95,17 +218,18 @@ struct BernArgs {
     uint64_t cap;
     int* status;
     const double* tab;
+    bool guard;   // skip_fast may decide
 };
 
 __global__ void bern_count_kernel(BernArgs A) {
-    const double R = 1.0 / dlog1p(-A.p, A.tab);
+    const SkipParams sp = skip_params(1.0 / dlog1p(-A.p, A.tab), A.guard);
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
     for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < A.nchunks; w += warps) {
         const uint64_t i = A.first + w;
         const uint64_t start = i << A.chunk_log2;
         const uint64_t end = min(start + A.C, A.N);
         bool err;
-        const uint64_t c = warp_walk(A.key, TAG_BERN, i, R, start, end, A.tab, &err, [](uint64_t, uint64_t) {});
+        const uint64_t c = warp_walk(A.key, TAG_BERN, i, sp, start, end, A.tab, &err, [](uint64_t, uint64_t) {});
         if ((threadIdx.x & 31) == 0) {
             A.counts[w] = c;
             if (err) set_status(A.status, RS_EITER);
@@ -114,7 +238,7 @@ __global__ void bern_count_kernel(BernArgs A) {
 }
 
 __global__ void bern_write_kernel(BernArgs A) {
-    const double R = 1.0 / dlog1p(-A.p, A.tab);
+    const SkipParams sp = skip_params(1.0 / dlog1p(-A.p, A.tab), A.guard);
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
     for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < A.nchunks; w += warps) {
         const uint64_t i = A.first + w;
@@ -125,7 +249,7 @@ __global__ void bern_write_kernel(BernArgs A) {
         uint64_t* out = A.out;
         const uint64_t cap = A.cap;
         bool err;
-        warp_walk(A.key, TAG_BERN, i, R, start, end, A.tab, &err, [=](uint64_t k, uint64_t pos) {
+        warp_walk(A.key, TAG_BERN, i, sp, start, end, A.tab, &err, [=](uint64_t k, uint64_t pos) {
             if (off + k < cap) out[off + k] = pos + 1;
         });
     }
@@ -134,7 +258,7 @@ __global__ void bern_write_kernel(BernArgs A) {
 // One walk per chunk: positions to the chunk's staging slots (the first
 // stage_per of them), the count to counts[w].
 __global__ void bern_stage_kernel(BernArgs A) {
-    const double R = 1.0 / dlog1p(-A.p, A.tab);
+    const SkipParams sp = skip_params(1.0 / dlog1p(-A.p, A.tab), A.guard);
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
     for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < A.nchunks; w += warps) {
         const uint64_t i = A.first + w;
@@ -143,7 +267,7 @@ __global__ void bern_stage_kernel(BernArgs A) {
         uint64_t* slot = A.stage + w * A.stage_per;
         const uint64_t per = A.stage_per;
         bool err;
-        const uint64_t c = warp_walk(A.key, TAG_BERN, i, R, start, end, A.tab, &err, [=](uint64_t k, uint64_t pos) {
+        const uint64_t c = warp_walk(A.key, TAG_BERN, i, sp, start, end, A.tab, &err, [=](uint64_t k, uint64_t pos) {
             if (k < per) slot[k] = pos + 1;
         });
         if ((threadIdx.x & 31) == 0) {
@@ -167,14 +291,14 @@ __global__ void bern_copy_kernel(BernArgs A) {
         return;
     }
     if (threadIdx.x >= 32) return;
-    const double R = 1.0 / dlog1p(-A.p, A.tab);
+    const SkipParams sp = skip_params(1.0 / dlog1p(-A.p, A.tab), A.guard);
     const uint64_t i = A.first + w;
     const uint64_t start = i << A.chunk_log2;
     const uint64_t end = min(start + A.C, A.N);
     uint64_t* out = A.out;
     const uint64_t cap = A.cap;
     bool err;
-    warp_walk(A.key, TAG_BERN, i, R, start, end, A.tab, &err, [=](uint64_t k, uint64_t pos) {
+    warp_walk(A.key, TAG_BERN, i, sp, start, end, A.tab, &err, [=](uint64_t k, uint64_t pos) {
         if (off + k < cap) out[off + k] = pos + 1;
     });
 }
@@ -318,6 +442,7 @@ cudaError_t launch_bernoulli(const BernLaunch& L, cudaStream_t st) {
     A.tab = L.tab;
     A.stage = L.stage;
     A.stage_per = L.stage_per;
+    A.guard = L.guard;
     const int threads = 256;
     const unsigned blocks = (unsigned)std::min<uint64_t>((L.nchunks * 32 + threads - 1) / threads,
                                                          (uint64_t)L.sms * 16);
@@ -373,50 +498,59 @@ struct LeafBShared {
     int err;
 };
 
-// Block-wide inclusive saturating scan of one value per thread.
-template <int NT, typename Sm>
-RS_DEV uint64_t block_inclusive_sat(uint64_t x, Sm& sm) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int NW = NT / 32;
-    uint64_t incl = warp_inclusive_sat(x);
-    if (lane == 31) sm.warp_tot[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        const uint64_t w = lane < NW ? sm.warp_tot[lane] : 0;
-        const uint64_t wi = warp_inclusive_sat(w);
-        if (lane < NW) sm.warp_tot[lane] = wi;   // inclusive prefix of warp totals
-    }
-    __syncthreads();
-    const uint64_t before = warp == 0 ? 0 : sm.warp_tot[warp - 1];
-    return sat_add(before, incl);
-}
-
-// Geometric-skip walk of [0, s) by the whole block; positions go to sm.pos
-// (up to the capacity).  Returns the count; sets sm.err on a run-out stream.
+// Geometric-skip walk of [0, s) by the whole block, V draws per thread per
+// round as in warp_walk; positions go to sm.pos (up to the capacity).
+// Returns the count; sets sm.err on a run-out stream.
 template <int NT, typename PosT>
-RS_DEV uint64_t block_walk(Key2 key, uint32_t tag, uint64_t id, double R, uint64_t s, LeafBShared<PosT>& sm,
+RS_DEV uint64_t block_walk(Key2 key, uint32_t tag, uint64_t id, const SkipParams& sp, uint64_t s, LeafBShared<PosT>& sm,
                            const double* __restrict__ tab) {
+    constexpr int V = kWalkV;
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t cmax = s + 2;
     uint64_t base = 0, count = 0;
-    for (uint64_t j = 0;; j += NT) {
-        const uint64_t jt = j + threadIdx.x;
-        const bool exhausted = jt >= 2 * c_caps.stream_blocks;
-        bool stop = true;
-        uint64_t step = 0;
-        if (!exhausted) step = step_of(skip_quotient(stream_value(key, tag, id, jt), R, tab), cmax, &stop);
-        if (threadIdx.x == 0) sm.first_bad = NT;
-        const uint64_t incl = block_inclusive_sat<NT>(step, sm);
-        const bool ok = !stop && incl <= s - base;
-        if (!ok) atomicMin(&sm.first_bad, (int)threadIdx.x);
-        if (threadIdx.x == NT - 1) sm.last_incl = incl;
+    for (uint64_t j = 0;; j += (uint64_t)NT * V) {
+        uint64_t step[V];
+        uint32_t endm, exhm;
+        draw_steps<V>(key, tag, id, sp, j + (uint64_t)V * threadIdx.x, cmax, tab, step, &endm, &exhm);
+        uint64_t loc[V];
+        loc[0] = step[0];
+#pragma unroll
+        for (int q = 1; q < V; ++q) loc[q] = sat_add(loc[q - 1], step[q]);
+        if (threadIdx.x == 0) sm.first_bad = NT * V;   // its last reads came before the last barrier
+        // exclusive saturating sum of the threads' totals before this one
+        const uint64_t wincl = warp_inclusive_sat(loc[V - 1]);
+        uint64_t wexcl = __shfl_up_sync(0xFFFFFFFFu, wincl, 1);
+        if (lane == 0) wexcl = 0;
+        if (lane == 31) sm.warp_tot[warp] = wincl;
+        __syncthreads();
+        if (warp == 0) {
+            const uint64_t w = lane < NW ? sm.warp_tot[lane] : 0;
+            const uint64_t wi = warp_inclusive_sat(w);
+            if (lane < NW) sm.warp_tot[lane] = wi;   // inclusive prefix of warp totals
+        }
+        __syncthreads();
+        const uint64_t excl = sat_add(warp == 0 ? 0 : sm.warp_tot[warp - 1], wexcl);
+        const uint64_t room = s - base;
+        uint32_t badm = endm;
+#pragma unroll
+        for (int q = 0; q < V; ++q)
+            if (sat_add(excl, loc[q]) > room) badm |= 1u << q;
+        const int qb = __ffs(badm) - 1;
+        if (badm) atomicMin(&sm.first_bad, (int)threadIdx.x * V + qb);
+        if (threadIdx.x == NT - 1) sm.last_incl = sat_add(excl, loc[V - 1]);
         __syncthreads();
         const int fb = sm.first_bad;
-        if ((int)threadIdx.x < fb && count + threadIdx.x < kLeafBCap) sm.pos[count + threadIdx.x] = (PosT)(base - 1 + incl);
-        if ((int)threadIdx.x == fb && exhausted) sm.err = 1;
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            const int k = (int)threadIdx.x * V + q;
+            if (k < fb && count + k < kLeafBCap) sm.pos[count + k] = (PosT)(base - 1 + sat_add(excl, loc[q]));
+        }
+        if (badm && (int)threadIdx.x * V + qb == fb && ((exhm >> qb) & 1u)) sm.err = 1;
         count += fb;
         const uint64_t last = sm.last_incl;
         __syncthreads();
-        if (fb < NT) return count;
+        if (fb < NT * V) return count;
         base += last;
     }
 }
@@ -428,6 +562,7 @@ struct LeafBArgs {
     uint64_t* out;
     int* status;
     const double* tab;
+    bool guard;
 };
 
 // One leaf of Algorithm B, by the whole block: the walk (retried while
@@ -437,7 +572,7 @@ struct LeafBArgs {
 // the number of kept indices below it).
 template <int NT, typename PosT>
 RS_DEV void leaf_b_one(LeafBShared<PosT>& sm, const NodeRec& r, uint64_t id, Key2 key, uint64_t* __restrict__ out,
-                       int* status, const double* __restrict__ tab) {
+                       int* status, const double* __restrict__ tab, bool guard) {
     constexpr int NW = NT / 32;
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (r.c == 0) return;
@@ -455,9 +590,9 @@ RS_DEV void leaf_b_one(LeafBShared<PosT>& sm, const NodeRec& r, uint64_t id, Key
         for (uint64_t i = tid; i < fill; i += NT) sm.pos[i] = (PosT)i;
         __syncthreads();
     } else {
-        const double R = 1.0 / dlog1p(-rho, tab);
+        const SkipParams sp = skip_params(1.0 / dlog1p(-rho, tab), guard);
         for (attempt = 0; (uint64_t)attempt < c_caps.b_attempts; ++attempt) {
-            c = block_walk<NT>(key, TAG_LEAF_B + 256u * (uint32_t)attempt, id, R, r.S, sm, tab);
+            c = block_walk<NT>(key, TAG_LEAF_B + 256u * (uint32_t)attempt, id, sp, r.S, sm, tab);
             if (sm.err) break;
             if (c >= r.c) break;
         }
@@ -519,7 +654,7 @@ __global__ void __launch_bounds__(kLeafBThreads) leaf_b_kernel(LeafBArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto& sm = *reinterpret_cast<LeafBShared<PosT>*>(smem_raw);
     for (uint64_t leaf = blockIdx.x; leaf < A.nleaves; leaf += gridDim.x)
-        leaf_b_one<kLeafBThreads>(sm, A.leaves[leaf], A.first_id + leaf, A.key, A.out, A.status, A.tab);
+        leaf_b_one<kLeafBThreads>(sm, A.leaves[leaf], A.first_id + leaf, A.key, A.out, A.status, A.tab, A.guard);
 }
 
 // Algorithm B leaves of a batch group or of range queries (leaf sizes not
@@ -530,7 +665,7 @@ __global__ void __launch_bounds__(kLeafBThreads) group_leaf_b_kernel(View G, con
     auto& sm = *reinterpret_cast<LeafBShared<uint64_t>*>(smem_raw);
     for (uint64_t g = blockIdx.x; g < G.nleaves; g += gridDim.x) {
         const ResolvedLeaf L = resolve_leaf(G, g);
-        leaf_b_one<kLeafBThreads>(sm, L.rec, L.id, make_key(L.seed), L.out, L.status, tab);
+        leaf_b_one<kLeafBThreads>(sm, L.rec, L.id, make_key(L.seed), L.out, L.status, tab, true);
     }
 }
 
@@ -569,7 +704,7 @@ static cudaError_t launch_leaves_b_t(const LeafBLaunch& L, cudaStream_t st) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLeafBThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    LeafBArgs A{L.leaves, L.nleaves, L.first_id, make_key(L.seed), L.out, L.status, L.tab};
+    LeafBArgs A{L.leaves, L.nleaves, L.first_id, make_key(L.seed), L.out, L.status, L.tab, L.guard};
     const uint64_t grid = std::min<uint64_t>(L.nleaves, (uint64_t)L.sms * per_sm);
     kern<<<(unsigned)grid, kLeafBThreads, smem, st>>>(A);
     return cudaGetLastError();

@@ -33,7 +33,7 @@ struct rs_ctx {
     uint64_t stage_max_words = 1ull << 31;   // rs_set_bernoulli_staging
     uint64_t stage_slots = 0;
     uint32_t leaf_cap = 0;          // testing knob, 0 = default
-    bool guard = true;              // single-precision guard of the split tree's tests (rs_set_exact_deviates)
+    bool guard = true;              // guarded fast paths of the deviates and skips (rs_set_exact_deviates)
     // pipelining of deep trees: 2^pipe_log2 subtrees, each built on the tree
     // stream while the caller's stream runs the leaves of the ones before
     int pipe_log2 = 0;
@@ -289,7 +289,7 @@ int sample_impl(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0,
         const uint64_t first = j * per_part;
         if (kind == RS_KIND_B) {
             rs::LeafBLaunch LB{ctx->nodes + nleaves + first, per_part, nleaves + first, seed, out, ctx->status,
-                               ctx->sms, ctx->tab, smax};
+                               ctx->sms, ctx->tab, smax, ctx->guard};
             ctx->launches += 1;
             rc = cuda_rc(rs::launch_leaves_b(LB, st));
         } else {
@@ -476,7 +476,7 @@ int rs_bernoulli(rs_ctx* ctx, double p, uint64_t N, uint64_t seed, uint32_t n0, 
         else (void)cudaGetLastError();
     }
     rs::BernLaunch L{p, N, seed, c, first, nchunks, a, b, out_dev, cap, ctx->words, ctx->words + nchunks + 1,
-                     ctx->words + nchunks + 2, ctx->status, ctx->sms, ctx->tab, stage, per};
+                     ctx->words + nchunks + 2, ctx->status, ctx->sms, ctx->tab, stage, per, ctx->guard};
     rc = cuda_rc(rs::launch_bernoulli(L, st));
     if (rc) return rc;
     uint64_t total = 0;

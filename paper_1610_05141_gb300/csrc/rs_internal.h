@@ -74,6 +74,7 @@ struct LeafBLaunch {
     int sms;
     const double* tab;       // the context's table (its logarithm)
     uint64_t smax;           // largest leaf size (32-bit positions up to 2^32)
+    bool guard = true;       // skips decided in fixed and single precision where safe
 };
 // Algorithm B leaves (positions of one attempt live in shared memory).
 cudaError_t launch_leaves_b(const LeafBLaunch& L, cudaStream_t st);
@@ -96,6 +97,7 @@ struct BernLaunch {
     const double* tab;       // the context's table (its logarithm)
     uint64_t* stage;         // nchunks * stage_per words, or null
     uint64_t stage_per;      // staged positions per chunk
+    bool guard = true;       // skips decided in fixed and single precision where safe
 };
 // With staging: one walk per chunk (positions staged, counted), exclusive
 // scan of the counts, copy to the output (a chunk above stage_per positions

@@ -103,6 +103,55 @@ def test_full_size_bernoulli(rs, ctx, oracle):
     torch.cuda.empty_cache()
 
 
+def _with_exact(rs, exact, fn):
+    c = rs.rs_create(0)
+    try:
+        rs.rs_set_exact_deviates(c, exact)
+        return fn(c)
+    finally:
+        c.close()
+
+
+@pytest.mark.parametrize("p", [1e-2, 1e-4])
+def test_full_size_bernoulli_guard_equals_fp64(rs, p):
+    """Bernoulli over 2^36 positions (6.9e8 skips at p = 1e-2): the guarded
+    skips and the FP64 definition give the same positions, compared on the
+    device."""
+    N, seed, n0 = 2**36, 7, 4096
+    cap = int(N * p + 10 * np.sqrt(N * p)) + 1024
+    outs = []
+    for exact in (False, True):
+        out = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
+
+        def call(c):
+            rc, cnt = rs.rs_bernoulli(c, p, N, seed, n0, 0, N, out, cap)
+            assert rs.rs_sync(c) == rs.RS_OK
+            return cnt
+        outs.append((_with_exact(rs, exact, call), out))
+    assert outs[0][0] == outs[1][0]
+    assert torch.equal(outs[0][1], outs[1][1])
+    del outs
+    torch.cuda.empty_cache()
+
+
+def test_full_size_leaf_b_guard_equals_fp64(rs):
+    """Algorithm B leaves at n = 1e9 from 2^50 (skips of mean 1.1e6 for
+    leaves of 2^32 positions): guarded and FP64 skips give the same sample."""
+    n, N, seed, n0 = 10**9, 2**50, 1, 4096
+    outs = []
+    for exact in (False, True):
+        out = torch.full((n,), -1, dtype=torch.int64, device="cuda")
+
+        def call(c):
+            rs.rs_sample_b(c, n, N, seed, n0, out)
+            assert rs.rs_sync(c) == rs.RS_OK
+        _with_exact(rs, exact, call)
+        outs.append(out)
+    assert torch.equal(outs[0], outs[1])
+    del outs
+    torch.cuda.empty_cache()
+
+
 def test_full_size_batch(rs, ctx, oracle):
     """The 100,000-request batch the benchmark times (7.19e9 values), as a
     graph-replayed run after the eager one and a tuning pass: every request

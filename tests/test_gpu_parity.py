@@ -112,6 +112,19 @@ def test_leaf_b_matches_oracle(rs, ctx, oracle, n, N, seed, n0):
     assert_same(got, oracle.sample(n, N, seed, n0, oracle.KIND_B), (n, N, seed, n0))
 
 
+@pytest.mark.parametrize("n,N,seed,n0", B_CASES)
+def test_leaf_b_exact_skips_match_oracle(rs, oracle, n, N, seed, n0):
+    """With every geometric skip evaluated in FP64 (rs_set_exact_deviates),
+    leaf B gives the oracle's sample too, so both settings give it."""
+    c = rs.rs_create(0)
+    try:
+        rs.rs_set_exact_deviates(c, True)
+        got = run(rs, c, rs.rs_sample_b, n, N, seed, n0)
+    finally:
+        c.close()
+    assert_same(got, oracle.sample(n, N, seed, n0, oracle.KIND_B), (n, N, seed, n0))
+
+
 @pytest.mark.parametrize("cap", [64, 1000])
 def test_general_leaf_path_matches_oracle(rs, oracle, cap):
     """Leaves whose selection exceeds the capacity take the global-memory
@@ -193,6 +206,24 @@ def test_bernoulli_matches_oracle(rs, ctx, oracle, p, N, seed, n0):
     out = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
     rc, cnt = rs.rs_bernoulli(ctx, p, N, seed, n0, 0, N, out, cap)
     assert rs.rs_sync(ctx) == rs.RS_OK
+    assert cnt == len(want)
+    assert_same(out[:cnt].cpu().numpy().view(np.uint64), want, (p, N))
+
+
+@pytest.mark.parametrize("p,N,seed,n0", BERN_CASES)
+def test_bernoulli_exact_skips_match_oracle(rs, oracle, p, N, seed, n0):
+    """Every skip in FP64 (rs_set_exact_deviates): the oracle's positions,
+    as with the guarded skips above."""
+    want = oracle.bernoulli(p, N, seed, n0)
+    cap = len(want) + 16
+    out = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
+    c = rs.rs_create(0)
+    try:
+        rs.rs_set_exact_deviates(c, True)
+        rc, cnt = rs.rs_bernoulli(c, p, N, seed, n0, 0, N, out, cap)
+        assert rs.rs_sync(c) == rs.RS_OK
+    finally:
+        c.close()
     assert cnt == len(want)
     assert_same(out[:cnt].cpu().numpy().view(np.uint64), want, (p, N))
 
