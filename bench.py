@@ -367,37 +367,44 @@ def run_rows(rs, ctx, stream, args):
     def want(name):
         return name in rows
 
-    buf = torch.empty(10**9, dtype=torch.int64, device="cuda")
-    for name, call, N, steps in (("a5_with_replacement", rs.rs_sample_with_replacement, 2**40, args.row_steps),
-                                 ("a7_leaf_b", rs.rs_sample_b, 2**50, max(1, args.row_steps // 3))):
+    K = args.row_scale_log2   # profiling cases only: n and N of a5/a7 and N of a6 divided by 2^K
+    n_rows = 10**9 >> K
+    NB = 2**36 >> K
+    buf = torch.empty(n_rows, dtype=torch.int64, device="cuda")
+    for name, call, N, steps in (("a5_with_replacement", rs.rs_sample_with_replacement, 2**40 >> K, args.row_steps),
+                                 ("a7_leaf_b", rs.rs_sample_b, 2**50 >> K, max(1, args.row_steps // 3))):
         if not want(name.split("_")[0]):
             continue
         rs.rs_set_profiling(ctx, True)
-        ms = timed(lambda: call(ctx, 10**9, N, 3, N0, buf, stream), steps)
+        ms = timed(lambda: call(ctx, n_rows, N, 3, N0, buf, stream), steps)
         tree_ms, leaf_ms, calls = rs.rs_phase_totals(ctx)
         rs.rs_set_profiling(ctx, False)
         if rs.rs_sync(ctx, stream) != rs.RS_OK:
             raise RuntimeError(f"{name} failed")
         leaf = leaf_ms / calls
-        out[name] = {"workload": f"n=1e9 from 1..2^{N.bit_length() - 1}, n0={N0}", "ms_per_step": ms,
-                     "samples_per_s": 1e9 / (ms / 1000), "phases_ms": {"split_tree": tree_ms / calls, "leaves": leaf},
-                     "leaf_write_gbs": 8e9 / (leaf / 1000) / 1e9, "leaf_frac_of_hbm": 8e9 / (leaf / 1000) / 1e9 / peak}
+        out[name] = {"workload": f"n={n_rows:.3g} from 1..2^{N.bit_length() - 1}, n0={N0}", "ms_per_step": ms,
+                     "samples_per_s": n_rows / (ms / 1000),
+                     "phases_ms": {"split_tree": tree_ms / calls, "leaves": leaf},
+                     "leaf_write_gbs": 8 * n_rows / (leaf / 1000) / 1e9,
+                     "leaf_frac_of_hbm": 8 * n_rows / (leaf / 1000) / 1e9 / peak}
     if want("a6"):
         bern = {}
         for p, windows, steps in ((1e-4, 1, args.row_steps), (1e-2, 1, args.row_steps), (0.5, 8, 2)):
+            if windows > 1 and K:   # scaled profiling runs stop before the 34 GB buffer
+                continue
             if windows > 1:   # p = 0.5: a 34 GB buffer reused by every window, and room to stage its positions
                 del buf
                 torch.cuda.empty_cache()
                 buf = torch.empty((1 << 32) + (1 << 20), dtype=torch.int64, device="cuda")
                 rs.rs_set_bernoulli_staging(ctx, 48 << 30)
             cap = buf.numel()
-            width = 2**36 // windows
+            width = NB // windows
             holder = {"rc": rs.RS_OK, "count": 0}
 
             def call_b():
                 total = 0
                 for w in range(windows):
-                    rc, c = rs.rs_bernoulli(ctx, p, 2**36, 5, N0, w * width, (w + 1) * width, buf, cap, stream,
+                    rc, c = rs.rs_bernoulli(ctx, p, NB, 5, N0, w * width, (w + 1) * width, buf, cap, stream,
                                             check=False)
                     if rc != rs.RS_OK:
                         holder["rc"] = rc
@@ -408,13 +415,13 @@ def run_rows(rs, ctx, stream, args):
             if holder["rc"] != rs.RS_OK:
                 raise RuntimeError(f"bernoulli p={p} failed: {holder['rc']}")
             cnt = holder["count"]
-            bern[f"p={p:g}"] = {"positions": 2**36, "windows": windows, "emitted": cnt, "ms_per_call": ms,
-                                "emitted_per_s": cnt / (ms / 1000), "positions_per_s": 2**36 / (ms / 1000),
+            bern[f"p={p:g}"] = {"positions": NB, "windows": windows, "emitted": cnt, "ms_per_call": ms,
+                                "emitted_per_s": cnt / (ms / 1000), "positions_per_s": NB / (ms / 1000),
                                 "write_gbs": 8 * cnt / (ms / 1000) / 1e9,
                                 "note": "whole range: per window one walk with staged positions, the scan of the "
                                         "counts, the copy into place, and the count read back"}
         rs.rs_set_bernoulli_staging(ctx)
-        out["a6_bernoulli"] = {"N": 2**36, "n0": N0, "by_p": bern}
+        out["a6_bernoulli"] = {"N": NB, "n0": N0, "by_p": bern}
     if want("f2"):
         if buf.numel() < (1 << 32):   # p = 0.5: windows of 2^32 expected values
             del buf
@@ -857,6 +864,8 @@ def main():
     ap.add_argument("--rows", default="a5,a7,a6,f2,f3,f1,f4",
                     help="which of the other rows to run (comma-separated: a5,a7,a6,f2,f3,f1,f4)")
     ap.add_argument("--row-steps", type=int, default=6)
+    ap.add_argument("--row-scale-log2", type=int, default=0,
+                    help="divide the a5/a7 sizes and the a6 range by 2^K (profiling cases only)")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="length of each open-loop serving run")
     ap.add_argument("--serve-capacity-jobs", type=int, default=4000)
     ap.add_argument("--serve-unbatched-jobs", type=int, default=1000)

@@ -43,21 +43,24 @@ RS_DEV double skip_quotient(uint64_t x, double R, const double* __restrict__ tab
 
 // The skip of one draw decided without FP64 where that is safe.  The
 // definition floors q64 = RN(dlog(U) R) (skip_quotient); here, with
-// A = -qlog_u57(m) (U = m 2^-53, |A 2^-57 - |ln U|| <= 2^-55):
-// - Lh + Lm = A 2^-57 (1 - tau), 0 <= tau < 2^-47: the top 48 of A's 63
-//   bits as two exact singles;
+// A = qnlog_u57(m) (U = m 2^-53, |A 2^-57 - |ln U|| <= 2^-55):
+// - Lh + Lm = A 2^-57 (1 - tau), 0 <= tau < 2^-46: the top 47 of A's 63
+//   bits as two exact singles, made from their bits;
 // - rh + rl = |R| (1 + rho), |rho| <= 2^-48;
 // - p = RN(Lh rh) and e = fma(Lh, rh, -p) + (Lh rl + Lm rh), whose roundings
 //   stay below 2^-45 p; the dropped Lm rl is below 2^-48 p; so
-//   |p + e - |ln U| |R|| <= |R| 2^-55 + p 2^-44.3;
+//   |p + e - |ln U| |R|| <= |R| 2^-55 + p 2^-44.2;
 // - dlog is within 2 ulp of ln U and the product is rounded once, so
 //   |q64 - |ln U| |R|| <= 2^-50.6 q64;
 // - r = RN((p - floor(p)) + e), p - floor(p) exact, rounds by 2^-24 |r|.
 // Hence |floor(p) + r - q64| <= b / 2 for b = (|r| + 1) 2^-23 + p 2^-43 +
 // |R| 2^-54, and when floor(r - b) = floor(r + b) (rounded outward) that is
-// floor(q64 - floor(p)).  Otherwise, or for p >= 2^61 (where the range's
-// end test of 2^62 could be near), the draw takes the FP64 definition.  The
-// skips, and so the sample, are the definition's in every case.
+// floor(q64 - floor(p)).  Otherwise, or for p >= 2^44 (skips that long
+// need p below about 1e-12), the draw takes the FP64 definition.  The skips,
+// and so the sample, are the definition's in every case.  No conversion
+// instruction is used (they run on the slow FP64 pipe of this GPU): the
+// singles are assembled from bits, and floors of x with |x| < 2^22 are
+// (x + 1.5 2^23) - 1.5 2^23 with the sum rounded down.
 struct SkipParams {
     double R;        // RN(1 / ln(1 - p)), negative
     float rh, rl;    // |R| as an unevaluated sum of two singles
@@ -76,6 +79,16 @@ RS_DEV SkipParams skip_params(double R, bool guard) {
     return s;
 }
 
+// An integer-valued single in [0, 2^63) as a 64-bit integer, from its bits
+// (the 64-bit conversion instructions would run on the FP64 pipe).
+RS_DEV uint64_t f2u64_exact(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const int e = (int)(b >> 23) - 127;
+    if (e < 0) return 0;
+    const uint64_t m = (b & 0x7FFFFFu) | 0x800000u;
+    return e >= 23 ? m << (e - 23) : m >> (23 - e);
+}
+
 // Skip + 1 of the draw with 64-bit value x; false if it must take FP64.
 RS_DEV bool skip_fast(uint64_t x, const SkipParams& sp, const double* __restrict__ tab, uint64_t* step) {
     const uint64_t m = (x >> 11) + 1;
@@ -83,22 +96,36 @@ RS_DEV bool skip_fast(uint64_t x, const SkipParams& sp, const double* __restrict
         *step = 1;
         return true;
     }
-    const int64_t A = -qlog_u57(m, tab);   // below 2^62.2 (|ln U| <= 53 ln 2)
+    const int64_t A = qnlog_u57(m, tab);   // below 2^62.2 (|ln U| <= 53 ln 2)
     if (A <= 0) return false;
     const int lz = __clzll(A);
-    const uint64_t nn = (uint64_t)A << lz;
-    const float Lh = (float)(uint32_t)(nn >> 40) * __int_as_float((110 - lz) << 23);              // * 2^(-17-lz)
-    const float Lm = (float)((uint32_t)(nn >> 16) & 0xFFFFFFu) * __int_as_float((86 - lz) << 23);  // * 2^(-41-lz)
+    const uint64_t nn = (uint64_t)A << lz;   // A 2^lz, top bit set: A 2^-57 = nn 2^(-57-lz)
+    // Lh = bits 40..63 of nn times 2^(-17-lz): exponent field 127 + (6 - lz)
+    const float Lh = __int_as_float(((133 - lz) << 23) | ((uint32_t)(nn >> 40) & 0x7FFFFFu));
+    // Lm = bits 17..39 times 2^(-40-lz): 2^E (1 + f 2^-23) - 2^E, E = -17 - lz
+    const float Lm = __int_as_float(((110 - lz) << 23) | ((uint32_t)(nn >> 17) & 0x7FFFFFu)) -
+                     __int_as_float((110 - lz) << 23);
     const float p = Lh * sp.rh;
     const float e = __fmaf_rn(Lh, sp.rh, -p) + (Lh * sp.rl + Lm * sp.rh);
-    if (!(p < 0x1p61f)) return false;
-    const float fl = floorf(p);
-    const float r = (p - fl) + e;
+    if (!(p < 0x1p44f)) return false;
+    const float fl = p < 0x1p23f ? __fadd_rd(p, 0x1p23f) - 0x1p23f : p;   // floor(p)
+    const float r = (p - fl) + e;   // |r| < 2^21 + 1
     const float b = (fabsf(r) + 1.0f) * 0x1p-23f + p * 0x1p-43f + sp.rb;
-    const float klo = floorf(__fadd_rd(r, -b));
-    if (klo != floorf(__fadd_ru(r, b))) return false;
-    *step = __float2ull_rz(fl) + (uint64_t)__float2ll_rz(klo) + 1;
+    constexpr float kM = 12582912.0f;   // 1.5 2^23
+    const float klo = __fadd_rd(__fadd_rd(r, -b), kM) - kM;   // floor(r - b)
+    if (klo != __fadd_rd(__fadd_ru(r, b), kM) - kM) return false;
+    const uint64_t k = klo < 0.0f ? 0 - f2u64_exact(-klo) : f2u64_exact(klo);   // mod 2^64
+    *step = f2u64_exact(fl) + k + 1;
     return true;
+}
+
+// The FP64 definition of one draw's step, a call of its own so that the
+// compiler cannot evaluate it, predicated off, for every draw: skip + 1
+// clamped to cmax, or ~0 for a draw that ends the range.
+__device__ __noinline__ uint64_t draw_step_fp64(uint64_t x, double R, uint64_t cmax, const double* __restrict__ tab) {
+    bool stop;
+    const uint64_t s = step_of(skip_quotient(x, R, tab), cmax, &stop);
+    return stop ? ~0ull : s;
 }
 
 // Skip + 1 of one draw (or 0 with *stop), by skip_fast where it decides.
@@ -109,7 +136,9 @@ RS_DEV uint64_t draw_step(uint64_t x, const SkipParams& sp, uint64_t cmax, bool*
         *stop = false;
         return s < cmax ? s : cmax;
     }
-    return step_of(skip_quotient(x, sp.R, tab), cmax, stop);
+    s = draw_step_fp64(x, sp.R, cmax, tab);
+    *stop = s == ~0ull;
+    return *stop ? 0 : s;
 }
 
 RS_DEV uint64_t warp_inclusive_sat(uint64_t x) {
@@ -221,8 +250,18 @@ struct BernArgs {
     bool guard;   // skip_fast may decide
 };
 
+// The launch's skip parameters (FP64, the same for every chunk), by one
+// thread per block: the FP64 pipe of this GPU is too slow to let every
+// thread repeat them.  All threads of the block call it.
+RS_DEV SkipParams block_skip_params(const BernArgs& A) {
+    __shared__ SkipParams sh;
+    if (threadIdx.x == 0) sh = skip_params(1.0 / dlog1p(-A.p, A.tab), A.guard);
+    __syncthreads();
+    return sh;
+}
+
 __global__ void bern_count_kernel(BernArgs A) {
-    const SkipParams sp = skip_params(1.0 / dlog1p(-A.p, A.tab), A.guard);
+    const SkipParams sp = block_skip_params(A);
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
     for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < A.nchunks; w += warps) {
         const uint64_t i = A.first + w;
@@ -238,7 +277,7 @@ __global__ void bern_count_kernel(BernArgs A) {
 }
 
 __global__ void bern_write_kernel(BernArgs A) {
-    const SkipParams sp = skip_params(1.0 / dlog1p(-A.p, A.tab), A.guard);
+    const SkipParams sp = block_skip_params(A);
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
     for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < A.nchunks; w += warps) {
         const uint64_t i = A.first + w;
@@ -258,7 +297,7 @@ __global__ void bern_write_kernel(BernArgs A) {
 // One walk per chunk: positions to the chunk's staging slots (the first
 // stage_per of them), the count to counts[w].
 __global__ void bern_stage_kernel(BernArgs A) {
-    const SkipParams sp = skip_params(1.0 / dlog1p(-A.p, A.tab), A.guard);
+    const SkipParams sp = block_skip_params(A);
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
     for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < A.nchunks; w += warps) {
         const uint64_t i = A.first + w;
@@ -291,7 +330,7 @@ __global__ void bern_copy_kernel(BernArgs A) {
         return;
     }
     if (threadIdx.x >= 32) return;
-    const SkipParams sp = skip_params(1.0 / dlog1p(-A.p, A.tab), A.guard);
+    const SkipParams sp = skip_params(1.0 / dlog1p(-A.p, A.tab), A.guard);   // rare: one warp per restaged chunk
     const uint64_t i = A.first + w;
     const uint64_t start = i << A.chunk_log2;
     const uint64_t end = min(start + A.C, A.N);
@@ -496,6 +535,8 @@ struct LeafBShared {
     uint64_t last_incl;
     int first_bad;
     int err;
+    int rho_one;                      // the leaf's rate is 1: every position
+    SkipParams sp;                    // the leaf's skip parameters
 };
 
 // Geometric-skip walk of [0, s) by the whole block, V draws per thread per
@@ -576,21 +617,27 @@ RS_DEV void leaf_b_one(LeafBShared<PosT>& sm, const NodeRec& r, uint64_t id, Key
     constexpr int NW = NT / 32;
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (r.c == 0) return;
-    const double dn = (double)r.c;
-    double rho = (dn + 3.0 * sqrt(dn) + 10.0) / (double)r.S;
-    if (rho > 1.0) rho = 1.0;
+    // the leaf's rate and skip parameters in FP64, once, by thread 0 (the
+    // FP64 pipe of this GPU is too slow to let every thread repeat them);
+    // the last reads of these fields came before the last leaf's final barrier
+    if (tid == 0) {
+        const double dn = (double)r.c;
+        const double rho = (dn + 3.0 * sqrt(dn) + 10.0) / (double)r.S;
+        sm.rho_one = rho >= 1.0;
+        if (rho < 1.0) sm.sp = skip_params(1.0 / dlog1p(-rho, tab), guard);
+        sm.err = 0;
+    }
     uint64_t c = 0;
     int attempt = 0;
     bool fail = false;
-    if (tid == 0) sm.err = 0;
     __syncthreads();
-    if (rho == 1.0) {
+    if (sm.rho_one) {
         c = r.S;
         const uint64_t fill = c < kLeafBCap ? c : kLeafBCap;
         for (uint64_t i = tid; i < fill; i += NT) sm.pos[i] = (PosT)i;
         __syncthreads();
     } else {
-        const SkipParams sp = skip_params(1.0 / dlog1p(-rho, tab), guard);
+        const SkipParams sp = sm.sp;
         for (attempt = 0; (uint64_t)attempt < c_caps.b_attempts; ++attempt) {
             c = block_walk<NT>(key, TAG_LEAF_B + 256u * (uint32_t)attempt, id, sp, r.S, sm, tab);
             if (sm.err) break;

@@ -25,17 +25,20 @@ struct __align__(16) NodeRec {
 // the reciprocal of the interval's centre and minus its logarithm as a
 // double-double (kTabInv, kTabHi, kTabLo); see rs_math.cuh.  Then, from
 // double slot kTabF on, ln i! (i < 256) rounded to single precision, for
-// the single-precision guard of the ratio-of-uniforms test.  Then the same
-// 128 intervals in fixed point for the guarded geometric skips: -ln(inv) in
-// Q62 (kTabQLn, a signed 64-bit word per slot) and inv in Q64 (kTabQInv).
+// the single-precision guard of the ratio-of-uniforms test.  Then, for the
+// fixed-point logarithm of the guarded geometric skips (rs_math.cuh
+// qnlog_u57), 512 intervals of [1, 2) with left ends c = 1 + i/512: inv =
+// ceil(2^64 / c) (kTabQInv, an unsigned 64-bit word per slot) and -ln(inv
+// 2^-64) in Q63 (kTabQLn).
 constexpr int kTabLf = 0;
 constexpr int kTabInv = 256;
 constexpr int kTabHi = 384;
 constexpr int kTabLo = 512;
 constexpr int kTabF = 640;
-constexpr int kTabQLn = 768;
-constexpr int kTabQInv = 896;
-constexpr int kTabWords = 1024;
+constexpr int kQLogIntervals = 512;
+constexpr int kTabQInv = 768;
+constexpr int kTabQLn = kTabQInv + kQLogIntervals;
+constexpr int kTabWords = kTabQLn + kQLogIntervals;
 
 // First error wins; later errors are dropped until the host clears the word.
 RS_DEV void set_status(int* status, int code) {

@@ -64,18 +64,46 @@ RS_DEV DD dd_div(DD a, DD b) {
 // centre c = 1 + (2i+1)/256 and inv = RN(1/c); -ln(inv) = -2 atanh(s),
 // s = (inv-1)/(inv+1), summed in double-double to s^71/71 (|s| <= 1/3).
 // Intervals 0 and 127 use c = 1 (see dlog).
-// The fixed-point copy of the entry (used by qlog_u57): -ln(inv) = hi + lo
-// rounded to Q62 (hi * 2^62 is an integer, as |hi| >= 2^-7; lo * 2^62 is
-// rounded to the nearest integer: error at most half a unit), and inv in
-// Q64, exact (inv in (1/2, 1) has 53 significant bits).
-RS_DEV void build_log_entry(int i, double* tab) {
+// -ln(x) for x = hi + lo in (1/2, 1] in double-double: -2 atanh(s),
+// s = (x - 1)/(x + 1) (|s| < 1/3), summed to s^71/71.
+RS_DEV DD dd_neg_log(DD x) {
+    const DD s = dd_div(dd_add(x, DD{-1.0, 0.0}), dd_add(x, DD{1.0, 0.0}));
+    const DD s2 = dd_mul(s, s);
+    DD term = s, sum = s;
+    for (int k = 1; k < 36; ++k) {
+        term = dd_mul(term, s2);
+        sum = dd_add(sum, dd_div(term, DD{(double)(2 * k + 1), 0.0}));
+    }
+    return DD{-2.0 * sum.hi, -2.0 * sum.lo};
+}
+
+// Entry i of the fixed-point table (i = 1 .. 511; entry 0 is unused):
+// inv = ceil(2^64 / c) = ceil(2^73 / (512 + i)) exactly, and -ln(inv 2^-64)
+// in Q63 from its double-double value (the high part times 2^63 is an
+// integer, as the value exceeds 2^-10; the low part is rounded: error at
+// most half a unit).
+RS_DEV void build_qlog_entry(int i, double* tab) {
     uint64_t* q = reinterpret_cast<uint64_t*>(tab);
+    if (i == 0) {
+        q[kTabQInv] = 0;
+        q[kTabQLn] = 0;
+        return;
+    }
+    const unsigned __int128 num = (unsigned __int128)1 << 73;
+    const uint64_t d = 512 + (uint64_t)i;
+    const uint64_t inv = (uint64_t)((num + d - 1) / d);
+    const double hi = __ull2double_rn(inv) * 0x1p-64;   // inv 2^-64 = hi + lo exactly
+    const double lo = (double)(int64_t)(inv - __double2ull_rn(hi * 0x1p64)) * 0x1p-64;
+    const DD v = dd_neg_log(DD{hi, lo});
+    q[kTabQInv + i] = inv;
+    q[kTabQLn + i] = (uint64_t)(__double2ll_rn(v.hi * 0x1p63) + __double2ll_rn(v.lo * 0x1p63));
+}
+
+RS_DEV void build_log_entry(int i, double* tab) {
     if (i == 0 || i == 127) {
         tab[kTabInv + i] = 1.0;
         tab[kTabHi + i] = 0.0;
         tab[kTabLo + i] = 0.0;
-        q[kTabQLn + i] = 0;
-        q[kTabQInv + i] = 0;
         return;
     }
     const double c = 1.0 + (double)(2 * i + 1) / 256.0;
@@ -90,11 +118,6 @@ RS_DEV void build_log_entry(int i, double* tab) {
     tab[kTabInv + i] = inv;
     tab[kTabHi + i] = -(2.0 * sum.hi);
     tab[kTabLo + i] = -(2.0 * sum.lo);
-    const double two62 = 4611686018427387904.0;
-    q[kTabQLn + i] = (uint64_t)(__double2ll_rn(-(2.0 * sum.hi) * two62) + __double2ll_rn(-(2.0 * sum.lo) * two62));
-    const uint64_t ib = double_to_bits(inv);
-    const int ie = (int)((ib >> 52) & 0x7FF) - 1023;   // -1
-    q[kTabQInv + i] = ((ib & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull) << (ie + 12);
 }
 
 // ln x for a normal x > 0: x = 2^e m, m in [1, 2); the top 7 bits of m pick
@@ -130,59 +153,49 @@ RS_DEV double dlog(double x, const double* __restrict__ tab) {
     return (de * RS_LN2_HI + __ldg(tab + kTabHi + i)) + ((de * RS_LN2_LO + __ldg(tab + kTabLo + i)) + p);
 }
 
-// ln U in fixed point for U = m 2^-53, 1 <= m < 2^53 (the uniforms of the
-// geometric skips): the result times 2^-57 is within 2^-55 of ln U.  Only
-// integer operations: m = 2^t f with f in [1, 2) as a Q63 integer F; the
-// top 7 bits of f pick the interval of dlog, r = f inv - 1 by one high
-// product (|r| < 2^-7; the intervals next to 1 use r = f - 1 and r = f/2 - 1,
-// exact), ln(1 + r) = r + r^2 g with g = sum_{k=2..9} (-1)^(k+1) r^(k-2)/k by
-// Horner's rule on signed high products (Q64 times Q63 gives Q63), and
-// ln U = (t - 53) ln 2 - ln(inv) + ln(1 + r).  Errors, in units of 2^-57:
-// the high products truncate by at most 2^-6 each and shrink by |r| as they
-// propagate (about 0.07 in all with the table's half unit of 2^-62 and the
-// truncation r^10/10 of the series); the shift from Q62 to Q57 truncates by
-// less than 1; (t - 53) ln 2 takes ln 2 as A + phi, A the integer part of
-// ln 2 * 2^57 (times t - 53 exactly) and phi in Q32 (times t - 53, then
-// truncated: less than 1 + 53 * 2^-33).  In all below 2.1 units, 2^-55.9.
-// (-1)^(k+1) / k in Q63, rounded, k = 2 .. 9
-constexpr int64_t kQlnC2 = -4611686018427387904ll;
-constexpr int64_t kQlnC3 = 3074457345618258603ll;
-constexpr int64_t kQlnC4 = -2305843009213693952ll;
-constexpr int64_t kQlnC5 = 1844674407370955162ll;
-constexpr int64_t kQlnC6 = -1537228672809129301ll;
-constexpr int64_t kQlnC7 = 1317624576693539401ll;
-constexpr int64_t kQlnC8 = -1152921504606846976ll;
-constexpr int64_t kQlnC9 = 1024819115206086201ll;
+// -ln U in fixed point for U = m 2^-53, 1 <= m < 2^53 (the uniforms of the
+// geometric skips): the result times 2^-57 is within 2^-55 of -ln U.  Only
+// integer operations, all unsigned: m = 2^t f with f in [1, 2) as a Q63
+// integer F; the top 9 bits of f pick an interval with left end c and
+// inv = ceil(2^64/c) >= 1/c, so that r = f inv - 1 is in [0, 2^-9) (one high
+// product, truncated by less than 2^-63; interval 0 takes r = f - 1 exactly);
+// ln(1 + r) = r - r^2/2 + r^3 h with h = 1/3 - r/4 + r^2/5 - r^3/6, r^2 and
+// r^3 by 64-bit high products (Q64) and h by 32-bit ones (Q32, error below
+// 1.5 2^-32, times r^3 < 2^-27); the series stops before r^7/7 < 2^-65.
+// Then -ln U = (53 - t) ln 2 - ln(inv) - ln(1 + r).  In units of 2^-57:
+// ln(1 + r) within 2^-1.2, the table's half unit of 2^-63 and the shift from
+// Q63 to Q57 below 1, and (53 - t) ln 2 with ln 2 = (A + phi) 2^-57, A an
+// integer taken exactly and phi in Q32 truncated after the product (below
+// 1 + 53 2^-33): in all below 2.1 units, 2^-55.9.
+constexpr uint32_t kQh3 = 1431655765u;   // round(2^32 / 3)
+constexpr uint32_t kQh4 = 1073741824u;   // 2^32 / 4
+constexpr uint32_t kQh5 = 858993459u;    // round(2^32 / 5)
+constexpr uint32_t kQh6 = 715827883u;    // round(2^32 / 6)
 constexpr int64_t kLn2Q57 = 99893036290645747ll;   // floor(ln 2 * 2^57)
 constexpr int64_t kLn2Q57Frac32 = 1469302631ll;    // the rest of ln 2 * 2^57, times 2^32, rounded
-RS_DEV int64_t qlog_u57(uint64_t m, const double* __restrict__ tab) {
+RS_DEV int64_t qnlog_u57(uint64_t m, const double* __restrict__ tab) {
     const int t = 63 - __clzll((long long)m);
     const uint64_t F = m << (63 - t);
-    const int i = (int)((F >> 56) & 0x7F);
-    int e = t - 53;
-    int64_t r64;   // r in Q64
-    int64_t lninv = 0;
-    if (i == 127) {
-        r64 = (int64_t)F;   // (f/2 - 1) 2^64 = F - 2^64
-        e += 1;
-    } else if (i == 0) {
-        r64 = (int64_t)((F - (1ull << 63)) << 1);
+    const int i = (int)((F >> 54) & (kQLogIntervals - 1));
+    uint64_t r64;   // r in Q64, below 2^55
+    uint64_t lninv = 0;
+    if (i == 0) {
+        r64 = (F - (1ull << 63)) << 1;
     } else {
         const uint64_t inv = (uint64_t)__double_as_longlong(__ldg(tab + kTabQInv + i));
-        r64 = (int64_t)(__umul64hi(F, inv) - (1ull << 63)) * 2;
-        lninv = __double_as_longlong(__ldg(tab + kTabQLn + i));
+        r64 = (__umul64hi(F, inv) - (1ull << 63)) << 1;
+        lninv = (uint64_t)__double_as_longlong(__ldg(tab + kTabQLn + i));
     }
-    int64_t g = kQlnC8 + __mul64hi(r64, kQlnC9);
-    g = kQlnC7 + __mul64hi(r64, g);
-    g = kQlnC6 + __mul64hi(r64, g);
-    g = kQlnC5 + __mul64hi(r64, g);
-    g = kQlnC4 + __mul64hi(r64, g);
-    g = kQlnC3 + __mul64hi(r64, g);
-    g = kQlnC2 + __mul64hi(r64, g);
-    const int64_t rg = __mul64hi(r64, g);
-    const int64_t l1p = (r64 >> 1) + __mul64hi(r64, rg);   // ln(1 + r), Q63
-    const int64_t lnf = lninv + (l1p >> 1);                // ln f, Q62
-    return (lnf >> 5) + (int64_t)e * kLn2Q57 + (((int64_t)e * kLn2Q57Frac32) >> 32);
+    const uint64_t r2 = __umul64hi(r64, r64);   // r^2, Q64
+    const uint64_t r3 = __umul64hi(r2, r64);    // r^3, Q64
+    const uint32_t r32 = (uint32_t)(r64 >> 32);
+    uint32_t h = kQh5 - __umulhi(r32, kQh6);
+    h = kQh4 - __umulhi(r32, h);
+    h = kQh3 - __umulhi(r32, h);
+    const uint64_t l1p = r64 - (r2 >> 1) + __umul64hi(r3, (uint64_t)h << 32);   // ln(1 + r), Q64
+    const uint64_t lnf = lninv + (l1p >> 1);                                      // ln f, Q63
+    const int64_t e = 53 - t;
+    return e * kLn2Q57 + ((e * kLn2Q57Frac32) >> 32) - (int64_t)(lnf >> 6);
 }
 
 // ln(1+z), z > -1: with u = 1+z rounded, ln(u) * (z / (u-1)) cancels the

@@ -16,11 +16,13 @@
 
 namespace rs {
 
-// The context's table: first the logarithm's 128 entries (one thread
-// each), then, in a second launch (the logarithm reads its entries through
-// the read-only cache), ln i! for i < 256.
+// The context's table: first the logarithm's 128 entries and the 512 of
+// the fixed-point logarithm (one thread each), then, in a second launch
+// (the logarithm reads its entries through the read-only cache), ln i! for
+// i < 256.
 __global__ void log_table_kernel(double* tab) {
     if (blockIdx.x == 0 && threadIdx.x < 128) build_log_entry((int)threadIdx.x, tab);
+    if (blockIdx.x == 0 && threadIdx.x < kQLogIntervals) build_qlog_entry((int)threadIdx.x, tab);
 }
 
 __global__ void lf_table_kernel(double* tab) {
@@ -33,7 +35,7 @@ __global__ void lf_table_kernel(double* tab) {
 }
 
 cudaError_t launch_lf_table(double* tab, cudaStream_t st) {
-    log_table_kernel<<<1, 128, 0, st>>>(tab);
+    log_table_kernel<<<1, kQLogIntervals, 0, st>>>(tab);
     lf_table_kernel<<<1, 1, 0, st>>>(tab);
     return cudaGetLastError();
 }

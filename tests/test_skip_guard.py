@@ -1,5 +1,5 @@
 """The guarded geometric skip of the CUDA path (rs_bern.cu skip_fast, with
-rs_math.cuh qlog_u57), checked on the CPU through a model of its integer and
+rs_math.cuh qnlog_u57), checked on the CPU through a model of its integer and
 single-precision arithmetic.
 
 The skip of a draw is floor(q) for q = RN(ln U * R), R = RN(1 / ln(1 - p))
@@ -8,7 +8,7 @@ The CUDA path decides it without FP64 when a bound says the decision is
 safe, and evaluates the definition otherwise; both claims behind that are
 pinned here:
 
-* the fixed-point logarithm is within 2^-55 of ln U (exact rational
+* the fixed-point logarithm is within 2^-55 of -ln U (exact rational
   reference, every exponent, every table interval and its edges);
 * wherever the modelled single-precision decision is taken it equals the
   oracle's floor of q, on random draws and on draws whose q lies within
@@ -34,73 +34,67 @@ M64 = 1 << 64
 
 def _const(name):
     src = open(MATH).read()
-    m = re.search(r"constexpr int64_t %s = (-?\d+)ll;" % name, src)
+    m = re.search(r"constexpr (?:int64_t|uint32_t) %s = (-?\d+)(?:ll|u);" % name, src)
     assert m, name
     return int(m.group(1))
 
 
-C = {k: _const("kQlnC%d" % k) for k in range(2, 10)}
+H = {k: _const("kQh%d" % k) for k in range(3, 7)}
 LN2Q57 = _const("kLn2Q57")
 LN2FRAC32 = _const("kLn2Q57Frac32")
+INTERVALS = 512
 
 
 def test_constants_match_their_definitions():
     mpmath.mp.dps = 60
-    for k in range(2, 10):
-        want = Fraction((-1) ** (k + 1), k) * 2**63
-        assert abs(C[k] - want) <= Fraction(1, 2), k
+    for k in range(3, 7):
+        assert abs(H[k] - Fraction(2**32, k)) <= Fraction(1, 2), k
     ln2 = mpmath.log(2) * 2**57
     assert LN2Q57 == int(mpmath.floor(ln2))
     assert abs(LN2FRAC32 - (ln2 - LN2Q57) * 2**32) <= 0.5
 
 
-def _s64(x):
-    x &= M64 - 1
-    return x - M64 if x >= 1 << 63 else x
-
-
-def _mulhi(a, b):   # signed or unsigned high 64 bits (Python's >> floors)
+def _mulhi(a, b):   # unsigned high 64 bits
     return (a * b) >> 64
 
 
 @pytest.fixture(scope="module")
-def table(oracle):
-    """The fixed-point entries as the device builds them from the
-    logarithm's table (inv, -ln inv as hi + lo)."""
+def table():
+    """The fixed-point table: inv = ceil(2^64 / c) for the left ends
+    c = 1 + i/512, and -ln(inv 2^-64) rounded to Q63 (the device builds it
+    from a double-double value; within the same half unit)."""
+    mpmath.mp.dps = 50
     inv_q, ln_q = {}, {}
-    for i in range(1, 127):
-        inv, hi, lo = oracle.log_table_entry(i)
-        m, e = math.frexp(inv)           # inv = m 2^e, m in [1/2, 1)
-        inv_q[i] = int(Fraction(inv) * M64)
-        assert inv_q[i] == Fraction(inv) * M64 and e == 0
-        h = Fraction(hi) * 2**62
-        assert h.denominator == 1        # hi * 2^62 is an integer
-        ln_q[i] = int(h) + round(Fraction(lo) * 2**62)
+    for i in range(1, INTERVALS):
+        inv_q[i] = -(-(1 << 73) // (512 + i))
+        assert inv_q[i] * (512 + i) >= 1 << 73 and inv_q[i] < M64
+        ln_q[i] = int(mpmath.nint(-mpmath.log(mpmath.mpf(inv_q[i]) / M64) * 2**63))
     return inv_q, ln_q
 
 
-def qlog_u57(m, table):
+def qnlog_u57(m, table):
     inv_q, ln_q = table
     t = m.bit_length() - 1
     F = m << (63 - t)
-    i = (F >> 56) & 0x7F
-    e = t - 53
+    i = (F >> 54) & (INTERVALS - 1)
     lninv = 0
-    if i == 127:
-        r64 = _s64(F)
-        e += 1
-    elif i == 0:
-        r64 = _s64((F - (1 << 63)) << 1)
+    if i == 0:
+        r64 = (F - (1 << 63)) << 1
     else:
-        r64 = _s64(_mulhi(F, inv_q[i]) - (1 << 63)) * 2
+        r64 = (_mulhi(F, inv_q[i]) - (1 << 63)) << 1
         lninv = ln_q[i]
-    g = C[8] + _mulhi(r64, C[9])
-    for k in (7, 6, 5, 4, 3, 2):
-        g = C[k] + _mulhi(r64, g)
-    rg = _mulhi(r64, g)
-    l1p = (r64 >> 1) + _mulhi(r64, rg)
+    assert 0 <= r64 < 1 << 55
+    r2 = _mulhi(r64, r64)
+    r3 = _mulhi(r2, r64)
+    r32 = r64 >> 32
+    h = H[5] - ((r32 * H[6]) >> 32)
+    h = H[4] - ((r32 * h) >> 32)
+    h = H[3] - ((r32 * h) >> 32)
+    l1p = r64 - (r2 >> 1) + _mulhi(r3, h << 32)
     lnf = lninv + (l1p >> 1)
-    return (lnf >> 5) + e * LN2Q57 + ((e * LN2FRAC32) >> 32)
+    assert lnf < 1 << 64
+    e = 53 - t
+    return e * LN2Q57 + ((e * LN2FRAC32) >> 32) - (lnf >> 6)
 
 
 def _draws():
@@ -108,9 +102,9 @@ def _draws():
     ms = [1, 2, 3, 2**52 - 1, 2**52, 2**52 + 1, 2**53 - 2, 2**53 - 1]
     for t in range(53):
         ms += [int(v) for v in rng.integers(1 << t, 1 << (t + 1), 40, dtype=np.uint64)] if t < 63 else []
-    for i in range(128):
-        for t in (52, 47, 30, 9):
-            base = (1 << t) + ((i << t) >> 7)
+    for i in range(INTERVALS):
+        for t in (52, 47, 30, 12):
+            base = (1 << t) + ((i << t) >> 9)
             ms += [base + d for d in (-2, -1, 0, 1, 2) if 1 <= base + d < 1 << 53]
     return ms
 
@@ -119,8 +113,8 @@ def test_fixed_point_log_within_its_bound(table):
     mpmath.mp.dps = 50
     worst = mpmath.mpf(0)
     for m in _draws():
-        exact = mpmath.log(mpmath.mpf(m) / 2**53) * 2**57
-        worst = max(worst, abs(qlog_u57(m, table) - exact))
+        exact = -mpmath.log(mpmath.mpf(m) / 2**53) * 2**57
+        worst = max(worst, abs(qnlog_u57(m, table) - exact))
     assert worst <= 2.1, float(worst)   # units of 2^-57: the bound 2^-55.9
 
 
@@ -166,17 +160,17 @@ def skip_fast(x, R, table):
     m = (x >> 11) + 1
     if m == 1 << 53:
         return 1
-    A = -qlog_u57(m, table)
+    A = qnlog_u57(m, table)
     if A <= 0:
         return None
     lz = 64 - A.bit_length()
     nn = A << lz
     Lh = f32((nn >> 40) * 2.0 ** (-17 - lz))
-    Lm = f32(((nn >> 16) & 0xFFFFFF) * 2.0 ** (-41 - lz))
+    Lm = f32(((nn >> 17) & 0x7FFFFF) * 2.0 ** (-40 - lz))
     p = f32(Lh * rh)
     e0 = _rn(Fraction(float(Lh)) * Fraction(float(rh)) - Fraction(float(p)))
     e = f32(e0 + f32(f32(Lh * rl) + f32(Lm * rh)))
-    if not p < f32(2.0**61):
+    if not p < f32(2.0**44):
         return None
     fl = f32(math.floor(p))
     r = f32(f32(p - fl) + e)
