@@ -471,31 +471,34 @@ RS_COLD bool bucket_ties(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, K
 }
 
 // Pass 1 of the bucket path for leaves with void candidates (sizes that are
-// not powers of two): the first k valid candidates to A[0..k), counted per
-// bucket, sm.jnext set to the index after the k-th.  Rounds of up to q Philox
-// blocks per thread, contiguous so that a thread's candidates are in index
-// order: the values are staged in B (not yet in use), one block scan numbers
-// the valid ones in index order, and the first k are kept.  A round covers
-// the missing values plus an eighth, within B's room, so most leaves need one
-// round and one scan.  False if the stream runs out.
+// not powers of two): the first k valid candidates to A[0..k) (in no
+// particular order: later passes only need the set), counted per bucket,
+// sm.jnext set to the index after the k-th.  Rounds of up to q Philox blocks
+// per thread, contiguous so that a thread's candidates are in index order:
+// the values are staged in B (not yet in use) transposed, candidate p of
+// thread t at B[p NT + t], so that a warp's stores and loads hit 32 banks;
+// one block scan numbers the valid ones in index order and the first k are
+// kept, each warp writing its kept values to consecutive slots of A (the
+// warp's slots start where the scan puts its first lane).  A round covers
+// the missing values plus an eighth, within B's room, so most leaves need
+// one round and one scan.  False if the stream runs out.
 template <typename KeyT, int NT, int BAR, uint32_t CAP, typename K2>
 RS_COLD bool void_leaf_pass1(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, const K2& key, uint32_t tag,
                              uint32_t k, uint64_t thr, uint64_t mult, KeyT* A, KeyT* B, uint32_t* cw, uint32_t tid) {
-    auto keep = [&](uint32_t j, uint64_t v) {
-        A[j] = (KeyT)v;
-        const uint32_t b = hash_slot((KeyT)v, mult);
-        atomicAdd(&cw[b >> 1], 1u << ((b & 1u) << 4));
-    };
+    static_assert(CAP + 61 >= 16 * NT, "B's room must take four rounds of blocks per thread");
     const bool w32 = r.s <= (1ull << 32);
     const uint32_t cpb = w32 ? 4u : 2u;
     const uint32_t qmax = 32u / cpb;   // a thread's candidates fit one 32-bit mask
     const uint32_t room = HashShared<KeyT, NT / 32, CAP>::kSlots - ((k + 3) & ~3u);
+    const uint32_t qcap = min(qmax, room / (cpb * NT));   // >= 4
+    const uint32_t lane = tid & 31;
+    const uint32_t lt = (1u << lane) - 1u;
     uint32_t got = 0;
     for (uint64_t b0 = 0; got < k;) {
         if (b0 >= c_caps.stream_blocks) return false;   // the stream ran out: the probing path reports it
         const uint32_t m = k - got;
         const uint32_t want = (m + m / 8 + 32 + cpb - 1) / cpb;
-        const uint32_t nbk = min(want, min(room / cpb, (uint32_t)NT * qmax));
+        const uint32_t nbk = min(want, (uint32_t)NT * qcap);
         const uint32_t q = (nbk + NT - 1) / NT;
         const uint32_t t0 = tid * q;   // this thread's first block of the round
         uint32_t mask = 0;
@@ -503,34 +506,41 @@ RS_COLD bool void_leaf_pass1(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& 
             const uint64_t blk = b0 + t0 + u;
             if (t0 + u >= nbk || blk >= (1ull << 32)) break;
             const uint4 w = philox_block((uint32_t)blk, tag, r.id, key);
-            const uint32_t rel = (t0 + u) * cpb;
             if (w32) {
                 const uint32_t s32 = (uint32_t)(r.s - 1), thr32 = (uint32_t)thr;
                 const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     const uint64_t prod = (uint64_t)ws[c] * s32 + ws[c];   // w * s, exact
-                    B[rel + c] = (KeyT)(prod >> 32);
+                    B[(u * 4 + c) * NT + tid] = (KeyT)(prod >> 32);
                     mask |= ((uint32_t)prod >= thr32 ? 1u : 0u) << (u * 4 + c);
                 }
             } else {
                 const uint64_t xs[2] = {((uint64_t)w.y << 32) | w.x, ((uint64_t)w.w << 32) | w.z};
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
-                    B[rel + c] = (KeyT)__umul64hi(xs[c], r.s);
+                    B[(u * 2 + c) * NT + tid] = (KeyT)__umul64hi(xs[c], r.s);
                     mask |= (xs[c] * r.s >= thr ? 1u : 0u) << (u * 2 + c);
                 }
             }
         }
         uint32_t total;
         uint32_t rank = got + block_exclusive_scan<NT>((uint32_t)__popc(mask), sm.scan_tmp, &total);
-        while (mask && rank < k) {
-            const uint32_t p = (uint32_t)__ffs(mask) - 1u;
-            mask &= mask - 1u;
-            const uint32_t rel = t0 * cpb + p;
-            keep(rank, B[rel]);
-            if (rank == k - 1) sm.jnext = b0 * cpb + rel + 1;
-            ++rank;
+        // the warp's kept values go to A[wslot ..): its lanes' valid
+        // candidates with rank < k, in (candidate, lane) order
+        uint32_t wslot = min(k, __shfl_sync(0xFFFFFFFFu, rank, 0));
+        for (uint32_t p = 0; p < q * cpb; ++p) {
+            const bool kp = ((mask >> p) & 1u) && rank < k;
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, kp);
+            if (kp) {
+                const KeyT v = B[p * NT + tid];
+                A[wslot + __popc(bal & lt)] = v;
+                const uint32_t b = hash_slot(v, mult);
+                atomicAdd(&cw[b >> 1], 1u << ((b & 1u) << 4));
+                if (rank == k - 1) sm.jnext = (b0 + t0) * cpb + p + 1;
+            }
+            rank += (mask >> p) & 1u;
+            wslot += __popc(bal);
         }
         got += total;
         b0 += nbk;
