@@ -161,10 +161,19 @@ int rs_batch_plan(rs_ctx* ctx, const rs_request* reqs_host, uint32_t R, rs_batch
  * (captured again if those pointers change). */
 int rs_batch_run(rs_batchplan* plan, uint64_t* out_pool_dev, int32_t* status_dev, void* stream);
 
-/* Picks, by timing whole runs, the leaf kernels' blocks per SM (an
- * output-invariant knob: the schedule of leaves over blocks never changes a
- * value).  Synchronizes `stream`. */
+/* Picks, by timing whole runs, the leaf kernels' blocks per SM and then the
+ * leaf block shape of each size class of leaves (output-invariant knobs:
+ * the schedule of leaves over blocks and the block's shape never change a
+ * value; Sec. 4.2 and 4.5).  Synchronizes `stream`. */
 int rs_batch_tune(rs_batchplan* plan, uint64_t* out_pool_dev, int32_t* status_dev, void* stream);
+
+/* Sets the leaf kernels' launch directly (what rs_batch_tune chooses):
+ * the threads of the leaf blocks for the small and the large size class
+ * (256 or 512; 0 = the class's default, 256 for leaves averaging up to
+ * about 4,100 values and 512 above), and the leaf blocks per SM (0 = the
+ * occupancy limit).  Output-invariant: no setting changes a value.  The
+ * next run captures its graph again.  Errors: RS_EINVAL. */
+int rs_batch_set_leaf_launch(rs_batchplan* plan, int small_threads, int large_threads, int blocks_per_sm);
 
 /* Kernels one run launches. */
 int rs_batch_launch_count(rs_batchplan* plan, uint64_t* per_run);

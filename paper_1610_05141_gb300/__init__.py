@@ -104,6 +104,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "rs_batch_run": (i32, [vp, vp, vp, vp]),
         "rs_batch_tune": (i32, [vp, vp, vp, vp]),
         "rs_batch_launch_count": (i32, [vp, ctypes.POINTER(u64)]),
+        "rs_batch_set_leaf_launch": (i32, [vp, i32, i32, i32]),
         "rs_batch_destroy": (i32, [vp]),
         "rs_batch": (i32, [vp, vp, u32, vp, vp, vp]),
         "rs_tree_create": (i32, [vp, u64, u64, u64, u32, i32, vp, ctypes.POINTER(vp)]),
@@ -412,6 +413,11 @@ def rs_batch_run(plan: BatchPlan, out_pool, status, stream=None) -> int:
 
 def rs_batch_tune(plan: BatchPlan, out_pool, status, stream=None) -> int:
     return _check(load().rs_batch_tune(plan.handle, _ptr(out_pool), _ptr(status), _stream(stream)), "rs_batch_tune")
+
+
+def rs_batch_set_leaf_launch(plan: BatchPlan, small_threads=0, large_threads=0, blocks_per_sm=0) -> int:
+    return _check(load().rs_batch_set_leaf_launch(plan.handle, small_threads, large_threads, blocks_per_sm),
+                  "rs_batch_set_leaf_launch")
 
 
 def rs_batch_launch_count(plan: BatchPlan) -> int:

@@ -75,17 +75,19 @@ __global__ void __launch_bounds__(kBatchTreeWarps * 32) batch_terms_kernel(const
 }
 
 // Leaf H / leaf WR over the leaves of a view, one block per leaf at a time;
-// leaves the shared-memory table cannot take go to the overflow list.
-template <typename KeyT, bool WR, class View>
-__global__ void __launch_bounds__(kBatchLeafThreads, 4) group_leaf_kernel(View G, uint32_t* ovf_list,
-                                                                       uint32_t* ovf_count, uint32_t cap) {
+// leaves the shared-memory table cannot take go to the overflow list.  Two
+// shapes as in the single-request path: 256 threads with room for 4,864
+// values, 512 with room for 9,728.
+template <typename KeyT, bool WR, class View, int NT, uint32_t CAP>
+__global__ void __launch_bounds__(NT, 1024 / NT) group_leaf_kernel(View G, uint32_t* ovf_list, uint32_t* ovf_count,
+                                                                  uint32_t cap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto& sm = *reinterpret_cast<HashShared<KeyT, kBatchLeafThreads / 32>*>(smem_raw);
+    auto& sm = *reinterpret_cast<HashShared<KeyT, NT / 32, CAP>*>(smem_raw);
     for (uint64_t g = blockIdx.x; g < G.nleaves; g += gridDim.x) {
         const ResolvedLeaf L = resolve_leaf(G, g);
         if (L.rec.c == 0) continue;
         const LeafRec lr{L.rec.lo, L.rec.S, L.rec.c, L.rec.off, L.id};
-        if (!hash_leaf<KeyT, kBatchLeafThreads, 0, WR>(sm, lr, make_key(L.seed), L.out, L.status, threadIdx.x, cap)) {
+        if (!hash_leaf<KeyT, NT, 0, WR, CAP>(sm, lr, make_key(L.seed), L.out, L.status, threadIdx.x, cap)) {
             if (threadIdx.x == 0) ovf_list[atomicAdd(ovf_count, 1u)] = (uint32_t)g;
         }
     }
@@ -186,12 +188,19 @@ namespace {
 constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
-int group_of(int kind, bool wide) { return kind == RS_KIND_B ? 4 : kind * 2 + (wide ? 1 : 0); }
+// Leaf groups: kind (H, WR) x key width x size class (the large class:
+// leaves averaging more than the 256-thread shape comfortably holds), and
+// Algorithm B (group 4).
+int group_of(int kind, bool wide, bool large) {
+    if (kind == RS_KIND_B) return 4;
+    return kind * 2 + (wide ? 1 : 0) + (large ? 5 : 0);
+}
+bool large_class(uint64_t mean_count) { return mean_count * 20 > (uint64_t)kLeafFastCap * 17; }
 
 // Counter slots of the zeroed block: sample leaf groups, query boundary
 // subgroups, query interior subgroups.
-constexpr int kCounters = 16;
-int counter_of(int part, int gi) { return part * 5 + gi; }
+constexpr int kCounters = 3 * GroupPlan::kGroups + 1;
+int counter_of(int part, int gi) { return part * GroupPlan::kGroups + gi; }
 
 int cuda_rc(cudaError_t e) {
     if (e == cudaSuccess) return RS_OK;
@@ -216,9 +225,25 @@ int blocks_per_sm(const void* kern, size_t smem, int threads) {
     return per;
 }
 
-// One leaf kernel (+ the general path) over the leaves of a view.
+// The leaf kernel of one shape for a view: its function, shared memory and
+// capacity.
+template <class View, int NT, uint32_t CAP>
+void leaf_flavour(bool wide, bool wr, void (**kern)(View, uint32_t*, uint32_t*, uint32_t), size_t* smem,
+                  uint32_t* cap) {
+    if (wide) {
+        *kern = wr ? group_leaf_kernel<uint64_t, true, View, NT, CAP> : group_leaf_kernel<uint64_t, false, View, NT, CAP>;
+        *smem = sizeof(HashShared<uint64_t, NT / 32, CAP>);
+    } else {
+        *kern = wr ? group_leaf_kernel<uint32_t, true, View, NT, CAP> : group_leaf_kernel<uint32_t, false, View, NT, CAP>;
+        *smem = sizeof(HashShared<uint32_t, NT / 32, CAP>);
+    }
+    *cap = CAP;
+}
+
+// One leaf kernel (+ the general path) over the leaves of a view; `threads`
+// picks the shape (256 or 512).
 template <class View>
-int issue_leaves(const View& V, int kind, bool wide, uint32_t* ovf, uint32_t* ovf_count, void* big,
+int issue_leaves(const View& V, int kind, bool wide, int threads, uint32_t* ovf, uint32_t* ovf_count, void* big,
                  uint64_t big_kmax, int per_sm_cap, bool persistent, const double* tab, int sms, cudaStream_t st,
                  uint64_t* nl) {
     if (V.nleaves == 0) return RS_OK;
@@ -229,19 +254,15 @@ int issue_leaves(const View& V, int kind, bool wide, uint32_t* ovf, uint32_t* ov
     const bool wr = kind == RS_KIND_WR;
     void (*kern)(View, uint32_t*, uint32_t*, uint32_t);
     size_t smem;
-    if (wide) {
-        kern = wr ? group_leaf_kernel<uint64_t, true, View> : group_leaf_kernel<uint64_t, false, View>;
-        smem = sizeof(HashShared<uint64_t, kBatchLeafThreads / 32>);
-    } else {
-        kern = wr ? group_leaf_kernel<uint32_t, true, View> : group_leaf_kernel<uint32_t, false, View>;
-        smem = sizeof(HashShared<uint32_t, kBatchLeafThreads / 32>);
-    }
-    int per = blocks_per_sm(reinterpret_cast<const void*>(kern), smem, kBatchLeafThreads);
+    uint32_t cap;
+    if (threads == 512) leaf_flavour<View, 512, 2 * kLeafFastCap>(wide, wr, &kern, &smem, &cap);
+    else leaf_flavour<View, kBatchLeafThreads, kLeafFastCap>(wide, wr, &kern, &smem, &cap);
+    int per = blocks_per_sm(reinterpret_cast<const void*>(kern), smem, threads == 512 ? 512 : kBatchLeafThreads);
     if (per < 0) return RS_ECUDA;
     if (per_sm_cap > 0) per = std::min(per, per_sm_cap);
     const uint64_t grid = persistent ? std::min<uint64_t>(V.nleaves, (uint64_t)sms * per)
                                      : std::min<uint64_t>(V.nleaves, 0x7FFFFFFFull);
-    kern<<<(unsigned)grid, kBatchLeafThreads, smem, st>>>(V, ovf, ovf_count, kLeafFastCap);
+    kern<<<(unsigned)grid, threads == 512 ? 512 : kBatchLeafThreads, smem, st>>>(V, ovf, ovf_count, cap);
     ++*nl;
     if (big_kmax) {
         const BigScratch sc = carve_big_scratch(big, big_kmax);
@@ -305,10 +326,11 @@ void GroupPlan::build(const rs_request* reqs, uint64_t* const* out_ptrs, uint32_
     levels_.clear();
     qdesc_.clear();
     qscratch_.clear();
-    for (int gi = 0; gi < 5; ++gi) {
+    for (int gi = 0; gi < kGroups; ++gi) {
         groups_[gi] = Sub{};
-        groups_[gi].kind = gi == 4 ? RS_KIND_B : gi / 2;
-        groups_[gi].wide = gi < 4 && (gi & 1);
+        groups_[gi].kind = gi == 4 ? RS_KIND_B : (gi % 5) / 2;
+        groups_[gi].wide = gi != 4 && ((gi % 5) & 1);
+        groups_[gi].large = gi > 4;
         qgroups_[gi] = groups_[gi];
     }
     nodes_ = 0;
@@ -344,7 +366,7 @@ void GroupPlan::build(const rs_request* reqs, uint64_t* const* out_ptrs, uint32_
         Dmax = std::max(Dmax, D);
         const uint64_t nleaves = 1ull << D;
         const uint64_t smax = (q.N >> D) + ((q.N & (nleaves - 1)) ? 1 : 0);
-        Sub& G = groups_[group_of((int)q.kind, smax > (1ull << 32))];
+        Sub& G = groups_[group_of((int)q.kind, smax > (1ull << 32), large_class(q.n >> D))];
         for (uint64_t i = 0; i < nleaves; ++i) G.desc.push_back(LeafDesc{b.node_base + nleaves + i, r, (uint32_t)i});
         G.n1 += nleaves;
         if (q.kind != RS_KIND_B) bound = std::max<uint64_t>(bound, wr ? q.n : std::min<uint64_t>(q.n, smax - smax / 2));
@@ -378,7 +400,7 @@ void GroupPlan::build(const rs_request* reqs, uint64_t* const* out_ptrs, uint32_
         d.scratch_cap = (d.m == 1 ? 1 : 2) * t.maxc;
         qdesc_.push_back(d);
         qscratch_.push_back(std::max<uint64_t>(d.scratch_cap, 1));
-        Sub& G = qgroups_[group_of(t.kind, t.wide)];
+        Sub& G = qgroups_[group_of(t.kind, t.wide, t.maxk > kLeafFastCap)];
         G.a32.push_back(qi << 1);
         if (d.m > 1) G.a32.push_back((qi << 1) | 1);
         G.n1 = G.a32.size();
@@ -392,6 +414,12 @@ void GroupPlan::build(const rs_request* reqs, uint64_t* const* out_ptrs, uint32_
     }
     big_kmax_ = bound > 64 ? std::min<uint64_t>(bound, kBigLeafMax) : 0;
     layout();
+}
+
+bool GroupPlan::has_class(bool large) const {
+    for (int gi = 0; gi < kGroups; ++gi)
+        if (groups_[gi].large == large && gi != 4 && (groups_[gi].n1 || qgroups_[gi].n1 || qgroups_[gi].n2)) return true;
+    return false;
 }
 
 void GroupPlan::layout() {
@@ -475,21 +503,21 @@ int GroupPlan::issue(const double* tab, int sms, uint64_t* pool, int* status, cu
                 batch_tree_kernel<<<blocks, kBatchTreeWarps * 32, tree_smem, st>>>(reqs, items, n, nodes, tab, status);
             ++nl;
         }
-        for (int gi = 0; !rc && gi < 5; ++gi) {
+        for (int gi = 0; !rc && gi < kGroups; ++gi) {
             const Sub& G = groups_[gi];
             if (G.n1 == 0) continue;
             BatchGroupView V{reqs, reinterpret_cast<const LeafDesc*>(up_ + G.o_desc), G.n1, nodes, pool, status};
-            rc = issue_leaves(V, G.kind, G.wide, reinterpret_cast<uint32_t*>(work_ + G.o_ovf1),
+            rc = issue_leaves(V, G.kind, G.wide, threads_of(G), reinterpret_cast<uint32_t*>(work_ + G.o_ovf1),
                               counters + counter_of(0, gi), big_, big_kmax_, per_sm_, persistent_, tab, sms, st, &nl);
         }
     }
     if (!rc && Q_ > 0) {
         const QueryDesc* qd = reinterpret_cast<const QueryDesc*>(up_ + o_qdesc_);
-        for (int gi = 0; !rc && gi < 5; ++gi) {
+        for (int gi = 0; !rc && gi < kGroups; ++gi) {
             const Sub& G = qgroups_[gi];
             if (G.n1 == 0) continue;
             QueryBoundView V{qd, qres_, reinterpret_cast<const uint32_t*>(up_ + G.o_a32), G.n1};
-            rc = issue_leaves(V, G.kind, G.wide, reinterpret_cast<uint32_t*>(work_ + G.o_ovf1),
+            rc = issue_leaves(V, G.kind, G.wide, threads_of(G), reinterpret_cast<uint32_t*>(work_ + G.o_ovf1),
                               counters + counter_of(1, gi), big_, big_kmax_, per_sm_, persistent_, tab, sms, st, &nl);
         }
         if (!rc) {
@@ -497,7 +525,7 @@ int GroupPlan::issue(const double* tab, int sms, uint64_t* pool, int* status, cu
             query_locate_kernel<<<grid, kLocateThreads, 0, st>>>(qd, qres_, Q_);
             ++nl;
         }
-        for (int gi = 0; !rc && gi < 5; ++gi) {
+        for (int gi = 0; !rc && gi < kGroups; ++gi) {
             const Sub& G = qgroups_[gi];
             if (G.n2 == 0) continue;
             QueryInnerView V{qd,
@@ -506,7 +534,7 @@ int GroupPlan::issue(const double* tab, int sms, uint64_t* pool, int* status, cu
                              reinterpret_cast<const uint64_t*>(up_ + G.o_p64),
                              (uint32_t)G.b32.size(),
                              G.n2};
-            rc = issue_leaves(V, G.kind, G.wide, reinterpret_cast<uint32_t*>(work_ + G.o_ovf2),
+            rc = issue_leaves(V, G.kind, G.wide, threads_of(G), reinterpret_cast<uint32_t*>(work_ + G.o_ovf2),
                               counters + counter_of(2, gi), big_, big_kmax_, per_sm_, persistent_, tab, sms, st, &nl);
         }
     }
@@ -653,6 +681,18 @@ int rs_batch_run(rs_batchplan* B, uint64_t* out_pool_dev, int32_t* status_dev, v
     return rs::cuda_rc(cudaGraphLaunch(B->exec, st));
 }
 
+int rs_batch_set_leaf_launch(rs_batchplan* B, int small_threads, int large_threads, int blocks_per_sm) {
+    auto ok = [](int t) { return t == 0 || t == 256 || t == 512; };
+    if (!B || !ok(small_threads) || !ok(large_threads) || blocks_per_sm < 0) return RS_EINVAL;
+    B->plan.set_leaf_threads(small_threads, large_threads);
+    B->plan.set_blocks_per_sm(blocks_per_sm);
+    if (B->exec) {   // the next run captures its graph again
+        cudaGraphExecDestroy(B->exec);
+        B->exec = nullptr;
+    }
+    return RS_OK;
+}
+
 int rs_batch_launch_count(rs_batchplan* B, uint64_t* per_run) {
     if (!B || !per_run) return RS_EINVAL;
     *per_run = B->launches_per_run;
@@ -666,30 +706,50 @@ int rs_batch_tune(rs_batchplan* B, uint64_t* out_pool_dev, int32_t* status_dev, 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return RS_ECUDA;
-    // Output-invariant knob: leaf blocks per SM (the leaf-to-block schedule
-    // does not change any value).  Try each setting on the whole run.
-    int best = 0;
-    float best_ms = 1e30f;
-    for (int per : {0, 4, 3, 2, 1}) {
-        B->plan.set_blocks_per_sm(per);
+    // Output-invariant knobs (the leaf-to-block schedule and the block's
+    // shape never change a value): leaf blocks per SM, then each size
+    // class's leaf shape, each setting timed on the whole run.
+    auto timed = [&](float* ms) {
         uint64_t nl = 0;
         int rc = issue_run(B, out_pool_dev, status_dev, st, &nl);   // warm
         cudaEventRecord(e0, st);
         if (!rc) rc = issue_run(B, out_pool_dev, status_dev, st, &nl);
         cudaEventRecord(e1, st);
-        if (rc || cudaEventSynchronize(e1) != cudaSuccess) {
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            return rc ? rc : RS_ECUDA;
-        }
+        if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = RS_ECUDA;
+        if (!rc) cudaEventElapsedTime(ms, e0, e1);
+        return rc;
+    };
+    int best = 0, rc = RS_OK;
+    float best_ms = 1e30f;
+    for (int per : {0, 4, 3, 2, 1}) {
+        B->plan.set_blocks_per_sm(per);
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
+        if ((rc = timed(&ms)) != RS_OK) break;
         if (ms < best_ms) {
             best_ms = ms;
             best = per;
         }
     }
     B->plan.set_blocks_per_sm(best);
+    int threads[2] = {0, 0};
+    for (int cls = 0; rc == RS_OK && cls < 2; ++cls) {
+        if (!B->plan.has_class(cls == 1)) continue;
+        int trial[2] = {threads[0], threads[1]};
+        trial[cls] = cls ? 256 : 512;   // the other shape
+        B->plan.set_leaf_threads(trial[0], trial[1]);
+        float ms = 0.f;
+        if ((rc = timed(&ms)) != RS_OK) break;
+        if (ms < best_ms) {
+            best_ms = ms;
+            threads[cls] = trial[cls];
+        }
+    }
+    B->plan.set_leaf_threads(threads[0], threads[1]);
+    if (rc) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return rc;
+    }
     if (B->exec) {
         cudaGraphExecDestroy(B->exec);
         B->exec = nullptr;

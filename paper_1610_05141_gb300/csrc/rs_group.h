@@ -68,6 +68,22 @@ public:
 
     // Leaf-kernel blocks per SM for every leaf group (0 = occupancy limit).
     void set_blocks_per_sm(int per) { per_sm_ = per; }
+    int blocks_per_sm() const { return per_sm_; }
+
+    // Threads of the leaf kernels (256 or 512; 0 = the class's default: 256
+    // for the small class, 512 for the large) of the small and the large
+    // size class.  Output-invariant, like the blocks per SM.
+    void set_leaf_threads(int small, int large) {
+        threads_[0] = small;
+        threads_[1] = large;
+    }
+    int leaf_threads(bool large) const { return threads_[large ? 1 : 0]; }
+    // Whether the plan has request or query leaves of the size class.
+    bool has_class(bool large) const;
+
+    // Leaf groups: (H, WR) x (32-, 64-bit keys) x (small, large class), and
+    // Algorithm B.
+    static constexpr int kGroups = 9;
 
     // Leaf kernels with one block per leaf instead of a persistent grid, so
     // that their blocks retire often and kernels of other streams (a
@@ -83,6 +99,7 @@ private:
     struct Sub {   // a leaf group (requests) or query subgroup, one kernel flavour
         int kind = 0;
         bool wide = false;
+        bool large = false;
         // requests: leaf descriptors; queries: bound items, then interior q_of/prefix
         std::vector<LeafDesc> desc;
         std::vector<uint32_t> a32, b32;
@@ -95,7 +112,7 @@ private:
     std::vector<std::vector<BatchTreeItem>> levels_;
     std::vector<QueryDesc> qdesc_;
     std::vector<uint64_t> qscratch_;   // scratch values per query
-    Sub groups_[5], qgroups_[5];
+    Sub groups_[kGroups], qgroups_[kGroups];
     uint32_t R_ = 0, Q_ = 0;
     uint64_t nodes_ = 0, big_kmax_ = 0;
     // layout
@@ -110,6 +127,11 @@ private:
     QueryRes* qres_ = nullptr;
     int per_sm_ = 0;
     bool persistent_ = true;
+    int threads_[2] = {0, 0};
+    int threads_of(const Sub& G) const {
+        const int t = threads_[G.large ? 1 : 0];
+        return t ? t : (G.large ? 512 : 256);
+    }
 
     void layout();
 };

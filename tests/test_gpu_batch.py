@@ -122,3 +122,57 @@ def test_batch_one_shot_device_requests_and_tune(rs, ctx, oracle):
     assert np.array_equal(pool.cpu().numpy().view(np.uint64), got)
     assert rs.rs_batch_launch_count(plan) > 0
     plan.close()
+
+
+def _large_class_requests():
+    """Requests of both size classes and both key widths: leaves averaging
+    ~1,000 to ~8,000 values (n0 up to 8192), with and without replacement,
+    sizes that are and are not powers of two."""
+    rng = np.random.default_rng(17)
+    reqs = []
+    for i in range(48):
+        kind = int(rng.integers(0, 2))
+        n0 = int(rng.choice([1024, 4096, 6000, 8192]))
+        n = int(n0 * rng.uniform(0.6, 1.0) * (1 << int(rng.integers(0, 4))))
+        N = int(rng.choice([2**31 + 12345, 2**33, 3 * 2**40 + 7, 10**9])) * (1 << int(rng.integers(0, 3)))
+        reqs.append((n, max(N, n), 3000 + i, n0, kind))
+    return reqs
+
+
+def test_batch_leaf_shapes_and_blocks_do_not_change_output(rs, ctx, oracle):
+    """rs_batch_tune's knobs are output-invariant: every leaf shape of either
+    size class (256 or 512 threads) and any blocks per SM give the same pool,
+    which equals the oracle's samples."""
+    reqs = _large_class_requests()
+    n = [r[0] for r in reqs]
+    off = np.zeros(len(reqs), dtype=np.uint64)
+    off[1:] = np.cumsum(n)[:-1]
+    arr = rs.requests_array(n, [r[1] for r in reqs], [r[2] for r in reqs], off, [r[3] for r in reqs],
+                            [r[4] for r in reqs])
+    plan = rs.rs_batch_plan(ctx, arr)
+    pool = torch.empty(int(sum(n)), dtype=torch.int64, device="cuda")
+    status = torch.empty(len(reqs), dtype=torch.int32, device="cuda")
+    pools = []
+    try:
+        for small, large, per in [(0, 0, 0), (256, 256, 0), (512, 512, 0), (512, 256, 2), (256, 512, 1)]:
+            rs.rs_batch_set_leaf_launch(plan, small, large, per)
+            for _ in range(2):   # eager and graph replay
+                pool.fill_(-1)
+                rs.rs_batch_run(plan, pool, status)
+                torch.cuda.synchronize()
+                assert (status.cpu().numpy() == rs.RS_OK).all(), (small, large, per)
+                pools.append(pool.cpu().numpy().view(np.uint64).copy())
+        rs.rs_batch_tune(plan, pool, status)
+        pool.fill_(-1)
+        rs.rs_batch_run(plan, pool, status)
+        torch.cuda.synchronize()
+        pools.append(pool.cpu().numpy().view(np.uint64).copy())
+        with pytest.raises(rs.RSError):
+            rs.rs_batch_set_leaf_launch(plan, 300, 0, 0)
+    finally:
+        plan.close()
+    for p in pools[1:]:
+        assert np.array_equal(p, pools[0])
+    for i in range(0, len(reqs), 5):
+        ni, Ni, si, n0i, k = reqs[i]
+        assert np.array_equal(pools[0][int(off[i]): int(off[i]) + ni], oracle.sample(ni, Ni, si, n0i, k)), i
