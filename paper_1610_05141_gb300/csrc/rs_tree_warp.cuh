@@ -27,6 +27,7 @@
 //    are summed in the scalar order after shuffles.
 #pragma once
 #include "rs_deviates.cuh"
+#include "rs_ff.cuh"
 
 namespace rs {
 
@@ -100,11 +101,13 @@ struct RouNode {
     double mu, h, alpha, top, logr;   // FP64 parameters, as defined (set up when a trial first needs them)
     float fa, fh, ftop;  // alpha, h, top in single precision, for the guards
     float logrf;         // binomial: ln(p / (1 - p)) in single precision, for the guard
+    FF ffa, ffh, fflogr; // alpha, h, ln(p / (1 - p)) in float-float, for the second guard (rs_ff.cuh)
     double lnP[4];       // ln of the fixed ends (lanes kernel), once per node
     uint32_t trial;
     bool flipN, flipK;
     bool fresh;          // set up, fixed-end logarithms not yet taken
     bool have64;         // h, alpha, top, logr are set
+    bool haveff;         // ffa, ffh, fflogr are set
 };
 
 // The hat's constants 2 sqrt(2/e) and 3 - 2 sqrt(3/e) in single precision.
@@ -135,6 +138,33 @@ RS_DEV void setup64(RouNode* q, const double* __restrict__ tab) {
     }
     q->top = (double)q->a + 1.0;
     q->have64 = true;
+}
+
+// The node's alpha, h (and ln(p / (1 - p))) in float-float, for the second
+// guard: the definition's formulas (setup64) with every operation in
+// float-float (each within 2^-42 of its result), the logarithm of K / (S - K)
+// as a difference of two fixed-point logarithms (within 2^-54).
+template <bool WR>
+RS_DEV void setupff(RouNode* q, const double* __restrict__ tab) {
+    const FF half{0.5f, 0.0f};
+    const FF d1{1.715527773e+00f, -2.982028846e-09f};   // RS_HAT_D1 as two singles
+    const FF d2{8.989161849e-01f, -2.284329170e-08f};   // RS_HAT_D2
+    FF mu, var;
+    if (WR) {
+        const FF pp = ff_div(ff_from_u64(q->K), ff_from_u64(q->S));
+        mu = ff_mul(ff_from_u64(q->a), pp);
+        var = ff_mul(mu, ff_sub(FF{1.0f, 0.0f}, pp));
+        q->fflogr = (2 * q->K == q->S) ? FF{0.0f, 0.0f}
+                                       : ff_from_q57(ln_u64_q57(q->K, tab) - ln_u64_q57(q->S - q->K, tab));
+    } else {
+        const FF S = ff_from_u64(q->S);
+        mu = ff_div(ff_mul(ff_from_u64(q->a), ff_from_u64(q->b)), S);
+        var = ff_mul(ff_mul(mu, ff_div(ff_from_u64(q->S - q->a), S)),
+                     ff_div(ff_from_u64(q->S - q->b), ff_from_u64(q->S - 1)));
+    }
+    q->ffh = ff_add(ff_mul(d1, ff_sqrt(ff_add(var, half))), d2);
+    q->ffa = ff_add(mu, half);
+    q->haveff = true;
 }
 
 template <bool WR>
@@ -218,6 +248,7 @@ RS_DEV bool node_setup(NodeRec* __restrict__ rec, uint64_t v, Key2 key, const do
     q->trial = 0;
     q->fresh = true;
     q->have64 = false;
+    q->haveff = false;
     q->fa = muf + 0.5f;
     q->ftop = __ull2float_rn(q->a + 1);
     // inversion below a mean of 16 (the FP64 mean decides when the single
@@ -280,6 +311,10 @@ RS_DEV void tree_batch_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
             const uint64_t vx = ((uint64_t)blk.w << 32) | blk.z;
             const float Uf = u_open_f(ux);
             int xd = guard ? guard_abscissa(q.fa, q.fh, q.ftop, Uf, v_closed_f(vx), &k) : 0;
+            if (guard && xd == 0) {   // the second guard
+                if (!q.haveff) setupff<WR>(&q, tab);
+                xd = ff_guard_abscissa(q.ffa, q.ffh, q.a + 1, ux, vx, &k);
+            }
             if (xd == 0) {   // the abscissa in FP64, as defined
                 if (!q.have64) setup64<WR>(&q, tab);
                 const double U = u_open(ux), V = v_closed(vx);
@@ -304,6 +339,24 @@ RS_DEV void tree_batch_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
                         fm += fabsf(rt) + fabsf(dk);
                     }
                     dec = guard_decide(Uf, ft, fm);
+                    if (dec == 0) {   // the second guard: the same terms in float-float
+                        if (!q.haveff) setupff<WR>(&q, tab);
+                        FF t2{0.0f, 0.0f};
+                        float m2 = 0.0f;
+#pragma unroll
+                        for (int j = 0; j < kTerms; ++j) {
+                            float m;
+                            t2 = ff_add(t2, ff_sd(fixed_end<WR>(q, j), moving_end<WR>(q, j, k), tab, &m));
+                            m2 += m;
+                        }
+                        if (WR) {
+                            const FF dk = k >= q.M ? ff_from_u64(k - q.M) : ff_neg(ff_from_u64(q.M - k));
+                            const FF rt = ff_mul(dk, q.fflogr);
+                            t2 = ff_add(t2, rt);
+                            m2 += fabsf(rt.hi) + fabsf(dk.hi);
+                        }
+                        dec = ff_guard_decide(ux, t2, m2, tab);
+                    }
                 }
                 if (dec == 0) {
                     if (WR && !q.have64) setup64<WR>(&q, tab);   // ln(p / (1 - p)) as defined
@@ -434,9 +487,12 @@ RS_DEV void tree_terms_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
     uint64_t P = 0;        // this lane's fixed end (term j); its logarithm once the node first needs FP64
     double lnP = 0.0;
     bool haveLnP = false;
-    // few nodes per launch (the top of the tree): latency, not the FP64 rate,
-    // bounds the launch, so the FP64 set-up and logarithms start at once
-    const bool eager = !guard || G >= 16;
+    // exact mode: the FP64 set-up and logarithms at once; few nodes per
+    // launch (the top of the tree, whose huge terms the first guard cannot
+    // settle): the second guard's float-float set-up at once, FP64 only for
+    // the trials both guards leave open
+    const bool eager = !guard;
+    const bool eager_ff = guard && G >= 16;
     for (;;) {
         // free groups take the next nodes, in order
         for (;;) {
@@ -450,6 +506,7 @@ RS_DEV void tree_terms_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
                     P = fixed_end<WR>(q, (int)j);
                     haveLnP = eager;
                     if (eager) lnP = log_fixed(P, tab);
+                    if (eager_ff) setupff<WR>(&q, tab);
                 }
             }
             next += take;
@@ -464,7 +521,13 @@ RS_DEV void tree_terms_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
             ux = ((uint64_t)blk.y << 32) | blk.x;
             const uint64_t vx = ((uint64_t)blk.w << 32) | blk.z;
             Uf = u_open_f(ux);
-            if (guard) xd = guard_abscissa(q.fa, q.fh, q.ftop, Uf, v_closed_f(vx), &k);
+            if (guard) {
+                xd = guard_abscissa(q.fa, q.fh, q.ftop, Uf, v_closed_f(vx), &k);
+                if (xd == 0) {   // the second guard
+                    if (!q.haveff) setupff<WR>(&q, tab);
+                    xd = ff_guard_abscissa(q.ffa, q.ffh, q.a + 1, ux, vx, &k);
+                }
+            }
             if (xd == 0) {   // the abscissa in FP64, as defined
                 if (!q.have64) setup64<WR>(&q, tab);
                 const double U = u_open(ux), V = v_closed(vx);
@@ -493,7 +556,28 @@ RS_DEV void tree_terms_warp(NodeRec* __restrict__ rec, uint64_t v0, uint32_t cou
             }
             if (active && inr) dec = guard_decide(Uf, ft, fm);
         }
-        // FP64, as the definition states, for the trials the guard left open
+        // the second guard for the trials the first left open: the same sum
+        // of the four lanes' terms in float-float
+        if (guard && __any_sync(0xFFFFFFFFu, active && inr && dec == 0)) {
+            const bool want = active && inr && dec == 0;   // the same in a trial's four lanes
+            if (want && !q.haveff) setupff<WR>(&q, tab);
+            float m2;
+            FF t2 = ff_sd(P, want ? Q : P, tab, &m2);
+#pragma unroll
+            for (int o = 1; o <= 2; o <<= 1) {
+                const FF y{__shfl_xor_sync(0xFFFFFFFFu, t2.hi, o), __shfl_xor_sync(0xFFFFFFFFu, t2.lo, o)};
+                t2 = ff_add(t2, y);
+                m2 += __shfl_xor_sync(0xFFFFFFFFu, m2, o);
+            }
+            if (WR && want) {
+                const FF dk = k >= q.M ? ff_from_u64(k - q.M) : ff_neg(ff_from_u64(q.M - k));
+                const FF rt = ff_mul(dk, q.fflogr);
+                t2 = ff_add(t2, rt);
+                m2 += fabsf(rt.hi) + fabsf(dk.hi);
+            }
+            if (want) dec = ff_guard_decide(ux, t2, m2, tab);
+        }
+        // FP64, as the definition states, for the trials both guards left open
         const bool need = active && inr && dec == 0;
         bool acc = dec > 0;
         if (__any_sync(0xFFFFFFFFu, need)) {
