@@ -14,6 +14,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "rs_big_leaf.cuh"
@@ -78,11 +79,70 @@ __global__ void __launch_bounds__(kBatchTreeWarps * 32) batch_terms_kernel(const
 // leaves the shared-memory table cannot take go to the overflow list.  Two
 // shapes as in the single-request path: 256 threads with room for 4,864
 // values, 512 with room for 9,728.
+// Copies `bytes` (a multiple of 16, both addresses 16-byte aligned) into
+// shared memory asynchronously; prefetch_all_wait() completes every copy
+// this thread started.
+RS_DEV void prefetch_bytes(void* dst, const void* src, int bytes) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    const unsigned char* p = static_cast<const unsigned char*>(src);
+    for (int o = 0; o < bytes; o += 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + o), "l"(p + o) : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+RS_DEV void prefetch_all_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 template <typename KeyT, bool WR, class View, int NT, uint32_t CAP>
 __global__ void __launch_bounds__(NT, 1024 / NT) group_leaf_kernel(View G, uint32_t* ovf_list, uint32_t* ovf_count,
                                                                   uint32_t cap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto& sm = *reinterpret_cast<HashShared<KeyT, NT / 32, CAP>*>(smem_raw);
+    if constexpr (std::is_same<View, BatchGroupView>::value) {
+        // A batch's leaf is resolved by three dependent loads (descriptor,
+        // then request and node record); thread 0 fetches them ahead by
+        // cp.async while the block works: the descriptor two leaves ahead
+        // (three slots) and the request and record one leaf ahead (two),
+        // each slot last read before the previous leaf's final barrier.
+        __shared__ __align__(16) LeafDesc dbuf[3];
+        __shared__ __align__(16) NodeRec rbuf[2];
+        __shared__ __align__(16) BatchReq qbuf[2];
+        const uint64_t n = G.nleaves, step = gridDim.x, g0 = blockIdx.x;
+        if (g0 >= n) return;
+        if (threadIdx.x == 0) {
+            prefetch_bytes(&dbuf[0], &G.desc[g0], sizeof(LeafDesc));
+            prefetch_all_wait();
+            prefetch_bytes(&rbuf[0], &G.nodes[dbuf[0].node], sizeof(NodeRec));
+            prefetch_bytes(&qbuf[0], &G.reqs[dbuf[0].req], sizeof(BatchReq));
+            if (g0 + step < n) prefetch_bytes(&dbuf[1], &G.desc[g0 + step], sizeof(LeafDesc));
+            prefetch_all_wait();
+        }
+        __syncthreads();
+        uint32_t t = 0;
+        for (uint64_t g = g0; g < n; g += step, ++t) {
+            const LeafDesc d = dbuf[t % 3];
+            const NodeRec rec = rbuf[t & 1];
+            const BatchReq& q = qbuf[t & 1];
+            const uint64_t id = (1ull << q.D) + d.i, seed = q.seed;
+            uint64_t* out = q.out_ptr ? q.out_ptr : G.pool + q.out_off;
+            int* status = G.status + d.req;
+            if (threadIdx.x == 0) {
+                if (g + step < n) {   // its descriptor arrived with the last leaf
+                    const LeafDesc& dn = dbuf[(t + 1) % 3];
+                    prefetch_bytes(&rbuf[(t + 1) & 1], &G.nodes[dn.node], sizeof(NodeRec));
+                    prefetch_bytes(&qbuf[(t + 1) & 1], &G.reqs[dn.req], sizeof(BatchReq));
+                }
+                if (g + 2 * step < n) prefetch_bytes(&dbuf[(t + 2) % 3], &G.desc[g + 2 * step], sizeof(LeafDesc));
+            }
+            if (rec.c != 0) {
+                const LeafRec lr{rec.lo, rec.S, rec.c, rec.off, id};
+                if (!hash_leaf<KeyT, NT, 0, WR, CAP>(sm, lr, make_key(seed), out, status, threadIdx.x, cap)) {
+                    if (threadIdx.x == 0) ovf_list[atomicAdd(ovf_count, 1u)] = (uint32_t)g;
+                }
+            }
+            if (threadIdx.x == 0) prefetch_all_wait();
+            __syncthreads();
+        }
+        return;
+    }
     for (uint64_t g = blockIdx.x; g < G.nleaves; g += gridDim.x) {
         const ResolvedLeaf L = resolve_leaf(G, g);
         if (L.rec.c == 0) continue;
