@@ -567,8 +567,19 @@ RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, co
     for (uint32_t i = tid; i < nb / 8; i += NT) reinterpret_cast<uint4*>(cw)[i] = make_uint4(0, 0, 0, 0);
     if (tid == 0) sm.cnt[3] = 0;
     if (tid == 0) {   // once per leaf; the last reads of these fields came before the last barrier
-        sm.mult = slot_mult_fast<KeyT>(r.s, nb);
-        sm.thr = lemire_threshold(r.s);
+        if ((r.s & (r.s - 1)) == 0) {
+            // a power of two 2^t: the map v -> v nb 2^-t by a shift (no
+            // division or conversion on the path to the barrier), no void
+            // candidates
+            const uint32_t t = 63u - (uint32_t)__clzll((long long)r.s);
+            const uint32_t w = sizeof(KeyT) == 4 ? 32u : 64u;
+            const uint64_t m = (uint64_t)nb << (w - t);
+            sm.mult = (sizeof(KeyT) == 4 && m > 0xFFFFFFFFull) ? 0xFFFFFFFFull : m;
+            sm.thr = 0;
+        } else {
+            sm.mult = slot_mult_fast<KeyT>(r.s, nb);
+            sm.thr = lemire_threshold(r.s);
+        }
     }
     group_sync<BAR, NT>();
     const uint64_t mult = sm.mult;
