@@ -8,6 +8,7 @@
 // no squeeze.  Uniforms are the 64-bit values of the node's SPLIT stream in
 // order: value r for inversion restart r, values 2i and 2i+1 for trial i.
 #pragma once
+#include "rs_ff.cuh"
 #include "rs_math.cuh"
 #include "rs_rng.cuh"
 
@@ -55,11 +56,14 @@ RS_DEV int hypergeometric_t(Key2 key, uint64_t node, uint64_t n, uint64_t K, uin
     if (flipN) n = S - n;
     const uint64_t a = n < K ? n : K;
     const uint64_t b = n < K ? K : n;
-    const double rS = drecip((double)S);
-    const double mu = ((double)a * (double)b) * rS;
+    // the parameters in float-float for the guards (rs_ff.cuh); the FP64
+    // ones, as defined, only where a guard leaves a decision open
+    const FFParams fp = ff_hg_params(a, b, S);
+    int below = ff_mean_below_16(fp.mu);
+    if (below < 0) below = ((double)a * (double)b) * drecip((double)S) < 16.0;
     uint64_t y = 0;
     bool done = false;
-    if (mu < 16.0) {
+    if (below) {
         // Inversion from k = 0 with the pmf recurrence
         // f(k+1) = f(k) (a-k)(b-k) / ((k+1)(S-a-b+k+1)).
         const double f0 = dexp(dsd(S - b, S - a - b, tab) - dsd(S, S - a, tab));
@@ -81,27 +85,55 @@ RS_DEV int hypergeometric_t(Key2 key, uint64_t node, uint64_t n, uint64_t K, uin
             done = TL::first(ok, yk, y);
         }
     } else {
-        const double var = mu * ((double)(S - a) * rS) * ((double)(S - b) * drecip((double)(S - 1)));
-        const double h = RS_HAT_D1 * sqrt(var + 0.5) + RS_HAT_D2;
-        const double alpha = mu + 0.5;
         const uint64_t M = (uint64_t)(((unsigned __int128)(a + 1) * (b + 1)) / (S + 2));
         const uint64_t m = S - a - b;
-        const double top = (double)a + 1.0;
-        const double l0 = log_fixed(M, tab), l1 = log_fixed(a - M, tab), l2 = log_fixed(b - M, tab),
-                     l3 = log_fixed(m + M, tab);
+        bool have64 = false, haveL = false;
+        double alpha = 0.0, h = 0.0, top = 0.0, l0 = 0.0, l1 = 0.0, l2 = 0.0, l3 = 0.0;
         for (uint64_t i0 = 0; i0 < c_caps.rou_trials && !done; i0 += TL::step) {
             const uint64_t i = i0 + TL::lane();
             const uint4 blk = philox_block((uint32_t)i, TAG_SPLIT, node, key);
-            const double U = u_open(((uint64_t)blk.y << 32) | blk.x);
-            const double V = v_closed(((uint64_t)blk.w << 32) | blk.z);
-            const double X = alpha + h * (V - 0.5) * drecip(U);
-            bool ok = false;
+            const uint64_t ux = ((uint64_t)blk.y << 32) | blk.x, vx = ((uint64_t)blk.w << 32) | blk.z;
             uint64_t k = 0;
-            if (X >= 0.0 && X < top && i < c_caps.rou_trials) {
-                k = (uint64_t)X;
-                const double T = dsd_fixed(M, k, l0, tab) + dsd_fixed(a - M, a - k, l1, tab) +
-                                 dsd_fixed(b - M, b - k, l2, tab) + dsd_fixed(m + M, m + k, l3, tab);
-                ok = 2.0 * dlog(U, tab) <= T;
+            int xd = ff_guard_abscissa(fp.alpha, fp.h, a + 1, ux, vx, &k);
+            if (xd == 0) {   // the abscissa in FP64, as defined
+                if (!have64) {
+                    const double rS = drecip((double)S);
+                    const double mu = ((double)a * (double)b) * rS;
+                    const double var = mu * ((double)(S - a) * rS) * ((double)(S - b) * drecip((double)(S - 1)));
+                    h = RS_HAT_D1 * sqrt(var + 0.5) + RS_HAT_D2;
+                    alpha = mu + 0.5;
+                    top = (double)a + 1.0;
+                    have64 = true;
+                }
+                const double X = alpha + h * (v_closed(vx) - 0.5) * drecip(u_open(ux));
+                xd = (X >= 0.0 && X < top) ? 1 : -1;
+                if (xd > 0) k = (uint64_t)X;
+            }
+            bool ok = false;
+            if (xd > 0 && i < c_caps.rou_trials) {
+                float mg, mj;
+                FF T = ff_sd(M, k, tab, &mg);
+                T = ff_add(T, ff_sd(a - M, a - k, tab, &mj));
+                mg += mj;
+                T = ff_add(T, ff_sd(b - M, b - k, tab, &mj));
+                mg += mj;
+                T = ff_add(T, ff_sd(m + M, m + k, tab, &mj));
+                mg += mj;
+                const int dec = ff_guard_decide(ux, T, mg, tab);
+                if (dec == 0) {   // the test in FP64, as defined
+                    if (!haveL) {
+                        l0 = log_fixed(M, tab);
+                        l1 = log_fixed(a - M, tab);
+                        l2 = log_fixed(b - M, tab);
+                        l3 = log_fixed(m + M, tab);
+                        haveL = true;
+                    }
+                    const double T64 = dsd_fixed(M, k, l0, tab) + dsd_fixed(a - M, a - k, l1, tab) +
+                                       dsd_fixed(b - M, b - k, l2, tab) + dsd_fixed(m + M, m + k, l3, tab);
+                    ok = 2.0 * dlog(u_open(ux), tab) <= T64;
+                } else {
+                    ok = dec > 0;
+                }
             }
             done = TL::first(ok, k, y);
         }
@@ -120,8 +152,10 @@ RS_DEV int binomial_t(Key2 key, uint64_t node, uint64_t c, uint64_t K, uint64_t 
     using TL = TrialLanes<WARP>;
     if (c == 0 || K == 0) { out = 0; return RS_OK; }
     const double p = (double)K / (double)S;
-    const double mu = (double)c * p;
-    if (mu < 16.0) {
+    const FFParams fp = ff_bin_params(c, K, S, tab);
+    int below = ff_mean_below_16(fp.mu);
+    if (below < 0) below = (double)c * p < 16.0;
+    if (below) {
         const double f0 = dexp((double)c * dlog1p(-p, tab));
         const double r = p / (1.0 - p);
         for (uint64_t q0 = 0; q0 < c_caps.inv_restarts; q0 += TL::step) {
@@ -140,27 +174,52 @@ RS_DEV int binomial_t(Key2 key, uint64_t node, uint64_t c, uint64_t K, uint64_t 
         }
         return RS_EITER;
     }
-    const double var = mu * (1.0 - p);
-    const double h = RS_HAT_D1 * sqrt(var + 0.5) + RS_HAT_D2;
-    const double alpha = mu + 0.5;
-    const double r = p / (1.0 - p);
-    const double logr = (r == 1.0) ? 0.0 : dlog(r, tab);
     const uint64_t M = (uint64_t)(((unsigned __int128)(c + 1) * K) / S);
-    const double top = (double)c + 1.0;
-    const double l0 = log_fixed(M, tab), l1 = log_fixed(c - M, tab);
+    bool have64 = false, haveL = false;
+    double alpha = 0.0, h = 0.0, top = 0.0, logr = 0.0, l0 = 0.0, l1 = 0.0;
     for (uint64_t i0 = 0; i0 < c_caps.rou_trials; i0 += TL::step) {
         const uint64_t i = i0 + TL::lane();
         const uint4 blk = philox_block((uint32_t)i, TAG_SPLIT, node, key);
-        const double U = u_open(((uint64_t)blk.y << 32) | blk.x);
-        const double V = v_closed(((uint64_t)blk.w << 32) | blk.z);
-        const double X = alpha + h * (V - 0.5) * drecip(U);
-        bool ok = false;
+        const uint64_t ux = ((uint64_t)blk.y << 32) | blk.x, vx = ((uint64_t)blk.w << 32) | blk.z;
         uint64_t k = 0;
-        if (X >= 0.0 && X < top && i < c_caps.rou_trials) {
-            k = (uint64_t)X;
-            const double T = dsd_fixed(M, k, l0, tab) + dsd_fixed(c - M, c - k, l1, tab) +
-                             (double)((int64_t)k - (int64_t)M) * logr;
-            ok = 2.0 * dlog(U, tab) <= T;
+        int xd = ff_guard_abscissa(fp.alpha, fp.h, c + 1, ux, vx, &k);
+        if (xd == 0) {   // the abscissa in FP64, as defined
+            if (!have64) {
+                const double mu = (double)c * p;
+                h = RS_HAT_D1 * sqrt(mu * (1.0 - p) + 0.5) + RS_HAT_D2;
+                alpha = mu + 0.5;
+                top = (double)c + 1.0;
+                have64 = true;
+            }
+            const double X = alpha + h * (v_closed(vx) - 0.5) * drecip(u_open(ux));
+            xd = (X >= 0.0 && X < top) ? 1 : -1;
+            if (xd > 0) k = (uint64_t)X;
+        }
+        bool ok = false;
+        if (xd > 0 && i < c_caps.rou_trials) {
+            float mg, mj;
+            FF T = ff_sd(M, k, tab, &mg);
+            T = ff_add(T, ff_sd(c - M, c - k, tab, &mj));
+            mg += mj;
+            const FF dk = k >= M ? ff_from_u64(k - M) : ff_neg(ff_from_u64(M - k));
+            const FF rt = ff_mul(dk, fp.logr);
+            T = ff_add(T, rt);
+            mg += fabsf(rt.hi) + fabsf(dk.hi);
+            const int dec = ff_guard_decide(ux, T, mg, tab);
+            if (dec == 0) {   // the test in FP64, as defined
+                if (!haveL) {
+                    const double r = p / (1.0 - p);
+                    logr = (r == 1.0) ? 0.0 : dlog(r, tab);
+                    l0 = log_fixed(M, tab);
+                    l1 = log_fixed(c - M, tab);
+                    haveL = true;
+                }
+                const double T64 = dsd_fixed(M, k, l0, tab) + dsd_fixed(c - M, c - k, l1, tab) +
+                                   (double)((int64_t)k - (int64_t)M) * logr;
+                ok = 2.0 * dlog(u_open(ux), tab) <= T64;
+            } else {
+                ok = dec > 0;
+            }
         }
         if (TL::first(ok, k, out)) return RS_OK;
     }

@@ -157,6 +157,48 @@ RS_DEV FF ff_sd(uint64_t P, uint64_t Q, const double* __restrict__ tab, float* m
     return P > Q ? ff_lfdiff(P, Q, tab, mag) : ff_neg(ff_lfdiff(Q, P, tab, mag));
 }
 
+// A ratio-of-uniforms node's parameters in float-float: the definition's
+// formulas (mean, variance, hat width h, alpha = mean + 1/2, and for the
+// binomial ln(p / (1 - p)) as a difference of two fixed-point logarithms)
+// with every operation in float-float.
+struct FFParams {
+    FF mu, alpha, h, logr;
+};
+RS_DEV FF ff_hat_width(FF var) {
+    const FF d1{1.715527773e+00f, -2.982028846e-09f};   // RS_HAT_D1 as two singles
+    const FF d2{8.989161849e-01f, -2.284329170e-08f};   // RS_HAT_D2
+    return ff_add(ff_mul(d1, ff_sqrt(ff_add(var, FF{0.5f, 0.0f}))), d2);
+}
+// Hypergeometric: a = min(n, K), b = max(n, K) after the reductions.
+RS_DEV FFParams ff_hg_params(uint64_t a, uint64_t b, uint64_t S) {
+    FFParams f;
+    const FF Sf = ff_from_u64(S);
+    f.mu = ff_div(ff_mul(ff_from_u64(a), ff_from_u64(b)), Sf);
+    const FF var = ff_mul(ff_mul(f.mu, ff_div(ff_from_u64(S - a), Sf)), ff_div(ff_from_u64(S - b), ff_from_u64(S - 1)));
+    f.h = ff_hat_width(var);
+    f.alpha = ff_add(f.mu, FF{0.5f, 0.0f});
+    f.logr = FF{0.0f, 0.0f};
+    return f;
+}
+// Binomial BIN(c, K / S), K / S <= 1/2.
+RS_DEV FFParams ff_bin_params(uint64_t c, uint64_t K, uint64_t S, const double* __restrict__ tab) {
+    FFParams f;
+    const FF pp = ff_div(ff_from_u64(K), ff_from_u64(S));
+    f.mu = ff_mul(ff_from_u64(c), pp);
+    f.h = ff_hat_width(ff_mul(f.mu, ff_sub(FF{1.0f, 0.0f}, pp)));
+    f.alpha = ff_add(f.mu, FF{0.5f, 0.0f});
+    f.logr = (2 * K == S) ? FF{0.0f, 0.0f} : ff_from_q57(ln_u64_q57(K, tab) - ln_u64_q57(S - K, tab));
+    return f;
+}
+// Whether the mean lies below 16 (inversion), from the float-float mean
+// where it is clear of 16: 1 yes, 0 no, -1 too close (the FP64 mean decides).
+RS_DEV int ff_mean_below_16(FF mu) {
+    const float m = ff_val(mu);
+    if (m < 15.999f) return 1;
+    if (m > 16.001f) return 0;
+    return -1;
+}
+
 // The second guard's margins (see the error model above).
 constexpr float kFFGuardEps = 0x1p-36f;
 constexpr float kFFGuardAbs = 0x1p-26f;

@@ -146,24 +146,10 @@ RS_DEV void setup64(RouNode* q, const double* __restrict__ tab) {
 // as a difference of two fixed-point logarithms (within 2^-54).
 template <bool WR>
 RS_DEV void setupff(RouNode* q, const double* __restrict__ tab) {
-    const FF half{0.5f, 0.0f};
-    const FF d1{1.715527773e+00f, -2.982028846e-09f};   // RS_HAT_D1 as two singles
-    const FF d2{8.989161849e-01f, -2.284329170e-08f};   // RS_HAT_D2
-    FF mu, var;
-    if (WR) {
-        const FF pp = ff_div(ff_from_u64(q->K), ff_from_u64(q->S));
-        mu = ff_mul(ff_from_u64(q->a), pp);
-        var = ff_mul(mu, ff_sub(FF{1.0f, 0.0f}, pp));
-        q->fflogr = (2 * q->K == q->S) ? FF{0.0f, 0.0f}
-                                       : ff_from_q57(ln_u64_q57(q->K, tab) - ln_u64_q57(q->S - q->K, tab));
-    } else {
-        const FF S = ff_from_u64(q->S);
-        mu = ff_div(ff_mul(ff_from_u64(q->a), ff_from_u64(q->b)), S);
-        var = ff_mul(ff_mul(mu, ff_div(ff_from_u64(q->S - q->a), S)),
-                     ff_div(ff_from_u64(q->S - q->b), ff_from_u64(q->S - 1)));
-    }
-    q->ffh = ff_add(ff_mul(d1, ff_sqrt(ff_add(var, half))), d2);
-    q->ffa = ff_add(mu, half);
+    const FFParams f = WR ? ff_bin_params(q->a, q->K, q->S, tab) : ff_hg_params(q->a, q->b, q->S);
+    q->ffa = f.alpha;
+    q->ffh = f.h;
+    q->fflogr = f.logr;
     q->haveff = true;
 }
 

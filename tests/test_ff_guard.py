@@ -9,7 +9,7 @@ rests on its evaluations being far closer than that to the exact values.
 Pinned here against mpmath on every argument regime of ln x! - ln y! (the
 table, the Stirling form against a table value, the series for ln(1 + d/y)
 and the difference of two fixed-point logarithms, up to 2^62) and on the
-nodes' alpha and h: the evaluations must stay within 2^-40 of their
+nodes' parameters (alpha, h, and the binomial log-odds): the evaluations must stay within 2^-40 of their
 magnitudes (plus 2^-30 for the single-precision Stirling tails)."""
 import math
 from fractions import Fraction
@@ -237,3 +237,34 @@ def test_ff_node_parameters_within_their_bound():
         for got, want in ((alpha, mu_x + mp.mpf(0.5)), (h, h_x)):
             g = mp.mpf(val(got).numerator) / val(got).denominator
             assert abs(g - want) <= mp.mpf(2) ** -40 * abs(want), (S, a, b, float(g), float(want))
+
+
+def test_ff_binomial_parameters_within_their_bound(table):
+    """alpha, h and ln(p / (1 - p)) of the binomial set-up in float-float
+    (ff_bin_params: p = K / S, mean c p, variance c p (1 - p), the log-odds
+    as a difference of two fixed-point logarithms), against exact values."""
+    mp.mp.dps = 60
+    rng = np.random.default_rng(38)
+    d1 = (f32(1.715527773e+00), f32(-2.982028846e-09))
+    d2 = (f32(8.989161849e-01), f32(-2.284329170e-08))
+    half = (f32(0.5), f32(0))
+    for _ in range(300):
+        S = int(np.exp(rng.uniform(np.log(4), np.log(2.0**62))))
+        K = int(rng.integers(1, S // 2 + 1))
+        c = max(1, int(np.exp(rng.uniform(0, np.log(2.0**62)))))
+        pp = ff_div(ff_from_u64(K), ff_from_u64(S))
+        mu = ff_mul(ff_from_u64(c), pp)
+        h = ff_add(ff_mul(d1, ff_sqrt(ff_add(ff_mul(mu, ff_sub((f32(1), f32(0)), pp)), half))), d2)
+        alpha = ff_add(mu, half)
+        logr = (f32(0), f32(0)) if 2 * K == S else ff_from_q57(ln_q57(K, table) - ln_q57(S - K, table))
+        p_x = mp.mpf(K) / S
+        mu_x = c * p_x
+        h_x = 2 * mp.sqrt(2 / mp.e) * mp.sqrt(mu_x * (1 - p_x) + mp.mpf(0.5)) + 3 - 2 * mp.sqrt(3 / mp.e)
+        lr_x = mp.log(mp.mpf(K)) - mp.log(mp.mpf(S - K))
+        for got, want in ((alpha, mu_x + mp.mpf(0.5)), (h, h_x)):
+            g = mp.mpf(val(got).numerator) / val(got).denominator
+            assert abs(g - want) <= mp.mpf(2) ** -40 * abs(want), (S, K, c, float(g), float(want))
+        g = mp.mpf(val(logr).numerator) / val(logr).denominator
+        # the log-odds enter the test times |k - M|; the guard's margin
+        # grants 2^-36 |k - M| for their error
+        assert abs(g - lr_x) <= mp.mpf(2) ** -44 * (1 + abs(lr_x)), (S, K, float(g), float(lr_x))
