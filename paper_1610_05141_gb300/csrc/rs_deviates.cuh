@@ -40,8 +40,10 @@ struct TrialLanes {
 };
 
 // HG(n, K, S): successes among n draws without replacement from S items
-// containing K successes.  Returns RS_OK or RS_EITER.
-template <bool WARP>
+// containing K successes.  Returns RS_OK or RS_EITER.  INV: the caller has
+// found the mean below 16 (by the same decision), so only inversion is
+// compiled in.
+template <bool WARP, bool INV = false>
 RS_DEV int hypergeometric_t(Key2 key, uint64_t node, uint64_t n, uint64_t K, uint64_t S,
                             const double* __restrict__ tab, uint64_t& out) {
     using TL = TrialLanes<WARP>;
@@ -58,8 +60,8 @@ RS_DEV int hypergeometric_t(Key2 key, uint64_t node, uint64_t n, uint64_t K, uin
     const uint64_t b = n < K ? K : n;
     // the parameters in float-float for the guards (rs_ff.cuh); the FP64
     // ones, as defined, only where a guard leaves a decision open
-    const FFParams fp = ff_hg_params(a, b, S);
-    int below = ff_mean_below_16(fp.mu);
+    const FFParams fp = INV ? FFParams{} : ff_hg_params(a, b, S);
+    int below = INV ? 1 : ff_mean_below_16(fp.mu);
     if (below < 0) below = ((double)a * (double)b) * drecip((double)S) < 16.0;
     uint64_t y = 0;
     bool done = false;
@@ -146,14 +148,14 @@ RS_DEV int hypergeometric_t(Key2 key, uint64_t node, uint64_t n, uint64_t K, uin
 }
 
 // BIN(c, p = K/S) with K/S <= 1/2.  Returns RS_OK or RS_EITER.
-template <bool WARP>
+template <bool WARP, bool INV = false>
 RS_DEV int binomial_t(Key2 key, uint64_t node, uint64_t c, uint64_t K, uint64_t S,
                       const double* __restrict__ tab, uint64_t& out) {
     using TL = TrialLanes<WARP>;
     if (c == 0 || K == 0) { out = 0; return RS_OK; }
     const double p = (double)K / (double)S;
-    const FFParams fp = ff_bin_params(c, K, S, tab);
-    int below = ff_mean_below_16(fp.mu);
+    const FFParams fp = INV ? FFParams{} : ff_bin_params(c, K, S, tab);
+    int below = INV ? 1 : ff_mean_below_16(fp.mu);
     if (below < 0) below = (double)c * p < 16.0;
     if (below) {
         const double f0 = dexp((double)c * dlog1p(-p, tab));
@@ -241,6 +243,15 @@ RS_DEV int binomial(Key2 key, uint64_t node, uint64_t c, uint64_t K, uint64_t S,
 RS_DEV int binomial_warp(Key2 key, uint64_t node, uint64_t c, uint64_t K, uint64_t S,
                          const double* __restrict__ tab, uint64_t& out) {
     return binomial_t<true>(key, node, c, K, S, tab, out);
+}
+// The inversion paths alone, for callers that have found the mean below 16.
+RS_DEV int hypergeometric_inversion(Key2 key, uint64_t node, uint64_t n, uint64_t K, uint64_t S,
+                                    const double* __restrict__ tab, uint64_t& out) {
+    return hypergeometric_t<false, true>(key, node, n, K, S, tab, out);
+}
+RS_DEV int binomial_inversion(Key2 key, uint64_t node, uint64_t c, uint64_t K, uint64_t S,
+                              const double* __restrict__ tab, uint64_t& out) {
+    return binomial_t<false, true>(key, node, c, K, S, tab, out);
 }
 
 }  // namespace rs

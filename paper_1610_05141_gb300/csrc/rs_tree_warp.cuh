@@ -246,7 +246,8 @@ RS_DEV bool node_setup(NodeRec* __restrict__ rec, uint64_t v, Key2 key, const do
     }
     if (inversion) {
         uint64_t L = 0;
-        const int rc = WR ? binomial(key, v, r.c, K, r.S, tab, L) : hypergeometric(key, v, r.c, K, r.S, tab, L);
+        const int rc = WR ? binomial_inversion(key, v, r.c, K, r.S, tab, L)
+                          : hypergeometric_inversion(key, v, r.c, K, r.S, tab, L);
         if (rc != RS_OK) { set_status(status, rc); L = 0; }
         return finish(L);
     }
