@@ -85,6 +85,7 @@ struct HashShared {
     uint32_t overflow;             // probing ran past the slack
     uint64_t jnext;                // bucket path: index of the candidate after the k-th valid one
     uint32_t nadded;               // bucket path: values drawn after a repeat
+    uint32_t fill;                 // bucket path, leaves with void candidates: values kept so far
     uint32_t repair_fail;
     uint32_t ranksum;              // bucket path: sum of the keys' ranks (k (k - 1) / 2 without ties)
     uint64_t thr;                  // Lemire rejection threshold of the leaf
@@ -473,78 +474,80 @@ RS_COLD bool bucket_ties(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, K
 // Pass 1 of the bucket path for leaves with void candidates (sizes that are
 // not powers of two): the first k valid candidates to A[0..k) (in no
 // particular order: later passes only need the set), counted per bucket,
-// sm.jnext set to the index after the k-th.  Rounds of up to q Philox blocks
-// per thread, contiguous so that a thread's candidates are in index order:
-// the values are staged in B (not yet in use) transposed, candidate p of
-// thread t at B[p NT + t], so that a warp's stores and loads hit 32 banks;
-// one block scan numbers the valid ones in index order and the first k are
-// kept, each warp writing its kept values to consecutive slots of A (the
-// warp's slots start where the scan puts its first lane).  A round covers
-// the missing values plus an eighth, within B's room, so most leaves need
-// one round and one scan.  False if the stream runs out.
+// sm.jnext set to the index after the k-th.  Round r takes the next m_r
+// candidates of the stream, m_r the number of values still missing (m_0 =
+// k), and keeps every valid one: a round can never take more than are
+// missing, so after the last round A holds exactly the first k valid
+// candidates, with no ordering or scan.  Each warp appends its valid values
+// at a shared fill counter (one atomic per warp and Philox round).  Void
+// candidates are rare unless the leaf size is near a power of two from
+// above (up to half of them void), so most leaves need one or two rounds.
+// False if the stream runs out.
 template <typename KeyT, int NT, int BAR, uint32_t CAP, typename K2>
 RS_COLD bool void_leaf_pass1(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, const K2& key, uint32_t tag,
                              uint32_t k, uint64_t thr, uint64_t mult, KeyT* A, KeyT* B, uint32_t* cw, uint32_t tid) {
-    static_assert(CAP + 61 >= 16 * NT, "B's room must take four rounds of blocks per thread");
     const bool w32 = r.s <= (1ull << 32);
-    const uint32_t cpb = w32 ? 4u : 2u;
-    const uint32_t qmax = 32u / cpb;   // a thread's candidates fit one 32-bit mask
-    const uint32_t room = HashShared<KeyT, NT / 32, CAP>::kSlots - ((k + 3) & ~3u);
-    const uint32_t qcap = min(qmax, room / (cpb * NT));   // >= 4
+    const uint32_t lg = w32 ? 2u : 1u;   // candidates per Philox block: 2^lg
     const uint32_t lane = tid & 31;
     const uint32_t lt = (1u << lane) - 1u;
+    // candidates come from blocks below the stream's limit (and 2^32)
+    const uint64_t jcap = min((uint64_t)c_caps.stream_blocks, (uint64_t)1 << 32) << lg;
+    uint64_t J = 0;   // next candidate index
     uint32_t got = 0;
-    for (uint64_t b0 = 0; got < k;) {
-        if (b0 >= c_caps.stream_blocks) return false;   // the stream ran out: the probing path reports it
-        const uint32_t m = k - got;
-        const uint32_t want = (m + m / 8 + 32 + cpb - 1) / cpb;
-        const uint32_t nbk = min(want, (uint32_t)NT * qcap);
-        const uint32_t q = (nbk + NT - 1) / NT;
-        const uint32_t t0 = tid * q;   // this thread's first block of the round
-        uint32_t mask = 0;
-        for (uint32_t u = 0; u < q; ++u) {
-            const uint64_t blk = b0 + t0 + u;
-            if (t0 + u >= nbk || blk >= (1ull << 32)) break;
-            const uint4 w = philox_block((uint32_t)blk, tag, r.id, key);
-            if (w32) {
-                const uint32_t s32 = (uint32_t)(r.s - 1), thr32 = (uint32_t)thr;
-                const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+    while (got < k) {   // the same in all threads
+        if (J >= jcap) return false;   // the stream ran out: the probing path reports it
+        const uint64_t jend = min(J + (uint64_t)(k - got), jcap);
+        const uint64_t bfirst = J >> lg;
+        const uint32_t nbr = (uint32_t)(((jend - 1) >> lg) - bfirst + 1);
+        for (uint32_t i0 = tid - lane; i0 < nbr; i0 += NT) {   // warp-uniform trips
+            const uint32_t i = i0 + lane;
+            const uint64_t blk = bfirst + i;
+            KeyT v[4] = {0, 0, 0, 0};
+            uint32_t ok = 0;   // bit c: candidate (blk << lg) + c is valid and in [J, jend)
+            if (i < nbr) {
+                const uint4 w = philox_block((uint32_t)blk, tag, r.id, key);
+                if (w32) {
+                    const uint32_t s32 = (uint32_t)(r.s - 1), thr32 = (uint32_t)thr;
+                    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const uint64_t prod = (uint64_t)ws[c] * s32 + ws[c];   // w * s, exact
-                    B[(u * 4 + c) * NT + tid] = (KeyT)(prod >> 32);
-                    mask |= ((uint32_t)prod >= thr32 ? 1u : 0u) << (u * 4 + c);
-                }
-            } else {
-                const uint64_t xs[2] = {((uint64_t)w.y << 32) | w.x, ((uint64_t)w.w << 32) | w.z};
+                    for (int c = 0; c < 4; ++c) {
+                        const uint64_t prod = (uint64_t)ws[c] * s32 + ws[c];   // w * s, exact
+                        const uint64_t j = (blk << 2) + c;
+                        v[c] = (KeyT)(prod >> 32);
+                        ok |= ((uint32_t)prod >= thr32 && j >= J && j < jend ? 1u : 0u) << c;
+                    }
+                } else {
+                    const uint64_t xs[2] = {((uint64_t)w.y << 32) | w.x, ((uint64_t)w.w << 32) | w.z};
 #pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    B[(u * 2 + c) * NT + tid] = (KeyT)__umul64hi(xs[c], r.s);
-                    mask |= (xs[c] * r.s >= thr ? 1u : 0u) << (u * 2 + c);
+                    for (int c = 0; c < 2; ++c) {
+                        const uint64_t j = (blk << 1) + c;
+                        v[c] = (KeyT)__umul64hi(xs[c], r.s);
+                        ok |= (xs[c] * r.s >= thr && j >= J && j < jend ? 1u : 0u) << c;
+                    }
                 }
             }
+            const uint32_t q0 = __ballot_sync(0xFFFFFFFFu, ok & 1u), q1 = __ballot_sync(0xFFFFFFFFu, ok & 2u);
+            const uint32_t q2 = __ballot_sync(0xFFFFFFFFu, ok & 4u), q3 = __ballot_sync(0xFFFFFFFFu, ok & 8u);
+            const uint32_t tot = __popc(q0) + __popc(q1) + __popc(q2) + __popc(q3);
+            uint32_t base = 0;
+            if (lane == 0 && tot) base = atomicAdd(&sm.fill, tot);
+            uint32_t pos = __shfl_sync(0xFFFFFFFFu, base, 0) + __popc(q0 & lt) + __popc(q1 & lt) +
+                           __popc(q2 & lt) + __popc(q3 & lt);
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if ((ok >> c) & 1u) {
+                    A[pos++] = v[c];
+                    const uint32_t b = hash_slot(v[c], mult);
+                    atomicAdd(&cw[b >> 1], 1u << ((b & 1u) << 4));
+                }
         }
-        uint32_t total;
-        uint32_t rank = got + block_exclusive_scan<NT>((uint32_t)__popc(mask), sm.scan_tmp, &total);
-        // the warp's kept values go to A[wslot ..): its lanes' valid
-        // candidates with rank < k, in (candidate, lane) order
-        uint32_t wslot = min(k, __shfl_sync(0xFFFFFFFFu, rank, 0));
-        for (uint32_t p = 0; p < q * cpb; ++p) {
-            const bool kp = ((mask >> p) & 1u) && rank < k;
-            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, kp);
-            if (kp) {
-                const KeyT v = B[p * NT + tid];
-                A[wslot + __popc(bal & lt)] = v;
-                const uint32_t b = hash_slot(v, mult);
-                atomicAdd(&cw[b >> 1], 1u << ((b & 1u) << 4));
-                if (rank == k - 1) sm.jnext = (b0 + t0) * cpb + p + 1;
-            }
-            rank += (mask >> p) & 1u;
-            wslot += __popc(bal);
-        }
-        got += total;
-        b0 += nbk;
-        if (got < k) group_sync<BAR, NT>();   // the next round stages over other threads' slots
+        group_sync<BAR, NT>();
+        const uint32_t now = sm.fill;
+        // every candidate of the last round was valid: the k-th is jend - 1
+        if (now == k && tid == 0) sm.jnext = jend;
+        got = now;
+        J = jend;
+        if (got < k) group_sync<BAR, NT>();   // every thread has read the count before the next round adds
     }
     return true;
 }
@@ -579,6 +582,7 @@ RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, co
         } else {
             sm.mult = slot_mult_fast<KeyT>(r.s, nb);
             sm.thr = lemire_threshold(r.s);
+            sm.fill = 0;
         }
     }
     group_sync<BAR, NT>();
