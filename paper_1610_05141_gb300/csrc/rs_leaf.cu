@@ -153,18 +153,7 @@ cudaError_t launch_leaves(const LeafLaunch& L, cudaStream_t st) {
                   : launch_shape<false, kHashThreads, kLeafFastCap>(job, L, st);
     if (e != cudaSuccess) return e;
     if (L.big_kmax == 0) return cudaSuccess;   // no leaf can exceed the capacity
-    BigScratch sc;
-    uint64_t kmax = L.big_kmax;
-    uint64_t tmax = 32;
-    while (tmax < kmax) tmax <<= 1;
-    unsigned char* p = static_cast<unsigned char*>(L.big_pool);
-    sc.keys = reinterpret_cast<uint64_t*>(p); p += kmax * 8;
-    sc.cand = reinterpret_cast<uint64_t*>(p); p += kmax * 8;
-    sc.tmp = reinterpret_cast<uint64_t*>(p); p += kmax * 8;
-    sc.bkt = reinterpret_cast<uint32_t*>(p); p += kmax * 4;
-    sc.arr = reinterpret_cast<uint32_t*>(p); p += kmax * 4;
-    sc.cnt = reinterpret_cast<uint32_t*>(p);
-    sc.kmax = kmax;
+    const BigScratch sc = carve_big_scratch(L.big_pool, L.big_kmax);
     if (L.with_replacement) big_leaf_kernel<true><<<1, kBigThreads, 0, st>>>(job, sc);
     else big_leaf_kernel<false><<<1, kBigThreads, 0, st>>>(job, sc);
     return cudaGetLastError();
