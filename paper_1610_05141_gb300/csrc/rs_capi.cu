@@ -279,6 +279,7 @@ int sample_impl(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0,
         L.big_kmax = big_kmax;
         L.cap = ctx->leaf_cap;
         L.mean_count = n >> D;
+        L.pow2_leaves = (N & (nleaves - 1)) == 0 && (smax & (smax - 1)) == 0;
         L.sms = ctx->sms;
         L.with_replacement = wr;
     }

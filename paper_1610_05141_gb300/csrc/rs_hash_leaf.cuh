@@ -85,7 +85,8 @@ struct HashShared {
     uint32_t overflow;             // probing ran past the slack
     uint64_t jnext;                // bucket path: index of the candidate after the k-th valid one
     uint32_t nadded;               // bucket path: values drawn after a repeat
-    uint32_t fill;                 // bucket path, leaves with void candidates: values kept so far
+    uint32_t fill;                 // bucket path, leaves with void candidates: holes left by round 1
+    uint32_t fill2;                //   and holes filled by the later rounds
     uint32_t repair_fail;
     uint32_t ranksum;              // bucket path: sum of the keys' ranks (k (k - 1) / 2 without ties)
     uint64_t thr;                  // Lemire rejection threshold of the leaf
@@ -471,32 +472,28 @@ RS_COLD bool bucket_ties(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, K
     return bucket_repair<KeyT, NT, BAR, CAP>(sm, r, key, k, thr, A, B, dst, tid);   // rewrites the whole leaf
 }
 
-// Pass 1 of the bucket path for leaves with void candidates (sizes that are
-// not powers of two): the first k valid candidates to A[0..k) (in no
-// particular order: later passes only need the set), counted per bucket,
-// sm.jnext set to the index after the k-th.  Round r takes the next m_r
-// candidates of the stream, m_r the number of values still missing (m_0 =
-// k), and keeps every valid one: a round can never take more than are
-// missing, so after the last round A holds exactly the first k valid
-// candidates, with no ordering or scan.  Each warp appends its valid values
-// at a shared fill counter (one atomic per warp and Philox round).  Void
-// candidates are rare unless the leaf size is near a power of two from
-// above (up to half of them void), so most leaves need one or two rounds.
-// False if the stream runs out.
+// The later rounds of the void-candidate pass 1: fill the nh holes listed in
+// B's room from candidates k, k + 1, ... (see void_leaf_pass1).
 template <typename KeyT, int NT, int BAR, uint32_t CAP, typename K2>
-RS_COLD bool void_leaf_pass1(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, const K2& key, uint32_t tag,
-                             uint32_t k, uint64_t thr, uint64_t mult, KeyT* A, KeyT* B, uint32_t* cw, uint32_t tid) {
+__device__ __forceinline__ bool fill_holes(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, const K2& key,
+                                           uint32_t tag, uint32_t k, uint32_t nh, uint64_t thr, uint64_t mult, KeyT* A,
+                                           KeyT* B, uint32_t* cw, uint32_t tid) {
     const bool w32 = r.s <= (1ull << 32);
-    const uint32_t lg = w32 ? 2u : 1u;   // candidates per Philox block: 2^lg
+    const uint32_t lg = w32 ? 2u : 1u;
+    const uint64_t jcap = min((uint64_t)c_caps.stream_blocks, (uint64_t)1 << 32) << lg;
+    const uint32_t* H = reinterpret_cast<const uint32_t*>(B);
+    auto count = [&](KeyT v) {
+        const uint32_t b = hash_slot(v, mult);
+        atomicAdd(&cw[b >> 1], 1u << ((b & 1u) << 4));
+    };
+    // later rounds: fill the holes from candidates k, k + 1, ...
     const uint32_t lane = tid & 31;
     const uint32_t lt = (1u << lane) - 1u;
-    // candidates come from blocks below the stream's limit (and 2^32)
-    const uint64_t jcap = min((uint64_t)c_caps.stream_blocks, (uint64_t)1 << 32) << lg;
-    uint64_t J = 0;   // next candidate index
+    uint64_t J = k;   // next candidate index
     uint32_t got = 0;
-    while (got < k) {   // the same in all threads
-        if (J >= jcap) return false;   // the stream ran out: the probing path reports it
-        const uint64_t jend = min(J + (uint64_t)(k - got), jcap);
+    while (got < nh) {   // the same in all threads
+        if (J >= jcap) return false;
+        const uint64_t jend = min(J + (uint64_t)(nh - got), jcap);
         const uint64_t bfirst = J >> lg;
         const uint32_t nbr = (uint32_t)(((jend - 1) >> lg) - bfirst + 1);
         for (uint32_t i0 = tid - lane; i0 < nbr; i0 += NT) {   // warp-uniform trips
@@ -511,7 +508,7 @@ RS_COLD bool void_leaf_pass1(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& 
                     const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
-                        const uint64_t prod = (uint64_t)ws[c] * s32 + ws[c];   // w * s, exact
+                        const uint64_t prod = (uint64_t)ws[c] * s32 + ws[c];
                         const uint64_t j = (blk << 2) + c;
                         v[c] = (KeyT)(prod >> 32);
                         ok |= ((uint32_t)prod >= thr32 && j >= J && j < jend ? 1u : 0u) << c;
@@ -530,32 +527,125 @@ RS_COLD bool void_leaf_pass1(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& 
             const uint32_t q2 = __ballot_sync(0xFFFFFFFFu, ok & 4u), q3 = __ballot_sync(0xFFFFFFFFu, ok & 8u);
             const uint32_t tot = __popc(q0) + __popc(q1) + __popc(q2) + __popc(q3);
             uint32_t base = 0;
-            if (lane == 0 && tot) base = atomicAdd(&sm.fill, tot);
+            if (lane == 0 && tot) base = atomicAdd(&sm.fill2, tot);
             uint32_t pos = __shfl_sync(0xFFFFFFFFu, base, 0) + __popc(q0 & lt) + __popc(q1 & lt) +
                            __popc(q2 & lt) + __popc(q3 & lt);
 #pragma unroll
             for (int c = 0; c < 4; ++c)
                 if ((ok >> c) & 1u) {
-                    A[pos++] = v[c];
-                    const uint32_t b = hash_slot(v[c], mult);
-                    atomicAdd(&cw[b >> 1], 1u << ((b & 1u) << 4));
+                    A[H[pos++]] = v[c];
+                    count(v[c]);
                 }
         }
         group_sync<BAR, NT>();
-        const uint32_t now = sm.fill;
+        const uint32_t now = sm.fill2;
         // every candidate of the last round was valid: the k-th is jend - 1
-        if (now == k && tid == 0) sm.jnext = jend;
+        if (now == nh && tid == 0) sm.jnext = jend;
         got = now;
         J = jend;
-        if (got < k) group_sync<BAR, NT>();   // every thread has read the count before the next round adds
+        if (got < nh) group_sync<BAR, NT>();   // every thread has read the count before the next round adds
     }
     return true;
+}
+
+// Pass 1 of the bucket path for leaves with void candidates (sizes that are
+// not powers of two): the first k valid candidates to A[0..k) (in no
+// particular order: later passes only need the set), counted per bucket,
+// sm.jnext set to the index after the k-th.  Round 1 runs as on the
+// power-of-two path: candidate j of [0, k) goes to A[j] (16-byte stores),
+// by Lemire's map (w s) >> width; a void one leaves a hole, listed in B's
+// room (not yet in use).  Void candidates are rare unless the leaf size is
+// just above a power of two (up to half of them), so most leaves end here.
+// Later rounds fill the h holes: round r takes the next m_r candidates of
+// the stream, m_r the holes still open, and puts every valid one into a
+// hole; a round can never take more values than are missing, so after the
+// last one A holds exactly the first k valid candidates, with no ordering
+// or scan.  False if the stream runs out.
+template <typename KeyT, int NT, int BAR, uint32_t CAP, typename K2>
+RS_COLD bool void_leaf_pass1(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, const K2& key, uint32_t tag,
+                             uint32_t k, uint64_t thr, uint64_t mult, KeyT* A, KeyT* B, uint32_t* cw, uint32_t tid) {
+    const bool w32 = r.s <= (1ull << 32);
+    const uint32_t lg = w32 ? 2u : 1u;   // candidates per Philox block: 2^lg
+    // candidates come from blocks below the stream's limit (and 2^32)
+    const uint64_t jcap = min((uint64_t)c_caps.stream_blocks, (uint64_t)1 << 32) << lg;
+    if (k > jcap) return false;   // the stream ran out: the probing path reports it
+    uint32_t* H = reinterpret_cast<uint32_t*>(B);   // the holes (B holds k + 3 keys)
+    auto count = [&](KeyT v) {
+        const uint32_t b = hash_slot(v, mult);
+        atomicAdd(&cw[b >> 1], 1u << ((b & 1u) << 4));
+    };
+    auto put = [&](uint32_t j, KeyT v, bool ok) {   // candidate j already in A[j]
+        if (ok) count(v);
+        else H[atomicAdd(&sm.fill, 1u)] = j;
+    };
+    // round 1: candidates [0, k)
+    if (w32) {
+        const uint32_t s32 = (uint32_t)(r.s - 1), thr32 = (uint32_t)thr;
+        const uint32_t full = k >> 2;   // Philox blocks whose four words are all used
+        for (uint32_t i = tid; i < full; i += NT) {
+            const uint4 w = philox_block(i, tag, r.id, key);
+            // w * s = w * (s - 1) + w, exact in 64 bits; valid when its low word >= thr
+            const uint64_t p0 = (uint64_t)w.x * s32 + w.x, p1 = (uint64_t)w.y * s32 + w.y;
+            const uint64_t p2 = (uint64_t)w.z * s32 + w.z, p3 = (uint64_t)w.w * s32 + w.w;
+            const uint4 v = make_uint4((uint32_t)(p0 >> 32), (uint32_t)(p1 >> 32), (uint32_t)(p2 >> 32),
+                                       (uint32_t)(p3 >> 32));
+            if (sizeof(KeyT) == 4) {
+                reinterpret_cast<uint4*>(A)[i] = v;   // one 16-byte store (A is 16-byte aligned)
+            } else {
+                A[4 * i] = v.x;
+                A[4 * i + 1] = v.y;
+                A[4 * i + 2] = v.z;
+                A[4 * i + 3] = v.w;
+            }
+            put(4 * i, (KeyT)v.x, (uint32_t)p0 >= thr32);
+            put(4 * i + 1, (KeyT)v.y, (uint32_t)p1 >= thr32);
+            put(4 * i + 2, (KeyT)v.z, (uint32_t)p2 >= thr32);
+            put(4 * i + 3, (KeyT)v.w, (uint32_t)p3 >= thr32);
+        }
+        if (tid == 0 && (k & 3u)) {
+            const uint4 w = philox_block(full, tag, r.id, key);
+            const uint32_t ws[3] = {w.x, w.y, w.z};
+            for (uint32_t c = 0; c < (k & 3u); ++c) {
+                const uint64_t p = (uint64_t)ws[c] * s32 + ws[c];
+                A[4 * full + c] = (KeyT)(p >> 32);
+                put(4 * full + c, (KeyT)(p >> 32), (uint32_t)p >= thr32);
+            }
+        }
+    } else {
+        const uint32_t full = k >> 1;
+        for (uint32_t i = tid; i < full; i += NT) {
+            const uint4 w = philox_block(i, tag, r.id, key);
+            const uint64_t x0 = ((uint64_t)w.y << 32) | w.x, x1 = ((uint64_t)w.w << 32) | w.z;
+            const KeyT v0 = (KeyT)__umul64hi(x0, r.s), v1 = (KeyT)__umul64hi(x1, r.s);
+            A[2 * i] = v0;
+            A[2 * i + 1] = v1;
+            put(2 * i, v0, x0 * r.s >= thr);
+            put(2 * i + 1, v1, x1 * r.s >= thr);
+        }
+        if (tid == 0 && (k & 1u)) {
+            const uint4 w = philox_block(full, tag, r.id, key);
+            const uint64_t x0 = ((uint64_t)w.y << 32) | w.x;
+            const KeyT v0 = (KeyT)__umul64hi(x0, r.s);
+            A[2 * full] = v0;
+            put(2 * full, v0, x0 * r.s >= thr);
+        }
+    }
+    group_sync<BAR, NT>();
+    const uint32_t nh = sm.fill;   // the same in all threads
+    if (nh == 0) {
+        if (tid == 0) sm.jnext = k;
+        return true;
+    }
+    return fill_holes<KeyT, NT, BAR, CAP>(sm, r, key, tag, k, nh, thr, mult, A, B, cw, tid);
 }
 
 // Bucket path.  Returns true on success (leaf written), false if the leaf
 // must take the probing path (whatever was written is overwritten later).
 // K2 is Key2 or RoundKeys (the same generator, round keys precomputed).
-template <typename KeyT, int NT, int BAR, bool WR, uint32_t CAP = kHashCap, typename K2 = Key2>
+// POW2: the caller knows every leaf size to be a power of two, so the code
+// for void candidates is left out (a leaf of another size then returns
+// false and takes the probing path).
+template <typename KeyT, int NT, int BAR, bool WR, uint32_t CAP = kHashCap, typename K2 = Key2, bool POW2 = false>
 RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, const K2& key, uint32_t k,
                         uint64_t* __restrict__ dst, uint32_t tid) {
     static_assert(HashShared<KeyT, NT / 32, CAP>::kBuckets <= 24 * NT, "scan_counts16 takes at most 24 NT counts");
@@ -583,6 +673,7 @@ RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, co
             sm.mult = slot_mult_fast<KeyT>(r.s, nb);
             sm.thr = lemire_threshold(r.s);
             sm.fill = 0;
+            sm.fill2 = 0;
         }
     }
     group_sync<BAR, NT>();
@@ -595,7 +686,8 @@ RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, co
         const uint32_t b = hash_slot((KeyT)v, mult);
         atomicAdd(&cw[b >> 1], 1u << ((b & 1u) << 4));
     };
-    if (thr == 0) {
+    if (POW2 && thr != 0) return false;   // not a power of two after all
+    if (POW2 || thr == 0) {
         // No candidate can be void (the leaf size is a power of two 2^t, the
         // only sizes that divide 2^32 or 2^64): candidates [0, k) are the
         // first k valid ones and Lemire's map (w s) >> width is w >> (width - t).
@@ -940,7 +1032,7 @@ RS_COLD bool probe_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, Ke
 // false if the leaf must go to the general (global-memory) path, having
 // written nothing of use.  All NT threads of the group call it; tid is the
 // thread's index in the group.
-template <typename KeyT, int NT, int BAR, bool WR, uint32_t CAP = kHashCap, typename K2 = Key2>
+template <typename KeyT, int NT, int BAR, bool WR, uint32_t CAP = kHashCap, typename K2 = Key2, bool POW2 = false>
 RS_DEV bool hash_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, const K2& key, uint64_t* __restrict__ out,
                       int* status, uint32_t tid, uint32_t cap) {
     const bool comp = !WR && (r.np > r.s - r.np);
@@ -959,7 +1051,7 @@ RS_DEV bool hash_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, cons
         bitmap_leaf<KeyT, NT, BAR, CAP>(sm, r, key, k, comp, dst, status, tid);
         return true;
     }
-    if (bucket_leaf<KeyT, NT, BAR, WR, CAP>(sm, r, key, k, dst, tid)) return true;
+    if (bucket_leaf<KeyT, NT, BAR, WR, CAP, K2, POW2>(sm, r, key, k, dst, tid)) return true;
     return probe_leaf<KeyT, NT, BAR, WR, CAP>(sm, r, key, k, dst, status, tid);
 }
 

@@ -57,6 +57,7 @@ struct LeafLaunch {
     bool with_replacement;
     int blocks_per_sm = 0;   // leaf-kernel blocks per SM, 0 = as many as fit
     uint64_t mean_count = 0; // samples per leaf on average (picks the kernel's shape)
+    bool pow2_leaves = false; // every leaf has the size smax, a power of two
 };
 
 // Leaf H (or leaf WR) for every leaf, then the general path for the leaves

@@ -49,7 +49,7 @@ RS_DEV void prefetch_record(NodeRec* dst, const NodeRec* src) {
 }
 RS_DEV void prefetch_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-template <typename KeyT, bool WR, int NT, uint32_t CAP>
+template <typename KeyT, bool WR, int NT, uint32_t CAP, bool POW2>
 __global__ void __launch_bounds__(NT, 1024 / NT) leaf_kernel(const __grid_constant__ LeafJob job) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto& sm = *reinterpret_cast<HashShared<KeyT, NT / 32, CAP>*>(smem_raw);
@@ -69,7 +69,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) leaf_kernel(const __grid_consta
             prefetch_record(&recbuf[par ^ 1u], &job.leaves[leaf + gridDim.x]);
         if (r.c != 0) {
             const LeafRec lr{r.lo, r.S, r.c, r.off, job.first_id + leaf};
-            if (!hash_leaf<KeyT, NT, 0, WR, CAP>(sm, lr, job.rk, job.out, job.status, threadIdx.x, job.cap)) {
+            if (!hash_leaf<KeyT, NT, 0, WR, CAP, RoundKeys, POW2>(sm, lr, job.rk, job.out, job.status, threadIdx.x,
+                                                                 job.cap)) {
                 if (threadIdx.x == 0) job.ovf_list[atomicAdd(job.ovf_count, 1u)] = (uint32_t)leaf;
             }
         }
@@ -115,11 +116,11 @@ __global__ void __launch_bounds__(kBigThreads) big_leaf_kernel(LeafJob job, BigS
 // Host launchers.
 // ---------------------------------------------------------------------------
 
-template <typename KeyT, bool WR, int NT, uint32_t CAP>
+template <typename KeyT, bool WR, int NT, uint32_t CAP, bool POW2>
 static cudaError_t launch_fast(LeafJob job, uint32_t cap_knob, int sms, int per_sm_cap, cudaStream_t st) {
     job.cap = cap_knob ? std::min<uint32_t>(cap_knob, CAP) : CAP;
     const size_t smem = sizeof(HashShared<KeyT, NT / 32, CAP>);
-    auto kern = leaf_kernel<KeyT, WR, NT, CAP>;
+    auto kern = leaf_kernel<KeyT, WR, NT, CAP, POW2>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -132,10 +133,18 @@ static cudaError_t launch_fast(LeafJob job, uint32_t cap_knob, int sms, int per_
     return cudaGetLastError();
 }
 
+// Launches whose leaves all have the same power-of-two size (N a power of
+// two times the leaf count, as in the benchmark's 2^50) take a kernel
+// without the code for void candidates, which would otherwise cost the
+// power-of-two path registers and time.
 template <bool WR, int NT, uint32_t CAP>
 static cudaError_t launch_shape(const LeafJob& job, const LeafLaunch& L, cudaStream_t st) {
-    if (L.smax <= (1ull << 32)) return launch_fast<uint32_t, WR, NT, CAP>(job, L.cap, L.sms, L.blocks_per_sm, st);
-    return launch_fast<uint64_t, WR, NT, CAP>(job, L.cap, L.sms, L.blocks_per_sm, st);
+    if (L.smax <= (1ull << 32)) {
+        if (L.pow2_leaves) return launch_fast<uint32_t, WR, NT, CAP, true>(job, L.cap, L.sms, L.blocks_per_sm, st);
+        return launch_fast<uint32_t, WR, NT, CAP, false>(job, L.cap, L.sms, L.blocks_per_sm, st);
+    }
+    if (L.pow2_leaves) return launch_fast<uint64_t, WR, NT, CAP, true>(job, L.cap, L.sms, L.blocks_per_sm, st);
+    return launch_fast<uint64_t, WR, NT, CAP, false>(job, L.cap, L.sms, L.blocks_per_sm, st);
 }
 
 cudaError_t launch_leaves(const LeafLaunch& L, cudaStream_t st) {

@@ -100,6 +100,7 @@ extern "C" int rs_sample_static(uint64_t n, uint64_t N, uint64_t seed, uint32_t 
     L.big_kmax = bound > 64 ? std::min<uint64_t>(bound, kStaticBigKeys) : 0;
     L.cap = 0;
     L.mean_count = n >> D;   // picks the leaf kernel's shape as rs_sample does (both use shared memory only)
+    L.pow2_leaves = (N & (nleaves - 1)) == 0 && (smax & (smax - 1)) == 0;
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return RS_ECUDA;
     L.sms = sms;

@@ -65,6 +65,7 @@ H_CASES = [
     (2 * 10**5, (2**31 + 12345) * 64, 31, 4096),   # leaves just above 2^31: half the candidates void
     (4000, 2**61 + 999, 33, 4096),                 # one leaf, 64-bit candidates, an eighth void
     (256000, 20480000, 41, 4096),                  # leaves of 320000 positions: ~25 repeats each
+    (256000, (2**22 + 12345) * 64, 43, 4096),      # ~4 void candidates and ~2 repeats per leaf
 ]
 
 
