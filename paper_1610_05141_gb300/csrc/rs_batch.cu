@@ -249,10 +249,12 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 // Leaf groups: kind (H, WR) x key width x size class (the large class:
-// leaves averaging more than the 256-thread shape comfortably holds), and
-// Algorithm B (group 4).
-int group_of(int kind, bool wide, bool large) {
+// leaves averaging more than the 256-thread shape comfortably holds),
+// Algorithm B (group 4), and for requests with 64-bit keys and small means
+// the compact table (groups 9 and 10).
+int group_of(int kind, bool wide, bool large, bool compact = false) {
     if (kind == RS_KIND_B) return 4;
+    if (compact && wide && !large) return 9 + kind;
     return kind * 2 + (wide ? 1 : 0) + (large ? 5 : 0);
 }
 bool large_class(uint64_t mean_count) { return mean_count * 20 > (uint64_t)kLeafFastCap * 17; }
@@ -300,12 +302,26 @@ void leaf_flavour(bool wide, bool wr, void (**kern)(View, uint32_t*, uint32_t*, 
     *cap = CAP;
 }
 
-// One leaf kernel (+ the general path) over the leaves of a view; `threads`
-// picks the shape (256 or 512).
+// The compact 64-bit-key shape (256 threads, room for kCompact64Cap
+// values), built for request groups only.
 template <class View>
-int issue_leaves(const View& V, int kind, bool wide, int threads, uint32_t* ovf, uint32_t* ovf_count, void* big,
-                 uint64_t big_kmax, int per_sm_cap, bool persistent, const double* tab, int sms, cudaStream_t st,
-                 uint64_t* nl) {
+void compact_flavour(bool wr, void (**kern)(View, uint32_t*, uint32_t*, uint32_t), size_t* smem, uint32_t* cap) {
+    if constexpr (std::is_same<View, BatchGroupView>::value) {
+        *kern = wr ? group_leaf_kernel<uint64_t, true, View, kBatchLeafThreads, kCompact64Cap>
+                   : group_leaf_kernel<uint64_t, false, View, kBatchLeafThreads, kCompact64Cap>;
+        *smem = sizeof(HashShared<uint64_t, kBatchLeafThreads / 32, kCompact64Cap>);
+        *cap = kCompact64Cap;
+    } else {
+        leaf_flavour<View, kBatchLeafThreads, kLeafFastCap>(true, wr, kern, smem, cap);
+    }
+}
+
+// One leaf kernel (+ the general path) over the leaves of a view; `threads`
+// picks the shape (256 or 512), `compact` the compact 64-bit table at 256.
+template <class View>
+int issue_leaves(const View& V, int kind, bool wide, int threads, bool compact, uint32_t* ovf, uint32_t* ovf_count,
+                 void* big, uint64_t big_kmax, int per_sm_cap, bool persistent, const double* tab, int sms,
+                 cudaStream_t st, uint64_t* nl) {
     if (V.nleaves == 0) return RS_OK;
     if (kind == RS_KIND_B) {
         ++*nl;
@@ -316,6 +332,7 @@ int issue_leaves(const View& V, int kind, bool wide, int threads, uint32_t* ovf,
     size_t smem;
     uint32_t cap;
     if (threads == 512) leaf_flavour<View, 512, 2 * kLeafFastCap>(wide, wr, &kern, &smem, &cap);
+    else if (compact && wide) compact_flavour<View>(wr, &kern, &smem, &cap);
     else leaf_flavour<View, kBatchLeafThreads, kLeafFastCap>(wide, wr, &kern, &smem, &cap);
     int per = blocks_per_sm(reinterpret_cast<const void*>(kern), smem, threads == 512 ? 512 : kBatchLeafThreads);
     if (per < 0) return RS_ECUDA;
@@ -390,8 +407,14 @@ void GroupPlan::build(const rs_request* reqs, uint64_t* const* out_ptrs, uint32_
         groups_[gi] = Sub{};
         groups_[gi].kind = gi == 4 ? RS_KIND_B : (gi % 5) / 2;
         groups_[gi].wide = gi != 4 && ((gi % 5) & 1);
-        groups_[gi].large = gi > 4;
+        groups_[gi].large = gi > 4 && gi < 9;
+        if (gi >= 9) {
+            groups_[gi].kind = gi - 9;
+            groups_[gi].wide = true;
+            groups_[gi].compact = true;
+        }
         qgroups_[gi] = groups_[gi];
+        qgroups_[gi].compact = false;   // (query groups 9 and 10 stay empty)
     }
     nodes_ = 0;
     uint64_t bound = 0;
@@ -426,7 +449,8 @@ void GroupPlan::build(const rs_request* reqs, uint64_t* const* out_ptrs, uint32_
         Dmax = std::max(Dmax, D);
         const uint64_t nleaves = 1ull << D;
         const uint64_t smax = (q.N >> D) + ((q.N & (nleaves - 1)) ? 1 : 0);
-        Sub& G = groups_[group_of((int)q.kind, smax > (1ull << 32), large_class(q.n >> D))];
+        Sub& G = groups_[group_of((int)q.kind, smax > (1ull << 32), large_class(q.n >> D),
+                                  (q.n >> D) <= kCompact64Mean)];
         for (uint64_t i = 0; i < nleaves; ++i) G.desc.push_back(LeafDesc{b.node_base + nleaves + i, r, (uint32_t)i});
         G.n1 += nleaves;
         if (q.kind != RS_KIND_B) bound = std::max<uint64_t>(bound, wr ? q.n : std::min<uint64_t>(q.n, smax - smax / 2));
@@ -567,8 +591,8 @@ int GroupPlan::issue(const double* tab, int sms, uint64_t* pool, int* status, cu
             const Sub& G = groups_[gi];
             if (G.n1 == 0) continue;
             BatchGroupView V{reqs, reinterpret_cast<const LeafDesc*>(up_ + G.o_desc), G.n1, nodes, pool, status};
-            rc = issue_leaves(V, G.kind, G.wide, threads_of(G), reinterpret_cast<uint32_t*>(work_ + G.o_ovf1),
-                              counters + counter_of(0, gi), big_, big_kmax_, per_sm_, persistent_, tab, sms, st, &nl);
+            rc = issue_leaves(V, G.kind, G.wide, threads_of(G), G.compact,
+                              reinterpret_cast<uint32_t*>(work_ + G.o_ovf1), counters + counter_of(0, gi), big_, big_kmax_, per_sm_, persistent_, tab, sms, st, &nl);
         }
     }
     if (!rc && Q_ > 0) {
@@ -577,8 +601,8 @@ int GroupPlan::issue(const double* tab, int sms, uint64_t* pool, int* status, cu
             const Sub& G = qgroups_[gi];
             if (G.n1 == 0) continue;
             QueryBoundView V{qd, qres_, reinterpret_cast<const uint32_t*>(up_ + G.o_a32), G.n1};
-            rc = issue_leaves(V, G.kind, G.wide, threads_of(G), reinterpret_cast<uint32_t*>(work_ + G.o_ovf1),
-                              counters + counter_of(1, gi), big_, big_kmax_, per_sm_, persistent_, tab, sms, st, &nl);
+            rc = issue_leaves(V, G.kind, G.wide, threads_of(G), false,
+                              reinterpret_cast<uint32_t*>(work_ + G.o_ovf1), counters + counter_of(1, gi), big_, big_kmax_, per_sm_, persistent_, tab, sms, st, &nl);
         }
         if (!rc) {
             const unsigned grid = (unsigned)std::min<uint64_t>(Q_, (uint64_t)sms * 8);
@@ -594,7 +618,7 @@ int GroupPlan::issue(const double* tab, int sms, uint64_t* pool, int* status, cu
                              reinterpret_cast<const uint64_t*>(up_ + G.o_p64),
                              (uint32_t)G.b32.size(),
                              G.n2};
-            rc = issue_leaves(V, G.kind, G.wide, threads_of(G), reinterpret_cast<uint32_t*>(work_ + G.o_ovf2),
+            rc = issue_leaves(V, G.kind, G.wide, threads_of(G), false, reinterpret_cast<uint32_t*>(work_ + G.o_ovf2),
                               counters + counter_of(2, gi), big_, big_kmax_, per_sm_, persistent_, tab, sms, st, &nl);
         }
     }

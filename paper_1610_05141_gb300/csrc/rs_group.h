@@ -83,7 +83,7 @@ public:
 
     // Leaf groups: (H, WR) x (32-, 64-bit keys) x (small, large class), and
     // Algorithm B.
-    static constexpr int kGroups = 9;
+    static constexpr int kGroups = 11;
 
     // Leaf kernels with one block per leaf instead of a persistent grid, so
     // that their blocks retire often and kernels of other streams (a
@@ -100,6 +100,7 @@ private:
         int kind = 0;
         bool wide = false;
         bool large = false;
+        bool compact = false;   // 64-bit keys, small means: the compact table (requests only)
         // requests: leaf descriptors; queries: bound items, then interior q_of/prefix
         std::vector<LeafDesc> desc;
         std::vector<uint32_t> a32, b32;

@@ -143,6 +143,11 @@ static cudaError_t launch_shape(const LeafJob& job, const LeafLaunch& L, cudaStr
         if (L.pow2_leaves) return launch_fast<uint32_t, WR, NT, CAP, true>(job, L.cap, L.sms, L.blocks_per_sm, st);
         return launch_fast<uint32_t, WR, NT, CAP, false>(job, L.cap, L.sms, L.blocks_per_sm, st);
     }
+    if (NT == kHashThreads && L.mean_count <= kCompact64Mean) {   // 64-bit keys: the compact table
+        if (L.pow2_leaves)
+            return launch_fast<uint64_t, WR, NT, kCompact64Cap, true>(job, L.cap, L.sms, L.blocks_per_sm, st);
+        return launch_fast<uint64_t, WR, NT, kCompact64Cap, false>(job, L.cap, L.sms, L.blocks_per_sm, st);
+    }
     if (L.pow2_leaves) return launch_fast<uint64_t, WR, NT, CAP, true>(job, L.cap, L.sms, L.blocks_per_sm, st);
     return launch_fast<uint64_t, WR, NT, CAP, false>(job, L.cap, L.sms, L.blocks_per_sm, st);
 }
