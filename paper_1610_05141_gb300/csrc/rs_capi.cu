@@ -13,6 +13,11 @@
 #include "rs_points.h"
 #include "rs_union.h"
 
+namespace rs {
+// Kernel launches that launch_tree_top(..., levels, ...) issues (rs_tree.cu).
+uint64_t tree_launches(int levels);
+}  // namespace rs
+
 struct rs_ctx {
     int device = 0;
     int sms = 0;
@@ -179,7 +184,7 @@ int build_tree(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0, 
     int rc = ensure(ctx->nodes, ctx->nodes_cap, 2ull << D);
     if (rc) return rc;
     *D_out = D;
-    ctx->launches += 1 + (uint64_t)D;
+    ctx->launches += rs::tree_launches(D);
     return cuda_rc(rs::launch_tree(ctx->nodes, n, N, seed, D, kind == RS_KIND_WR, ctx->tab, ctx->status, st, ctx->guard));
 }
 
@@ -220,7 +225,7 @@ int sample_impl(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0,
     }
     if (c == 0) {
         rc = cuda_rc(rs::launch_tree(ctx->nodes, n, N, seed, D, wr, ctx->tab, ctx->status, st, ctx->guard));
-        ctx->launches += 1 + (uint64_t)D;
+        ctx->launches += rs::tree_launches(D);
         if (prof) ctx->prof_calls[prof - 1].tree_end = record_event(ctx, st);
     } else {
         cudaStream_t ts = ctx->tree_stream;
@@ -231,7 +236,7 @@ int sample_impl(rs_ctx* ctx, uint64_t n, uint64_t N, uint64_t seed, uint32_t n0,
             rc = cuda_rc(rs::launch_tree_part(ctx->nodes, seed, D, c, j, wr, ctx->tab, ctx->status, ts, ctx->guard));
             if (!rc) rc = cuda_rc(cudaEventRecord(ctx->ev_part[j], ts));
         }
-        ctx->launches += 1 + (uint64_t)c + parts * (uint64_t)(D - c);
+        ctx->launches += rs::tree_launches(c) + parts * (uint64_t)(D - c);
         if (prof) ctx->prof_calls[prof - 1].tree_end = record_event(ctx, ts);
     }
     if (rc) return rc;

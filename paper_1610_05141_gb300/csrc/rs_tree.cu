@@ -249,6 +249,14 @@ cudaError_t launch_tree_top(NodeRec* rec, uint64_t n, uint64_t N, uint64_t seed,
     return cudaGetLastError();
 }
 
+uint64_t tree_launches(int levels) {
+    static const bool fusable = top_fusable();
+    // one fused launch for the top levels, or the root kernel; then as launch_tree_top
+    const int level = (fusable && levels > 1) ? std::min(levels, kTopFused) : 0;
+    const int L0 = levels - level >= 2 ? std::max(level, levels - kSubtreeLevels) : levels;
+    return 1 + (uint64_t)(L0 - level) + (L0 < levels ? 1 : 0);
+}
+
 cudaError_t launch_tree_part(NodeRec* rec, uint64_t seed, int D, int c, uint64_t part, bool with_replacement,
                              const double* tab, int* status, cudaStream_t st, bool guard) {
     const int sms = device_sms();
