@@ -21,6 +21,7 @@ workload (rank 0 only).
 """
 import argparse
 import hashlib
+import re
 
 import numpy as np
 import json
@@ -66,11 +67,24 @@ def hbm_peak():
         return 6800.0, "fallback"
 
 
-def leaf_source_hash():
+def _code_only(text):
+    """Source text without comments and trailing blanks: the hash follows the code."""
+    text = re.sub(rb"/\*.*?\*/", b"", text, flags=re.S)
+    text = re.sub(rb"//[^\n]*", b"", text)
+    return b"\n".join(line.rstrip() for line in text.split(b"\n") if line.strip())
+
+
+def leaf_source_hash(read=None):
+    """Hash of the leaf kernel's sources (code only, comments left out);
+    read(name) -> bytes overrides reading the working tree."""
     h = hashlib.sha256()
     for name in LEAF_SOURCES:
-        with open(os.path.join(ROOT, "paper_1610_05141_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        if read is None:
+            with open(os.path.join(ROOT, "paper_1610_05141_gb300", "csrc", name), "rb") as f:
+                data = f.read()
+        else:
+            data = read(name)
+        h.update(_code_only(data))
     return h.hexdigest()[:16]
 
 

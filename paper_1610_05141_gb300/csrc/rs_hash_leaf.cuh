@@ -20,10 +20,11 @@
 //    its output position, and is written there.  Equal keys share a rank and
 //    so lower the sum of the ranks: a second run then breaks the ties by
 //    position.  When the leaf size does not divide 2^32 (2^64)
-//    some candidates are void: each thread then generates a contiguous run
-//    of Philox blocks, staged in shared memory, and one block scan numbers
-//    the valid ones in index order, so that exactly the first k valid ones
-//    are kept.  If
+//    some candidates are void: each leaves a hole among candidates [0, k),
+//    and later rounds of exactly as many further candidates as holes
+//    remain fill them, so that exactly the first k valid ones are kept.
+//    Launches whose leaves are all one power-of-two size compile this out.
+//    If
 //    a key repeats (without replacement), the distinct values are kept and
 //    one warp draws the missing ones from the following candidates, each
 //    tested against the set (binary search) and against its batch, so that
