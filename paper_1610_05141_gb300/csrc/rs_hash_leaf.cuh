@@ -549,6 +549,13 @@ __device__ __forceinline__ bool fill_holes(HashShared<KeyT, NT / 32, CAP>& sm, c
     return true;
 }
 
+template <typename KeyT, int NT, int BAR, uint32_t CAP, typename K2>
+RS_COLD bool void_fill_holes(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, const K2& key, uint32_t tag,
+                             uint32_t k, uint32_t nh, uint64_t thr, uint64_t mult, KeyT* A, KeyT* B, uint32_t* cw,
+                             uint32_t tid) {
+    return fill_holes<KeyT, NT, BAR, CAP>(sm, r, key, tag, k, nh, thr, mult, A, B, cw, tid);
+}
+
 // Pass 1 of the bucket path for leaves with void candidates (sizes that are
 // not powers of two): the first k valid candidates to A[0..k) (in no
 // particular order: later passes only need the set), counted per bucket,
@@ -645,8 +652,11 @@ RS_COLD bool void_leaf_pass1(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& 
 // K2 is Key2 or RoundKeys (the same generator, round keys precomputed).
 // POW2: the caller knows every leaf size to be a power of two, so the code
 // for void candidates is left out (a leaf of another size then returns
-// false and takes the probing path).
-template <typename KeyT, int NT, int BAR, bool WR, uint32_t CAP = kHashCap, typename K2 = Key2, bool POW2 = false>
+// false and takes the probing path).  INL: with 32-bit words the first
+// round of the void pass runs inline (faster for the single-call kernel;
+// the batch's kernels are faster with the whole pass as one call).
+template <typename KeyT, int NT, int BAR, bool WR, uint32_t CAP = kHashCap, typename K2 = Key2, bool POW2 = false,
+          bool INL = false>
 RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, const K2& key, uint32_t k,
                         uint64_t* __restrict__ dst, uint32_t tid) {
     static_assert(HashShared<KeyT, NT / 32, CAP>::kBuckets <= 24 * NT, "scan_counts16 takes at most 24 NT counts");
@@ -735,6 +745,56 @@ RS_DEV bool bucket_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, co
             }
         }
         if (tid == 0) sm.jnext = k;
+        group_sync<BAR, NT>();
+    } else if (INL && r.s <= (1ull << 32)) {
+        // round 1 of void_leaf_pass1, inline; the hole rounds are a call
+        if (k > (min((uint64_t)c_caps.stream_blocks, (uint64_t)1 << 32) << 2)) return false;
+        const uint32_t s32 = (uint32_t)(r.s - 1), thr32 = (uint32_t)thr;
+        const uint32_t full = k >> 2;
+        uint32_t* H = reinterpret_cast<uint32_t*>(B);
+        auto put = [&](uint32_t j, uint32_t v, bool ok) {
+            if (ok) {
+                const uint32_t b = hash_slot((KeyT)v, mult);
+                atomicAdd(&cw[b >> 1], 1u << ((b & 1u) << 4));
+            } else {
+                H[atomicAdd(&sm.fill, 1u)] = j;
+            }
+        };
+        for (uint32_t i = tid; i < full; i += NT) {
+            const uint4 w = philox_block(i, tag, r.id, key);
+            const uint64_t p0 = (uint64_t)w.x * s32 + w.x, p1 = (uint64_t)w.y * s32 + w.y;
+            const uint64_t p2 = (uint64_t)w.z * s32 + w.z, p3 = (uint64_t)w.w * s32 + w.w;
+            const uint4 v = make_uint4((uint32_t)(p0 >> 32), (uint32_t)(p1 >> 32), (uint32_t)(p2 >> 32),
+                                       (uint32_t)(p3 >> 32));
+            if (sizeof(KeyT) == 4) {
+                reinterpret_cast<uint4*>(A)[i] = v;
+            } else {
+                A[4 * i] = v.x;
+                A[4 * i + 1] = v.y;
+                A[4 * i + 2] = v.z;
+                A[4 * i + 3] = v.w;
+            }
+            put(4 * i, v.x, (uint32_t)p0 >= thr32);
+            put(4 * i + 1, v.y, (uint32_t)p1 >= thr32);
+            put(4 * i + 2, v.z, (uint32_t)p2 >= thr32);
+            put(4 * i + 3, v.w, (uint32_t)p3 >= thr32);
+        }
+        if (tid == 0 && (k & 3u)) {
+            const uint4 w = philox_block(full, tag, r.id, key);
+            const uint32_t ws[3] = {w.x, w.y, w.z};
+            for (uint32_t c = 0; c < (k & 3u); ++c) {
+                const uint64_t p = (uint64_t)ws[c] * s32 + ws[c];
+                A[4 * full + c] = (KeyT)(p >> 32);
+                put(4 * full + c, (uint32_t)(p >> 32), (uint32_t)p >= thr32);
+            }
+        }
+        group_sync<BAR, NT>();
+        const uint32_t nh = sm.fill;
+        if (nh == 0) {
+            if (tid == 0) sm.jnext = k;
+        } else if (!void_fill_holes<KeyT, NT, BAR, CAP>(sm, r, key, tag, k, nh, thr, mult, A, B, cw, tid)) {
+            return false;
+        }
         group_sync<BAR, NT>();
     } else {
         // leaves with void candidates: a call of its own (its registers stay
@@ -1033,7 +1093,8 @@ RS_COLD bool probe_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, Ke
 // false if the leaf must go to the general (global-memory) path, having
 // written nothing of use.  All NT threads of the group call it; tid is the
 // thread's index in the group.
-template <typename KeyT, int NT, int BAR, bool WR, uint32_t CAP = kHashCap, typename K2 = Key2, bool POW2 = false>
+template <typename KeyT, int NT, int BAR, bool WR, uint32_t CAP = kHashCap, typename K2 = Key2, bool POW2 = false,
+          bool INL = false>
 RS_DEV bool hash_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, const K2& key, uint64_t* __restrict__ out,
                       int* status, uint32_t tid, uint32_t cap) {
     const bool comp = !WR && (r.np > r.s - r.np);
@@ -1052,7 +1113,7 @@ RS_DEV bool hash_leaf(HashShared<KeyT, NT / 32, CAP>& sm, const LeafRec& r, cons
         bitmap_leaf<KeyT, NT, BAR, CAP>(sm, r, key, k, comp, dst, status, tid);
         return true;
     }
-    if (bucket_leaf<KeyT, NT, BAR, WR, CAP, K2, POW2>(sm, r, key, k, dst, tid)) return true;
+    if (bucket_leaf<KeyT, NT, BAR, WR, CAP, K2, POW2, INL>(sm, r, key, k, dst, tid)) return true;
     return probe_leaf<KeyT, NT, BAR, WR, CAP>(sm, r, key, k, dst, status, tid);
 }
 

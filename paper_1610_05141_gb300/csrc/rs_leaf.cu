@@ -69,8 +69,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) leaf_kernel(const __grid_consta
             prefetch_record(&recbuf[par ^ 1u], &job.leaves[leaf + gridDim.x]);
         if (r.c != 0) {
             const LeafRec lr{r.lo, r.S, r.c, r.off, job.first_id + leaf};
-            if (!hash_leaf<KeyT, NT, 0, WR, CAP, RoundKeys, POW2>(sm, lr, job.rk, job.out, job.status, threadIdx.x,
-                                                                 job.cap)) {
+            if (!hash_leaf<KeyT, NT, 0, WR, CAP, RoundKeys, POW2, true>(sm, lr, job.rk, job.out, job.status,
+                                                                       threadIdx.x, job.cap)) {
                 if (threadIdx.x == 0) job.ovf_list[atomicAdd(job.ovf_count, 1u)] = (uint32_t)leaf;
             }
         }
