@@ -95,3 +95,25 @@ def test_bench_traffic_record_tracks_leaf_sources():
     else:
         assert bench.leaf_traffic() is None
     assert 7.0 < rec["dram_bytes_per_sample"] <= 8.5
+
+
+def test_leaf_hash_follows_code_not_comments():
+    """The traffic record is keyed to the leaf sources' code: a comment edit
+    keeps the hash, a code edit changes it."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    csrc = os.path.join(ROOT, "paper_1610_05141_gb300", "csrc")
+
+    def read(name):
+        with open(os.path.join(csrc, name), "rb") as f:
+            return f.read()
+
+    base = bench.leaf_source_hash(read)
+    assert base == bench.leaf_source_hash()
+    first = bench.LEAF_SOURCES[0]
+    commented = lambda name: read(name) + (b"\n// a note\n/* and a\n block */\n" if name == first else b"")
+    assert bench.leaf_source_hash(commented) == base
+    edited = lambda name: read(name) + (b"\nint rs_extra_symbol;\n" if name == first else b"")
+    assert bench.leaf_source_hash(edited) != base
